@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test fixes the oracle to a closed form, a textbook library routine, exact
+rational arithmetic, the brute-force transform of Eq. 1, or an invariant the
+mathematics guarantees, chosen so that a dropped term, a wrong sign, an
+off-by-one shift or a transposed axis fails at least one of them.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import oracle
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- kernel / I0 / taper
+
+@pytest.mark.parametrize("x", [0.0, 1e-3, 0.5, 3.75, 9.0, 16.25, 21.0, 30.0])
+def test_i0_series_matches_scipy(x):
+    assert oracle.i0(x) == pytest.approx(float(sp.i0(x)), rel=1e-13, abs=0)
+
+
+@pytest.mark.parametrize("W", [3, 5, 7, 9])
+def test_kb_kernel_ends_and_centre(W):
+    p = oracle.Params(n=64, n_w=1, fov=0.01, kernel=oracle.KB, support=W, tile=16)
+    beta = oracle.kb_beta_default(W)
+    assert oracle.kernel(p, 0.0) == pytest.approx(1.0, rel=1e-15)
+    assert oracle.kernel(p, W / 2) == pytest.approx(1.0 / sp.i0(beta), rel=1e-13)
+    assert oracle.kernel(p, -W / 2) == oracle.kernel(p, W / 2)
+    assert oracle.kernel(p, W / 2 + 1e-9) == 0.0
+    d = 0.37
+    t = 2 * d / W
+    assert oracle.kernel(p, d) == pytest.approx(sp.i0(beta * np.sqrt(1 - t * t)) / sp.i0(beta),
+                                                rel=1e-13)
+
+
+def test_gauss_kernel_and_delta():
+    p = oracle.Params(n=64, n_w=1, fov=0.01, kernel=oracle.GAUSS, support=7, tile=16)
+    s = 7 / 6
+    for d in (0.0, 0.3, -1.7, 3.5):
+        assert oracle.kernel(p, d) == pytest.approx(np.exp(-d * d / (2 * s * s)), rel=1e-15)
+    p1 = oracle.Params(n=64, n_w=1, fov=0.01, kernel=oracle.KB, support=1, tile=16)
+    assert oracle.kernel(p1, 0.4) == 1.0 and oracle.taper(p1, 0.3) == 1.0
+
+
+@pytest.mark.parametrize("W", [2, 3, 5, 7, 9])
+def test_taper_kb_closed_form(W):
+    """Jackson (1991): integral of I0(beta sqrt(1-(2d/W)^2)) e^{-2 pi i nu d} over
+    |d| <= W/2 equals W sinh(sqrt(beta^2 - (pi W nu)^2)) / sqrt(...)."""
+    p = oracle.Params(n=64, n_w=1, fov=0.01, kernel=oracle.KB, support=W, tile=16)
+    beta = oracle.kb_beta_default(W)
+    for nu in (0.0, 0.05, 0.2, 0.37, 0.5):
+        z = complex(beta ** 2 - (np.pi * W * nu) ** 2) ** 0.5
+        closed = (W * np.sinh(z) / z).real / sp.i0(beta) if abs(z) > 0 else W / sp.i0(beta)
+        assert oracle.taper(p, nu) == pytest.approx(closed, rel=1e-12)
+
+
+@pytest.mark.parametrize("W,sigma", [(7, 7 / 6), (5, 0.9), (9, 1.8)])
+def test_taper_gauss_closed_form(W, sigma):
+    """Truncated Gaussian: integral_{-a}^{a} e^{-d^2/(2 s^2)} cos(2 pi nu d) dd =
+    sqrt(pi/al) e^{-k^2/(4 al)} Re erf(sqrt(al) a + i k / (2 sqrt(al)))."""
+    p = oracle.Params(n=64, n_w=1, fov=0.01, kernel=oracle.GAUSS, support=W, gauss_sigma=sigma,
+                      tile=16)
+    a, al = W / 2, 1 / (2 * sigma ** 2)
+    for nu in (0.0, 0.1, 0.25, 0.5):
+        k = 2 * np.pi * nu
+        closed = np.sqrt(np.pi / al) * np.exp(-k * k / (4 * al)) * \
+            sp.erf(np.sqrt(al) * a + 1j * k / (2 * np.sqrt(al))).real
+        assert oracle.taper(p, nu) == pytest.approx(closed, rel=1e-12)
+
+
+# ---------------------------------------------------------------- FFT
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_fft1d_matches_naive_dft(n, sign):
+    x = rng(n).normal(size=n) + 1j * rng(n + 1).normal(size=n)
+    j = np.arange(n)
+    naive = np.exp(sign * 2j * np.pi * np.outer(j, j) / n) @ x
+    assert np.abs(oracle.fft1d(x, sign) - naive).max() <= 1e-12 * np.abs(naive).max()
+
+
+def test_fft2d_matches_numpy_and_parseval():
+    n = 128
+    x = rng(3).normal(size=(n, n)) + 1j * rng(4).normal(size=(n, n))
+    inv = oracle.fft2d(x, +1)
+    assert np.abs(inv - np.fft.ifft2(x) * n * n).max() <= 1e-11 * np.abs(inv).max()
+    fwd = oracle.fft2d(x, -1)
+    assert np.abs(fwd - np.fft.fft2(x)).max() <= 1e-11 * np.abs(fwd).max()
+    assert (np.abs(fwd) ** 2).sum() == pytest.approx(n * n * (np.abs(x) ** 2).sum(), rel=1e-12)
+    # transposed-axis mistakes would break this non-square-symmetric case
+    y = np.zeros((n, n), complex)
+    y[0, 1] = 1.0
+    assert np.allclose(oracle.fft2d(y, +1)[0, :], np.exp(2j * np.pi * np.arange(n) / n))
+
+
+# ---------------------------------------------------------------- geometry (exact arithmetic)
+
+def _fma_exact(a, b, c):
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def _ref_axis(u, fov, n, W):
+    """Footprint of one axis from exact rational arithmetic."""
+    x = _fma_exact(u, fov, n / 2)
+    X = Fraction(x)
+    h = (W - 1) // 2 if W % 2 else W // 2 - 1
+    c = int(np.floor(X + Fraction(1, 2))) if W % 2 else int(np.floor(X))
+    a = c - h
+    ok = a >= 0 and a + W - 1 <= n - 1
+    return ok, a, float(X - c)
+
+
+@pytest.mark.parametrize("W", [1, 4, 7])
+def test_coords_match_exact_rational_reference(W):
+    n, nw, fov = 64, 5, 0.03125 * 0.7
+    r = rng(10 + W)
+    m = 400
+    u = r.uniform(-1.2, 1.2, m) * (n / 2) / fov
+    v = r.uniform(-1.2, 1.2, m) * (n / 2) / fov
+    # exact half-cell positions and cell centres exercise the rounding ties
+    u[:20] = (np.arange(20) - 10 + 0.5) / fov
+    v[20:40] = (np.arange(20) - 10.0) / fov
+    w = r.uniform(-300, 200, m)
+    uvw = np.stack([u, v, w], 1)
+    p = oracle.Params(n=n, n_w=nw, fov=fov, kernel=oracle.KB, support=W, tile=16)
+    g = oracle.coords(p, uvw)
+    wmin, wmax = w.min(), w.max()
+    assert (g["w_min"], g["w_max"]) == (wmin, wmax)
+    dw = (wmax - wmin) / nw
+    bounds = [_fma_exact(j, dw, wmin) for j in range(1, nw)]
+    for i in range(m):
+        okx, ax, fx = _ref_axis(u[i], fov, n, W)
+        oky, ay, fy = _ref_axis(v[i], fov, n, W)
+        if not (okx and oky):
+            assert g["status"][i] == 1
+            continue
+        assert g["status"][i] == 0
+        assert (g["ax"][i], g["ay"][i]) == (ax, ay)
+        assert (g["fx"][i], g["fy"][i]) == (fx, fy)
+        if W % 2:
+            assert -0.5 <= fx < 0.5
+        k = sum(w[i] >= b for b in bounds)
+        assert g["plane"][i] == k
+
+
+def test_coords_given_w_range_drops_and_degenerate_range():
+    n, fov = 32, 0.05
+    uvw = np.array([[0.0, 0.0, -5.0], [0.0, 0.0, 0.0], [0.0, 0.0, 5.0], [0.0, 0.0, 10.0],
+                    [1e9, 0.0, 0.0]])
+    p = oracle.Params(n=n, n_w=4, fov=fov, kernel=oracle.GAUSS, support=3, w_min=0.0, w_max=5.0,
+                      tile=16)
+    g = oracle.coords(p, uvw)
+    assert list(g["status"]) == [2, 0, 0, 2, 1]
+    assert list(g["plane"][1:3]) == [0, 3]  # w == w_max lands in the top plane
+    p0 = oracle.Params(n=n, n_w=4, fov=fov, kernel=oracle.GAUSS, support=3, tile=16)
+    g0 = oracle.coords(p0, np.array([[0.0, 0.0, 7.0], [1.0, 1.0, 7.0]]))
+    assert list(g0["plane"]) == [0, 0]  # dw == 0 -> plane 0
+    assert oracle.plane_centre(p0, 0, 7.0, 7.0) == 7.0
+
+
+def test_bin_is_stable_counting_sort_with_edge_classes():
+    n, T, W = 128, 16, 5
+    p = oracle.Params(n=n, n_w=3, fov=0.02, kernel=oracle.KB, support=W, tile=T)
+    r = rng(7)
+    m = 3000
+    uvw = np.stack([r.normal(0, 1500, m), r.normal(0, 1500, m), r.uniform(-50, 50, m)], 1)
+    uvw[::7] = uvw[3]  # many exact repeats: stability is observable
+    b = oracle.bin(p, uvw)
+    key, perm, off = b["key"], b["perm"], b["offsets"]
+    kept = np.flatnonzero(key >= 0)
+    assert len(perm) == len(kept) and sorted(perm) == list(kept)
+    sk = key[perm]
+    assert np.all(np.diff(sk) >= 0)
+    same = np.diff(sk) == 0
+    assert np.all(np.diff(perm)[same] > 0)  # ties keep input order
+    counts = np.bincount(key[kept], minlength=oracle.nbins(p))
+    assert np.array_equal(off, np.concatenate([[0], np.cumsum(counts)]))
+    nt = n // T
+    for i in kept[:500]:
+        ax, ay, k = b["ax"][i], b["ay"][i], b["plane"][i]
+        east = (ax % T) + W - 1 >= T
+        south = (ay % T) + W - 1 >= T
+        cls = {(0, 0): 0, (1, 0): 1, (1, 1): 2, (0, 1): 3}[(int(east), int(south))]
+        assert key[i] == ((k * nt + ay // T) * nt + ax // T) * 4 + cls
+
+
+# ---------------------------------------------------------------- the image vs Eq. 1's DFT
+
+def _grid_node_case(seed, n=64, nw=4, m=300, nodes=True):
+    """fov = 2^-4 makes u * fov exact for u on grid nodes (multiples of 1/fov)."""
+    fov = 2.0 ** -4
+    r = rng(seed)
+    if nodes:
+        u = (r.integers(-n // 2 + 2, n // 2 - 2, m)) / fov
+        v = (r.integers(-n // 2 + 2, n // 2 - 2, m)) / fov
+    else:
+        u = r.uniform(-n / 2 + 2, n / 2 - 2, m) / fov
+        v = r.uniform(-n / 2 + 2, n / 2 - 2, m) / fov
+    # w range [-64, 64] in nw planes; plane centres are exact binary fractions
+    k = r.integers(0, nw, m)
+    dw = 128.0 / nw
+    w = -64.0 + (k + 0.5) * dw
+    vis = r.normal(size=m) + 1j * r.normal(size=m)
+    wt = r.uniform(0.5, 1.5, m)
+    p = oracle.Params(n=n, n_w=nw, fov=fov, kernel=oracle.KB, support=1, w_min=-64.0,
+                      w_max=64.0, tile=16)
+    return p, np.stack([u, v, w], 1), vis, wt
+
+
+@pytest.mark.parametrize("flags", [0, oracle.N_CORRECT | oracle.NORMALIZE])
+def test_exact_special_case_equals_dft(flags):
+    """W = 1, u,v on grid nodes, w at plane centres: w-stacking is exact (P1)."""
+    p, uvw, vis, wt = _grid_node_case(1)
+    img, st = oracle.image(p, uvw, vis, wt, flags=flags)
+    assert st["n_binned"] == len(vis)
+    ref = oracle.dft(p.n, p.fov, uvw, vis, wt, flags=flags, sum_weight=wt.sum())
+    assert np.abs(img - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_snapped_dft():
+    """W = 1, arbitrary uvw: the image is the DFT at the snapped (u', v', w_k) (P2)."""
+    p, uvw, vis, wt = _grid_node_case(2, nodes=False)
+    uvw[:, 2] = rng(5).uniform(-64, 64, len(vis))
+    img, _ = oracle.image(p, uvw, vis, wt, flags=0)
+    g = oracle.coords(p, uvw)
+    snapped = np.stack([(g["ax"] - p.n / 2) / p.fov, (g["ay"] - p.n / 2) / p.fov,
+                        [oracle.plane_centre(p, k, -64.0, 64.0) for k in g["plane"]]], 1)
+    ref = oracle.dft(p.n, p.fov, snapped, vis, wt, flags=0)
+    assert np.abs(img - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _point_source_vis(uvw, l0, m0, flux):
+    n0 = np.sqrt(1 - l0 * l0 - m0 * m0)
+    ph = -2j * np.pi * (uvw[:, 0] * l0 + uvw[:, 1] * m0 + uvw[:, 2] * (n0 - 1))
+    return flux / n0 * np.exp(ph)  # Eq. 1 for a point source
+
+
+def test_point_source_flux_exact_and_dft_sign():
+    """A source of flux S at a pixel centre comes back as S there (P4, W = 1)."""
+    p, uvw, _, wt = _grid_node_case(3, m=500)
+    p0, q0, S = 40, 21, 3.25
+    dl = p.fov / p.n
+    vis = _point_source_vis(uvw, (p0 - p.n / 2) * dl, (q0 - p.n / 2) * dl, S)
+    f = oracle.N_CORRECT | oracle.NORMALIZE
+    img, _ = oracle.image(p, uvw, vis, wt, flags=f)
+    assert img[q0, p0] == pytest.approx(S, rel=1e-12)
+    assert np.unravel_index(np.argmax(img), img.shape) == (q0, p0)
+    ref = oracle.dft(p.n, p.fov, uvw, vis, wt, flags=f, sum_weight=wt.sum())
+    assert ref[q0, p0] == pytest.approx(S, rel=1e-12)
+
+
+@pytest.mark.parametrize("kern,W", [(oracle.KB, 7), (oracle.GAUSS, 7), (oracle.KB, 9)])
+def test_point_source_flux_with_taper(kern, W):
+    """Tapered kernels recover the flux to the kernel's accuracy (reported, P4/P3)."""
+    n, fov = 128, 2.0 ** -4
+    r = rng(11)
+    m = 4000
+    uvw = np.stack([r.uniform(-40, 40, m) / fov, r.uniform(-40, 40, m) / fov,
+                    r.uniform(-30, 30, m)], 1)
+    p = oracle.Params(n=n, n_w=8, fov=fov, kernel=kern, support=W, tile=16)
+    p0, q0, S = 70, 50, 2.0
+    dl = fov / n
+    vis = _point_source_vis(uvw, (p0 - n / 2) * dl, (q0 - n / 2) * dl, S)
+    img, _ = oracle.image(p, uvw, vis, None)
+    assert abs(img[q0, p0] - S) / S < 5e-3
+
+
+def test_hermitian_mirror_gives_real_image():
+    """Gridding (u,v,w,V) and (-u,-v,-w,conj V) yields a real sum over planes
+    (P5) and the same normalised image as the original data alone."""
+    n, fov, W = 64, 0.05, 7
+    r = rng(12)
+    m = 600
+    lim = (n / 2 - W - 2) / fov
+    uvw = np.stack([r.uniform(-lim, lim, m), r.uniform(-lim, lim, m), r.uniform(-500, 500, m)], 1)
+    vis = r.normal(size=m) + 1j * r.normal(size=m)
+    wt = r.uniform(0.5, 1.5, m)
+    p = oracle.Params(n=n, n_w=8, fov=fov, kernel=oracle.KB, support=W, w_min=-512.0, w_max=512.0,
+                      tile=16)
+    both = np.concatenate([uvw, -uvw])
+    img2, acc2, _ = oracle.image(p, both, np.concatenate([vis, vis.conj()]),
+                                 np.concatenate([wt, wt]), want_acc=True)
+    peak = np.abs(acc2).max()
+    assert np.abs(acc2.imag).max() <= 1e-12 * peak
+    img1, _ = oracle.image(p, uvw, vis, wt)
+    assert np.abs(img2 - img1).max() <= 1e-12 * np.abs(img1).max()
+
+
+def test_weight_sum_identity_and_centre_pixel():
+    """Sum over cells of g_k = sum_m w V (sum_j Gx)(sum_j Gy), and the centre
+    pixel of the image is that total over C(0)^2 sum w (P6)."""
+    n, fov, W = 64, 0.05, 5
+    r = rng(13)
+    m = 500
+    lim = (n / 2 - W) / fov
+    uvw = np.stack([r.uniform(-lim, lim, m), r.uniform(-lim, lim, m), r.uniform(-100, 100, m)], 1)
+    vis = r.normal(size=m) + 1j * r.normal(size=m)
+    wt = r.uniform(0.5, 1.5, m)
+    p = oracle.Params(n=n, n_w=4, fov=fov, kernel=oracle.GAUSS, support=W, tile=16)
+    planes, st = oracle.grid(p, uvw, vis, wt)
+    g = oracle.coords(p, uvw)
+    h = (W - 1) // 2
+    sx = np.array([sum(oracle.kernel(p, (j - h) - f) for j in range(W)) for f in g["fx"]])
+    sy = np.array([sum(oracle.kernel(p, (j - h) - f) for j in range(W)) for f in g["fy"]])
+    for k in range(p.n_w):
+        sel = (g["plane"] == k)
+        want = np.sum(wt[sel] * vis[sel] * sx[sel] * sy[sel])
+        assert planes[k].sum() == pytest.approx(want, rel=1e-12)
+    img, _ = oracle.image(p, uvw, vis, wt, flags=oracle.NORMALIZE)
+    total = sum(planes[k].sum() for k in range(p.n_w)).real
+    c0 = oracle.taper(p, 0.0)
+    assert img[n // 2, n // 2] == pytest.approx(total / (c0 * c0 * wt.sum()), rel=1e-12)
+
+
+def test_linearity():
+    n, fov = 32, 0.04
+    r = rng(14)
+    m = 200
+    uvw = np.stack([r.uniform(-300, 300, m), r.uniform(-300, 300, m), r.uniform(-80, 80, m)], 1)
+    v1 = r.normal(size=m) + 1j * r.normal(size=m)
+    v2 = r.normal(size=m) + 1j * r.normal(size=m)
+    p = oracle.Params(n=n, n_w=4, fov=fov, kernel=oracle.KB, support=5, tile=16)
+    a, b = 0.7, -1.9
+    i12, _ = oracle.image(p, uvw, a * v1 + b * v2)
+    i1, _ = oracle.image(p, uvw, v1)
+    i2, _ = oracle.image(p, uvw, v2)
+    assert np.abs(i12 - (a * i1 + b * i2)).max() <= 1e-12 * np.abs(i12).max()
+
+
+@pytest.mark.parametrize("flags,weighted", [(oracle.N_CORRECT | oracle.NORMALIZE, True),
+                                            (oracle.N_DIVIDE, False), (0, True)])
+def test_adjoint_dot_product(flags, weighted):
+    """<A x, y> = Re <x, A^H y> for the image operator and its transpose (P9)."""
+    n, fov, W = 64, 0.06, 7
+    r = rng(15)
+    m = 700
+    lim = (n / 2 - 1) / fov
+    uvw = np.stack([r.uniform(-lim, lim, m), r.uniform(-lim, lim, m), r.uniform(-400, 400, m)], 1)
+    x = r.normal(size=m) + 1j * r.normal(size=m)
+    y = r.normal(size=(n, n))
+    wt = r.uniform(0.5, 1.5, m) if weighted else None
+    p = oracle.Params(n=n, n_w=6, fov=fov, kernel=oracle.KB, support=W, tile=16)
+    ax, st = oracle.image(p, uvw, x, wt, flags=flags)
+    aty = oracle.adjoint(p, uvw, y, wt, flags=flags, w_min=st["w_min"], w_max=st["w_max"],
+                         sum_weight=st["sum_weight"])
+    lhs = np.sum(ax * y)
+    rhs = np.real(np.sum(x * np.conj(aty)))
+    # both sides are sums of many signed terms: bound the error by their magnitude
+    assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(ax * y))
+    dropped = oracle.coords(p, uvw)["status"] != 0
+    assert np.all(aty[dropped] == 0)
+
+
+def test_single_plane_zero_w_is_plain_2d_imaging():
+    """n_w = 1 with w == 0: the phase screen is exactly 1 (P11)."""
+    p, uvw, vis, wt = _grid_node_case(16)
+    uvw[:, 2] = 0.0
+    p.w_min, p.w_max = float("nan"), float("nan")
+    p1 = oracle.Params(**{**p.__dict__, "n_w": 1})
+    img1, st = oracle.image(p1, uvw, vis, wt, flags=0)
+    assert st["w_min"] == st["w_max"] == 0.0
+    ref = oracle.dft(p.n, p.fov, uvw, vis, wt, flags=0)
+    assert np.abs(img1 - ref).max() <= 1e-12 * np.abs(ref).max()
+    img4, _ = oracle.image(oracle.Params(**{**p.__dict__, "n_w": 4}), uvw, vis, wt, flags=0)
+    assert np.abs(img4 - img1).max() <= 1e-13 * np.abs(ref).max()
