@@ -1,0 +1,199 @@
+/*
+ * rick.h -- C ABI of the GB300 (sm_103a) w-stacking imaging library.
+ *
+ * The library implements the w-stacking gridder of De Rubeis et al.,
+ * "Accelerating radio astronomy imaging with RICK" (§2): visibilities are
+ * binned, convolved onto a (u, v, w) mesh with a Gaussian or Kaiser-Bessel
+ * kernel (Eq. 3; each visibility goes to the closest w-plane), each w-plane is
+ * inverse Fourier transformed, and the planes are phase-corrected and summed
+ * into the image (Eq. 2, §2 step 4).  Degridding is the exact adjoint.
+ *
+ * Conventions (all calls):
+ *  - uvw are in wavelengths (§2, Eq. 1), float64, row-major [n_vis][3].
+ *  - Visibilities are complex64 stored as interleaved (re, im) float32 pairs.
+ *  - Grid cell i <-> u = (i - n/2) / fov; image pixel p <-> l = (p - n/2) fov / n.
+ *  - Planes are complex64 [n_w][n][n], row-major (v row, u fastest); after the
+ *    inverse FFT the same buffer holds [n_w][m row q][l column p].
+ *  - The image is float32 [n][n], row q (m) major, column p (l) fastest.
+ *  - Pointers named *_dev are device pointers, *_host host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call that takes a stream only enqueues work on it and returns;
+ *    results are ready when the stream reaches that point.
+ *  - The caller owns every buffer passed in.  A plan owns only its cuFFT plan
+ *    and a few small tables; it allocates them in rick_plan_create.
+ *  - No call throws; every call returns a rick_status.  Arguments are checked on
+ *    the host before anything is enqueued.  A CUDA or cuFFT error seen by a call
+ *    is returned by that call and kept in the plan (rick_plan_last_error) so
+ *    that later calls on the same plan return it too (sticky).
+ *  - A plan may be used from one host thread at a time.
+ */
+#ifndef RICK_H
+#define RICK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rick_status;
+#define RICK_OK 0
+#define RICK_EINVAL (-1)  /* invalid argument (checked before any launch)   */
+#define RICK_ENOMEM (-2)  /* device allocation failed                       */
+#define RICK_ECUDA (-3)   /* a CUDA runtime call or kernel launch failed    */
+#define RICK_ECUFFT (-4)  /* a cuFFT call failed                            */
+#define RICK_ERANGE (-5)  /* a size exceeds the plan's or workspace capacity */
+
+#define RICK_KERNEL_GAUSS 0 /* G(d) = exp(-d^2 / (2 sigma^2)), |d| <= W/2              */
+#define RICK_KERNEL_KB 1    /* G(d) = I0(beta sqrt(1 - (2d/W)^2)) / I0(beta) (Jackson 1991) */
+
+#define RICK_PREC_FP32 0             /* FP32 shared-memory tile accumulation          */
+#define RICK_PREC_FP32_COMPENSATED 1 /* FP32 sub-chunk sums folded with Neumaier's     */
+                                     /* compensated summation per tile cell          */
+
+/* Pixel scaling of rick_wcorrect_stack / rick_wspread (bit-or):               */
+#define RICK_N_CORRECT 1u /* multiply by n = sqrt(1 - l^2 - m^2) (Eq. 2 left side)      */
+#define RICK_NORMALIZE 2u /* divide by the sum of the binned weights                    */
+#define RICK_N_DIVIDE 4u  /* divide by n (the 1/n of Eq. 1, for prediction)             */
+#define RICK_PHASE_FP32 8u /* ablation: w-phase argument in plain FP32 instead of       */
+                           /* double-single (~48-bit) arithmetic                         */
+
+typedef struct rick_params {
+    int32_t n;          /* grid side = image side, power of two, 16 ... 32768           */
+    int32_t n_w;        /* number of w-planes, >= 1                                     */
+    double fov;         /* image side in direction-cosine units (> 0); cell du = 1/fov */
+    double w_min;       /* w range in wavelengths; both NaN: exact min/max over all    */
+    double w_max;       /*   input w.  Given: visibilities outside it are dropped.     */
+    int32_t kernel;     /* RICK_KERNEL_GAUSS or RICK_KERNEL_KB                          */
+    int32_t support;    /* W, kernel support in cells, 1 ... 16 (W == 1: nearest cell)  */
+    double kb_beta;     /* KB shape; NaN: pi sqrt((W/2)^2 1.5^2 - 0.8) (Beatty 2005)     */
+    double gauss_sigma; /* Gaussian sigma in cells; NaN: W / 6                           */
+    int32_t tile;       /* uv-tile side T: power of two, W <= T <= 128, T <= n           */
+    int32_t precision;  /* RICK_PREC_*                                                   */
+} rick_params;
+
+/* Geometry and counts of the last rick_bin, written to device memory. */
+typedef struct rick_bin_stats {
+    int64_t n_binned;     /* visibilities kept                                        */
+    int64_t n_dropped_uv; /* footprint not inside the grid (or non-finite u, v)       */
+    int64_t n_dropped_w;  /* w outside a given range                                  */
+    double sum_weight;    /* sum of the kept visibilities' weights                    */
+    double w_min, w_max;  /* the w range used                                         */
+} rick_bin_stats;
+
+typedef struct rick_plan rick_plan;
+
+/* Text for a status code (static storage). */
+const char *rick_status_string(rick_status s);
+
+/* Create a plan for `params` on the current CUDA device: validates params,
+ * creates the batched cuFFT plan (n_w transforms of n x n, complex64), and
+ * precomputes the taper table.  max_vis bounds n_vis in later calls.
+ * Errors: RICK_EINVAL (bad params or max_vis < 0 or >= 2^31), RICK_ENOMEM,
+ * RICK_ECUFFT, RICK_ECUDA.  *out is set only on success. */
+rick_status rick_plan_create(const rick_params *params, int64_t max_vis, rick_plan **out);
+
+/* Release a plan (NULL is accepted).  Synchronises the device first. */
+rick_status rick_plan_destroy(rick_plan *plan);
+
+/* Sticky error of a plan (RICK_OK if none). */
+rick_status rick_plan_last_error(const rick_plan *plan);
+
+/* Bytes of the binning workspace of a plan created with max_vis = n_vis
+ * (bin_bytes; the workspace layout depends only on params and that capacity)
+ * and of the planes buffer (plane_bytes = n_w n^2 8).  Either output may be
+ * NULL.  rick_plan_fft_bytes gives the cuFFT work area a plan holds. */
+rick_status rick_workspace_bytes(const rick_params *params, int64_t n_vis, size_t *bin_bytes,
+                                 size_t *plane_bytes);
+rick_status rick_plan_fft_bytes(const rick_plan *plan, size_t *fft_bytes);
+
+/* Binning (§2, gridding sub-step 1: "an array ... for each slab", here per
+ * (w-plane, uv-tile)).  For each visibility: grid coordinates
+ * x = fma(u, fov, n/2), y = fma(v, fov, n/2) in FP64; centre cell
+ * c = floor(x + 1/2) (odd W) or floor(x) (even W); footprint corner
+ * a = c - h, h = (W-1)/2 (odd) or W/2 - 1 (even); dropped unless
+ * 0 <= a and a + W - 1 <= n - 1 on both axes.  Closest w-plane (§2):
+ * k = #{j = 1..n_w-1 : w >= fma(j, dw, w_min)}, dw = (w_max - w_min)/n_w
+ * (k = 0 when dw == 0).  Each kept visibility becomes one record
+ * {vis * weight, (x - c_x, y - c_y) as float32, corner (a_x, a_y)} stored in
+ * bin order: key = ((k (n/T) + a_y/T) (n/T) + a_x/T) 4 + edge class
+ * (0: footprint inside its tile, 1: reaches the east tile only, 2: east and
+ * south, 3: south only).  Records of one bin are contiguous; their order
+ * within a bin is unspecified.
+ *   uvw_dev:    float64 [n_vis][3]
+ *   vis_dev:    complex64 [n_vis] (interleaved float32 re, im)
+ *   weight_dev: float32 [n_vis], or NULL for unit weights
+ *   ws_dev:     workspace of rick_workspace_bytes(params, plan max_vis)
+ *               bytes, 256-byte aligned; overwritten; the later calls of
+ *               this binning (grid, wcorrect, wspread, degrid) read it
+ *   stats_dev:  device rick_bin_stats, or NULL
+ * Errors: RICK_EINVAL (NULL pointer, misalignment), RICK_ERANGE (n_vis >
+ * max_vis or ws_bytes too small), RICK_ECUDA. */
+rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw_dev, const void *vis_dev,
+                     const float *weight_dev, void *ws_dev, size_t ws_bytes,
+                     rick_bin_stats *stats_dev, void *stream);
+
+/* Where the binning arrays sit inside a workspace (byte offsets from ws_dev),
+ * for callers that read the binned records directly:
+ *   offsets  uint32 [n_bins + 1]  bin b holds records [offsets[b], offsets[b+1])
+ *   perm     uint32 [n_binned]    record r came from input visibility perm[r]
+ *   rec_val  complex64 [n_binned] vis * weight
+ *   rec_frac float32 [n_binned][2] x - c_x, y - c_y
+ *   rec_cell uint32 [n_binned]    a_x | a_y << 16
+ *   stats    rick_bin_stats       the last binning's stats
+ * n_bins = 4 n_w (n/T)^2.  Host-only; enqueues nothing. */
+typedef struct rick_bin_view {
+    size_t offsets, perm, rec_val, rec_frac, rec_cell, stats;
+    int64_t n_bins;
+} rick_bin_view;
+rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out);
+
+/* Replace the record values of an existing binning by vis * weight for new
+ * visibilities at the same uvw (weight NULL: unit), and recompute the weight
+ * sum.  Used to grid gradients through the same geometry. */
+rick_status rick_bin_values(rick_plan *plan, const void *vis_dev, const float *weight_dev,
+                            void *ws_dev, rick_bin_stats *stats_dev, void *stream);
+
+/* Gridding (Eq. 3): planes[k][a_y + jy][a_x + jx] +=
+ * vis w G(jx - h - fx) G(jy - h - fy) for every record, with the
+ * checkerboard (-1)^(i+j) of the centred FFT folded in.  Every element of
+ * planes_dev (complex64 [n_w][n][n]) is overwritten.  Each uv-tile is summed
+ * in shared memory and written once (plain stores; tiles with more records
+ * than one chunk add their chunk sums with float atomics). */
+rick_status rick_grid(rick_plan *plan, const void *ws_dev, void *planes_dev, void *stream);
+
+/* Per-plane 2D FFT (§2 step 3, §3.1): cuFFT complex64, unnormalised, in place,
+ * batched over the n_w planes.  direction +1: inverse (e^{+2 pi i}), used for
+ * imaging; -1: forward, used by degridding. */
+rick_status rick_fft_wplanes(rick_plan *plan, void *planes_dev, int32_t direction, void *stream);
+
+/* w-correction and plane sum (§2 step 4, Eq. 2):
+ * image[q][p] = Re( sum_k (-1)^(p+q) F_k[q][p] e^{2 pi i w_k (n - 1)} ) s(p,q),
+ * w_k = fma(k + 1/2, dw, w_min), n - 1 = -(l^2+m^2) / (1 + sqrt(1 - l^2 - m^2)),
+ * s = [n if RICK_N_CORRECT] [1/n if RICK_N_DIVIDE] [1/sum w if RICK_NORMALIZE]
+ *     / (C(l) C(m)),  C the continuous transform of G (C == 1 for W == 1).
+ * The phase w_k (n - 1) is formed in double-single arithmetic from FP64 inputs
+ * (RICK_PHASE_FP32: plain FP32, for comparison).
+ * ws_dev supplies the w range and weight sum of the last rick_bin. */
+rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_dev, const void *ws_dev,
+                                float *image_dev, uint32_t flags, void *stream);
+
+/* Adjoint of rick_wcorrect_stack (same flags): for every plane k,
+ * planes[k][q][p] = image[q][p] s(p,q) (-1)^(p+q) e^{-2 pi i w_k (n - 1)}. */
+rick_status rick_wspread(rick_plan *plan, const float *image_dev, const void *ws_dev,
+                         void *planes_dev, uint32_t flags, void *stream);
+
+/* Degridding, the adjoint of rick_grid: for every binned visibility m,
+ * vis_out[m] = [weight[m]] sum_{jx,jy} G(jx-h-fx) G(jy-h-fy)
+ *              (-1)^(i+j) planes[k][a_y+jy][a_x+jx],
+ * written in input order; dropped visibilities get 0.
+ *   weight_dev: float32 [n_vis] (the weights given to rick_bin) or NULL (none)
+ *   vis_out_dev: complex64 [n_vis] */
+rick_status rick_degrid(rick_plan *plan, const void *ws_dev, const void *planes_dev,
+                        const float *weight_dev, void *vis_out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RICK_H */

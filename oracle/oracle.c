@@ -237,17 +237,19 @@ void or_fft2d(double complex *a, int32_t n, int32_t sign)
 /* ------------------------------------------------------------------------ */
 /* Geometry of one visibility: grid coordinates, footprint, w-plane.         */
 
-/* Exact min / max of w over all input visibilities. */
+/* Exact min / max of the finite w over all input visibilities (0, 0 if none). */
 void or_wrange(int64_t nvis, const double *uvw, double *wmin, double *wmax)
 {
     double lo = INFINITY, hi = -INFINITY;
     for (int64_t i = 0; i < nvis; ++i) {
         double w = uvw[3 * i + 2];
+        if (!isfinite(w)) continue;
         if (w < lo) lo = w;
         if (w > hi) hi = w;
     }
-    *wmin = lo;
-    *wmax = hi;
+    if (lo > hi) lo = hi = 0.0;
+    *wmin = lo == 0.0 ? 0.0 : lo; /* -0 -> +0 */
+    *wmax = hi == 0.0 ? 0.0 : hi;
 }
 
 /* One axis: returns 1 and the footprint corner a and fractional offset x - c
@@ -290,7 +292,8 @@ double or_plane_centre(const or_params *p, int32_t k, double wmin, double wmax)
 }
 
 /* Per-visibility geometry.  status: 0 kept, 1 dropped (footprint off the
- * grid), 2 dropped (w outside a user-given range).  Returns the kept count. */
+ * grid, or u / v not finite), 2 dropped (w not finite, or outside a
+ * user-given range).  Returns the kept count. */
 int64_t or_coords(const or_params *p, int64_t nvis, const double *uvw, double wmin, double wmax,
                   int32_t given_range, int32_t *plane, int32_t *ax, int32_t *ay, double *fx,
                   double *fy, int32_t *status)
@@ -308,7 +311,7 @@ int64_t or_coords(const or_params *p, int64_t nvis, const double *uvw, double wm
             status[i] = 1;
             continue;
         }
-        if (given_range && !(w >= wmin && w <= wmax)) {
+        if (!isfinite(w) || (given_range && !(w >= wmin && w <= wmax))) {
             ax[i] = ay[i] = -1;
             fx[i] = fy[i] = 0.0;
             status[i] = 2;
@@ -383,7 +386,7 @@ static void or_scale_plane(const or_params *p, uint32_t flags, double sumw, doub
             double nn = sqrt(1.0 - l * l - m * m), s = 1.0 / (tap[pp] * tap[q]);
             if (flags & OR_N_CORRECT) s *= nn;
             if (flags & OR_N_DIVIDE) s /= nn;
-            if (flags & OR_NORMALIZE) s /= sumw;
+            if ((flags & OR_NORMALIZE) && sumw != 0.0) s /= sumw; /* nothing gridded: no scaling */
             scale[(size_t)q * n + pp] = s;
         }
     free(tap);
@@ -647,7 +650,7 @@ void or_dft(int32_t n, double fov, int64_t nvis, const double *uvw, const double
             double nn = 1.0 + nm1;
             if (flags & OR_N_CORRECT) s *= nn;
             if (flags & OR_N_DIVIDE) s /= nn;
-            if (flags & OR_NORMALIZE) s /= sumw;
+            if ((flags & OR_NORMALIZE) && sumw != 0.0) s /= sumw;
             image[(size_t)q * n + pp] = s;
         }
 }

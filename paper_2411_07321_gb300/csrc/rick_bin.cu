@@ -1,0 +1,460 @@
+// rick_bin.cu -- binning of visibilities by (w-plane, uv-tile, edge class)
+// (§2, gridding sub-step 1: "an array is created for each slab, concatenating
+// the data with u-v coordinates inside the corresponding slab"; here the slab
+// is a T x T uv-tile of one w-plane, and a visibility goes to the closest
+// w-plane, §2).
+//
+// Passes, all stream-ordered:
+//   1. w range: min / max of the finite w as order-preserving integer keys
+//      (exact, deterministic), unless the range is given;
+//   2. setup: plane width, the plane boundaries as keys, plane centres;
+//   3. key: per visibility two FP64 FMAs give the grid coordinates, everything
+//      else (floor, rounding, fraction, plane search) is integer work on the
+//      bit patterns -- GB300 runs FP64 at a small fraction of FP32;
+//      warp-aggregated histogram; deterministic weight-sum partials;
+//   4. exclusive scan of the histogram -> bin offsets;
+//   5. scatter: warp-aggregated cursors place each record in its bin;
+//   6. work lists of the tile kernels (chunks of at most chunk_cap records).
+#include <math.h>
+
+#include "rick_common.cuh"
+
+#define FULL 0xffffffffu
+
+// ------------------------------------------------------------------------
+// Exclusive scan of uint32 (block of 2048, recursive over block sums)
+
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(const uint32_t *in, uint32_t *out,
+                                                           int64_t n, uint32_t *block_sums)
+{
+    __shared__ uint32_t warp_tot[32];
+    int64_t base = (int64_t)blockIdx.x * 2048;
+    int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int64_t i0 = base + 2 * t;
+    uint32_t a = i0 < n ? in[i0] : 0u, b = i0 + 1 < n ? in[i0 + 1] : 0u;
+    uint32_t s = a + b, inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_tot[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += v;
+        }
+        warp_tot[lane] = wi - w;  // exclusive prefix of the warps
+        if (lane == 31) block_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t ex = warp_tot[wid] + inc - s;
+    if (i0 < n) out[i0] = ex;
+    if (i0 + 1 < n) out[i0 + 1] = ex + a;
+}
+
+__global__ void scan_add_kernel(uint32_t *out, int64_t n, const uint32_t *block_off)
+{
+    int64_t i = (int64_t)blockIdx.x * 2048 + threadIdx.x;
+    uint32_t add = block_off[blockIdx.x];
+    if (i < n) out[i] += add;
+    if (i + 1024 < n) out[i + 1024] += add;
+}
+
+// out[i] = sum_{j < i} in[i]; in may equal out.  tmp: rick_scan_tmp(n) words.
+static cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
+                            cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t nb = (n + 2047) / 2048;
+    scan_blocks_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, out, n, tmp);
+    if (nb == 1) return cudaGetLastError();
+    cudaError_t e = scan_u32(tmp, tmp, nb, tmp + nb + 1, st);
+    if (e != cudaSuccess) return e;
+    scan_add_kernel<<<(unsigned)nb, 1024, 0, st>>>(out, n, tmp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Pass 1: w range
+
+__global__ void bin_init_kernel(WsHeader *hdr, uint64_t n_vis, uint32_t chunk_cap, int given,
+                                uint64_t wmin_key, uint64_t wmax_key, uint32_t n_key_blocks)
+{
+    hdr->n_vis = n_vis;
+    hdr->drop_uv = 0;
+    hdr->drop_w = 0;
+    hdr->chunk_cap = chunk_cap;
+    hdr->range_given = given;
+    hdr->n_key_blocks = n_key_blocks;
+    hdr->wmin_key = given ? wmin_key : ~0ull;
+    hdr->wmax_key = given ? wmax_key : 0ull;
+}
+
+__global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr)
+{
+    uint64_t lo = ~0ull, hi = 0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t b = rick_dbits(uvw[3 * i + 2]);
+        if (((b >> 52) & 0x7FF) == 0x7FF) continue;  // not finite
+        uint64_t k = rick_dkey(rick_bitsd(b));
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lo != ~0ull) atomicMin(&hdr->wmin_key, (unsigned long long)lo);
+        if (hi != 0ull) atomicMax(&hdr->wmax_key, (unsigned long long)hi);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Pass 2: plane geometry (one thread; n_w <= 1024)
+
+__global__ void bin_setup_kernel(WsHeader *hdr, unsigned long long *bkey, float4 *wplane, int n_w)
+{
+    double wmin, wmax;
+    if (hdr->wmin_key == ~0ull) {  // no finite w at all
+        wmin = wmax = 0.0;
+    } else {
+        wmin = rick_dunkey(hdr->wmin_key);
+        wmax = rick_dunkey(hdr->wmax_key);
+    }
+    double dw = (wmax - wmin) / n_w;
+    hdr->dw = dw;
+    hdr->stats.w_min = wmin;
+    hdr->stats.w_max = wmax;
+    for (int j = 1; j < n_w; ++j) bkey[j - 1] = rick_dkey(fma((double)j, dw, wmin));
+    for (int k = 0; k < n_w; ++k) {
+        double wk = dw == 0.0 ? wmin : fma(k + 0.5, dw, wmin);
+        ff s = ff_from_double(wk);
+        wplane[k] = make_float4(s.hi, s.lo, (float)wk, 0.0f);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Pass 3: keys, histogram, weight-sum partials
+
+struct KeyArgs {
+    int64_t n_vis;
+    const double *uvw;
+    const float *weight;
+    int n, n_w, W, log2T, nt;
+    double fov, half_n;
+    uint64_t key_lo, key_hi;  // rick_dkey(-0.5), rick_dkey(n + 0.5)
+    WsPtrs ws;
+};
+
+__device__ __forceinline__ uint32_t plane_of(uint64_t kw, const unsigned long long *sb, int nb)
+{
+    int lo = 0, hi = nb;  // number of boundaries <= w
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (sb[mid] <= kw)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+__global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
+{
+    extern __shared__ unsigned long long s_bkey[];
+    __shared__ double s_wsum[RICK_KEY_THREADS / 32];
+    __shared__ unsigned long long s_drop[2][RICK_KEY_THREADS / 32];
+    const WsHeader *hdr = a.ws.hdr;
+    int nb = a.n_w - 1;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) s_bkey[j] = a.ws.bkey[j];
+    __syncthreads();
+    const bool degenerate = rick_dbits(hdr->dw) == 0;
+    const bool given = hdr->range_given;
+    const uint64_t wlo = hdr->wmin_key, whi = hdr->wmax_key;
+    const int T = 1 << a.log2T, tmask = T - 1;
+    int lane = threadIdx.x & 31;
+
+    float wsum = 0.0f, wcomp = 0.0f;  // Kahan sum of this thread's weights
+    unsigned long long du = 0, dwn = 0;
+    int64_t base = (int64_t)blockIdx.x * RICK_KEY_THREADS * RICK_KEY_ITEMS + threadIdx.x;
+#pragma unroll 2
+    for (int it = 0; it < RICK_KEY_ITEMS; ++it) {
+        int64_t i = base + (int64_t)it * RICK_KEY_THREADS;
+        uint32_t key = 0xFFFFFFFFu;
+        if (i < a.n_vis) {
+            double u = a.uvw[3 * i], v = a.uvw[3 * i + 1], w = a.uvw[3 * i + 2];
+            int32_t ax, ay;
+            float fx, fy;
+            bool ok = rick_footprint(fma(u, a.fov, a.half_n), a.n, a.W, a.key_lo, a.key_hi, &ax,
+                                     &fx) &&
+                      rick_footprint(fma(v, a.fov, a.half_n), a.n, a.W, a.key_lo, a.key_hi, &ay,
+                                     &fy);
+            if (!ok) {
+                ++du;
+            } else {
+                uint64_t wb = rick_dbits(w);
+                uint64_t kw = rick_dkey(w);
+                if (((wb >> 52) & 0x7FF) == 0x7FF || (given && (kw < wlo || kw > whi))) {
+                    ++dwn;
+                } else {
+                    uint32_t k = degenerate ? 0u : plane_of(kw, s_bkey, nb);
+                    int lx = ax & tmask, ly = ay & tmask;
+                    int ex = lx > T - a.W, ey = ly > T - a.W;
+                    uint32_t cls = ex ? (ey ? 2u : 1u) : (ey ? 3u : 0u);
+                    key = (((k * a.nt + (uint32_t)(ay >> a.log2T)) * a.nt +
+                            (uint32_t)(ax >> a.log2T)) << 2) | cls;
+                    a.ws.cell[i] = (uint32_t)ax | ((uint32_t)ay << 16);
+                    a.ws.frac[i] = make_float2(fx, fy);
+                    float wt = a.weight ? a.weight[i] : 1.0f;
+                    float y = wt - wcomp, t = wsum + y;
+                    wcomp = (t - wsum) - y;
+                    wsum = t;
+                }
+            }
+            a.ws.key[i] = key;
+        }
+        // histogram: one atomic per distinct key of the warp
+        unsigned peers = __match_any_sync(FULL, key);
+        if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+            atomicAdd(&a.ws.hist[key], (uint32_t)__popc(peers));
+    }
+    // deterministic block reduction of the weight sum and the drop counts
+    double ws = (double)wsum - (double)wcomp;
+    for (int o = 16; o > 0; o >>= 1) {
+        ws += __shfl_xor_sync(FULL, ws, o);
+        du += __shfl_xor_sync(FULL, du, o);
+        dwn += __shfl_xor_sync(FULL, dwn, o);
+    }
+    int wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_wsum[wid] = ws;
+        s_drop[0][wid] = du;
+        s_drop[1][wid] = dwn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long d0 = 0, d1 = 0;
+        for (int j = 0; j < RICK_KEY_THREADS / 32; ++j) {
+            t += s_wsum[j];
+            d0 += s_drop[0][j];
+            d1 += s_drop[1][j];
+        }
+        a.ws.wpart[blockIdx.x] = t;
+        if (d0) atomicAdd(&a.ws.hdr->drop_uv, d0);
+        if (d1) atomicAdd(&a.ws.hdr->drop_w, d1);
+    }
+}
+
+// Weight sum over the block partials in a fixed order; stats.
+__global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const double *wpart,
+                                                            int nparts, int unit_weights)
+{
+    __shared__ double s[1024];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 1024) t += wpart[i];
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long binned = (long long)hdr->n_vis - (long long)hdr->drop_uv - (long long)hdr->drop_w;
+        hdr->stats.n_binned = binned;
+        hdr->stats.n_dropped_uv = (long long)hdr->drop_uv;
+        hdr->stats.n_dropped_w = (long long)hdr->drop_w;
+        hdr->stats.sum_weight = unit_weights ? (double)binned : s[0];
+    }
+}
+
+// ------------------------------------------------------------------------
+// Pass 5: scatter records into their bins
+
+__global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const float2 *vis,
+                                                          const float *weight, WsPtrs ws)
+{
+    int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n_vis;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        uint32_t key = i < n_vis ? ws.key[i] : 0xFFFFFFFFu;
+        unsigned peers = __match_any_sync(FULL, key);
+        int leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (key != 0xFFFFFFFFu && lane == leader) b = atomicAdd(&ws.hist[key], (uint32_t)__popc(peers));
+        b = __shfl_sync(FULL, b, leader);
+        if (key != 0xFFFFFFFFu) {
+            uint32_t pos = ws.offsets[key] + b + __popc(peers & ((1u << lane) - 1));
+            float2 v = vis[i];
+            float wt = weight ? weight[i] : 1.0f;
+            ws.perm[pos] = (uint32_t)i;
+            ws.rval[pos] = make_float2(v.x * wt, v.y * wt);
+            ws.rfrac[pos] = ws.frac[i];
+            ws.rcell[pos] = ws.cell[i];
+        }
+    }
+}
+
+// Re-pack record values for new visibilities through an existing permutation.
+__global__ void bin_values_kernel(const float2 *vis, const float *weight, WsPtrs ws)
+{
+    const WsHeader *hdr = ws.hdr;
+    int64_t nb = hdr->stats.n_binned;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i = ws.perm[r];
+        float2 v = vis[i];
+        float wt = weight ? weight[i] : 1.0f;
+        ws.rval[r] = make_float2(v.x * wt, v.y * wt);
+    }
+}
+
+__global__ void __launch_bounds__(1024) values_wsum_kernel(const float *weight, WsPtrs ws)
+{
+    __shared__ double s[1024];
+    WsHeader *hdr = ws.hdr;
+    int64_t nb = hdr->stats.n_binned;
+    double t = 0.0;
+    if (weight) {
+        for (int64_t r = threadIdx.x; r < nb; r += 1024) t += (double)weight[ws.perm[r]];
+    }
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) hdr->stats.sum_weight = weight ? s[0] : (double)nb;
+}
+
+// ------------------------------------------------------------------------
+// Pass 6: work lists.  The grid work of tile t covers its own bin (all four
+// edge classes) plus the records of the west, north and north-west tiles
+// whose footprints reach into t; degridding needs only the own bin.
+
+__global__ void tile_count_kernel(const uint32_t *off, uint32_t *gcnt, uint32_t *dcnt,
+                                  uint32_t ntiles, int nt, uint32_t cap)
+{
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    if (t == ntiles) {
+        gcnt[t] = 0;
+        dcnt[t] = 0;
+        return;
+    }
+    uint32_t tx = t % nt, ty = (t / nt) % nt;
+    uint32_t own = off[4 * t + 4] - off[4 * t];
+    uint32_t L = own;
+    if (tx > 0) L += off[4 * (t - 1) + 3] - off[4 * (t - 1) + 1];
+    if (ty > 0) L += off[4 * (t - nt) + 4] - off[4 * (t - nt) + 2];
+    if (tx > 0 && ty > 0) L += off[4 * (t - nt - 1) + 3] - off[4 * (t - nt - 1) + 2];
+    gcnt[t] = L == 0 ? 1u : (L + cap - 1) / cap;
+    dcnt[t] = (own + cap - 1) / cap;
+}
+
+// ------------------------------------------------------------------------
+
+extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw,
+                                const void *vis, const float *weight, void *ws_dev,
+                                size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
+{
+    if (!plan || !ws_dev || n_vis < 0) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (n_vis > 0 && (!uvw || !vis)) return RICK_EINVAL;
+    if (((uintptr_t)ws_dev & 255) || ((uintptr_t)uvw & 7) || ((uintptr_t)vis & 7) ||
+        ((uintptr_t)weight & 3) || ((uintptr_t)stats_dev & 7))
+        return RICK_EINVAL;
+    if (n_vis > plan->max_vis) return RICK_ERANGE;
+    const rick_params &p = plan->p;
+    WsLayout L = rick_ws_layout(&p, plan->max_vis);
+    if (ws_bytes < L.total) return RICK_ERANGE;
+    const int64_t nkb = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) /
+                        (RICK_KEY_THREADS * RICK_KEY_ITEMS);
+    WsPtrs w = rick_ws_ptrs(ws_dev, L);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
+    int given = !isnan(p.w_min);
+
+    bin_init_kernel<<<1, 1, 0, st>>>(w.hdr, (uint64_t)n_vis, cap, given,
+                                     given ? rick_dkey(p.w_min) : 0, given ? rick_dkey(p.w_max) : 0,
+                                     (uint32_t)nkb);
+    RICK_LAUNCH_CHECK(plan);
+    if (!given && n_vis > 0) {
+        int blocks = plan->num_sms * 4;
+        wrange_kernel<<<blocks, 256, 0, st>>>(uvw, n_vis, w.hdr);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
+    RICK_LAUNCH_CHECK(plan);
+    RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+
+    if (n_vis > 0) {
+        KeyArgs ka;
+        ka.n_vis = n_vis;
+        ka.uvw = uvw;
+        ka.weight = weight;
+        ka.n = p.n;
+        ka.n_w = p.n_w;
+        ka.W = p.support;
+        ka.log2T = 0;
+        while ((1 << ka.log2T) < p.tile) ++ka.log2T;
+        ka.nt = p.n / p.tile;
+        ka.fov = p.fov;
+        ka.half_n = 0.5 * p.n;
+        ka.key_lo = rick_dkey(-0.5);
+        ka.key_hi = rick_dkey((double)p.n + 0.5);
+        ka.ws = w;
+        size_t smem = 8 * (size_t)(p.n_w > 1 ? p.n_w - 1 : 1);
+        bin_key_kernel<<<(unsigned)nkb, RICK_KEY_THREADS, smem, st>>>(ka);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL);
+    RICK_LAUNCH_CHECK(plan);
+    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.offsets, L.nbins + 1, w.scan, st));
+    if (n_vis > 0) {
+        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+        int64_t blocks = (n_vis + 255) / 256;
+        if (blocks > (int64_t)plan->num_sms * 32) blocks = (int64_t)plan->num_sms * 32;
+        bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    uint32_t nt = (uint32_t)L.ntiles;
+    tile_count_kernel<<<(nt + 256) / 256, 256, 0, st>>>(w.offsets, w.gbase, w.dbase, nt,
+                                                        p.n / p.tile, cap);
+    RICK_LAUNCH_CHECK(plan);
+    RICK_CUDA_TRY(plan, scan_u32(w.gbase, w.gbase, L.ntiles + 1, w.scan, st));
+    RICK_CUDA_TRY(plan, scan_u32(w.dbase, w.dbase, L.ntiles + 1, w.scan, st));
+    if (stats_dev)
+        RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
+                                            cudaMemcpyDeviceToDevice, st));
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const float *weight,
+                                       void *ws_dev, rick_bin_stats *stats_dev, void *stream)
+{
+    if (!plan || !vis || !ws_dev) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (((uintptr_t)ws_dev & 255) || ((uintptr_t)vis & 7) || ((uintptr_t)weight & 3) ||
+        ((uintptr_t)stats_dev & 7))
+        return RICK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&plan->p, plan->max_vis));
+    int blocks = plan->num_sms * 8;
+    bin_values_kernel<<<blocks, 256, 0, st>>>((const float2 *)vis, weight, w);
+    RICK_LAUNCH_CHECK(plan);
+    values_wsum_kernel<<<1, 1024, 0, st>>>(weight, w);
+    RICK_LAUNCH_CHECK(plan);
+    if (stats_dev)
+        RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
+                                            cudaMemcpyDeviceToDevice, st));
+    return RICK_OK;
+}

@@ -1,0 +1,393 @@
+// rick_common.cuh -- shared definitions of the sm_103a w-stacking library:
+// plan and workspace layout, launch-argument structs, and the device helpers
+// that several kernels use (coordinate split, double-single arithmetic, the
+// gridding kernel G).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/rick.h"
+
+#if defined(__CUDACC__)
+#define RICK_HD __host__ __device__ __forceinline__
+#else
+#define RICK_HD inline
+#endif
+
+// ------------------------------------------------------------------------
+// Plan
+
+struct rick_plan {
+    rick_params p;
+    int64_t max_vis;
+    int device;
+    int num_sms;
+    cufftHandle fft;
+    size_t fft_bytes;
+    float *taper_inv;  // device [n]: 1 / C(nu_p), nu_p = (p - n/2) / n
+    double beta, sigma, i0_beta;
+    rick_status sticky;
+};
+
+// ------------------------------------------------------------------------
+// Workspace layout (caller-owned device buffer, 256-byte aligned pieces)
+
+struct WsHeader {
+    rick_bin_stats stats;               // the stats of the last rick_bin
+    unsigned long long wmin_key, wmax_key;  // monotone keys of the w range
+    unsigned long long n_vis;           // n_vis of the last rick_bin
+    unsigned long long drop_uv, drop_w; // counters
+    double dw;                          // plane width (0: one degenerate plane)
+    uint32_t grid_total, degrid_total;  // work items of rick_grid / rick_degrid
+    uint32_t chunk_cap;                 // records per work item (at most)
+    uint32_t range_given;
+    uint32_t n_key_blocks;
+    uint32_t pad;
+};
+
+struct WsLayout {
+    size_t header, key, cell, frac, perm, rval, rfrac, rcell, hist, offsets, gbase, dbase, scan,
+        wpart, bkey, wplane, total;
+    int64_t n_vis, nbins, ntiles, nscan, nkeyblocks;
+};
+
+#define RICK_KEY_THREADS 256
+#define RICK_KEY_ITEMS 8
+
+RICK_HD size_t rick_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Temporary elements of the recursive exclusive scan of `n` elements.
+static inline int64_t rick_scan_tmp(int64_t n)
+{
+    int64_t t = 0;
+    while (n > 2048) {
+        n = (n + 2047) / 2048;
+        t += n + 1;
+    }
+    return t + 1;
+}
+
+static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
+{
+    WsLayout L;
+    int64_t nt = p->n / p->tile;
+    L.n_vis = n_vis;
+    L.ntiles = (int64_t)p->n_w * nt * nt;
+    L.nbins = 4 * L.ntiles;
+    L.nkeyblocks = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) / (RICK_KEY_THREADS * RICK_KEY_ITEMS);
+    int64_t longest = L.nbins + 1 > L.ntiles + 1 ? L.nbins + 1 : L.ntiles + 1;
+    L.nscan = rick_scan_tmp(longest);
+    int64_t nv = n_vis > 0 ? n_vis : 1;
+    size_t o = 0;
+    L.header = o; o += rick_align256(sizeof(WsHeader));
+    L.key = o;    o += rick_align256(4 * (size_t)nv);
+    L.cell = o;   o += rick_align256(4 * (size_t)nv);
+    L.frac = o;   o += rick_align256(8 * (size_t)nv);
+    L.perm = o;   o += rick_align256(4 * (size_t)nv);
+    L.rval = o;   o += rick_align256(8 * (size_t)nv);
+    L.rfrac = o;  o += rick_align256(8 * (size_t)nv);
+    L.rcell = o;  o += rick_align256(4 * (size_t)nv);
+    L.hist = o;   o += rick_align256(4 * (size_t)(L.nbins + 1));
+    L.offsets = o; o += rick_align256(4 * (size_t)(L.nbins + 1));
+    L.gbase = o;  o += rick_align256(4 * (size_t)(L.ntiles + 1));
+    L.dbase = o;  o += rick_align256(4 * (size_t)(L.ntiles + 1));
+    L.scan = o;   o += rick_align256(4 * (size_t)L.nscan);
+    L.wpart = o;  o += rick_align256(8 * (size_t)(L.nkeyblocks + 1));
+    L.bkey = o;   o += rick_align256(8 * (size_t)(p->n_w + 1));
+    L.wplane = o; o += rick_align256(16 * (size_t)(p->n_w + 1));
+    L.total = o;
+    return L;
+}
+
+// Device pointers into a workspace.
+struct WsPtrs {
+    WsHeader *hdr;
+    uint32_t *key, *cell, *perm, *rcell, *hist, *offsets, *gbase, *dbase, *scan;
+    float2 *frac, *rval, *rfrac;
+    double *wpart;
+    unsigned long long *bkey;
+    float4 *wplane;  // per plane: (w_k hi, w_k lo, w_k as float, 0)
+};
+
+static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
+{
+    char *b = (char *)ws;
+    WsPtrs w;
+    w.hdr = (WsHeader *)(b + L.header);
+    w.key = (uint32_t *)(b + L.key);
+    w.cell = (uint32_t *)(b + L.cell);
+    w.frac = (float2 *)(b + L.frac);
+    w.perm = (uint32_t *)(b + L.perm);
+    w.rval = (float2 *)(b + L.rval);
+    w.rfrac = (float2 *)(b + L.rfrac);
+    w.rcell = (uint32_t *)(b + L.rcell);
+    w.hist = (uint32_t *)(b + L.hist);
+    w.offsets = (uint32_t *)(b + L.offsets);
+    w.gbase = (uint32_t *)(b + L.gbase);
+    w.dbase = (uint32_t *)(b + L.dbase);
+    w.scan = (uint32_t *)(b + L.scan);
+    w.wpart = (double *)(b + L.wpart);
+    w.bkey = (unsigned long long *)(b + L.bkey);
+    w.wplane = (float4 *)(b + L.wplane);
+    return w;
+}
+
+// Records per work item of the tile kernels: about 16 items per SM in total,
+// at least 1024.
+static inline uint32_t rick_chunk_cap(int64_t n_vis, int num_sms)
+{
+    int64_t c = (n_vis + (int64_t)num_sms * 16 - 1) / ((int64_t)num_sms * 16);
+    if (c < 1024) c = 1024;
+    c = (c + 255) & ~(int64_t)255;
+    if (c > (1 << 30)) c = 1 << 30;
+    return (uint32_t)c;
+}
+
+// ------------------------------------------------------------------------
+// Bit-level helpers (identical on host and device)
+
+RICK_HD uint64_t rick_dbits(double x)
+{
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+}
+
+RICK_HD double rick_bitsd(uint64_t b)
+{
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+}
+
+// Order-preserving map of a double to an unsigned key (-0 is treated as +0):
+// a <= b  <=>  key(a) <= key(b) for all non-NaN a, b.
+RICK_HD uint64_t rick_dkey(double x)
+{
+    uint64_t b = rick_dbits(x);
+    if (b == 0x8000000000000000ull) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+RICK_HD double rick_dunkey(uint64_t k)
+{
+    return rick_bitsd((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k);
+}
+
+RICK_HD int rick_clz64(uint64_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)x);
+#else
+    return __builtin_clzll(x);
+#endif
+}
+
+// Round the exact value s * 2^-sh (|s| < 2^53, s != 0, 0 <= sh <= 60) to the
+// nearest float, ties to even, with integer operations only.
+RICK_HD float rick_scaled_int_to_float(int64_t s, int sh)
+{
+    uint32_t sign = s < 0 ? 0x80000000u : 0u;
+    uint64_t mag = s < 0 ? (uint64_t)(-s) : (uint64_t)s;
+    int lz = rick_clz64(mag);
+    uint64_t norm = mag << lz;  // top bit at 63
+    uint64_t hi = norm >> 40;   // 24 significant bits
+    uint64_t rem = norm & 0xFFFFFFFFFFull, half = 1ull << 39;
+    int e = 63 - lz - sh;       // value = (hi / 2^23) 2^e
+    if (rem > half || (rem == half && (hi & 1))) {
+        ++hi;
+        if (hi == (1ull << 24)) {
+            hi >>= 1;
+            ++e;
+        }
+    }
+    uint32_t bits = sign | ((uint32_t)(e + 127) << 23) | (uint32_t)(hi & 0x7FFFFFu);
+    float f;
+    memcpy(&f, &bits, 4);
+    return f;
+}
+
+// Footprint of one axis (see rick_bin in rick.h): from the FP64 grid
+// coordinate x, the corner a and the offset x - c rounded to float.  Returns
+// false when the footprint is not inside [0, n-1] or x is not finite.
+// key_lo = rick_dkey(-0.5), key_hi = rick_dkey(n + 0.5).  Apart from the rare
+// x < 1 case, only integer operations act on x.
+RICK_HD bool rick_footprint(double x, int n, int W, uint64_t key_lo, uint64_t key_hi, int32_t *a,
+                            float *fx)
+{
+    const bool odd = W & 1;
+    const int h = odd ? (W - 1) / 2 : W / 2 - 1;
+    uint64_t kx = rick_dkey(x);
+    if (kx < key_lo || kx >= key_hi) return false;
+    uint64_t b = rick_dbits(x);
+    int32_t c;
+    float f;
+    if (b >> 63) {  // -0.5 <= x < 0: only W odd can have c = 0
+        if (!odd) return false;
+        c = 0;
+        f = (float)x;
+    } else if (b < 0x3FF0000000000000ull) {  // 0 <= x < 1
+        c = (odd && b >= 0x3FE0000000000000ull) ? 1 : 0;
+        f = (float)(x - (double)c);
+    } else {
+        int e = (int)(b >> 52) - 1023;  // 0 <= e <= 15
+        int sh = 52 - e;
+        uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        uint64_t fb = m & ((1ull << sh) - 1);
+        int32_t fl = (int32_t)(m >> sh);
+        int up = odd ? (int)((fb >> (sh - 1)) & 1) : 0;
+        c = fl + up;
+        int64_t s = up ? (int64_t)fb - (int64_t)(1ull << sh) : (int64_t)fb;
+        f = s == 0 ? 0.0f : rick_scaled_int_to_float(s, sh);
+    }
+    int32_t a0 = c - h;
+    if (a0 < 0 || a0 + W - 1 > n - 1) return false;
+    *a = a0;
+    *fx = f;
+    return true;
+}
+
+// ------------------------------------------------------------------------
+// Double-single ("float-float") arithmetic: a value is hi + lo with
+// |lo| <= ulp(hi)/2.  Products use the exact FMA residual (Dekker/Knuth).
+
+struct ff {
+    float hi, lo;
+};
+
+RICK_HD ff ff_from_double(double x)
+{
+    ff r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+#if defined(__CUDACC__)
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = ff_two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return ff_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return ff_fast_two_sum(p, e);
+}
+
+// i * d for an integer |i| < 2^24
+__device__ __forceinline__ ff ff_mul_int(int i, ff d)
+{
+    float fi = (float)i;
+    float p = __fmul_rn(fi, d.hi);
+    float e = __fmaf_rn(fi, d.hi, -p);
+    e = __fmaf_rn(fi, d.lo, e);
+    return ff_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_sqrt(ff a)  // a > 0
+{
+    float s = sqrtf(a.hi);
+    float p = __fmul_rn(s, s);
+    float e = __fmaf_rn(s, s, -p);
+    float r = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo), __fmul_rn(2.0f, s));
+    return ff_fast_two_sum(s, r);
+}
+
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    ff qb = ff_mul({q1, 0.0f}, b);
+    ff r = ff_add(a, {-qb.hi, -qb.lo});
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return ff_fast_two_sum(q1, q2);
+}
+
+// n - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)) in double-single arithmetic.
+__device__ __forceinline__ ff ff_nm1(ff l, ff m, ff *r2_out)
+{
+    ff r2 = ff_add(ff_mul(l, l), ff_mul(m, m));
+    ff t = ff_add({1.0f, 0.0f}, {-r2.hi, -r2.lo});
+    ff den = ff_add({1.0f, 0.0f}, ff_sqrt(t));
+    ff q = ff_div(r2, den);
+    *r2_out = r2;
+    return {-q.hi, -q.lo};
+}
+
+// Fraction of a double-single phase in cycles: (hi - rint(hi)) + lo, in
+// [-1/2 - |lo|, 1/2 + |lo|].  hi - rint(hi) is exact for |hi| < 2^23.
+__device__ __forceinline__ float ff_frac(ff t)
+{
+    return __fadd_rn(__fsub_rn(t.hi, rintf(t.hi)), t.lo);
+}
+#endif
+
+// ------------------------------------------------------------------------
+// Gridding kernel G(d) in FP32 (d in cells, |d| <= W/2)
+
+struct KernelShape {
+    int kind;        // RICK_KERNEL_GAUSS / RICK_KERNEL_KB
+    float beta;      // KB
+    float inv_i0b;   // 1 / I0(beta)
+    float two_over_w;
+    float inv_2s2;   // Gaussian 1 / (2 sigma^2)
+};
+
+#if defined(__CUDACC__)
+template <int KIND>
+__device__ __forceinline__ float rick_g(const KernelShape &k, float d)
+{
+    if (KIND == RICK_KERNEL_GAUSS) {
+        return expf(-d * d * k.inv_2s2);
+    } else {
+        float t = d * k.two_over_w;
+        float s = fmaxf(0.0f, __fmaf_rn(-t, t, 1.0f));
+        return cyl_bessel_i0f(k.beta * sqrtf(s)) * k.inv_i0b;
+    }
+}
+#endif
+
+// ------------------------------------------------------------------------
+// Error plumbing
+
+#define RICK_CUDA_TRY(plan, expr)                                  \
+    do {                                                           \
+        cudaError_t e_ = (expr);                                   \
+        if (e_ != cudaSuccess) {                                   \
+            if (plan) (plan)->sticky = RICK_ECUDA;                 \
+            return e_ == cudaErrorMemoryAllocation ? RICK_ENOMEM : RICK_ECUDA; \
+        }                                                          \
+    } while (0)
+
+#define RICK_LAUNCH_CHECK(plan) RICK_CUDA_TRY(plan, cudaGetLastError())
+
+// Launch arguments shared by the tile kernels.
+struct TileArgs {
+    int n, n_w, T, nt, W;
+    uint32_t ntiles, chunk_cap;
+    const uint32_t *offsets, *base, *perm, *rcell;
+    const float2 *rval, *rfrac;
+    const WsHeader *hdr;
+    KernelShape ks;
+};

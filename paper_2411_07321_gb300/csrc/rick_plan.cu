@@ -1,0 +1,227 @@
+// rick_plan.cu -- plans, parameter checks, workspace sizing and the per-plane
+// FFT stage (§2 step 3; §3.1 of De Rubeis et al. describe the cuFFT usage,
+// here single-GPU and batched over w-planes instead of cuFFTMp descriptors).
+#include <math.h>
+#include <stddef.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include "rick_common.cuh"
+
+extern "C" const char *rick_status_string(rick_status s)
+{
+    switch (s) {
+    case RICK_OK: return "ok";
+    case RICK_EINVAL: return "invalid argument";
+    case RICK_ENOMEM: return "device out of memory";
+    case RICK_ECUDA: return "CUDA error";
+    case RICK_ECUFFT: return "cuFFT error";
+    case RICK_ERANGE: return "size exceeds capacity";
+    default: return "unknown status";
+    }
+}
+
+static bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+static rick_status check_params(const rick_params *p)
+{
+    if (!p) return RICK_EINVAL;
+    if (!is_pow2(p->n) || p->n < 16 || p->n > 32768) return RICK_EINVAL;
+    if (p->n_w < 1 || p->n_w > 1024) return RICK_EINVAL;
+    if (!(p->fov > 0.0) || !isfinite(p->fov)) return RICK_EINVAL;
+    // the image must stay inside the unit circle of direction cosines
+    if (!(p->fov * 0.5 * sqrt(2.0) < 1.0)) return RICK_EINVAL;
+    if (isnan(p->w_min) != isnan(p->w_max)) return RICK_EINVAL;
+    if (!isnan(p->w_min) && !(isfinite(p->w_min) && isfinite(p->w_max) && p->w_min <= p->w_max))
+        return RICK_EINVAL;
+    if (p->kernel != RICK_KERNEL_GAUSS && p->kernel != RICK_KERNEL_KB) return RICK_EINVAL;
+    if (p->support < 1 || p->support > 16) return RICK_EINVAL;
+    if (!is_pow2(p->tile) || p->tile < p->support || p->tile > 128 || p->tile > p->n ||
+        p->tile < 8)
+        return RICK_EINVAL;
+    if (p->precision != RICK_PREC_FP32 && p->precision != RICK_PREC_FP32_COMPENSATED)
+        return RICK_EINVAL;
+    // the binning keys are 32-bit
+    int64_t nt = p->n / p->tile;
+    if (4 * (int64_t)p->n_w * nt * nt >= (1ll << 31)) return RICK_EINVAL;
+    if (p->kernel == RICK_KERNEL_KB && p->support > 1) {
+        double b = p->kb_beta;
+        if (isnan(b)) {
+            double t = (p->support / 2.0) * (p->support / 2.0) * 2.25 - 0.8;
+            if (!(t > 0)) return RICK_EINVAL;
+        } else if (!(b > 0.0) || !isfinite(b)) {
+            return RICK_EINVAL;
+        }
+    }
+    if (p->kernel == RICK_KERNEL_GAUSS && !isnan(p->gauss_sigma) &&
+        !(p->gauss_sigma > 0.0 && isfinite(p->gauss_sigma)))
+        return RICK_EINVAL;
+    return RICK_OK;
+}
+
+// Taper correction C(nu) = integral_{-W/2}^{W/2} G(d) cos(2 pi nu d) dd for
+// nu_p = (p - n/2)/n, stored as 1/C.  KB: closed form of Jackson (1991),
+// W sinh(sqrt(beta^2 - (pi W nu)^2)) / sqrt(...) / I0(beta); Gaussian:
+// composite Simpson rule on 4096 panels (the integrand is entire).  FP64.
+__global__ void taper_kernel(float *taper_inv, int n, int W, int kind, double beta, double i0b,
+                             double sigma)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double nu = (double)(p - n / 2) / n, c;
+    if (W == 1) {
+        c = 1.0;
+    } else if (kind == RICK_KERNEL_KB) {
+        double a = beta * beta - (M_PI * W * nu) * (M_PI * W * nu);
+        if (a > 1e-30) {
+            double r = sqrt(a);
+            c = W * sinh(r) / r;
+        } else if (a < -1e-30) {
+            double r = sqrt(-a);
+            c = W * sin(r) / r;
+        } else {
+            c = W;
+        }
+        c /= i0b;
+    } else {
+        const int panels = 4096;
+        double h = (double)W / panels, s = 0.0;
+        for (int j = 0; j <= panels; ++j) {
+            double d = -0.5 * W + j * h;
+            double f = exp(-d * d / (2.0 * sigma * sigma)) * cos(2.0 * M_PI * nu * d);
+            s += f * ((j == 0 || j == panels) ? 1.0 : ((j & 1) ? 4.0 : 2.0));
+        }
+        c = s * h / 3.0;
+    }
+    taper_inv[p] = (float)(1.0 / c);
+}
+
+static double kb_beta_of(const rick_params *p)
+{
+    if (!isnan(p->kb_beta)) return p->kb_beta;
+    double t = (p->support / 2.0) * (p->support / 2.0) * 2.25 - 0.8;
+    return M_PI * sqrt(t > 0 ? t : 0.0);
+}
+
+static double bessel_i0_host(double x)
+{
+    double q = 0.25 * x * x, term = 1.0, sum = 1.0;
+    for (int j = 1; j < 1000 && term > 1e-18 * sum; ++j) {
+        term *= q / ((double)j * j);
+        sum += term;
+    }
+    return sum;
+}
+
+extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_vis, rick_plan **out)
+{
+    if (!out) return RICK_EINVAL;
+    rick_status st = check_params(params);
+    if (st != RICK_OK) return st;
+    if (max_vis < 0 || max_vis >= (1ll << 31)) return RICK_EINVAL;
+    rick_plan *pl = (rick_plan *)calloc(1, sizeof(rick_plan));
+    if (!pl) return RICK_ENOMEM;
+    pl->p = *params;
+    pl->max_vis = max_vis;
+    pl->fft = 0;
+    if (cudaGetDevice(&pl->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device) !=
+            cudaSuccess) {
+        free(pl);
+        return RICK_ECUDA;
+    }
+    pl->beta = kb_beta_of(params);
+    pl->sigma = isnan(params->gauss_sigma) ? params->support / 6.0 : params->gauss_sigma;
+    pl->i0_beta = bessel_i0_host(pl->beta);
+
+    int n = params->n;
+    long long dims[2] = {n, n}, dist = (long long)n * n;
+    cufftResult fr = cufftCreate(&pl->fft);
+    if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany64(pl->fft, 2, dims, NULL, 1, dist, NULL, 1, dist, CUFFT_C2C,
+                                 params->n_w, &pl->fft_bytes);
+    if (fr != CUFFT_SUCCESS) {
+        cufftDestroy(pl->fft);
+        free(pl);
+        return fr == CUFFT_ALLOC_FAILED ? RICK_ENOMEM : RICK_ECUFFT;
+    }
+    if (cudaMalloc(&pl->taper_inv, sizeof(float) * n) != cudaSuccess) {
+        cufftDestroy(pl->fft);
+        free(pl);
+        return RICK_ENOMEM;
+    }
+    taper_kernel<<<(n + 255) / 256, 256>>>(pl->taper_inv, n, params->support, params->kernel,
+                                           pl->beta, pl->i0_beta, pl->sigma);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(pl->taper_inv);
+        cufftDestroy(pl->fft);
+        free(pl);
+        return RICK_ECUDA;
+    }
+    pl->sticky = RICK_OK;
+    *out = pl;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_plan_destroy(rick_plan *plan)
+{
+    if (!plan) return RICK_OK;
+    cudaDeviceSynchronize();
+    cufftDestroy(plan->fft);
+    cudaFree(plan->taper_inv);
+    free(plan);
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_plan_last_error(const rick_plan *plan)
+{
+    return plan ? plan->sticky : RICK_EINVAL;
+}
+
+extern "C" rick_status rick_workspace_bytes(const rick_params *params, int64_t n_vis,
+                                            size_t *bin_bytes, size_t *plane_bytes)
+{
+    rick_status st = check_params(params);
+    if (st != RICK_OK) return st;
+    if (n_vis < 0 || n_vis >= (1ll << 31)) return RICK_EINVAL;
+    WsLayout L = rick_ws_layout(params, n_vis);
+    if (bin_bytes) *bin_bytes = L.total;
+    if (plane_bytes) *plane_bytes = (size_t)params->n_w * params->n * params->n * 8;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_plan_fft_bytes(const rick_plan *plan, size_t *fft_bytes)
+{
+    if (!plan || !fft_bytes) return RICK_EINVAL;
+    *fft_bytes = plan->fft_bytes;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_fft_wplanes(rick_plan *plan, void *planes, int32_t direction,
+                                        void *stream)
+{
+    if (!plan || !planes || (direction != 1 && direction != -1)) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (((uintptr_t)planes & 7) != 0) return RICK_EINVAL;
+    if (cufftSetStream(plan->fft, (cudaStream_t)stream) != CUFFT_SUCCESS ||
+        cufftExecC2C(plan->fft, (cufftComplex *)planes, (cufftComplex *)planes,
+                     direction > 0 ? CUFFT_INVERSE : CUFFT_FORWARD) != CUFFT_SUCCESS) {
+        plan->sticky = RICK_ECUFFT;
+        return RICK_ECUFFT;
+    }
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out)
+{
+    if (!plan || !out) return RICK_EINVAL;
+    WsLayout L = rick_ws_layout(&plan->p, plan->max_vis);
+    out->offsets = L.offsets;
+    out->perm = L.perm;
+    out->rec_val = L.rval;
+    out->rec_frac = L.rfrac;
+    out->rec_cell = L.rcell;
+    out->stats = L.header + offsetof(WsHeader, stats);
+    out->n_bins = L.nbins;
+    return RICK_OK;
+}

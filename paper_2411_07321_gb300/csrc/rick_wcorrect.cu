@@ -1,0 +1,180 @@
+// rick_wcorrect.cu -- w-correction and plane reduction (§2 step 4: "we apply
+// the phase shift and reduce the w-planes to obtain the final image"; Eq. 2,
+// with the integral over w becoming the sum over the plane centres w_k), the
+// taper correction, and the adjoint of all of it (w-spreading, used by
+// degridding).
+//
+// One thread per pixel walks the n_w planes: each plane is one coalesced
+// float2 read per pixel, so the kernel is bound by reading the planes once.
+// The phase w_k (n - 1) reaches tens of cycles for wide fields and large |w|,
+// so it is formed in double-single arithmetic (hi + lo floats, about 48
+// significant bits) from the FP64 plane centres and the pixel's n - 1, which
+// itself is evaluated in double-single from l, m; only its fraction in cycles
+// goes to sincospif.  This keeps FP64-class accuracy without per-pixel FP64
+// instructions, which GB300 issues at a small fraction of the FP32 rate.
+#include "rick_common.cuh"
+
+struct WcArgs {
+    int n, n_w;
+    const float2 *planes_in;
+    float2 *planes_out;
+    const float *image_in;
+    float *image_out;
+    const float *taper_inv;
+    const WsHeader *hdr;
+    const float4 *wplane;
+    ff dl;        // fov / n as hi + lo
+    float dl_f;   // fov / n as float
+    uint32_t flags;
+};
+
+struct PixelGeom {
+    ff nm1;      // n - 1 (double-single)
+    float nm1_f; // n - 1 in plain FP32 (ablation)
+    float scale; // s(p, q) including the checkerboard sign
+};
+
+__device__ __forceinline__ PixelGeom pixel_geom(const WcArgs &a, int p, int q, float inv_sumw)
+{
+    PixelGeom g;
+    const int h = a.n / 2;
+    ff r2;
+    g.nm1 = ff_nm1(ff_mul_int(p - h, a.dl), ff_mul_int(q - h, a.dl), &r2);
+    float l = (p - h) * a.dl_f, m = (q - h) * a.dl_f, r2f = l * l + m * m;
+    g.nm1_f = -r2f / (1.0f + sqrtf(1.0f - r2f));
+    float s = a.taper_inv[p] * a.taper_inv[q];
+    float nn = sqrtf(1.0f - r2.hi);
+    if (a.flags & RICK_N_CORRECT) s *= nn;
+    if (a.flags & RICK_N_DIVIDE) s /= nn;
+    if (a.flags & RICK_NORMALIZE) s *= inv_sumw;
+    g.scale = ((p + q) & 1) ? -s : s;
+    return g;
+}
+
+// cos / sin of 2 pi w_k (n - 1)
+__device__ __forceinline__ void wphase(const WcArgs &a, const float4 &wk, const PixelGeom &g,
+                                       float *c, float *s)
+{
+    float f;
+    if (a.flags & RICK_PHASE_FP32) {
+        float th = wk.z * g.nm1_f;
+        f = th - rintf(th);
+    } else {
+        f = ff_frac(ff_mul(ff{wk.x, wk.y}, g.nm1));
+    }
+    sincospif(2.0f * f, s, c);
+}
+
+__global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
+{
+    extern __shared__ float4 s_w[];
+    __shared__ float s_inv_sumw;
+    for (int k = threadIdx.x; k < a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
+    if (threadIdx.x == 0) {
+        double sw = a.hdr->stats.sum_weight;  // nothing gridded: no normalisation
+        s_inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
+    }
+    __syncthreads();
+    const size_t nn = (size_t)a.n * a.n;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    int p = (int)(idx % a.n), q = (int)(idx / a.n);
+    PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
+    float acc = 0.0f;
+    const float2 *src = a.planes_in + idx;
+#pragma unroll 4
+    for (int k = 0; k < a.n_w; ++k) {
+        float2 F = src[(size_t)k * nn];
+        float c, s;
+        wphase(a, s_w[k], g, &c, &s);
+        acc = fmaf(F.x, c, fmaf(-F.y, s, acc));
+    }
+    a.image_out[idx] = acc * g.scale;
+}
+
+__global__ void __launch_bounds__(256) wspread_kernel(WcArgs a)
+{
+    extern __shared__ float4 s_w[];
+    __shared__ float s_inv_sumw;
+    for (int k = threadIdx.x; k < a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
+    if (threadIdx.x == 0) {
+        double sw = a.hdr->stats.sum_weight;  // nothing gridded: no normalisation
+        s_inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
+    }
+    __syncthreads();
+    const size_t nn = (size_t)a.n * a.n;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    int p = (int)(idx % a.n), q = (int)(idx / a.n);
+    PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
+    float v = a.image_in[idx] * g.scale;
+    float2 *dst = a.planes_out + idx;
+#pragma unroll 4
+    for (int k = 0; k < a.n_w; ++k) {
+        float c, s;
+        wphase(a, s_w[k], g, &c, &s);
+        dst[(size_t)k * nn] = make_float2(v * c, -v * s);
+    }
+}
+
+static WcArgs make_args(rick_plan *plan, const void *ws_dev, uint32_t flags)
+{
+    const rick_params &p = plan->p;
+    WsPtrs w = rick_ws_ptrs((void *)ws_dev, rick_ws_layout(&p, plan->max_vis));
+    WcArgs a;
+    a.n = p.n;
+    a.n_w = p.n_w;
+    a.taper_inv = plan->taper_inv;
+    a.hdr = w.hdr;
+    a.wplane = w.wplane;
+    double dl = p.fov / p.n;
+    a.dl = ff_from_double(dl);
+    a.dl_f = (float)dl;
+    a.flags = flags;
+    a.planes_in = NULL;
+    a.planes_out = NULL;
+    a.image_in = NULL;
+    a.image_out = NULL;
+    return a;
+}
+
+static bool valid_flags(uint32_t f)
+{
+    return (f & ~(RICK_N_CORRECT | RICK_NORMALIZE | RICK_N_DIVIDE | RICK_PHASE_FP32)) == 0 &&
+           !((f & RICK_N_CORRECT) && (f & RICK_N_DIVIDE));
+}
+
+extern "C" rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_dev,
+                                           const void *ws_dev, float *image_dev, uint32_t flags,
+                                           void *stream)
+{
+    if (!plan || !planes_dev || !ws_dev || !image_dev || !valid_flags(flags)) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (((uintptr_t)ws_dev & 255) || ((uintptr_t)planes_dev & 7) || ((uintptr_t)image_dev & 3))
+        return RICK_EINVAL;
+    WcArgs a = make_args(plan, ws_dev, flags);
+    a.planes_in = (const float2 *)planes_dev;
+    a.image_out = image_dev;
+    size_t nn = (size_t)a.n * a.n;
+    wcorrect_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * a.n_w,
+                      (cudaStream_t)stream>>>(a);
+    RICK_LAUNCH_CHECK(plan);
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_wspread(rick_plan *plan, const float *image_dev, const void *ws_dev,
+                                    void *planes_dev, uint32_t flags, void *stream)
+{
+    if (!plan || !planes_dev || !ws_dev || !image_dev || !valid_flags(flags)) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (((uintptr_t)ws_dev & 255) || ((uintptr_t)planes_dev & 7) || ((uintptr_t)image_dev & 3))
+        return RICK_EINVAL;
+    WcArgs a = make_args(plan, ws_dev, flags);
+    a.image_in = image_dev;
+    a.planes_out = (float2 *)planes_dev;
+    size_t nn = (size_t)a.n * a.n;
+    wspread_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * a.n_w,
+                     (cudaStream_t)stream>>>(a);
+    RICK_LAUNCH_CHECK(plan);
+    return RICK_OK;
+}

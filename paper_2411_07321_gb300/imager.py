@@ -1,0 +1,168 @@
+"""Torch-facing wrapper of the C ABI: device buffers, streams and stage order.
+
+``Imager`` keeps one configuration's state resident on the GPU -- the plan
+(cuFFT plan, taper table), the binning workspace, the w-planes and the image
+-- and calls the library's stages on the current torch stream.  It does no
+arithmetic of its own: every stage is a librick.so kernel (or cuFFT).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import rick as R
+
+KERNELS = {"gauss": R.RICK_KERNEL_GAUSS, "kb": R.RICK_KERNEL_KB}
+PRECISIONS = {"fp32": R.RICK_PREC_FP32, "compensated": R.RICK_PREC_FP32_COMPENSATED}
+IMAGE_FLAGS = R.RICK_N_CORRECT | R.RICK_NORMALIZE     # the image of Eq. 2, flux-normalised
+PREDICT_FLAGS = R.RICK_N_DIVIDE                       # the 1/n of Eq. 1, for model visibilities
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stats_from_bytes(raw: np.ndarray) -> dict:
+    i = raw[:24].view(np.int64)
+    d = raw[24:48].view(np.float64)
+    return dict(n_binned=int(i[0]), n_dropped_uv=int(i[1]), n_dropped_w=int(i[2]),
+                sum_weight=float(d[0]), w_min=float(d[1]), w_max=float(d[2]))
+
+
+class Imager:
+    def __init__(self, n: int, n_w: int, fov: float, kernel: str = "kb", support: int = 7,
+                 tile: int = 64, w_range: tuple[float, float] | None = None,
+                 kb_beta: float = math.nan, gauss_sigma: float = math.nan,
+                 precision: str = "fp32", max_vis: int = 1 << 20, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("Imager runs on a CUDA device only")
+        wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)
+        self.params = R.make_params(n, n_w, fov, KERNELS[kernel], support, wmin, wmax, kb_beta,
+                                    gauss_sigma, tile, PRECISIONS[precision])
+        self.n, self.n_w, self.max_vis = int(n), int(n_w), int(max_vis)
+        with torch.cuda.device(self.device):
+            self.plan = R.rick_plan_create(self.params, self.max_vis)
+            self.ws_bytes, self.plane_bytes = R.rick_workspace_bytes(self.params, self.max_vis)
+            self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            self.planes = torch.empty((self.n_w, self.n, self.n), dtype=torch.complex64,
+                                      device=self.device)
+            self.stats_buf = torch.zeros(48, dtype=torch.uint8, device=self.device)
+        self.fft_bytes = R.rick_plan_fft_bytes(self.plan)
+        self.n_vis = 0
+
+    # ---------------------------------------------------------------- helpers
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _check(self, t: torch.Tensor, dtype, shape=None, name="tensor"):
+        if t.device != self.device or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor on {self.device}")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+    def footprint_bytes(self) -> int:
+        """Device bytes this imager holds (workspace, planes, cuFFT area)."""
+        return self.ws_bytes + self.plane_bytes + self.fft_bytes + 48
+
+    # ---------------------------------------------------------------- stages
+    def bin(self, uvw: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor | None = None):
+        n = uvw.shape[0]
+        self._check(uvw, torch.float64, (n, 3), "uvw")
+        self._check(vis, torch.complex64, (n,), "vis")
+        if weight is not None:
+            self._check(weight, torch.float32, (n,), "weight")
+        R.rick_bin(self.plan, n, uvw.data_ptr(), vis.data_ptr(), _ptr(weight), self.ws.data_ptr(),
+                   self.ws_bytes, self.stats_buf.data_ptr(), self._stream())
+        self.n_vis = n
+
+    def bin_values(self, vis: torch.Tensor, weight: torch.Tensor | None = None):
+        self._check(vis, torch.complex64, (self.n_vis,), "vis")
+        if weight is not None:
+            self._check(weight, torch.float32, (self.n_vis,), "weight")
+        R.rick_bin_values(self.plan, vis.data_ptr(), _ptr(weight), self.ws.data_ptr(),
+                          self.stats_buf.data_ptr(), self._stream())
+
+    def grid(self):
+        R.rick_grid(self.plan, self.ws.data_ptr(), self.planes.data_ptr(), self._stream())
+
+    def fft(self, direction: int):
+        R.rick_fft_wplanes(self.plan, self.planes.data_ptr(), direction, self._stream())
+
+    def wcorrect(self, flags: int = IMAGE_FLAGS, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
+        self._check(out, torch.float32, (self.n, self.n), "image")
+        R.rick_wcorrect_stack(self.plan, self.planes.data_ptr(), self.ws.data_ptr(),
+                              out.data_ptr(), flags, self._stream())
+        return out
+
+    def wspread(self, image: torch.Tensor, flags: int = IMAGE_FLAGS):
+        self._check(image, torch.float32, (self.n, self.n), "image")
+        R.rick_wspread(self.plan, image.data_ptr(), self.ws.data_ptr(), self.planes.data_ptr(),
+                       flags, self._stream())
+
+    def degrid(self, weight: torch.Tensor | None = None,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.n_vis, dtype=torch.complex64, device=self.device)
+        self._check(out, torch.complex64, (self.n_vis,), "vis_out")
+        if weight is not None:
+            self._check(weight, torch.float32, (self.n_vis,), "weight")
+        R.rick_degrid(self.plan, self.ws.data_ptr(), self.planes.data_ptr(), _ptr(weight),
+                      out.data_ptr(), self._stream())
+        return out
+
+    # ---------------------------------------------------------------- compositions
+    def image(self, uvw, vis, weight=None, flags: int = IMAGE_FLAGS, out=None) -> torch.Tensor:
+        """bin -> grid -> inverse FFT per plane -> w-correct + stack (§2 steps 2-4)."""
+        self.bin(uvw, vis, weight)
+        return self.image_from_binned(flags, out)
+
+    def image_from_binned(self, flags: int = IMAGE_FLAGS, out=None) -> torch.Tensor:
+        self.grid()
+        self.fft(+1)
+        return self.wcorrect(flags, out)
+
+    def adjoint(self, image: torch.Tensor, weight=None, flags: int = IMAGE_FLAGS,
+                out=None) -> torch.Tensor:
+        """Transpose of image_from_binned: w-spread -> forward FFT -> degrid."""
+        self.wspread(image, flags)
+        self.fft(-1)
+        return self.degrid(weight, out)
+
+    def predict(self, image: torch.Tensor, out=None) -> torch.Tensor:
+        """Model visibilities of a sky image through the binned geometry (Eq. 1)."""
+        return self.adjoint(image, None, PREDICT_FLAGS, out)
+
+    def stats(self) -> dict:
+        return _stats_from_bytes(self.stats_buf.cpu().numpy())
+
+    def binned(self) -> dict:
+        """Copies of the binned records (host numpy), via the C ABI's layout view."""
+        v = R.rick_bin_layout(self.plan)
+        st = self.stats()
+        nb = st["n_binned"]
+        raw = self.ws
+
+        def take(off, nbytes):
+            return raw[off:off + nbytes].cpu().numpy()
+
+        return dict(offsets=take(v.offsets, 4 * (v.n_bins + 1)).view(np.uint32),
+                    perm=take(v.perm, 4 * nb).view(np.uint32),
+                    rec_val=take(v.rec_val, 8 * nb).view(np.complex64),
+                    rec_frac=take(v.rec_frac, 8 * nb).view(np.float32).reshape(-1, 2),
+                    rec_cell=take(v.rec_cell, 4 * nb).view(np.uint32), stats=st)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            R.rick_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,173 @@
+"""ctypes binding of librick.so -- the C ABI declared in include/rick.h.
+
+Argument marshalling only: every function here forwards to the entry point of
+the same name and raises ``RickError`` on a non-zero status.  Pointers are
+plain integers (device addresses, e.g. ``tensor.data_ptr()``); streams are
+``cudaStream_t`` values as integers (``torch.cuda.current_stream().cuda_stream``).
+
+There is no fallback: if the in-tree librick.so is missing this module raises
+on import, naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librick.so")
+
+RICK_OK, RICK_EINVAL, RICK_ENOMEM, RICK_ECUDA, RICK_ECUFFT, RICK_ERANGE = 0, -1, -2, -3, -4, -5
+RICK_KERNEL_GAUSS, RICK_KERNEL_KB = 0, 1
+RICK_PREC_FP32, RICK_PREC_FP32_COMPENSATED = 0, 1
+RICK_N_CORRECT, RICK_NORMALIZE, RICK_N_DIVIDE, RICK_PHASE_FP32 = 1, 2, 4, 8
+
+
+class RickError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn}: {status_string(status)} ({status})")
+
+
+class rick_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_w", ctypes.c_int32), ("fov", ctypes.c_double),
+                ("w_min", ctypes.c_double), ("w_max", ctypes.c_double),
+                ("kernel", ctypes.c_int32), ("support", ctypes.c_int32),
+                ("kb_beta", ctypes.c_double), ("gauss_sigma", ctypes.c_double),
+                ("tile", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class rick_bin_stats(ctypes.Structure):
+    _fields_ = [("n_binned", ctypes.c_int64), ("n_dropped_uv", ctypes.c_int64),
+                ("n_dropped_w", ctypes.c_int64), ("sum_weight", ctypes.c_double),
+                ("w_min", ctypes.c_double), ("w_max", ctypes.c_double)]
+
+
+class rick_bin_view(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_size_t), ("perm", ctypes.c_size_t),
+                ("rec_val", ctypes.c_size_t), ("rec_frac", ctypes.c_size_t),
+                ("rec_cell", ctypes.c_size_t), ("stats", ctypes.c_size_t),
+                ("n_bins", ctypes.c_int64)]
+
+
+EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
+           "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
+           "rick_bin_values",
+           "rick_grid", "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, \
+        ctypes.c_size_t
+    P = ctypes.POINTER(rick_params)
+    L.rick_status_string.restype = ctypes.c_char_p
+    L.rick_status_string.argtypes = [i32]
+    for name, args in {
+        "rick_plan_create": [P, i64, ctypes.POINTER(vp)],
+        "rick_plan_destroy": [vp],
+        "rick_plan_last_error": [vp],
+        "rick_workspace_bytes": [P, i64, ctypes.POINTER(sz), ctypes.POINTER(sz)],
+        "rick_plan_fft_bytes": [vp, ctypes.POINTER(sz)],
+        "rick_bin_layout": [vp, ctypes.POINTER(rick_bin_view)],
+        "rick_bin": [vp, i64, vp, vp, vp, vp, sz, vp, vp],
+        "rick_bin_values": [vp, vp, vp, vp, vp, vp],
+        "rick_grid": [vp, vp, vp, vp],
+        "rick_fft_wplanes": [vp, vp, i32, vp],
+        "rick_wcorrect_stack": [vp, vp, vp, vp, u32, vp],
+        "rick_wspread": [vp, vp, vp, vp, u32, vp],
+        "rick_degrid": [vp, vp, vp, vp, vp, vp],
+    }.items():
+        f = getattr(L, name)
+        f.restype = i32
+        f.argtypes = args
+    return L
+
+
+_L = _load()
+
+
+def status_string(s: int) -> str:
+    return _L.rick_status_string(int(s)).decode()
+
+
+def _check(fn: str, s: int) -> None:
+    if s != RICK_OK:
+        raise RickError(fn, s)
+
+
+def make_params(n, n_w, fov, kernel=RICK_KERNEL_KB, support=7, w_min=math.nan, w_max=math.nan,
+                kb_beta=math.nan, gauss_sigma=math.nan, tile=64,
+                precision=RICK_PREC_FP32) -> rick_params:
+    return rick_params(int(n), int(n_w), float(fov), float(w_min), float(w_max), int(kernel),
+                       int(support), float(kb_beta), float(gauss_sigma), int(tile),
+                       int(precision))
+
+
+def rick_plan_create(params: rick_params, max_vis: int) -> int:
+    h = ctypes.c_void_p()
+    _check("rick_plan_create", _L.rick_plan_create(ctypes.byref(params), int(max_vis),
+                                                   ctypes.byref(h)))
+    return h.value
+
+
+def rick_plan_destroy(plan: int) -> None:
+    _check("rick_plan_destroy", _L.rick_plan_destroy(plan))
+
+
+def rick_plan_last_error(plan: int) -> int:
+    return int(_L.rick_plan_last_error(plan))
+
+
+def rick_workspace_bytes(params: rick_params, n_vis: int) -> tuple[int, int]:
+    b, p = ctypes.c_size_t(), ctypes.c_size_t()
+    _check("rick_workspace_bytes", _L.rick_workspace_bytes(ctypes.byref(params), int(n_vis),
+                                                           ctypes.byref(b), ctypes.byref(p)))
+    return b.value, p.value
+
+
+def rick_plan_fft_bytes(plan: int) -> int:
+    b = ctypes.c_size_t()
+    _check("rick_plan_fft_bytes", _L.rick_plan_fft_bytes(plan, ctypes.byref(b)))
+    return b.value
+
+
+def rick_bin_layout(plan: int) -> rick_bin_view:
+    v = rick_bin_view()
+    _check("rick_bin_layout", _L.rick_bin_layout(plan, ctypes.byref(v)))
+    return v
+
+
+def rick_bin(plan, n_vis, uvw, vis, weight, ws, ws_bytes, stats, stream) -> None:
+    _check("rick_bin", _L.rick_bin(plan, int(n_vis), uvw, vis, weight or None, ws, int(ws_bytes),
+                                   stats or None, stream or None))
+
+
+def rick_bin_values(plan, vis, weight, ws, stats, stream) -> None:
+    _check("rick_bin_values", _L.rick_bin_values(plan, vis, weight or None, ws, stats or None,
+                                                 stream or None))
+
+
+def rick_grid(plan, ws, planes, stream) -> None:
+    _check("rick_grid", _L.rick_grid(plan, ws, planes, stream or None))
+
+
+def rick_fft_wplanes(plan, planes, direction, stream) -> None:
+    _check("rick_fft_wplanes", _L.rick_fft_wplanes(plan, planes, int(direction), stream or None))
+
+
+def rick_wcorrect_stack(plan, planes, ws, image, flags, stream) -> None:
+    _check("rick_wcorrect_stack", _L.rick_wcorrect_stack(plan, planes, ws, image, int(flags),
+                                                         stream or None))
+
+
+def rick_wspread(plan, image, ws, planes, flags, stream) -> None:
+    _check("rick_wspread", _L.rick_wspread(plan, image, ws, planes, int(flags), stream or None))
+
+
+def rick_degrid(plan, ws, planes, weight, vis_out, stream) -> None:
+    _check("rick_degrid", _L.rick_degrid(plan, ws, planes, weight or None, vis_out,
+                                         stream or None))

@@ -1,0 +1,79 @@
+"""CPU checks of the C ABI library: it loads, exports every declared entry
+point, and validates arguments on the host (no GPU work is enqueued here)."""
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2411_07321_gb300 import build
+
+    build.build()
+    from paper_2411_07321_gb300 import rick
+
+    return rick
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rick.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rick_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(R):
+    names = declared_functions()
+    assert "rick_bin" in names and "rick_degrid" in names and len(names) >= 13
+    for name in names:
+        assert hasattr(R._L, name), name
+    assert sorted(R.EXPORTS) == names
+
+
+def test_status_strings(R):
+    for s in (R.RICK_OK, R.RICK_EINVAL, R.RICK_ENOMEM, R.RICK_ECUDA, R.RICK_ECUFFT, R.RICK_ERANGE):
+        assert R.status_string(s) and R.status_string(s) != "unknown status"
+
+
+def test_struct_layout_matches_header(R):
+    import ctypes
+    assert ctypes.sizeof(R.rick_params) == 64
+    assert ctypes.sizeof(R.rick_bin_stats) == 48
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=100), dict(n=8), dict(n_w=0), dict(fov=0.0), dict(fov=2.0), dict(support=0),
+    dict(support=17), dict(tile=4), dict(tile=48), dict(tile=256), dict(kernel=7),
+    dict(w_min=1.0), dict(w_min=2.0, w_max=1.0), dict(precision=3), dict(kb_beta=-1.0),
+    dict(gauss_sigma=0.0, kernel=0),
+])
+def test_invalid_params_rejected_on_host(R, bad):
+    kw = dict(n=256, n_w=8, fov=0.035, kernel=1, support=7, w_min=math.nan, w_max=math.nan,
+              kb_beta=math.nan, gauss_sigma=math.nan, tile=32, precision=0)
+    kw.update(bad)
+    p = R.make_params(**kw)
+    with pytest.raises(R.RickError) as e:
+        R.rick_workspace_bytes(p, 1000)
+    assert e.value.status == R.RICK_EINVAL
+
+
+def test_workspace_bytes_scale_with_capacity(R):
+    p = R.make_params(4096, 16, 0.1396, 1, 7, tile=64)
+    b1, planes = R.rick_workspace_bytes(p, 1_000_000)
+    b2, _ = R.rick_workspace_bytes(p, 2_000_000)
+    assert planes == 16 * 4096 * 4096 * 8
+    assert 30_000_000 < b2 - b1 < 50_000_000  # tens of bytes per visibility
+    with pytest.raises(R.RickError):
+        R.rick_workspace_bytes(p, -1)
+
+
+def test_null_plan_rejected(R):
+    import ctypes
+    assert R._L.rick_grid(None, None, None, None) == R.RICK_EINVAL
+    assert R._L.rick_plan_destroy(None) == R.RICK_OK
+    assert R._L.rick_plan_last_error(None) == R.RICK_EINVAL
+    v = R.rick_bin_view()
+    assert R._L.rick_bin_layout(None, ctypes.byref(v)) == R.RICK_EINVAL

@@ -1,0 +1,190 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Binning is compared bit for bit (keys/offsets, the set of visibilities in each
+bin, each record's cell, fractional offsets and value); within a bin the order
+of records is unspecified, so records are matched through their input index.
+Floating-point stages are compared element by element within 1e-5 of the
+stage's peak magnitude (FP32 accumulation and FP32 cuFFT against FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2411_07321_gb300 as P
+    return P
+
+
+def small_data(n_keep=65536):
+    return synth.generate(synth.scaled("small", n_keep=n_keep).obs)
+
+
+# name -> (imaging overrides, n_keep)
+CASES = {
+    "gauss7_t32": (dict(kernel="gauss", support=7, tile=32), 65536),
+    "kb7_t16": (dict(kernel="kb", support=7, tile=16), 65536),
+    "kb9_t32_ragged": (dict(kernel="kb", support=9, tile=32), 12345),
+    "w1_t8": (dict(kernel="kb", support=1, tile=8), 40000),
+    "even_w4_t16": (dict(kernel="kb", support=4, tile=16), 30001),
+    "nw1": (dict(kernel="gauss", support=5, tile=16, n_w=1), 20000),
+    "given_range": (dict(kernel="kb", support=7, tile=32, w_range=(-150.0, 120.0)), 50000),
+    "compensated": (dict(kernel="kb", support=7, tile=32, precision="compensated"), 65536),
+    "gauss_small_fov_drops": (dict(kernel="gauss", support=7, tile=32, fov=1.0 * math.pi / 180),
+                              30000),
+}
+
+
+def build_case(P, name, dev):
+    over, n_keep = CASES[name]
+    d = small_data(n_keep)
+    wl = synth.WORKLOADS["small"]
+    cfg = dict(n=wl.n, n_w=wl.n_w, fov=wl.fov, kernel=wl.kernel, support=wl.support,
+               tile=wl.tile, w_range=None, precision="fp32")
+    cfg.update(over)
+    im = P.Imager(cfg["n"], cfg["n_w"], cfg["fov"], kernel=cfg["kernel"], support=cfg["support"],
+                  tile=cfg["tile"], w_range=cfg["w_range"], precision=cfg["precision"],
+                  max_vis=n_keep, device=dev)
+    wr = cfg["w_range"] or (math.nan, math.nan)
+    op = oracle.Params(n=cfg["n"], n_w=cfg["n_w"], fov=cfg["fov"],
+                       kernel=oracle.KB if cfg["kernel"] == "kb" else oracle.GAUSS,
+                       support=cfg["support"], tile=cfg["tile"], w_min=wr[0], w_max=wr[1])
+    t = dict(uvw=torch.from_numpy(d["uvw"]).to(dev), vis=torch.from_numpy(d["vis"]).to(dev),
+             weight=torch.from_numpy(d["weight"]).to(dev))
+    return im, op, d, t
+
+
+def checker(n):
+    i = np.arange(n)
+    return np.where((i[:, None] + i[None, :]) % 2, -1.0, 1.0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_bin_bitwise(P, name):
+    dev = torch.device("cuda:0")
+    im, op, d, t = build_case(P, name, dev)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    torch.cuda.synchronize()
+    g = im.binned()
+    ob = oracle.bin(op, d["uvw"])
+    st = g["stats"]
+    kept = ob["status"] == 0
+    assert st["n_binned"] == int(kept.sum())
+    assert st["n_dropped_uv"] == int((ob["status"] == 1).sum())
+    assert st["n_dropped_w"] == int((ob["status"] == 2).sum())
+    assert (st["w_min"], st["w_max"]) == (ob["w_min"], ob["w_max"])
+    assert st["sum_weight"] == pytest.approx(float(d["weight"][kept].astype(np.float64).sum()),
+                                             rel=1e-12)
+    assert np.array_equal(g["offsets"].astype(np.int64), ob["offsets"])
+    off = ob["offsets"]
+    perm = g["perm"].astype(np.int64)
+    # the same visibilities in every bin (order inside a bin is unspecified)
+    gsorted = perm.copy()
+    for b in np.flatnonzero(np.diff(off) > 1):
+        gsorted[off[b]:off[b + 1]] = np.sort(perm[off[b]:off[b + 1]])
+    assert np.array_equal(gsorted, ob["perm"])
+    # per-record geometry and value
+    assert np.array_equal(g["rec_cell"] & 0xFFFF, ob["ax"][perm])
+    assert np.array_equal(g["rec_cell"] >> 16, ob["ay"][perm])
+    assert np.array_equal(g["rec_frac"][:, 0], ob["fx"][perm].astype(np.float32))
+    assert np.array_equal(g["rec_frac"][:, 1], ob["fy"][perm].astype(np.float32))
+    v = d["vis"][perm]
+    w = d["weight"][perm].astype(np.float64)
+    want = (v.real.astype(np.float64) * w).astype(np.float32) + \
+        1j * (v.imag.astype(np.float64) * w).astype(np.float32)
+    assert np.array_equal(g["rec_val"], want.astype(np.complex64))
+    im.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_stages_match_oracle(P, name):
+    dev = torch.device("cuda:0")
+    im, op, d, t = build_case(P, name, dev)
+    wt64 = d["weight"].astype(np.float64)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    im.grid()
+    gp = im.planes.cpu().numpy()
+    og, ost = oracle.grid(op, d["uvw"], d["vis"], wt64)
+    cb = checker(op.n)
+    want = og * cb[None]
+    scale = max(np.abs(want).max(), 1e-300)
+    assert np.abs(gp - want).max() <= TOL * scale, "gridded planes"
+    im.fft(+1)
+    fp = im.planes.cpu().numpy()
+    fw = np.stack([oracle.fft2d(want[k], +1) for k in range(op.n_w)])
+    fscale = max(np.abs(fw).max(), 1e-300)
+    assert np.abs(fp - fw).max() <= TOL * fscale, "FFT of the planes"
+    img = im.wcorrect().cpu().numpy()
+    ref, rst = oracle.image(op, d["uvw"], d["vis"], wt64)
+    iscale = max(np.abs(ref).max(), 1e-300)
+    err = np.abs(img - ref).max() / iscale
+    assert err <= TOL, f"image error {err:.3e} of peak"
+    im.close()
+
+
+@pytest.mark.parametrize("name", ["gauss7_t32", "kb9_t32_ragged", "w1_t8", "even_w4_t16",
+                                  "given_range"])
+def test_adjoint_matches_oracle(P, name):
+    dev = torch.device("cuda:0")
+    im, op, d, t = build_case(P, name, dev)
+    wt64 = d["weight"].astype(np.float64)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    torch.cuda.synchronize()
+    st = im.stats()
+    y = np.random.default_rng(1).normal(size=(op.n, op.n)).astype(np.float32)
+    vg = im.adjoint(torch.from_numpy(y).to(dev), t["weight"]).cpu().numpy()
+    vr = oracle.adjoint(op, d["uvw"], y.astype(np.float64), wt64, w_min=st["w_min"],
+                        w_max=st["w_max"], sum_weight=st["sum_weight"])
+    assert np.abs(vg - vr).max() <= TOL * np.abs(vr).max()
+    dropped = oracle.coords(op, d["uvw"])["status"] != 0
+    assert np.all(vg[dropped] == 0)
+    # predictor (no weights, 1/n)
+    pg = im.predict(torch.from_numpy(y).to(dev)).cpu().numpy()
+    pr = oracle.adjoint(op, d["uvw"], y.astype(np.float64), None, flags=oracle.N_DIVIDE,
+                        w_min=st["w_min"], w_max=st["w_max"], sum_weight=st["sum_weight"])
+    assert np.abs(pg - pr).max() <= TOL * np.abs(pr).max()
+    im.close()
+
+
+def test_gpu_adjoint_dot_product(P):
+    dev = torch.device("cuda:0")
+    im, op, d, t = build_case(P, "kb7_t16", dev)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    rng = np.random.default_rng(2)
+    x = (rng.normal(size=len(d["vis"])) + 1j * rng.normal(size=len(d["vis"]))).astype(np.complex64)
+    y = rng.normal(size=(op.n, op.n)).astype(np.float32)
+    im.bin_values(torch.from_numpy(x).to(dev), t["weight"])
+    ax = im.image_from_binned().double().cpu().numpy()
+    aty = im.adjoint(torch.from_numpy(y).to(dev), t["weight"]).cpu().numpy().astype(np.complex128)
+    lhs = np.sum(ax * y)
+    rhs = np.real(np.sum(x.astype(np.complex128) * np.conj(aty)))
+    assert abs(lhs - rhs) <= 1e-5 * np.sum(np.abs(ax * y))
+    im.close()
+
+
+def test_empty_and_all_dropped(P):
+    dev = torch.device("cuda:0")
+    im = P.Imager(64, 4, 0.05, kernel="kb", support=7, tile=16, max_vis=100, device=dev)
+    z = torch.zeros((0, 3), dtype=torch.float64, device=dev)
+    img = im.image(z, torch.zeros(0, dtype=torch.complex64, device=dev))
+    assert torch.count_nonzero(img).item() == 0
+    assert im.stats()["n_binned"] == 0
+    far = torch.tensor([[1e7, 0.0, 1.0], [0.0, -1e7, 2.0], [float("nan"), 0.0, 0.0]],
+                       dtype=torch.float64, device=dev)
+    img = im.image(far, torch.ones(3, dtype=torch.complex64, device=dev))
+    st = im.stats()
+    assert st["n_binned"] == 0 and st["n_dropped_uv"] == 3
+    assert torch.count_nonzero(img).item() == 0
+    im.close()
