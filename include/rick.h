@@ -69,7 +69,8 @@ typedef struct rick_params {
     int32_t support;    /* W, kernel support in cells, 1 ... 16 (W == 1: nearest cell)  */
     double kb_beta;     /* KB shape; NaN: pi sqrt((W/2)^2 1.5^2 - 0.8) (Beatty 2005)     */
     double gauss_sigma; /* Gaussian sigma in cells; NaN: W / 6                           */
-    int32_t tile;       /* uv-tile side T: power of two, W <= T <= 128, T <= n           */
+    int32_t tile;       /* uv-tile side T: power of two, max(8, W) <= T <= min(128, n);  */
+                        /*   T <= 64 with RICK_PREC_FP32_COMPENSATED                    */
     int32_t precision;  /* RICK_PREC_*                                                   */
 } rick_params;
 

@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 
@@ -39,12 +40,20 @@ N_CORRECT, NORMALIZE, N_DIVIDE = 1, 2, 4
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (gcc, FP64, no contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stamp = _LIB + ".arch"
+    try:
+        same_arch = open(stamp).read().strip() == platform.machine()
+    except OSError:
+        same_arch = False
+    if force or not same_arch or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB
 
 

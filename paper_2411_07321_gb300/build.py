@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -36,8 +37,18 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _arch_stamp_ok(stamp: str) -> bool:
+    try:
+        return open(stamp).read().strip() == platform.machine()
+    except OSError:
+        return False
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(OBJ, exist_ok=True)
+    stamp = os.path.join(OBJ, "ARCH")
+    if not _arch_stamp_ok(stamp):  # objects from another host architecture
+        force = True
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
         [os.path.join(os.path.dirname(HERE), "include", "rick.h")]
@@ -64,6 +75,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(platform.machine())
     return LIB
 
 

@@ -41,6 +41,8 @@ static rick_status check_params(const rick_params *p)
         return RICK_EINVAL;
     if (p->precision != RICK_PREC_FP32 && p->precision != RICK_PREC_FP32_COMPENSATED)
         return RICK_EINVAL;
+    // the compensated tile holds six T x T float arrays in shared memory
+    if (p->precision == RICK_PREC_FP32_COMPENSATED && p->tile > 64) return RICK_EINVAL;
     // the binning keys are 32-bit
     int64_t nt = p->n / p->tile;
     if (4 * (int64_t)p->n_w * nt * nt >= (1ll << 31)) return RICK_EINVAL;

@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import platform
 import subprocess
 from dataclasses import dataclass, field, replace
 
@@ -27,11 +28,19 @@ _LIB = os.path.join(_HERE, "libsynth.so")
 
 
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stamp = _LIB + ".arch"
+    try:
+        same_arch = open(stamp).read().strip() == platform.machine()
+    except OSError:
+        same_arch = False
+    if force or not same_arch or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
                         "-fopenmp", "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB
 
 
