@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the end-to-end w-stacked image on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one batch of visibilities:
+bin -> grid -> per-plane inverse FFT -> w-correct + stack + taper (the stages of
+§2 of De Rubeis et al.), on the LOFAR-like workload: 5e7 synthetic
+visibilities, 4096^2 grid, 16 w-planes, Kaiser-Bessel support 7.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line.  ``value`` is visibilities/s with the inputs already
+resident in HBM; ``e2e`` is the same metric through the host-buffer API call
+(pinned host inputs copied in and the image copied back inside the timed
+region).  The inputs (1.8 GB) are larger than L2, so no L2 flush is needed
+between steps.  ``--impl reference`` times the FP64 oracle on the host cores
+instead (on a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "visibilities/s end-to-end w-stacked image vs roofline; served p50/p99 vs plain"
+UNIT = "vis/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons around the timed region."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "20", "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 9]
+        os.unlink(self.f.name)
+        from datetime import datetime
+
+        def ts(s):
+            try:
+                return datetime.strptime(s.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                return None
+
+        inside = [r for r in rows if (ts(r[0]) or 0) >= t0 - 0.02 and (ts(r[0]) or 0) <= t1 + 0.02]
+        use = inside or rows
+        sm = [float(r[2]) for r in use if r[2].strip().replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in use if r[3].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in use for j in range(4)
+                          if r[6 + j].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(use), "samples_in_window": len(inside)}
+
+
+def algorithmic_bytes(n_vis: int, n_binned: int, n: int, n_w: int) -> dict:
+    planes = n_w * n * n * 8
+    return {
+        # read uvw f64x3, vis c64, weight f32; write records (value c64, offsets 2xf32,
+        # cell u32) and the permutation u32
+        "bin": n_vis * (24 + 8 + 4) + n_binned * (8 + 8 + 4 + 4),
+        # read each record once, write every plane cell once
+        "grid": n_binned * (8 + 8 + 4) + planes,
+        # one read and one write of the planes
+        "fft": 2 * planes,
+        # read every plane once, write the image
+        "wcorrect": planes + n * n * 4,
+    }
+
+
+def traffic_of(kernel: str, n_vis: int):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != rec["source_sha256_16"]:
+        return None
+    return rec["bytes_per_vis"] * n_vis if "bytes_per_vis" in rec else rec["bytes_per_launch"]
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(wl, data, n_sample: int) -> dict:
+    """The FP64 oracle as it stands, on the first n_sample visibilities of the
+    workload, full grid and plane count."""
+    import numpy as np
+
+    import oracle
+
+    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov,
+                       kernel=oracle.KB if wl.kernel == "kb" else oracle.GAUSS,
+                       support=wl.support, tile=wl.tile)
+    s = slice(0, n_sample)
+    t0 = time.perf_counter()
+    oracle.image(op, data["uvw"][s], data["vis"][s], data["weight"][s].astype(np.float64))
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {n_sample} of {len(data['vis'])} visibilities of the workload, "
+                      f"full {wl.n}^2 x {wl.n_w}-plane grid (FFT and w-correction at full size); "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+
+    n_sample = args.ref_sample
+    data = synth.generate(synth.scaled(args.workload, n_keep=n_sample).obs)
+    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov,
+                       kernel=oracle.KB if wl.kernel == "kb" else oracle.GAUSS,
+                       support=wl.support, tile=wl.tile)
+    wt = data["weight"].astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.image(op, data["uvw"], data["vis"], wt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.image(op, data["uvw"], data["vis"], wt)
+    dt = time.perf_counter() - t0
+    value = n_sample * args.steps / dt
+    cores = oracle.max_threads()
+    sample = (f"each step: the first {n_sample} of {wl.obs.n_keep} visibilities of the workload "
+              f"on the full {wl.n}^2 x {wl.n_w}-plane grid")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_of(wl) -> dict:
+    return {"workload": f"{wl.name}: {wl.obs.n_keep} visibilities ({wl.obs.n_ant} stations, "
+                        f"{wl.obs.n_chan} channels), {wl.n}^2 grid, {wl.n_w} w-planes, "
+                        f"{'Kaiser-Bessel' if wl.kernel == 'kb' else 'Gaussian'} support "
+                        f"{wl.support}, uv-tile {wl.tile}",
+            "n_vis": wl.obs.n_keep, "grid": wl.n, "w_planes": wl.n_w, "kernel": wl.kernel,
+            "support": wl.support, "tile": wl.tile, "precision": "fp32",
+            "l2": "inputs (uvw+vis+weight) larger than L2; no flush"}
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2411_07321_gb300 as P
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    data = synth.generate(wl.obs)
+    n_vis = len(data["vis"])
+    uvw_h = torch.from_numpy(data["uvw"]).pin_memory()
+    vis_h = torch.from_numpy(data["vis"]).pin_memory()
+    wt_h = torch.from_numpy(data["weight"]).pin_memory()
+    uvw, vis, wt = uvw_h.to(dev), vis_h.to(dev), wt_h.to(dev)
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                  max_vis=n_vis, device=dev)
+    img = torch.empty((wl.n, wl.n), dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        im.bin(uvw, vis, wt)
+        if ev is not None:
+            ev[1].record()
+        im.grid()
+        if ev is not None:
+            ev[2].record()
+        im.fft(+1)
+        if ev is not None:
+            ev[3].record()
+        im.wcorrect(out=img)
+        if ev is not None:
+            ev[4].record()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = im.stats()
+    n_binned = st["n_binned"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = im.launches()
+    h0 = time.time()
+    t_start.record()
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    h1 = time.time()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop(h0, h1)
+    launches = im.launches() - l0
+    ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stage_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
+                for i, name in enumerate(["bin", "grid", "fft", "wcorrect"])}
+    value = n_vis * args.steps * world / (ms / 1e3)
+
+    # end to end through the host-buffer call (pinned host in, image back to host)
+    out_h = torch.empty((wl.n, wl.n), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        im.image_from_host(uvw_h, vis_h, wt_h, out_h)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        im.image_from_host(uvw_h, vis_h, wt_h, out_h)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        dist.barrier()
+    e2e_value = n_vis * args.steps * world / (e2e_ms / 1e3)
+
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(n_vis, n_binned, wl.n, wl.n_w)
+    gbps = {k: alg[k] / (stage_ms[k] * 1e-3) / 1e9 for k in alg}
+    own = ["bin", "grid", "wcorrect"]
+    dom = max(own, key=lambda k: stage_ms[k])
+    kernel_name = {"bin": "rick_bin (all binning kernels)", "grid": "grid_kernel",
+                   "wcorrect": "wcorrect_kernel"}[dom]
+    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": gbps[dom], "peak": peak,
+                "unit": "GB/s", "frac": gbps[dom] / peak,
+                "traffic": traffic_of(dom, n_vis), "algorithmic_bytes": alg[dom],
+                "peak_source": f"{peak_kind} (HBM copy bandwidth)"}
+
+    if rank != 0:
+        im.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, data, args.cpu_sample)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**config_of(wl), "parallelism": f"replicas{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_vis * (24 + 8 + 4),
+                "d2h_bytes_per_step": wl.n * wl.n * 4, "ms_per_step": e2e_ms / args.steps},
+        "roofline": roofline,
+        "stages": {"ms": stage_ms, "gbps": gbps, "algorithmic_bytes": alg,
+                   "n_binned": n_binned},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    im.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lofar")
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--ref-sample", type=int, default=500_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("bench.py: --warmup must be at least 3")
+    import synth
+
+    wl = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

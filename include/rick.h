@@ -101,6 +101,10 @@ rick_status rick_plan_destroy(rick_plan *plan);
 /* Sticky error of a plan (RICK_OK if none). */
 rick_status rick_plan_last_error(const rick_plan *plan);
 
+/* Number of library kernels this plan has enqueued since it was created
+ * (cuFFT's kernels are not included), for launch accounting. */
+rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count);
+
 /* Bytes of the binning workspace of a plan created with max_vis = n_vis
  * (bin_bytes; the workspace layout depends only on params and that capacity)
  * and of the planes buffer (plane_bytes = n_w n^2 8).  Either output may be

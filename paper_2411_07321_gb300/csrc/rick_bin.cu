@@ -64,17 +64,20 @@ __global__ void scan_add_kernel(uint32_t *out, int64_t n, const uint32_t *block_
     if (i + 1024 < n) out[i + 1024] += add;
 }
 
-// out[i] = sum_{j < i} in[i]; in may equal out.  tmp: rick_scan_tmp(n) words.
+// out[i] = sum_{j < i} in[j]; in may equal out.  tmp: rick_scan_tmp(n) words.
+// *launches counts the kernels enqueued.
 static cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
-                            cudaStream_t st)
+                            cudaStream_t st, unsigned long long *launches)
 {
     if (n <= 0) return cudaSuccess;
     int64_t nb = (n + 2047) / 2048;
     scan_blocks_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, out, n, tmp);
+    ++*launches;
     if (nb == 1) return cudaGetLastError();
-    cudaError_t e = scan_u32(tmp, tmp, nb, tmp + nb + 1, st);
+    cudaError_t e = scan_u32(tmp, tmp, nb, tmp + nb + 1, st, launches);
     if (e != cudaSuccess) return e;
     scan_add_kernel<<<(unsigned)nb, 1024, 0, st>>>(out, n, tmp);
+    ++*launches;
     return cudaGetLastError();
 }
 
@@ -418,7 +421,7 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
     }
     bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL);
     RICK_LAUNCH_CHECK(plan);
-    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.offsets, L.nbins + 1, w.scan, st));
+    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.offsets, L.nbins + 1, w.scan, st, &plan->launches));
     if (n_vis > 0) {
         RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
         int64_t blocks = (n_vis + 255) / 256;
@@ -430,8 +433,8 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
     tile_count_kernel<<<(nt + 256) / 256, 256, 0, st>>>(w.offsets, w.gbase, w.dbase, nt,
                                                         p.n / p.tile, cap);
     RICK_LAUNCH_CHECK(plan);
-    RICK_CUDA_TRY(plan, scan_u32(w.gbase, w.gbase, L.ntiles + 1, w.scan, st));
-    RICK_CUDA_TRY(plan, scan_u32(w.dbase, w.dbase, L.ntiles + 1, w.scan, st));
+    RICK_CUDA_TRY(plan, scan_u32(w.gbase, w.gbase, L.ntiles + 1, w.scan, st, &plan->launches));
+    RICK_CUDA_TRY(plan, scan_u32(w.dbase, w.dbase, L.ntiles + 1, w.scan, st, &plan->launches));
     if (stats_dev)
         RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
                                             cudaMemcpyDeviceToDevice, st));

@@ -30,6 +30,7 @@ struct rick_plan {
     float *taper_inv;  // device [n]: 1 / C(nu_p), nu_p = (p - n/2) / n
     double beta, sigma, i0_beta;
     rick_status sticky;
+    unsigned long long launches;  // library kernels enqueued so far (cuFFT's not included)
 };
 
 // ------------------------------------------------------------------------
@@ -380,7 +381,11 @@ __device__ __forceinline__ float rick_g(const KernelShape &k, float d)
         }                                                          \
     } while (0)
 
-#define RICK_LAUNCH_CHECK(plan) RICK_CUDA_TRY(plan, cudaGetLastError())
+#define RICK_LAUNCH_CHECK(plan)                    \
+    do {                                           \
+        ++(plan)->launches;                        \
+        RICK_CUDA_TRY(plan, cudaGetLastError());   \
+    } while (0)
 
 // Launch arguments shared by the tile kernels.
 struct TileArgs {

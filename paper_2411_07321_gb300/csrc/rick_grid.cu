@@ -395,6 +395,7 @@ extern "C" rick_status rick_grid(rick_plan *plan, const void *ws_dev, void *plan
 #define CALL_GRID(WW) err = launch_grid<WW>(a, comp, (unsigned)bound, st)
     RICK_W_SWITCH(p.support, CALL_GRID);
 #undef CALL_GRID
+    ++plan->launches;
     RICK_CUDA_TRY(plan, err);
     return RICK_OK;
 }
@@ -424,6 +425,7 @@ extern "C" rick_status rick_degrid(rick_plan *plan, const void *ws_dev, const vo
 #define CALL_DEGRID(WW) err = launch_degrid<WW>(a, (unsigned)bound, st)
     RICK_W_SWITCH(p.support, CALL_DEGRID);
 #undef CALL_DEGRID
+    ++plan->launches;
     RICK_CUDA_TRY(plan, err);
     return RICK_OK;
 }

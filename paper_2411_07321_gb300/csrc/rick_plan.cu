@@ -152,6 +152,7 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
         free(pl);
         return RICK_ENOMEM;
     }
+    pl->launches = 1;
     taper_kernel<<<(n + 255) / 256, 256>>>(pl->taper_inv, n, params->support, params->kernel,
                                            pl->beta, pl->i0_beta, pl->sigma);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
@@ -178,6 +179,13 @@ extern "C" rick_status rick_plan_destroy(rick_plan *plan)
 extern "C" rick_status rick_plan_last_error(const rick_plan *plan)
 {
     return plan ? plan->sticky : RICK_EINVAL;
+}
+
+extern "C" rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count)
+{
+    if (!plan || !count) return RICK_EINVAL;
+    *count = plan->launches;
+    return RICK_OK;
 }
 
 extern "C" rick_status rick_workspace_bytes(const rick_params *params, int64_t n_vis,

@@ -137,6 +137,35 @@ class Imager:
         """Model visibilities of a sky image through the binned geometry (Eq. 1)."""
         return self.adjoint(image, None, PREDICT_FLAGS, out)
 
+    def image_from_host(self, uvw_host: torch.Tensor, vis_host: torch.Tensor,
+                        weight_host: torch.Tensor | None, out_host: torch.Tensor,
+                        flags: int = IMAGE_FLAGS) -> torch.Tensor:
+        """The image from host buffers (pinned for asynchronous copies): the
+        inputs are copied into resident device buffers, imaged, and the image is
+        copied back into ``out_host``, all on the current stream."""
+        n = uvw_host.shape[0]
+        if n > self.max_vis:
+            raise ValueError(f"{n} visibilities exceed this imager's capacity {self.max_vis}")
+        if getattr(self, "_in_uvw", None) is None:
+            self._in_uvw = torch.empty((self.max_vis, 3), dtype=torch.float64, device=self.device)
+            self._in_vis = torch.empty(self.max_vis, dtype=torch.complex64, device=self.device)
+            self._in_wt = torch.empty(self.max_vis, dtype=torch.float32, device=self.device)
+            self._out_img = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
+        uvw, vis = self._in_uvw[:n], self._in_vis[:n]
+        uvw.copy_(uvw_host, non_blocking=True)
+        vis.copy_(vis_host, non_blocking=True)
+        wt = None
+        if weight_host is not None:
+            wt = self._in_wt[:n]
+            wt.copy_(weight_host, non_blocking=True)
+        self.image(uvw, vis, wt, flags, out=self._out_img)
+        out_host.copy_(self._out_img, non_blocking=True)
+        return out_host
+
+    def launches(self) -> int:
+        """Library kernels this imager's plan has enqueued so far."""
+        return R.rick_plan_launch_count(self.plan)
+
     def stats(self) -> dict:
         return _stats_from_bytes(self.stats_buf.cpu().numpy())
 

@@ -51,6 +51,7 @@ class rick_bin_view(ctypes.Structure):
 
 
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
+           "rick_plan_launch_count",
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
            "rick_bin_values",
            "rick_grid", "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid"]
@@ -70,6 +71,7 @@ def _load():
         "rick_plan_create": [P, i64, ctypes.POINTER(vp)],
         "rick_plan_destroy": [vp],
         "rick_plan_last_error": [vp],
+        "rick_plan_launch_count": [vp, ctypes.POINTER(ctypes.c_uint64)],
         "rick_workspace_bytes": [P, i64, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "rick_plan_fft_bytes": [vp, ctypes.POINTER(sz)],
         "rick_bin_layout": [vp, ctypes.POINTER(rick_bin_view)],
@@ -120,6 +122,12 @@ def rick_plan_destroy(plan: int) -> None:
 
 def rick_plan_last_error(plan: int) -> int:
     return int(_L.rick_plan_last_error(plan))
+
+
+def rick_plan_launch_count(plan: int) -> int:
+    c = ctypes.c_uint64()
+    _check("rick_plan_launch_count", _L.rick_plan_launch_count(plan, ctypes.byref(c)))
+    return c.value
 
 
 def rick_workspace_bytes(params: rick_params, n_vis: int) -> tuple[int, int]:
