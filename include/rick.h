@@ -165,8 +165,12 @@ rick_status rick_bin_values(rick_plan *plan, const void *vis_dev, const float *w
  * checkerboard (-1)^(i+j) of the centred FFT folded in.  Every element of
  * planes_dev (complex64 [n_w][n][n]) is overwritten.  Each uv-tile is summed
  * in shared memory and written once (plain stores; tiles with more records
- * than one chunk add their chunk sums with float atomics). */
-rick_status rick_grid(rick_plan *plan, const void *ws_dev, void *planes_dev, void *stream);
+ * than one chunk add their chunk sums with float atomics).  The kernel
+ * weights G are degree-12 polynomial fits per unit segment (FP64 fit at plan
+ * creation, FP32 evaluation).  rick_grid and rick_degrid use a word of the
+ * workspace header as a work counter: calls that share a workspace must not
+ * overlap on the device. */
+rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream);
 
 /* Per-plane 2D FFT (§2 step 3, §3.1): cuFFT complex64, unnormalised, in place,
  * batched over the n_w planes.  direction +1: inverse (e^{+2 pi i}), used for
@@ -195,7 +199,7 @@ rick_status rick_wspread(rick_plan *plan, const float *image_dev, const void *ws
  * written in input order; dropped visibilities get 0.
  *   weight_dev: float32 [n_vis] (the weights given to rick_bin) or NULL (none)
  *   vis_out_dev: complex64 [n_vis] */
-rick_status rick_degrid(rick_plan *plan, const void *ws_dev, const void *planes_dev,
+rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
                         const float *weight_dev, void *vis_out_dev, void *stream);
 
 #ifdef __cplusplus

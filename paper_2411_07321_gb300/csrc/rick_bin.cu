@@ -359,7 +359,7 @@ __global__ void tile_count_kernel(const uint32_t *off, uint32_t *gcnt, uint32_t 
     if (tx > 0) L += off[4 * (t - 1) + 3] - off[4 * (t - 1) + 1];
     if (ty > 0) L += off[4 * (t - nt) + 4] - off[4 * (t - nt) + 2];
     if (tx > 0 && ty > 0) L += off[4 * (t - nt - 1) + 3] - off[4 * (t - nt - 1) + 2];
-    gcnt[t] = L == 0 ? 1u : (L + cap - 1) / cap;
+    gcnt[t] = (L + cap - 1) / cap;  // tiles without records: no work item
     dcnt[t] = (own + cap - 1) / cap;
 }
 

@@ -18,6 +18,53 @@
 #endif
 
 // ------------------------------------------------------------------------
+// Gridding kernel weights.  For a visibility at fractional offset f the W
+// weights are G((j - h) - f), j = 0..W-1.  Each segment j is a polynomial in
+// s = 2 (f - fc) in [-1, 1) (fc = 0 for odd W, where f is in [-1/2, 1/2);
+// fc = 1/2 for even W, f in [0, 1)), fitted at plan creation by Chebyshev
+// interpolation of degree RICK_POLY_DEG in FP64 and evaluated by Horner's rule
+// in FP32.  The coefficients travel in the kernel-argument (constant) space.
+
+#define RICK_MAX_W 16
+#define RICK_POLY_DEG 12
+#define RICK_POLY_N (RICK_POLY_DEG + 1)
+
+struct KernelPoly {
+    float c[RICK_MAX_W][RICK_POLY_N];
+    float fc;
+};
+
+#if defined(__CUDACC__)
+// Weight of segment j at s = 2 (f - fc).
+template <int W>
+__device__ __forceinline__ float kernel_weight_one(const KernelPoly &kp, int j, float s)
+{
+    if (W == 1) return 1.0f;
+    float y = kp.c[j][RICK_POLY_DEG];
+#pragma unroll
+    for (int k = RICK_POLY_DEG - 1; k >= 0; --k) y = __fmaf_rn(y, s, kp.c[j][k]);
+    return y;
+}
+
+template <int W>
+__device__ __forceinline__ void kernel_weights(const KernelPoly &kp, float f, float *g)
+{
+    if (W == 1) {
+        g[0] = 1.0f;
+        return;
+    }
+    const float s = 2.0f * (f - kp.fc);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        float y = kp.c[j][RICK_POLY_DEG];
+#pragma unroll
+        for (int k = RICK_POLY_DEG - 1; k >= 0; --k) y = __fmaf_rn(y, s, kp.c[j][k]);
+        g[j] = y;
+    }
+}
+#endif
+
+// ------------------------------------------------------------------------
 // Plan
 
 struct rick_plan {
@@ -29,6 +76,7 @@ struct rick_plan {
     size_t fft_bytes;
     float *taper_inv;  // device [n]: 1 / C(nu_p), nu_p = (p - n/2) / n
     double beta, sigma, i0_beta;
+    KernelPoly poly;   // kernel-weight polynomials (host copy, passed to kernels)
     rick_status sticky;
     unsigned long long launches;  // library kernels enqueued so far (cuFFT's not included)
 };
@@ -46,7 +94,7 @@ struct WsHeader {
     uint32_t chunk_cap;                 // records per work item (at most)
     uint32_t range_given;
     uint32_t n_key_blocks;
-    uint32_t pad;
+    uint32_t grid_next, degrid_next;    // work counters of the persistent tile kernels
 };
 
 struct WsLayout {
@@ -345,31 +393,6 @@ __device__ __forceinline__ float ff_frac(ff t)
 #endif
 
 // ------------------------------------------------------------------------
-// Gridding kernel G(d) in FP32 (d in cells, |d| <= W/2)
-
-struct KernelShape {
-    int kind;        // RICK_KERNEL_GAUSS / RICK_KERNEL_KB
-    float beta;      // KB
-    float inv_i0b;   // 1 / I0(beta)
-    float two_over_w;
-    float inv_2s2;   // Gaussian 1 / (2 sigma^2)
-};
-
-#if defined(__CUDACC__)
-template <int KIND>
-__device__ __forceinline__ float rick_g(const KernelShape &k, float d)
-{
-    if (KIND == RICK_KERNEL_GAUSS) {
-        return expf(-d * d * k.inv_2s2);
-    } else {
-        float t = d * k.two_over_w;
-        float s = fmaxf(0.0f, __fmaf_rn(-t, t, 1.0f));
-        return cyl_bessel_i0f(k.beta * sqrtf(s)) * k.inv_i0b;
-    }
-}
-#endif
-
-// ------------------------------------------------------------------------
 // Error plumbing
 
 #define RICK_CUDA_TRY(plan, expr)                                  \
@@ -393,6 +416,6 @@ struct TileArgs {
     uint32_t ntiles, chunk_cap;
     const uint32_t *offsets, *base, *perm, *rcell;
     const float2 *rval, *rfrac;
-    const WsHeader *hdr;
-    KernelShape ks;
+    WsHeader *hdr;
+    KernelPoly kp;
 };

@@ -9,8 +9,9 @@
 // tile, then writes the tile once with plain coalesced stores.  The
 // checkerboard (-1)^(i+j) of the centred FFT is applied in that write.  A tile
 // with more than one chunk is zeroed first and its chunks add their sums with
-// float2 atomics.  No global atomics otherwise, and no separate zero-fill of
-// the planes: every cell is written by the CTA that owns it.
+// float2 atomics.  Tiles without records are not work items: a light
+// grid-stride kernel writes their zeros, so the register-heavy gridding CTAs
+// only run where there are records.
 //
 // Degridding: one CTA per chunk of a non-empty tile's own bin; the CTA stages
 // the (T + W - 1)^2 plane region its records can touch into shared memory and
@@ -45,44 +46,6 @@ __device__ __forceinline__ uint32_t find_tile(const uint32_t *base, uint32_t nti
     return lo;
 }
 
-template <int W>
-__device__ __forceinline__ void kernel_weights(const KernelShape &ks, float f, float *g)
-{
-    const int h = (W & 1) ? (W - 1) / 2 : W / 2 - 1;
-    if (W == 1) {
-        g[0] = 1.0f;
-        return;
-    }
-    if (ks.kind == RICK_KERNEL_KB) {
-#pragma unroll
-        for (int j = 0; j < W; ++j) g[j] = rick_g<RICK_KERNEL_KB>(ks, (float)(j - h) - f);
-    } else {
-#pragma unroll
-        for (int j = 0; j < W; ++j) g[j] = rick_g<RICK_KERNEL_GAUSS>(ks, (float)(j - h) - f);
-    }
-}
-
-// Add one record's footprint, clipped to the tile, into the accumulator.
-template <int W>
-__device__ __forceinline__ void splat(float *acc_re, float *acc_im, int T, int log2T, int lx,
-                                      int ly, float2 val, const float *gx, const float *gy)
-{
-#pragma unroll
-    for (int jy = 0; jy < W; ++jy) {
-        int row = ly + jy;
-        if ((unsigned)row >= (unsigned)T) continue;
-        float vr = val.x * gy[jy], vi = val.y * gy[jy];
-        int rbase = row << log2T;
-#pragma unroll
-        for (int jx = 0; jx < W; ++jx) {
-            int col = lx + jx;
-            if ((unsigned)col >= (unsigned)T) continue;
-            atomicAdd(&acc_re[rbase + col], vr * gx[jx]);
-            atomicAdd(&acc_im[rbase + col], vi * gx[jx]);
-        }
-    }
-}
-
 // Neumaier's compensated summation of a into (s, c).
 __device__ __forceinline__ void neumaier(float &s, float &c, float a)
 {
@@ -94,17 +57,142 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float a)
     s = t;
 }
 
-template <int W, bool COMP>
-__global__ void __launch_bounds__(256) grid_kernel(GridArgs a)
+// Record index of position v in the concatenation of the four ranges.
+struct Ranges {
+    uint32_t s0, L0, s1, L1, s2, L2, s3;
+    __device__ __forceinline__ uint32_t at(uint32_t v) const
+    {
+        if (v < L0) return s0 + v;
+        v -= L0;
+        if (v < L1) return s1 + v;
+        v -= L1;
+        if (v < L2) return s2 + v;
+        return s3 + (v - L2);
+    }
+};
+
+// Add a W x W footprint at corner (lx, ly) (tile coordinates), clipped to the
+// tile, into the shared accumulator.
+template <int W>
+__device__ __forceinline__ void flush_footprint(float *acc_re, float *acc_im, int T, int log2T,
+                                                int lx, int ly, const float (&ar)[W][W],
+                                                const float (&ai)[W][W])
 {
-    extern __shared__ float sm[];
+#pragma unroll
+    for (int jy = 0; jy < W; ++jy) {
+        int row = ly + jy;
+        if ((unsigned)row >= (unsigned)T) continue;
+        int rbase = row << log2T;
+#pragma unroll
+        for (int jx = 0; jx < W; ++jx) {
+            int col = lx + jx;
+            if ((unsigned)col >= (unsigned)T) continue;
+            atomicAdd(&acc_re[rbase + col], ar[jy][jx]);
+            atomicAdd(&acc_im[rbase + col], ai[jy][jx]);
+        }
+    }
+}
+
+// One thread's contiguous run of records [v0, v1).  Records whose footprint
+// corner repeats (the channels of one baseline-time, the same cell) are summed
+// in registers; the footprint is added to shared memory once per change of
+// corner.  This keeps the shared-memory atomics few and spread out: threads
+// walk different runs, so they rarely hit the same cells at the same time.
+template <int W>
+__device__ __forceinline__ void grid_run_direct(const TileArgs &ta, const Ranges &rg, uint32_t v0,
+                                                uint32_t v1, int x0, int y0, float *acc_re,
+                                                float *acc_im, int T, int log2T)
+{
+    for (uint32_t v = v0; v < v1; ++v) {
+        uint32_t r = rg.at(v);
+        float2 val = ta.rval[r], fr = ta.rfrac[r];
+        uint32_t cell = ta.rcell[r];
+        int lx = (int)(cell & 0xFFFFu) - x0, ly = (int)(cell >> 16) - y0;
+        float gx[W];
+        kernel_weights<W>(ta.kp, fr.x, gx);
+        const float sy = 2.0f * (fr.y - ta.kp.fc);
+#pragma unroll
+        for (int jy = 0; jy < W; ++jy) {
+            int row = ly + jy;
+            if ((unsigned)row >= (unsigned)T) continue;
+            const float gyv = kernel_weight_one<W>(ta.kp, jy, sy);
+            float vr = val.x * gyv, vi = val.y * gyv;
+            int rbase = row << log2T;
+#pragma unroll
+            for (int jx = 0; jx < W; ++jx) {
+                int col = lx + jx;
+                if ((unsigned)col >= (unsigned)T) continue;
+                atomicAdd(&acc_re[rbase + col], vr * gx[jx]);
+                atomicAdd(&acc_im[rbase + col], vi * gx[jx]);
+            }
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void grid_run(const TileArgs &ta, const Ranges &rg, uint32_t v0,
+                                         uint32_t v1, int x0, int y0, float *acc_re,
+                                         float *acc_im, int T, int log2T)
+{
+    if (v0 >= v1) return;
+    if (W > 9) {  // a W x W register accumulator would not fit
+        grid_run_direct<W>(ta, rg, v0, v1, x0, y0, acc_re, acc_im, T, log2T);
+        return;
+    }
+    float ar[W][W], ai[W][W];
+    uint32_t cur = 0xFFFFFFFFu;
+    uint32_t r = rg.at(v0);
+    float2 val = ta.rval[r], fr = ta.rfrac[r];
+    uint32_t cell = ta.rcell[r];
+    for (uint32_t v = v0; v < v1; ++v) {
+        // prefetch the next record
+        float2 nval = val, nfr = fr;
+        uint32_t ncell = cell;
+        if (v + 1 < v1) {
+            uint32_t rn = rg.at(v + 1);
+            nval = ta.rval[rn];
+            nfr = ta.rfrac[rn];
+            ncell = ta.rcell[rn];
+        }
+        if (cell != cur) {
+            if (cur != 0xFFFFFFFFu)
+                flush_footprint<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0,
+                                   (int)(cur >> 16) - y0, ar, ai);
+#pragma unroll
+            for (int jy = 0; jy < W; ++jy)
+#pragma unroll
+                for (int jx = 0; jx < W; ++jx) ar[jy][jx] = ai[jy][jx] = 0.0f;
+            cur = cell;
+        }
+        float gx[W];
+        kernel_weights<W>(ta.kp, fr.x, gx);
+        const float sy = 2.0f * (fr.y - ta.kp.fc);
+#pragma unroll
+        for (int jy = 0; jy < W; ++jy) {
+            const float gyv = kernel_weight_one<W>(ta.kp, jy, sy);
+            float vr = val.x * gyv, vi = val.y * gyv;
+#pragma unroll
+            for (int jx = 0; jx < W; ++jx) {
+                ar[jy][jx] = __fmaf_rn(vr, gx[jx], ar[jy][jx]);
+                ai[jy][jx] = __fmaf_rn(vi, gx[jx], ai[jy][jx]);
+            }
+        }
+        val = nval;
+        fr = nfr;
+        cell = ncell;
+    }
+    flush_footprint<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0,
+                       ar, ai);
+}
+
+// Records at least this many per thread, so that a thread's run spans the
+// channels of a baseline-time rather than one record each.
+#define RICK_MIN_RUN 16u
+
+template <int W, bool COMP>
+__device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm)
+{
     const TileArgs &ta = a.t;
-    const uint32_t b = blockIdx.x;
-    if (b >= ta.base[ta.ntiles]) return;
-    __shared__ uint32_t s_tile;
-    if (threadIdx.x == 0) s_tile = find_tile(ta.base, ta.ntiles, b);
-    __syncthreads();
-    const uint32_t t = s_tile;
     const uint32_t chunk = b - ta.base[t], nch = ta.base[t + 1] - ta.base[t];
     const int T = 1 << a.log2T, TT = T * T, nt = ta.nt;
     const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
@@ -112,21 +200,24 @@ __global__ void __launch_bounds__(256) grid_kernel(GridArgs a)
     const uint32_t *off = ta.offsets;
 
     // the four record ranges that can touch this tile
-    uint32_t s0 = off[4 * t], L0 = off[4 * t + 4] - s0;
-    uint32_t s1 = 0, L1 = 0, s2 = 0, L2 = 0, s3 = 0, L3 = 0;
+    Ranges rg;
+    rg.s0 = off[4 * t];
+    rg.L0 = off[4 * t + 4] - rg.s0;
+    rg.s1 = rg.L1 = rg.s2 = rg.L2 = rg.s3 = 0;
+    uint32_t L3 = 0;
     if (tx > 0) {
-        s1 = off[4 * (t - 1) + 1];
-        L1 = off[4 * (t - 1) + 3] - s1;
+        rg.s1 = off[4 * (t - 1) + 1];
+        rg.L1 = off[4 * (t - 1) + 3] - rg.s1;
     }
     if (ty > 0) {
-        s2 = off[4 * (t - nt) + 2];
-        L2 = off[4 * (t - nt) + 4] - s2;
+        rg.s2 = off[4 * (t - nt) + 2];
+        rg.L2 = off[4 * (t - nt) + 4] - rg.s2;
     }
     if (tx > 0 && ty > 0) {
-        s3 = off[4 * (t - nt - 1) + 2];
-        L3 = off[4 * (t - nt - 1) + 3] - s3;
+        rg.s3 = off[4 * (t - nt - 1) + 2];
+        L3 = off[4 * (t - nt - 1) + 3] - rg.s3;
     }
-    const uint32_t Ltot = L0 + L1 + L2 + L3;
+    const uint32_t Ltot = rg.L0 + rg.L1 + rg.L2 + L3;
     const uint32_t vbeg = chunk * ta.chunk_cap;
     const uint32_t vend = min(Ltot, vbeg + ta.chunk_cap);
 
@@ -135,34 +226,18 @@ __global__ void __launch_bounds__(256) grid_kernel(GridArgs a)
     for (int i = threadIdx.x; i < TT; i += blockDim.x) {
         acc_re[i] = 0.0f;
         acc_im[i] = 0.0f;
-        if (COMP) {
-            sum_re[i] = sum_im[i] = cmp_re[i] = cmp_im[i] = 0.0f;
-        }
+        if (COMP) sum_re[i] = sum_im[i] = cmp_re[i] = cmp_im[i] = 0.0f;
     }
     __syncthreads();
 
-    const uint32_t SUB = COMP ? 1024u : 0xFFFFFFFFu;  // records per compensated fold
-    for (uint32_t sb = vbeg; sb < vend; sb += (COMP ? SUB : (vend - vbeg))) {
-        const uint32_t se = COMP ? min(vend, sb + SUB) : vend;
-        for (uint32_t v = sb + threadIdx.x; v < se; v += blockDim.x) {
-            uint32_t r;
-            if (v < L0)
-                r = s0 + v;
-            else if (v < L0 + L1)
-                r = s1 + (v - L0);
-            else if (v < L0 + L1 + L2)
-                r = s2 + (v - L0 - L1);
-            else
-                r = s3 + (v - L0 - L1 - L2);
-            float2 val = ta.rval[r];
-            float2 fr = ta.rfrac[r];
-            uint32_t cell = ta.rcell[r];
-            int lx = (int)(cell & 0xFFFFu) - x0, ly = (int)(cell >> 16) - y0;
-            float gx[W], gy[W];
-            kernel_weights<W>(ta.ks, fr.x, gx);
-            kernel_weights<W>(ta.ks, fr.y, gy);
-            splat<W>(acc_re, acc_im, T, a.log2T, lx, ly, val, gx, gy);
-        }
+    // plain: one round over the chunk; compensated: rounds of 4096 records,
+    // each folded into the (sum, compensation) pair of every cell
+    const uint32_t round = COMP ? 4096u : max(vend - vbeg, 1u);
+    for (uint32_t rb = vbeg; rb < vend; rb += round) {
+        const uint32_t re = min(vend, rb + round);
+        const uint32_t per = max(RICK_MIN_RUN, (re - rb + blockDim.x - 1) / blockDim.x);
+        const uint32_t v0 = rb + threadIdx.x * per;
+        grid_run<W>(ta, rg, min(v0, re), min(v0 + per, re), x0, y0, acc_re, acc_im, T, a.log2T);
         if (COMP) {
             __syncthreads();
             for (int i = threadIdx.x; i < TT; i += blockDim.x) {
@@ -197,36 +272,57 @@ __global__ void __launch_bounds__(256) grid_kernel(GridArgs a)
     }
 }
 
-// Zero the tiles that several chunks add into (grid-stride, one warp per tile).
-__global__ void zero_multi_kernel(const uint32_t *base, uint32_t ntiles, int nt, int log2T, int n,
-                                  float2 *planes)
+// Persistent: one wave of CTAs takes work items (tile, chunk) from a counter
+// in the workspace header (reset by zero_tiles_kernel, launched just before).
+template <int W, bool COMP>
+__global__ void __launch_bounds__(256, 1) grid_kernel(GridArgs a)
 {
+    extern __shared__ float sm[];
+    __shared__ uint32_t s_b, s_tile;
+    const uint32_t total = a.t.base[a.t.ntiles];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
+            s_b = b;
+            s_tile = b < total ? find_tile(a.t.base, a.t.ntiles, b) : 0u;
+        }
+        __syncthreads();
+        const uint32_t b = s_b, t = s_tile;
+        if (b >= total) break;
+        grid_item<W, COMP>(a, b, t, sm);
+        __syncthreads();  // the accumulator is reused by the next item
+    }
+}
+
+// Zero every tile that is not written by exactly one grid work item: tiles
+// without records (no work item) and tiles whose chunks add into them with
+// atomics.  Grid-stride, one warp per tile, 16-byte stores.
+__global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, uint32_t ntiles,
+                                                         int nt, int log2T, int n, float2 *planes,
+                                                         WsHeader *hdr)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->grid_next = 0;
     int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int T = 1 << log2T;
+    const int T = 1 << log2T, half = T >> 1;  // float4 = two cells
     for (uint32_t t = warp; t < ntiles; t += nwarps) {
-        if (base[t + 1] - base[t] <= 1) continue;
+        if (base[t + 1] - base[t] == 1) continue;
         uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
-        float2 *plane = planes + (size_t)k * n * n;
-        for (int i = lane; i < T * T; i += 32) {
-            int row = i >> log2T, col = i & (T - 1);
-            plane[(size_t)((ty << log2T) + row) * n + (tx << log2T) + col] = make_float2(0.f, 0.f);
+        float4 *plane = (float4 *)(planes + (size_t)k * n * n);
+        for (int i = lane; i < T * half; i += 32) {
+            int row = i / half, col2 = i - row * half;
+            plane[((size_t)((ty << log2T) + row) * n + (tx << log2T)) / 2 + col2] =
+                make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
 }
 
 template <int W>
-__global__ void __launch_bounds__(256) degrid_kernel(DegridArgs a)
+__device__ __forceinline__ void degrid_item(const DegridArgs &a, uint32_t b, uint32_t t,
+                                            float2 *stage)
 {
-    extern __shared__ float2 stage[];
     const TileArgs &ta = a.t;
-    const uint32_t b = blockIdx.x;
-    if (b >= ta.base[ta.ntiles]) return;
-    __shared__ uint32_t s_tile;
-    if (threadIdx.x == 0) s_tile = find_tile(ta.base, ta.ntiles, b);
-    __syncthreads();
-    const uint32_t t = s_tile;
     const uint32_t chunk = b - ta.base[t];
     const int T = 1 << a.log2T, S = T + W - 1, nt = ta.nt, n = ta.n;
     const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
@@ -254,8 +350,8 @@ __global__ void __launch_bounds__(256) degrid_kernel(DegridArgs a)
         uint32_t cell = ta.rcell[r];
         int lx = (int)(cell & 0xFFFFu) - x0, ly = (int)(cell >> 16) - y0;
         float gx[W], gy[W];
-        kernel_weights<W>(ta.ks, fr.x, gx);
-        kernel_weights<W>(ta.ks, fr.y, gy);
+        kernel_weights<W>(ta.kp, fr.x, gx);
+        kernel_weights<W>(ta.kp, fr.y, gy);
         float sr = 0.f, si = 0.f;
 #pragma unroll
         for (int jy = 0; jy < W; ++jy) {
@@ -276,9 +372,30 @@ __global__ void __launch_bounds__(256) degrid_kernel(DegridArgs a)
     }
 }
 
-// Dropped visibilities (key == all ones) get a zero model value.
-__global__ void degrid_zero_dropped_kernel(const WsHeader *hdr, const uint32_t *key, float2 *vis_out)
+template <int W>
+__global__ void __launch_bounds__(256) degrid_kernel(DegridArgs a)
 {
+    extern __shared__ float2 stage[];
+    __shared__ uint32_t s_b, s_tile;
+    const uint32_t total = a.t.base[a.t.ntiles];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t b = atomicAdd(&a.t.hdr->degrid_next, 1u);
+            s_b = b;
+            s_tile = b < total ? find_tile(a.t.base, a.t.ntiles, b) : 0u;
+        }
+        __syncthreads();
+        const uint32_t b = s_b, t = s_tile;
+        if (b >= total) break;
+        degrid_item<W>(a, b, t, stage);
+        __syncthreads();
+    }
+}
+
+// Dropped visibilities (key == all ones) get a zero model value.
+__global__ void degrid_zero_dropped_kernel(WsHeader *hdr, const uint32_t *key, float2 *vis_out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->degrid_next = 0;
     int64_t n = (int64_t)hdr->n_vis;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -306,11 +423,7 @@ static TileArgs make_tile_args(const rick_plan *plan, const WsPtrs &w, const uin
     t.rval = w.rval;
     t.rfrac = w.rfrac;
     t.hdr = w.hdr;
-    t.ks.kind = p.kernel;
-    t.ks.beta = (float)plan->beta;
-    t.ks.inv_i0b = (float)(1.0 / plan->i0_beta);
-    t.ks.two_over_w = 2.0f / p.support;
-    t.ks.inv_2s2 = (float)(1.0 / (2.0 * plan->sigma * plan->sigma));
+    t.kp = plan->poly;
     return t;
 }
 
@@ -321,30 +434,40 @@ static int ilog2(int x)
     return l;
 }
 
-template <int W>
-static cudaError_t launch_grid(const GridArgs &a, bool comp, unsigned blocks, cudaStream_t st)
+// One wave of persistent CTAs: SMs x resident CTAs per SM.
+template <typename K>
+static unsigned persistent_blocks(K kernel, size_t smem, int num_sms)
 {
-    size_t TT = (size_t)a.t.T * a.t.T;
-    size_t smem = (comp ? 6 : 2) * TT * sizeof(float);
-    if (comp) {
-        cudaFuncSetAttribute(grid_kernel<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        grid_kernel<W, true><<<blocks, 256, smem, st>>>(a);
-    } else {
-        cudaFuncSetAttribute(grid_kernel<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        grid_kernel<W, false><<<blocks, 256, smem, st>>>(a);
-    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return (unsigned)(per_sm * num_sms);
+}
+
+template <int W, bool COMP>
+static cudaError_t launch_grid_t(const GridArgs &a, int num_sms, cudaStream_t st)
+{
+    size_t smem = (COMP ? 6 : 2) * (size_t)a.t.T * a.t.T * sizeof(float);
+    cudaFuncSetAttribute(grid_kernel<W, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    grid_kernel<W, COMP><<<persistent_blocks(grid_kernel<W, COMP>, smem, num_sms), 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int W>
-static cudaError_t launch_degrid(const DegridArgs &a, unsigned blocks, cudaStream_t st)
+static cudaError_t launch_grid(const GridArgs &a, bool comp, int num_sms, cudaStream_t st)
+{
+    return comp ? launch_grid_t<W, true>(a, num_sms, st) : launch_grid_t<W, false>(a, num_sms, st);
+}
+
+template <int W>
+static cudaError_t launch_degrid(const DegridArgs &a, int num_sms, cudaStream_t st)
 {
     size_t S = a.t.T + W - 1;
     size_t smem = S * S * sizeof(float2);
     cudaFuncSetAttribute(degrid_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    degrid_kernel<W><<<blocks, 256, smem, st>>>(a);
+    degrid_kernel<W><<<persistent_blocks(degrid_kernel<W>, smem, num_sms), 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -369,30 +492,26 @@ static cudaError_t launch_degrid(const DegridArgs &a, unsigned blocks, cudaStrea
     default: err = cudaErrorInvalidValue; \
     }
 
-extern "C" rick_status rick_grid(rick_plan *plan, const void *ws_dev, void *planes_dev,
+extern "C" rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev,
                                  void *stream)
 {
     if (!plan || !ws_dev || !planes_dev) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (((uintptr_t)ws_dev & 255) || ((uintptr_t)planes_dev & 15)) return RICK_EINVAL;
     const rick_params &p = plan->p;
-    WsPtrs w = rick_ws_ptrs((void *)ws_dev, rick_ws_layout(&p, plan->max_vis));
+    WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&p, plan->max_vis));
     cudaStream_t st = (cudaStream_t)stream;
-    // The chunk cap and work totals live on the device; the launch uses the
-    // host-side bound: every tile has at least one item, and the items of the
-    // records are at most 4 n_vis / cap (a record touches at most 4 tiles).
     uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
     GridArgs a;
     a.t = make_tile_args(plan, w, w.gbase, cap);
     a.planes = (float2 *)planes_dev;
     a.log2T = ilog2(p.tile);
-    int64_t bound = (int64_t)a.t.ntiles + (4 * plan->max_vis + cap - 1) / cap + 1;
     cudaError_t err = cudaSuccess;
-    zero_multi_kernel<<<plan->num_sms * 4, 256, 0, st>>>(w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n,
-                                                         a.planes);
+    zero_tiles_kernel<<<plan->num_sms * 8, 256, 0, st>>>(w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n,
+                                                          a.planes, w.hdr);
     RICK_LAUNCH_CHECK(plan);
     bool comp = p.precision == RICK_PREC_FP32_COMPENSATED;
-#define CALL_GRID(WW) err = launch_grid<WW>(a, comp, (unsigned)bound, st)
+#define CALL_GRID(WW) err = launch_grid<WW>(a, comp, plan->num_sms, st)
     RICK_W_SWITCH(p.support, CALL_GRID);
 #undef CALL_GRID
     ++plan->launches;
@@ -400,7 +519,7 @@ extern "C" rick_status rick_grid(rick_plan *plan, const void *ws_dev, void *plan
     return RICK_OK;
 }
 
-extern "C" rick_status rick_degrid(rick_plan *plan, const void *ws_dev, const void *planes_dev,
+extern "C" rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
                                    const float *weight_dev, void *vis_out_dev, void *stream)
 {
     if (!plan || !ws_dev || !planes_dev || !vis_out_dev) return RICK_EINVAL;
@@ -409,7 +528,7 @@ extern "C" rick_status rick_degrid(rick_plan *plan, const void *ws_dev, const vo
         ((uintptr_t)weight_dev & 3))
         return RICK_EINVAL;
     const rick_params &p = plan->p;
-    WsPtrs w = rick_ws_ptrs((void *)ws_dev, rick_ws_layout(&p, plan->max_vis));
+    WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&p, plan->max_vis));
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
     DegridArgs a;
@@ -420,9 +539,8 @@ extern "C" rick_status rick_degrid(rick_plan *plan, const void *ws_dev, const vo
     a.log2T = ilog2(p.tile);
     degrid_zero_dropped_kernel<<<plan->num_sms * 4, 256, 0, st>>>(w.hdr, w.key, a.vis_out);
     RICK_LAUNCH_CHECK(plan);
-    int64_t bound = (int64_t)a.t.ntiles + (plan->max_vis + cap - 1) / cap + 1;
     cudaError_t err = cudaSuccess;
-#define CALL_DEGRID(WW) err = launch_degrid<WW>(a, (unsigned)bound, st)
+#define CALL_DEGRID(WW) err = launch_degrid<WW>(a, plan->num_sms, st)
     RICK_W_SWITCH(p.support, CALL_DEGRID);
 #undef CALL_DEGRID
     ++plan->launches;

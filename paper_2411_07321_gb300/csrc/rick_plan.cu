@@ -98,6 +98,53 @@ __global__ void taper_kernel(float *taper_inv, int n, int W, int kind, double be
     taper_inv[p] = (float)(1.0 / c);
 }
 
+// Kernel-weight polynomials (one thread per segment j, FP64): G((j - h) - f)
+// sampled at the RICK_POLY_N Chebyshev nodes of s = 2 (f - fc) in [-1, 1],
+// Chebyshev coefficients by the discrete orthogonality sums, then the
+// Chebyshev series rewritten in powers of s with T_{k+1} = 2 s T_k - T_{k-1}.
+__global__ void kernel_poly_kernel(float *coef, int W, int kind, double beta, double i0b,
+                                   double sigma)
+{
+    const int j = threadIdx.x;
+    if (j >= W) return;
+    const int N = RICK_POLY_N;
+    const int h = (W & 1) ? (W - 1) / 2 : W / 2 - 1;
+    const double fc = (W & 1) ? 0.0 : 0.5;
+    double val[RICK_POLY_N], a[RICK_POLY_N], c[RICK_POLY_N], t0[RICK_POLY_N], t1[RICK_POLY_N],
+        t2[RICK_POLY_N];
+    for (int q = 0; q < N; ++q) {
+        double s = cos(M_PI * (q + 0.5) / N);
+        double d = (double)(j - h) - (fc + 0.5 * s);
+        double g;
+        if (kind == RICK_KERNEL_KB) {
+            double t = 2.0 * d / W, u = 1.0 - t * t;
+            g = u > 0.0 ? cyl_bessel_i0(beta * sqrt(u)) / i0b : 1.0 / i0b;
+        } else {
+            g = exp(-d * d / (2.0 * sigma * sigma));
+        }
+        val[q] = g;
+    }
+    for (int k = 0; k < N; ++k) {
+        double sum = 0.0;
+        for (int q = 0; q < N; ++q) sum += val[q] * cos(M_PI * k * (q + 0.5) / N);
+        a[k] = (k == 0 ? 1.0 : 2.0) * sum / N;
+    }
+    for (int k = 0; k < N; ++k) c[k] = t0[k] = t1[k] = 0.0;
+    t0[0] = 1.0;
+    t1[1] = 1.0;
+    c[0] = a[0];
+    for (int k = 0; k < N; ++k) c[k] += a[1] * t1[k];
+    for (int m = 2; m < N; ++m) {
+        for (int k = 0; k < N; ++k) t2[k] = (k > 0 ? 2.0 * t1[k - 1] : 0.0) - t0[k];
+        for (int k = 0; k < N; ++k) {
+            c[k] += a[m] * t2[k];
+            t0[k] = t1[k];
+            t1[k] = t2[k];
+        }
+    }
+    for (int k = 0; k < N; ++k) coef[j * N + k] = (float)c[k];
+}
+
 static double kb_beta_of(const rick_params *p)
 {
     if (!isnan(p->kb_beta)) return p->kb_beta;
@@ -152,10 +199,23 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
         free(pl);
         return RICK_ENOMEM;
     }
-    pl->launches = 1;
+    pl->launches = 2;
     taper_kernel<<<(n + 255) / 256, 256>>>(pl->taper_inv, n, params->support, params->kernel,
                                            pl->beta, pl->i0_beta, pl->sigma);
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    float *coef = NULL;
+    bool ok = cudaGetLastError() == cudaSuccess &&
+              cudaMalloc(&coef, sizeof(float) * RICK_MAX_W * RICK_POLY_N) == cudaSuccess;
+    if (ok) {
+        cudaMemset(coef, 0, sizeof(float) * RICK_MAX_W * RICK_POLY_N);
+        kernel_poly_kernel<<<1, RICK_MAX_W>>>(coef, params->support, params->kernel, pl->beta,
+                                              pl->i0_beta, pl->sigma);
+        ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+             cudaMemcpy(pl->poly.c, coef, sizeof(pl->poly.c), cudaMemcpyDeviceToHost) ==
+                 cudaSuccess;
+    }
+    if (coef) cudaFree(coef);
+    pl->poly.fc = (params->support & 1) ? 0.0f : 0.5f;
+    if (!ok) {
         cudaFree(pl->taper_inv);
         cufftDestroy(pl->fft);
         free(pl);
