@@ -312,9 +312,10 @@ def run_ours(args, wl):
             dist.destroy_process_group()
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.n_vis is None:
         cpu = cpu_baseline(wl, data, args.cpu_sample)
     line = {
+        **({"profiling_subset": True} if args.n_vis is not None else {}),
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -344,12 +345,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-vis", type=int, default=None,
+                    help="profiling aid: image only the first N visibilities (not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: --warmup must be at least 3")
     import synth
 
-    wl = synth.WORKLOADS[args.workload]
+    wl = synth.WORKLOADS[args.workload] if args.n_vis is None else \
+        synth.scaled(args.workload, n_keep=args.n_vis)
     if args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -186,7 +186,7 @@ def test_adjoint_matches_oracle(P, name):
     v2 = im.adjoint(torch.from_numpy(y2).to(dev), t["weight"]).cpu().numpy()
     r2 = oracle.adjoint(op, d["uvw"], y2.astype(np.float64), wt64, w_min=st["w_min"],
                         w_max=st["w_max"], sum_weight=st["sum_weight"])
-    kappa = 1.0 / taper_2d(op).min()
+    kappa = 1.0 / np.abs(taper_2d(op)).min()  # a truncated Gaussian's C can cross zero
     e2 = np.abs(v2 - r2).max() / np.abs(r2).max()
     print(f"{name}: raw random-image adjoint error {e2:.2e} (taper amplification {kappa:.1e})")
     assert e2 <= 1e-6 * max(kappa, 10.0)
