@@ -71,126 +71,108 @@ struct Ranges {
     }
 };
 
-// Add a W x W footprint at corner (lx, ly) (tile coordinates), clipped to the
-// tile, into the shared accumulator.
-template <int W>
-__device__ __forceinline__ void flush_footprint(float *acc_re, float *acc_im, int T, int log2T,
-                                                int lx, int ly, const float (&ar)[W][W],
-                                                const float (&ai)[W][W])
-{
-#pragma unroll
-    for (int jy = 0; jy < W; ++jy) {
-        int row = ly + jy;
-        if ((unsigned)row >= (unsigned)T) continue;
-        int rbase = row << log2T;
-#pragma unroll
-        for (int jx = 0; jx < W; ++jx) {
-            int col = lx + jx;
-            if ((unsigned)col >= (unsigned)T) continue;
-            atomicAdd(&acc_re[rbase + col], ar[jy][jx]);
-            atomicAdd(&acc_im[rbase + col], ai[jy][jx]);
-        }
-    }
-}
+// ------------------------------------------------------------------------
+// Record streams.  A group of G lanes (a half-warp for W <= 8, a warp above)
+// walks a contiguous run of records.  Per record, lanes [0, W) evaluate the u
+// weights G((j - h) - fx) and lanes [G/2, G/2 + W) the v weights, one segment
+// each (Horner, coefficients held in the lane's registers).  The W x W cells of
+// the footprint are dealt to the G lanes (slot s of lane l is cell l + s G);
+// each lane fetches the two weights of its cells with shuffles and accumulates
+// vis * gx * gy in registers.  While consecutive records share the footprint
+// corner (the channels of one baseline-time land on the same cells) nothing
+// touches shared memory; when the corner changes the group adds its cells to
+// the tile accumulator at once -- distinct cells per lane, so the group's
+// atomics never collide with each other.
 
-// One thread's contiguous run of records [v0, v1).  Records whose footprint
-// corner repeats (the channels of one baseline-time, the same cell) are summed
-// in registers; the footprint is added to shared memory once per change of
-// corner.  This keeps the shared-memory atomics few and spread out: threads
-// walk different runs, so they rarely hit the same cells at the same time.
 template <int W>
-__device__ __forceinline__ void grid_run_direct(const TileArgs &ta, const Ranges &rg, uint32_t v0,
-                                                uint32_t v1, int x0, int y0, float *acc_re,
-                                                float *acc_im, int T, int log2T)
+struct StreamShape {
+    static constexpr int G = W <= 8 ? 16 : 32;                 // lanes per stream
+    static constexpr int SLOTS = (W * W + G - 1) / G;           // cells per lane
+};
+
+template <int W>
+struct LaneCells {
+    int jx[StreamShape<W>::SLOTS], jy[StreamShape<W>::SLOTS];
+    bool live[StreamShape<W>::SLOTS];
+};
+
+template <int W>
+__device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T, int log2T, int lx,
+                                            int ly, const LaneCells<W> &lc, const float *ar,
+                                            const float *ai)
 {
-    for (uint32_t v = v0; v < v1; ++v) {
-        uint32_t r = rg.at(v);
-        float2 val = ta.rval[r], fr = ta.rfrac[r];
-        uint32_t cell = ta.rcell[r];
-        int lx = (int)(cell & 0xFFFFu) - x0, ly = (int)(cell >> 16) - y0;
-        float gx[W];
-        kernel_weights<W>(ta.kp, fr.x, gx);
-        const float sy = 2.0f * (fr.y - ta.kp.fc);
 #pragma unroll
-        for (int jy = 0; jy < W; ++jy) {
-            int row = ly + jy;
-            if ((unsigned)row >= (unsigned)T) continue;
-            const float gyv = kernel_weight_one<W>(ta.kp, jy, sy);
-            float vr = val.x * gyv, vi = val.y * gyv;
-            int rbase = row << log2T;
-#pragma unroll
-            for (int jx = 0; jx < W; ++jx) {
-                int col = lx + jx;
-                if ((unsigned)col >= (unsigned)T) continue;
-                atomicAdd(&acc_re[rbase + col], vr * gx[jx]);
-                atomicAdd(&acc_im[rbase + col], vi * gx[jx]);
-            }
+    for (int sl = 0; sl < StreamShape<W>::SLOTS; ++sl) {
+        int row = ly + lc.jy[sl], col = lx + lc.jx[sl];
+        if (lc.live[sl] && (unsigned)row < (unsigned)T && (unsigned)col < (unsigned)T) {
+            int i = (row << log2T) + col;
+            atomicAdd(&acc_re[i], ar[sl]);
+            atomicAdd(&acc_im[i], ai[sl]);
         }
     }
 }
 
 template <int W>
-__device__ __forceinline__ void grid_run(const TileArgs &ta, const Ranges &rg, uint32_t v0,
-                                         uint32_t v1, int x0, int y0, float *acc_re,
-                                         float *acc_im, int T, int log2T)
+__device__ __forceinline__ void grid_stream(const TileArgs &ta, const Ranges &rg, uint32_t v0,
+                                            uint32_t v1, int x0, int y0, float *acc_re,
+                                            float *acc_im, int T, int log2T, const float *coef,
+                                            const LaneCells<W> &lc)
 {
+    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = G / 2;
+    const int gl = threadIdx.x & (G - 1);  // lane within the group
+    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
     if (v0 >= v1) return;
-    if (W > 9) {  // a W x W register accumulator would not fit
-        grid_run_direct<W>(ta, rg, v0, v1, x0, y0, acc_re, acc_im, T, log2T);
-        return;
-    }
-    float ar[W][W], ai[W][W];
+    float ar[SL], ai[SL];
+#pragma unroll
+    for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
     uint32_t cur = 0xFFFFFFFFu;
     uint32_t r = rg.at(v0);
     float2 val = ta.rval[r], fr = ta.rfrac[r];
     uint32_t cell = ta.rcell[r];
     for (uint32_t v = v0; v < v1; ++v) {
-        // prefetch the next record
         float2 nval = val, nfr = fr;
         uint32_t ncell = cell;
-        if (v + 1 < v1) {
+        if (v + 1 < v1) {  // prefetch the next record
             uint32_t rn = rg.at(v + 1);
             nval = ta.rval[rn];
             nfr = ta.rfrac[rn];
             ncell = ta.rcell[rn];
         }
         if (cell != cur) {
-            if (cur != 0xFFFFFFFFu)
-                flush_footprint<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0,
-                                   (int)(cur >> 16) - y0, ar, ai);
+            if (cur != 0xFFFFFFFFu) {
+                group_flush<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0,
+                               (int)(cur >> 16) - y0, lc, ar, ai);
 #pragma unroll
-            for (int jy = 0; jy < W; ++jy)
-#pragma unroll
-                for (int jx = 0; jx < W; ++jx) ar[jy][jx] = ai[jy][jx] = 0.0f;
+                for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
+            }
             cur = cell;
         }
-        float gx[W];
-        kernel_weights<W>(ta.kp, fr.x, gx);
-        const float sy = 2.0f * (fr.y - ta.kp.fc);
+        // this lane's segment weight: u weights on the first half, v on the second
+        const float f = gl < HALF ? fr.x : fr.y;
+        const float s = 2.0f * (f - ta.kp.fc);
+        float g = coef[RICK_POLY_DEG];
 #pragma unroll
-        for (int jy = 0; jy < W; ++jy) {
-            const float gyv = kernel_weight_one<W>(ta.kp, jy, sy);
-            float vr = val.x * gyv, vi = val.y * gyv;
+        for (int k = RICK_POLY_DEG - 1; k >= 0; --k) g = __fmaf_rn(g, s, coef[k]);
+        if (W == 1) g = 1.0f;
 #pragma unroll
-            for (int jx = 0; jx < W; ++jx) {
-                ar[jy][jx] = __fmaf_rn(vr, gx[jx], ar[jy][jx]);
-                ai[jy][jx] = __fmaf_rn(vi, gx[jx], ai[jy][jx]);
-            }
+        for (int sl = 0; sl < SL; ++sl) {
+            float gx = __shfl_sync(gmask, g, lc.jx[sl], G);
+            float gy = __shfl_sync(gmask, g, HALF + lc.jy[sl], G);
+            float w = gx * gy;
+            ar[sl] = __fmaf_rn(val.x, w, ar[sl]);
+            ai[sl] = __fmaf_rn(val.y, w, ai[sl]);
         }
         val = nval;
         fr = nfr;
         cell = ncell;
     }
-    flush_footprint<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0,
-                       ar, ai);
+    group_flush<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0, lc,
+                   ar, ai);
 }
 
-// Records at least this many per thread, so that a thread's run spans the
-// channels of a baseline-time rather than one record each.
-#define RICK_MIN_RUN 16u
-
 template <int W, bool COMP>
-__device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm)
+__device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm,
+                                          const float *coef, const LaneCells<W> &lc)
 {
     const TileArgs &ta = a.t;
     const uint32_t chunk = b - ta.base[t], nch = ta.base[t + 1] - ta.base[t];
@@ -231,13 +213,17 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     __syncthreads();
 
     // plain: one round over the chunk; compensated: rounds of 4096 records,
-    // each folded into the (sum, compensation) pair of every cell
+    // each folded into the (sum, compensation) pair of every cell.  Each round
+    // is split into one contiguous run per record stream.
+    constexpr int G = StreamShape<W>::G;
+    const uint32_t nstreams = blockDim.x / G, stream = threadIdx.x / G;
     const uint32_t round = COMP ? 4096u : max(vend - vbeg, 1u);
     for (uint32_t rb = vbeg; rb < vend; rb += round) {
         const uint32_t re = min(vend, rb + round);
-        const uint32_t per = max(RICK_MIN_RUN, (re - rb + blockDim.x - 1) / blockDim.x);
-        const uint32_t v0 = rb + threadIdx.x * per;
-        grid_run<W>(ta, rg, min(v0, re), min(v0 + per, re), x0, y0, acc_re, acc_im, T, a.log2T);
+        const uint32_t per = (re - rb + nstreams - 1) / nstreams;
+        const uint32_t v0 = rb + stream * per;
+        grid_stream<W>(ta, rg, min(v0, re), min(v0 + per, re), x0, y0, acc_re, acc_im, T, a.log2T,
+                       coef, lc);
         if (COMP) {
             __syncthreads();
             for (int i = threadIdx.x; i < TT; i += blockDim.x) {
@@ -275,11 +261,27 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
 // Persistent: one wave of CTAs takes work items (tile, chunk) from a counter
 // in the workspace header (reset by zero_tiles_kernel, launched just before).
 template <int W, bool COMP>
-__global__ void __launch_bounds__(256, 1) grid_kernel(GridArgs a)
+__global__ void __launch_bounds__(256) grid_kernel(GridArgs a)
 {
     extern __shared__ float sm[];
     __shared__ uint32_t s_b, s_tile;
     const uint32_t total = a.t.base[a.t.ntiles];
+    // this lane's kernel segment (u weights on the first half of its group, v
+    // weights on the second) and the footprint cells it accumulates
+    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = G / 2;
+    const int gl = threadIdx.x & (G - 1);
+    const int seg = min(gl % HALF, W - 1);
+    float coef[RICK_POLY_N];
+#pragma unroll
+    for (int k = 0; k < RICK_POLY_N; ++k) coef[k] = a.t.kp.c[seg][k];
+    LaneCells<W> lc;
+#pragma unroll
+    for (int sl = 0; sl < SL; ++sl) {
+        int c = gl + sl * G;
+        lc.live[sl] = c < W * W;
+        lc.jx[sl] = lc.live[sl] ? c % W : 0;
+        lc.jy[sl] = lc.live[sl] ? c / W : 0;
+    }
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(256, 1) grid_kernel(GridArgs a)
         __syncthreads();
         const uint32_t b = s_b, t = s_tile;
         if (b >= total) break;
-        grid_item<W, COMP>(a, b, t, sm);
+        grid_item<W, COMP>(a, b, t, sm, coef, lc);
         __syncthreads();  // the accumulator is reused by the next item
     }
 }
