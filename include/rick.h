@@ -141,15 +141,14 @@ rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw_dev, cons
 
 /* Where the binning arrays sit inside a workspace (byte offsets from ws_dev),
  * for callers that read the binned records directly:
- *   offsets  uint32 [n_bins + 1]  bin b holds records [offsets[b], offsets[b+1])
- *   perm     uint32 [n_binned]    record r came from input visibility perm[r]
- *   rec_val  complex64 [n_binned] vis * weight
- *   rec_frac float32 [n_binned][2] x - c_x, y - c_y
- *   rec_cell uint32 [n_binned]    a_x | a_y << 16
- *   stats    rick_bin_stats       the last binning's stats
+ *   offsets  uint32 [n_bins + 1]   bin b holds records [offsets[b], offsets[b+1])
+ *   perm     uint32 [n_binned]     record r came from input visibility perm[r]
+ *   rec      float32 [n_binned][4] (re, im) of vis * weight, x - c_x, y - c_y
+ *   rec_cell uint32 [n_binned]     a_x | a_y << 16
+ *   stats    rick_bin_stats        the last binning's stats
  * n_bins = 4 n_w (n/T)^2.  Host-only; enqueues nothing. */
 typedef struct rick_bin_view {
-    size_t offsets, perm, rec_val, rec_frac, rec_cell, stats;
+    size_t offsets, perm, rec, rec_cell, stats;
     int64_t n_bins;
 } rick_bin_view;
 rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out);
@@ -166,7 +165,7 @@ rick_status rick_bin_values(rick_plan *plan, const void *vis_dev, const float *w
  * planes_dev (complex64 [n_w][n][n]) is overwritten.  Each uv-tile is summed
  * in shared memory and written once (plain stores; tiles with more records
  * than one chunk add their chunk sums with float atomics).  The kernel
- * weights G are degree-12 polynomial fits per unit segment (FP64 fit at plan
+ * weights G are degree-9 polynomial fits per unit segment (FP64 fit at plan
  * creation, FP32 evaluation).  rick_grid and rick_degrid use a word of the
  * workspace header as a work counter: calls that share a workspace must not
  * overlap on the device. */

@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
             float2 v = vis[i];
             float wt = weight ? weight[i] : 1.0f;
             ws.perm[pos] = (uint32_t)i;
-            ws.rval[pos] = make_float2(v.x * wt, v.y * wt);
-            ws.rfrac[pos] = ws.frac[i];
+            float2 fr = ws.frac[i];
+            ws.rec[pos] = make_float4(v.x * wt, v.y * wt, fr.x, fr.y);
             ws.rcell[pos] = ws.cell[i];
         }
     }
@@ -316,7 +316,8 @@ __global__ void bin_values_kernel(const float2 *vis, const float *weight, WsPtrs
         uint32_t i = ws.perm[r];
         float2 v = vis[i];
         float wt = weight ? weight[i] : 1.0f;
-        ws.rval[r] = make_float2(v.x * wt, v.y * wt);
+        float2 *val = (float2 *)&ws.rec[r];  // the value half of the record
+        *val = make_float2(v.x * wt, v.y * wt);
     }
 }
 

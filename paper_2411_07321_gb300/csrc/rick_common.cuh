@@ -23,10 +23,11 @@
 // s = 2 (f - fc) in [-1, 1) (fc = 0 for odd W, where f is in [-1/2, 1/2);
 // fc = 1/2 for even W, f in [0, 1)), fitted at plan creation by Chebyshev
 // interpolation of degree RICK_POLY_DEG in FP64 and evaluated by Horner's rule
-// in FP32.  The coefficients travel in the kernel-argument (constant) space.
+// in FP32 (degree 9 already reaches FP32 rounding, ~1e-7 of the peak, for the
+// Gaussian and Kaiser-Bessel kernels with W = 3..16).  The coefficients travel in the kernel-argument (constant) space.
 
 #define RICK_MAX_W 16
-#define RICK_POLY_DEG 12
+#define RICK_POLY_DEG 9
 #define RICK_POLY_N (RICK_POLY_DEG + 1)
 
 struct KernelPoly {
@@ -98,7 +99,7 @@ struct WsHeader {
 };
 
 struct WsLayout {
-    size_t header, key, cell, frac, perm, rval, rfrac, rcell, hist, offsets, gbase, dbase, scan,
+    size_t header, key, cell, frac, perm, rec, rcell, hist, offsets, gbase, dbase, scan,
         wpart, bkey, wplane, total;
     int64_t n_vis, nbins, ntiles, nscan, nkeyblocks;
 };
@@ -136,8 +137,7 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
     L.cell = o;   o += rick_align256(4 * (size_t)nv);
     L.frac = o;   o += rick_align256(8 * (size_t)nv);
     L.perm = o;   o += rick_align256(4 * (size_t)nv);
-    L.rval = o;   o += rick_align256(8 * (size_t)nv);
-    L.rfrac = o;  o += rick_align256(8 * (size_t)nv);
+    L.rec = o;    o += rick_align256(16 * (size_t)nv);
     L.rcell = o;  o += rick_align256(4 * (size_t)nv);
     L.hist = o;   o += rick_align256(4 * (size_t)(L.nbins + 1));
     L.offsets = o; o += rick_align256(4 * (size_t)(L.nbins + 1));
@@ -155,7 +155,8 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
 struct WsPtrs {
     WsHeader *hdr;
     uint32_t *key, *cell, *perm, *rcell, *hist, *offsets, *gbase, *dbase, *scan;
-    float2 *frac, *rval, *rfrac;
+    float2 *frac;
+    float4 *rec;  // per record: vis*weight (re, im), fractional offsets (fx, fy)
     double *wpart;
     unsigned long long *bkey;
     float4 *wplane;  // per plane: (w_k hi, w_k lo, w_k as float, 0)
@@ -170,8 +171,7 @@ static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
     w.cell = (uint32_t *)(b + L.cell);
     w.frac = (float2 *)(b + L.frac);
     w.perm = (uint32_t *)(b + L.perm);
-    w.rval = (float2 *)(b + L.rval);
-    w.rfrac = (float2 *)(b + L.rfrac);
+    w.rec = (float4 *)(b + L.rec);
     w.rcell = (uint32_t *)(b + L.rcell);
     w.hist = (uint32_t *)(b + L.hist);
     w.offsets = (uint32_t *)(b + L.offsets);
@@ -415,7 +415,7 @@ struct TileArgs {
     int n, n_w, T, nt, W;
     uint32_t ntiles, chunk_cap;
     const uint32_t *offsets, *base, *perm, *rcell;
-    const float2 *rval, *rfrac;
+    const float4 *rec;
     WsHeader *hdr;
     KernelPoly kp;
 };

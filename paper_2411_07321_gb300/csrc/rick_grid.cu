@@ -57,152 +57,138 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float a)
     s = t;
 }
 
-// Record index of position v in the concatenation of the four ranges.
-struct Ranges {
-    uint32_t s0, L0, s1, L1, s2, L2, s3;
-    __device__ __forceinline__ uint32_t at(uint32_t v) const
-    {
-        if (v < L0) return s0 + v;
-        v -= L0;
-        if (v < L1) return s1 + v;
-        v -= L1;
-        if (v < L2) return s2 + v;
-        return s3 + (v - L2);
-    }
-};
-
 // ------------------------------------------------------------------------
 // Record streams.  A group of G lanes (a half-warp for W <= 8, a warp above)
 // walks a contiguous run of records.  Per record, lanes [0, W) evaluate the u
 // weights G((j - h) - fx) and lanes [G/2, G/2 + W) the v weights, one segment
-// each (Horner, coefficients held in the lane's registers).  The W x W cells of
-// the footprint are dealt to the G lanes (slot s of lane l is cell l + s G);
-// each lane fetches the two weights of its cells with shuffles and accumulates
-// vis * gx * gy in registers.  While consecutive records share the footprint
-// corner (the channels of one baseline-time land on the same cells) nothing
-// touches shared memory; when the corner changes the group adds its cells to
-// the tile accumulator at once -- distinct cells per lane, so the group's
-// atomics never collide with each other.
+// each (Horner, coefficients held in the lane's registers).  The footprint is
+// dealt out by rows: lanes 2 jy and 2 jy + 1 own the first and second half of
+// row jy, so a lane fetches its row's v weight once, scales the visibility by
+// it, and then needs one shuffle (the u weight) and two FMAs per cell.  While
+// consecutive records share the footprint corner (the channels of one
+// baseline-time land on the same cells) the sums stay in registers; when the
+// corner changes the group adds its cells to the tile accumulator at once --
+// distinct cells per lane, so the group's atomics never collide.
 
 template <int W>
 struct StreamShape {
-    static constexpr int G = W <= 8 ? 16 : 32;                 // lanes per stream
-    static constexpr int SLOTS = (W * W + G - 1) / G;           // cells per lane
+    static constexpr int G = W <= 8 ? 16 : 32;  // lanes per stream
+    static constexpr int HALF = G / 2;           // v weights live on lanes [HALF, HALF + W)
+    static constexpr int SLOTS = (W + 1) / 2;    // cells per lane (half a row)
 };
 
-template <int W>
 struct LaneCells {
-    int jx[StreamShape<W>::SLOTS], jy[StreamShape<W>::SLOTS];
-    bool live[StreamShape<W>::SLOTS];
+    int jy, jx0, ncol;  // row, first column, columns owned (0: idle lane)
 };
 
 template <int W>
-__device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T, int log2T, int lx,
-                                            int ly, const LaneCells<W> &lc, const float *ar,
+__device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T, int TP, int lx,
+                                            int ly, const LaneCells &lc, const float *ar,
                                             const float *ai)
 {
+    const int row = ly + lc.jy;
+    if ((unsigned)row >= (unsigned)T) return;
 #pragma unroll
     for (int sl = 0; sl < StreamShape<W>::SLOTS; ++sl) {
-        int row = ly + lc.jy[sl], col = lx + lc.jx[sl];
-        if (lc.live[sl] && (unsigned)row < (unsigned)T && (unsigned)col < (unsigned)T) {
-            int i = (row << log2T) + col;
+        int col = lx + lc.jx0 + sl;
+        if (sl < lc.ncol && (unsigned)col < (unsigned)T) {
+            int i = row * TP + col;
             atomicAdd(&acc_re[i], ar[sl]);
             atomicAdd(&acc_im[i], ai[sl]);
         }
     }
 }
 
+// Records [v0, v1) of one segment of the tile's record list, start index r0.
 template <int W>
-__device__ __forceinline__ void grid_stream(const TileArgs &ta, const Ranges &rg, uint32_t v0,
-                                            uint32_t v1, int x0, int y0, float *acc_re,
-                                            float *acc_im, int T, int log2T, const float *coef,
-                                            const LaneCells<W> &lc)
+__device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n, int x0,
+                                            int y0, float *acc_re, float *acc_im, int T, int TP,
+                                            const float *coef, const LaneCells &lc)
 {
-    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = G / 2;
-    const int gl = threadIdx.x & (G - 1);  // lane within the group
+    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = StreamShape<W>::HALF;
+    const int gl = threadIdx.x & (G - 1);
     const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
-    if (v0 >= v1) return;
+    if (n == 0) return;
     float ar[SL], ai[SL];
 #pragma unroll
     for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
-    uint32_t cur = 0xFFFFFFFFu;
-    uint32_t r = rg.at(v0);
-    float2 val = ta.rval[r], fr = ta.rfrac[r];
-    uint32_t cell = ta.rcell[r];
-    for (uint32_t v = v0; v < v1; ++v) {
-        float2 nval = val, nfr = fr;
+    const float4 *rec = ta.rec + r0;
+    const uint32_t *rcell = ta.rcell + r0;
+    uint32_t cur = rcell[0];
+    float4 q = rec[0];
+    uint32_t cell = cur;
+    for (uint32_t i = 0; i < n; ++i) {
+        float4 nq = q;
         uint32_t ncell = cell;
-        if (v + 1 < v1) {  // prefetch the next record
-            uint32_t rn = rg.at(v + 1);
-            nval = ta.rval[rn];
-            nfr = ta.rfrac[rn];
-            ncell = ta.rcell[rn];
+        if (i + 1 < n) {  // prefetch the next record
+            nq = rec[i + 1];
+            ncell = rcell[i + 1];
         }
         if (cell != cur) {
-            if (cur != 0xFFFFFFFFu) {
-                group_flush<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0,
-                               (int)(cur >> 16) - y0, lc, ar, ai);
+            group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0,
+                           lc, ar, ai);
 #pragma unroll
-                for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
-            }
+            for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
             cur = cell;
         }
         // this lane's segment weight: u weights on the first half, v on the second
-        const float f = gl < HALF ? fr.x : fr.y;
-        const float s = 2.0f * (f - ta.kp.fc);
-        float g = coef[RICK_POLY_DEG];
+        float g = 1.0f;
+        if (W > 1) {
+            const float s = 2.0f * ((gl < HALF ? q.z : q.w) - ta.kp.fc);
+            g = coef[RICK_POLY_DEG];
 #pragma unroll
-        for (int k = RICK_POLY_DEG - 1; k >= 0; --k) g = __fmaf_rn(g, s, coef[k]);
-        if (W == 1) g = 1.0f;
+            for (int k = RICK_POLY_DEG - 1; k >= 0; --k) g = __fmaf_rn(g, s, coef[k]);
+        }
+        const float gy = __shfl_sync(gmask, g, HALF + lc.jy, G);
+        const float vr = q.x * gy, vi = q.y * gy;
 #pragma unroll
         for (int sl = 0; sl < SL; ++sl) {
-            float gx = __shfl_sync(gmask, g, lc.jx[sl], G);
-            float gy = __shfl_sync(gmask, g, HALF + lc.jy[sl], G);
-            float w = gx * gy;
-            ar[sl] = __fmaf_rn(val.x, w, ar[sl]);
-            ai[sl] = __fmaf_rn(val.y, w, ai[sl]);
+            const float gx = __shfl_sync(gmask, g, lc.jx0 + sl, G);
+            ar[sl] = __fmaf_rn(vr, gx, ar[sl]);
+            ai[sl] = __fmaf_rn(vi, gx, ai[sl]);
         }
-        val = nval;
-        fr = nfr;
+        q = nq;
         cell = ncell;
     }
-    group_flush<W>(acc_re, acc_im, T, log2T, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0, lc,
-                   ar, ai);
+    group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0, lc, ar,
+                   ai);
 }
 
 template <int W, bool COMP>
 __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm,
-                                          const float *coef, const LaneCells<W> &lc)
+                                          const float *coef, const LaneCells &lc)
 {
     const TileArgs &ta = a.t;
     const uint32_t chunk = b - ta.base[t], nch = ta.base[t + 1] - ta.base[t];
-    const int T = 1 << a.log2T, TT = T * T, nt = ta.nt;
+    const int T = 1 << a.log2T, TP = T + 1, TT = T * TP, nt = ta.nt;
     const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
     const int x0 = tx << a.log2T, y0 = ty << a.log2T;
     const uint32_t *off = ta.offsets;
 
-    // the four record ranges that can touch this tile
-    Ranges rg;
-    rg.s0 = off[4 * t];
-    rg.L0 = off[4 * t + 4] - rg.s0;
-    rg.s1 = rg.L1 = rg.s2 = rg.L2 = rg.s3 = 0;
-    uint32_t L3 = 0;
+    // the four record ranges that can touch this tile: its own bin, and the
+    // edge classes of the west, north and north-west bins that reach into it
+    uint32_t rs[4], rl[4];
+    rs[0] = off[4 * t];
+    rl[0] = off[4 * t + 4] - rs[0];
+    rs[1] = rl[1] = rs[2] = rl[2] = rs[3] = rl[3] = 0;
     if (tx > 0) {
-        rg.s1 = off[4 * (t - 1) + 1];
-        rg.L1 = off[4 * (t - 1) + 3] - rg.s1;
+        rs[1] = off[4 * (t - 1) + 1];
+        rl[1] = off[4 * (t - 1) + 3] - rs[1];
     }
     if (ty > 0) {
-        rg.s2 = off[4 * (t - nt) + 2];
-        rg.L2 = off[4 * (t - nt) + 4] - rg.s2;
+        rs[2] = off[4 * (t - nt) + 2];
+        rl[2] = off[4 * (t - nt) + 4] - rs[2];
     }
     if (tx > 0 && ty > 0) {
-        rg.s3 = off[4 * (t - nt - 1) + 2];
-        L3 = off[4 * (t - nt - 1) + 3] - rg.s3;
+        rs[3] = off[4 * (t - nt - 1) + 2];
+        rl[3] = off[4 * (t - nt - 1) + 3] - rs[3];
     }
-    const uint32_t Ltot = rg.L0 + rg.L1 + rg.L2 + L3;
+    const uint32_t Ltot = rl[0] + rl[1] + rl[2] + rl[3];
     const uint32_t vbeg = chunk * ta.chunk_cap;
     const uint32_t vend = min(Ltot, vbeg + ta.chunk_cap);
 
+    // accumulators with padded rows (stride T + 1): the lanes of a group own
+    // different rows, which then fall in different banks
     float *acc_re = sm, *acc_im = sm + TT;
     float *sum_re = sm + 2 * TT, *sum_im = sm + 3 * TT, *cmp_re = sm + 4 * TT, *cmp_im = sm + 5 * TT;
     for (int i = threadIdx.x; i < TT; i += blockDim.x) {
@@ -214,16 +200,24 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
 
     // plain: one round over the chunk; compensated: rounds of 4096 records,
     // each folded into the (sum, compensation) pair of every cell.  Each round
-    // is split into one contiguous run per record stream.
+    // is split into one contiguous run per record stream, and each run into
+    // its pieces of the four ranges.
     constexpr int G = StreamShape<W>::G;
     const uint32_t nstreams = blockDim.x / G, stream = threadIdx.x / G;
     const uint32_t round = COMP ? 4096u : max(vend - vbeg, 1u);
     for (uint32_t rb = vbeg; rb < vend; rb += round) {
         const uint32_t re = min(vend, rb + round);
         const uint32_t per = (re - rb + nstreams - 1) / nstreams;
-        const uint32_t v0 = rb + stream * per;
-        grid_stream<W>(ta, rg, min(v0, re), min(v0 + per, re), x0, y0, acc_re, acc_im, T, a.log2T,
-                       coef, lc);
+        uint32_t v0 = min(rb + stream * per, re), v1 = min(v0 + per, re);
+        uint32_t base = 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t a0 = max(v0, base), a1 = min(v1, base + rl[g]);
+            if (a0 < a1)
+                grid_stream<W>(ta, rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
+                               coef, lc);
+            base += rl[g];
+        }
         if (COMP) {
             __syncthreads();
             for (int i = threadIdx.x; i < TT; i += blockDim.x) {
@@ -240,11 +234,11 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     // flush: (-1)^(i+j) folded in; plain stores unless the tile has several chunks
     const int n = ta.n;
     float2 *plane = a.planes + (size_t)k * n * n;
-    for (int i = threadIdx.x; i < TT; i += blockDim.x) {
-        int row = i >> a.log2T, col = i & (T - 1);
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        int row = i >> a.log2T, col = i & (T - 1), ip = row * TP + col;
         int gi = x0 + col, gj = y0 + row;
-        float re = COMP ? sum_re[i] + cmp_re[i] : acc_re[i];
-        float im = COMP ? sum_im[i] + cmp_im[i] : acc_im[i];
+        float re = COMP ? sum_re[ip] + cmp_re[ip] : acc_re[ip];
+        float im = COMP ? sum_im[ip] + cmp_im[ip] : acc_im[ip];
         if ((gi + gj) & 1) {
             re = -re;
             im = -im;
@@ -261,27 +255,24 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
 // Persistent: one wave of CTAs takes work items (tile, chunk) from a counter
 // in the workspace header (reset by zero_tiles_kernel, launched just before).
 template <int W, bool COMP>
-__global__ void __launch_bounds__(256) grid_kernel(GridArgs a)
+__global__ void __launch_bounds__(256, 3) grid_kernel(GridArgs a)
 {
     extern __shared__ float sm[];
     __shared__ uint32_t s_b, s_tile;
     const uint32_t total = a.t.base[a.t.ntiles];
     // this lane's kernel segment (u weights on the first half of its group, v
     // weights on the second) and the footprint cells it accumulates
-    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = G / 2;
+    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = StreamShape<W>::HALF;
     const int gl = threadIdx.x & (G - 1);
     const int seg = min(gl % HALF, W - 1);
     float coef[RICK_POLY_N];
 #pragma unroll
     for (int k = 0; k < RICK_POLY_N; ++k) coef[k] = a.t.kp.c[seg][k];
-    LaneCells<W> lc;
-#pragma unroll
-    for (int sl = 0; sl < SL; ++sl) {
-        int c = gl + sl * G;
-        lc.live[sl] = c < W * W;
-        lc.jx[sl] = lc.live[sl] ? c % W : 0;
-        lc.jy[sl] = lc.live[sl] ? c / W : 0;
-    }
+    // lanes 2 jy and 2 jy + 1 own the two halves of footprint row jy
+    LaneCells lc;
+    lc.jy = min(gl >> 1, W - 1);
+    lc.jx0 = (gl & 1) * SL;
+    lc.ncol = (gl >> 1) < W ? min(SL, W - lc.jx0) : 0;
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
@@ -348,7 +339,8 @@ __device__ __forceinline__ void degrid_item(const DegridArgs &a, uint32_t b, uin
     }
     __syncthreads();
     for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        float2 fr = ta.rfrac[r];
+        const float4 q = ta.rec[r];
+        const float2 fr = make_float2(q.z, q.w);
         uint32_t cell = ta.rcell[r];
         int lx = (int)(cell & 0xFFFFu) - x0, ly = (int)(cell >> 16) - y0;
         float gx[W], gy[W];
@@ -422,8 +414,7 @@ static TileArgs make_tile_args(const rick_plan *plan, const WsPtrs &w, const uin
     t.base = base;
     t.perm = w.perm;
     t.rcell = w.rcell;
-    t.rval = w.rval;
-    t.rfrac = w.rfrac;
+    t.rec = w.rec;
     t.hdr = w.hdr;
     t.kp = plan->poly;
     return t;
@@ -450,7 +441,7 @@ static unsigned persistent_blocks(K kernel, size_t smem, int num_sms)
 template <int W, bool COMP>
 static cudaError_t launch_grid_t(const GridArgs &a, int num_sms, cudaStream_t st)
 {
-    size_t smem = (COMP ? 6 : 2) * (size_t)a.t.T * a.t.T * sizeof(float);
+    size_t smem = (COMP ? 6 : 2) * (size_t)a.t.T * (a.t.T + 1) * sizeof(float);
     cudaFuncSetAttribute(grid_kernel<W, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     grid_kernel<W, COMP><<<persistent_blocks(grid_kernel<W, COMP>, smem, num_sms), 256, smem, st>>>(a);

@@ -288,8 +288,7 @@ extern "C" rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out
     WsLayout L = rick_ws_layout(&plan->p, plan->max_vis);
     out->offsets = L.offsets;
     out->perm = L.perm;
-    out->rec_val = L.rval;
-    out->rec_frac = L.rfrac;
+    out->rec = L.rec;
     out->rec_cell = L.rcell;
     out->stats = L.header + offsetof(WsHeader, stats);
     out->n_bins = L.nbins;

@@ -179,10 +179,11 @@ class Imager:
         def take(off, nbytes):
             return raw[off:off + nbytes].cpu().numpy()
 
+        rec = take(v.rec, 16 * nb).view(np.float32).reshape(-1, 4)
         return dict(offsets=take(v.offsets, 4 * (v.n_bins + 1)).view(np.uint32),
                     perm=take(v.perm, 4 * nb).view(np.uint32),
-                    rec_val=take(v.rec_val, 8 * nb).view(np.complex64),
-                    rec_frac=take(v.rec_frac, 8 * nb).view(np.float32).reshape(-1, 2),
+                    rec_val=np.ascontiguousarray(rec[:, :2]).view(np.complex64).reshape(-1),
+                    rec_frac=np.ascontiguousarray(rec[:, 2:]),
                     rec_cell=take(v.rec_cell, 4 * nb).view(np.uint32), stats=st)
 
     def close(self):

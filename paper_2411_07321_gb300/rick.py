@@ -45,9 +45,8 @@ class rick_bin_stats(ctypes.Structure):
 
 class rick_bin_view(ctypes.Structure):
     _fields_ = [("offsets", ctypes.c_size_t), ("perm", ctypes.c_size_t),
-                ("rec_val", ctypes.c_size_t), ("rec_frac", ctypes.c_size_t),
-                ("rec_cell", ctypes.c_size_t), ("stats", ctypes.c_size_t),
-                ("n_bins", ctypes.c_int64)]
+                ("rec", ctypes.c_size_t), ("rec_cell", ctypes.c_size_t),
+                ("stats", ctypes.c_size_t), ("n_bins", ctypes.c_int64)]
 
 
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
