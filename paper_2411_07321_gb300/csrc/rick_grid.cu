@@ -58,60 +58,54 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float a)
 }
 
 // ------------------------------------------------------------------------
-// Record streams.  A group of G lanes (a half-warp for W <= 8, a warp above)
-// walks a contiguous run of records.  Per record, lanes [0, W) evaluate the u
-// weights G((j - h) - fx) and lanes [G/2, G/2 + W) the v weights, one segment
-// each (Horner, coefficients held in the lane's registers).  The footprint is
-// dealt out by rows: lanes 2 jy and 2 jy + 1 own the first and second half of
-// row jy, so a lane fetches its row's v weight once, scales the visibility by
-// it, and then needs one shuffle (the u weight) and two FMAs per cell.  While
-// consecutive records share the footprint corner (the channels of one
-// baseline-time land on the same cells) the sums stay in registers; when the
-// corner changes the group adds its cells to the tile accumulator at once --
-// distinct cells per lane, so the group's atomics never collide.
+// Record streams.  A group of G = next_pow2(W) lanes walks a contiguous run of
+// records; lane j of the group owns footprint row j (W cells).  Per record,
+// lane j evaluates kernel segment j at both offsets -- gx[j] = G((j - h) - fx)
+// and gy[j] = G((j - h) - fy), Horner with the segment's coefficients held in
+// the lane's registers -- so it already has its row's v weight, scales the
+// visibility by it, and takes the W u weights from its group with shuffles:
+// W shuffles and 2W FMAs per record and lane.  While consecutive records share
+// the footprint corner (the channels of one baseline-time land on the same
+// cells) the row sums stay in registers; when the corner changes the group
+// adds its rows to the tile accumulator at once -- one row per lane, so the
+// group's atomics never collide.
 
 template <int W>
 struct StreamShape {
-    static constexpr int G = W <= 8 ? 16 : 32;  // lanes per stream
-    static constexpr int HALF = G / 2;           // v weights live on lanes [HALF, HALF + W)
-    static constexpr int SLOTS = (W + 1) / 2;    // cells per lane (half a row)
-};
-
-struct LaneCells {
-    int jy, jx0, ncol;  // row, first column, columns owned (0: idle lane)
+    static constexpr int G = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : 16;
 };
 
 template <int W>
 __device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T, int TP, int lx,
-                                            int ly, const LaneCells &lc, const float *ar,
-                                            const float *ai)
+                                            int row, bool live, const float *ar, const float *ai)
 {
-    const int row = ly + lc.jy;
-    if ((unsigned)row >= (unsigned)T) return;
+    if (!live || (unsigned)row >= (unsigned)T) return;
 #pragma unroll
-    for (int sl = 0; sl < StreamShape<W>::SLOTS; ++sl) {
-        int col = lx + lc.jx0 + sl;
-        if (sl < lc.ncol && (unsigned)col < (unsigned)T) {
+    for (int jx = 0; jx < W; ++jx) {
+        int col = lx + jx;
+        if ((unsigned)col < (unsigned)T) {
             int i = row * TP + col;
-            atomicAdd(&acc_re[i], ar[sl]);
-            atomicAdd(&acc_im[i], ai[sl]);
+            atomicAdd(&acc_re[i], ar[jx]);
+            atomicAdd(&acc_im[i], ai[jx]);
         }
     }
 }
 
-// Records [v0, v1) of one segment of the tile's record list, start index r0.
+// n records of one segment of the tile's record list, starting at record r0.
 template <int W>
 __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n, int x0,
                                             int y0, float *acc_re, float *acc_im, int T, int TP,
-                                            const float *coef, const LaneCells &lc)
+                                            const float *coef)
 {
-    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = StreamShape<W>::HALF;
-    const int gl = threadIdx.x & (G - 1);
-    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    constexpr int G = StreamShape<W>::G;
+    const int j = threadIdx.x & (G - 1);  // this lane's row / kernel segment
+    const bool live = j < W;
+    const unsigned gmask = G == 32 ? 0xffffffffu
+                                   : (((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1)));
     if (n == 0) return;
-    float ar[SL], ai[SL];
+    float ar[W], ai[W];
 #pragma unroll
-    for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
+    for (int jx = 0; jx < W; ++jx) ar[jx] = ai[jx] = 0.0f;
     const float4 *rec = ta.rec + r0;
     const uint32_t *rcell = ta.rcell + r0;
     uint32_t cur = rcell[0];
@@ -125,38 +119,40 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
             ncell = rcell[i + 1];
         }
         if (cell != cur) {
-            group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0,
-                           lc, ar, ai);
+            group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
+                           (int)(cur >> 16) - y0 + j, live, ar, ai);
 #pragma unroll
-            for (int sl = 0; sl < SL; ++sl) ar[sl] = ai[sl] = 0.0f;
+            for (int jx = 0; jx < W; ++jx) ar[jx] = ai[jx] = 0.0f;
             cur = cell;
         }
-        // this lane's segment weight: u weights on the first half, v on the second
-        float g = 1.0f;
+        float gx = 1.0f, gy = 1.0f;
         if (W > 1) {
-            const float s = 2.0f * ((gl < HALF ? q.z : q.w) - ta.kp.fc);
-            g = coef[RICK_POLY_DEG];
+            const float sx = 2.0f * (q.z - ta.kp.fc), sy = 2.0f * (q.w - ta.kp.fc);
+            gx = coef[RICK_POLY_DEG];
+            gy = coef[RICK_POLY_DEG];
 #pragma unroll
-            for (int k = RICK_POLY_DEG - 1; k >= 0; --k) g = __fmaf_rn(g, s, coef[k]);
+            for (int k = RICK_POLY_DEG - 1; k >= 0; --k) {
+                gx = __fmaf_rn(gx, sx, coef[k]);
+                gy = __fmaf_rn(gy, sy, coef[k]);
+            }
         }
-        const float gy = __shfl_sync(gmask, g, HALF + lc.jy, G);
         const float vr = q.x * gy, vi = q.y * gy;
 #pragma unroll
-        for (int sl = 0; sl < SL; ++sl) {
-            const float gx = __shfl_sync(gmask, g, lc.jx0 + sl, G);
-            ar[sl] = __fmaf_rn(vr, gx, ar[sl]);
-            ai[sl] = __fmaf_rn(vi, gx, ai[sl]);
+        for (int jx = 0; jx < W; ++jx) {
+            const float w = G == 1 ? gx : __shfl_sync(gmask, gx, jx, G);
+            ar[jx] = __fmaf_rn(vr, w, ar[jx]);
+            ai[jx] = __fmaf_rn(vi, w, ai[jx]);
         }
         q = nq;
         cell = ncell;
     }
-    group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0, lc, ar,
-                   ai);
+    group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0 + j,
+                   live, ar, ai);
 }
 
 template <int W, bool COMP>
 __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm,
-                                          const float *coef, const LaneCells &lc)
+                                          const float *coef)
 {
     const TileArgs &ta = a.t;
     const uint32_t chunk = b - ta.base[t], nch = ta.base[t + 1] - ta.base[t];
@@ -215,7 +211,7 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
             uint32_t a0 = max(v0, base), a1 = min(v1, base + rl[g]);
             if (a0 < a1)
                 grid_stream<W>(ta, rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
-                               coef, lc);
+                               coef);
             base += rl[g];
         }
         if (COMP) {
@@ -262,17 +258,12 @@ __global__ void __launch_bounds__(256, 3) grid_kernel(GridArgs a)
     const uint32_t total = a.t.base[a.t.ntiles];
     // this lane's kernel segment (u weights on the first half of its group, v
     // weights on the second) and the footprint cells it accumulates
-    constexpr int G = StreamShape<W>::G, SL = StreamShape<W>::SLOTS, HALF = StreamShape<W>::HALF;
-    const int gl = threadIdx.x & (G - 1);
-    const int seg = min(gl % HALF, W - 1);
+    // this lane's kernel segment (= its footprint row within its group)
+    constexpr int G = StreamShape<W>::G;
+    const int seg = min((int)(threadIdx.x & (G - 1)), W - 1);
     float coef[RICK_POLY_N];
 #pragma unroll
     for (int k = 0; k < RICK_POLY_N; ++k) coef[k] = a.t.kp.c[seg][k];
-    // lanes 2 jy and 2 jy + 1 own the two halves of footprint row jy
-    LaneCells lc;
-    lc.jy = min(gl >> 1, W - 1);
-    lc.jx0 = (gl & 1) * SL;
-    lc.ncol = (gl >> 1) < W ? min(SL, W - lc.jx0) : 0;
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
@@ -282,7 +273,7 @@ __global__ void __launch_bounds__(256, 3) grid_kernel(GridArgs a)
         __syncthreads();
         const uint32_t b = s_b, t = s_tile;
         if (b >= total) break;
-        grid_item<W, COMP>(a, b, t, sm, coef, lc);
+        grid_item<W, COMP>(a, b, t, sm, coef);
         __syncthreads();  // the accumulator is reused by the next item
     }
 }
