@@ -153,6 +153,28 @@ typedef struct rick_bin_view {
 } rick_bin_view;
 rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out);
 
+/* rick_bin for callers that cannot allocate device memory.  Some callers run
+ * where allocation is not an option: a host program may hand a plug-in only
+ * the buffers it owns, a real-time loop may forbid allocator calls (they can
+ * block and synchronise the device), or memory may be carved up in advance
+ * from a fixed budget.  This entry point computes exactly what rick_bin
+ * computes -- into the same workspace layout, which the later calls read --
+ * but keeps its temporaries (per-visibility keys, cells and offsets, the
+ * histogram, scan temporaries, weight-sum partials) in a fixed array compiled
+ * into the library (about 5 MB, held on every GPU that loads the library until
+ * the process exits) instead of in ws_dev's scratch regions.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart; this is an interface convenience.
+ *   Limits: n_vis <= 262144 and 4 n_w (n/T)^2 <= 262144 bins, else
+ *   RICK_ERANGE.  Arguments as for rick_bin.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  Every call shares the one array: calls that overlap on the GPU
+ *   (other streams, other threads, other plans) race and must be serialised. */
+rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const double *uvw_dev,
+                             const void *vis_dev, const float *weight_dev, void *ws_dev,
+                             size_t ws_bytes, rick_bin_stats *stats_dev, void *stream);
+
 /* Replace the record values of an existing binning by vis * weight for new
  * visibilities at the same uvw (weight NULL: unit), and recompute the weight
  * sum.  Used to grid gradients through the same geometry. */

@@ -17,6 +17,8 @@
 //   6. work lists of the tile kernels (chunks of at most chunk_cap records).
 #include <math.h>
 
+#include <mutex>
+
 #include "rick_common.cuh"
 
 #define FULL 0xffffffffu
@@ -457,6 +459,138 @@ extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const f
     RICK_LAUNCH_CHECK(plan);
     values_wsum_kernel<<<1, 1024, 0, st>>>(weight, w);
     RICK_LAUNCH_CHECK(plan);
+    if (stats_dev)
+        RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
+                                            cudaMemcpyDeviceToDevice, st));
+    return RICK_OK;
+}
+
+// ------------------------------------------------------------------------
+// rick_bin_noalloc: the binning above for callers that must not allocate
+// device memory.  Its temporaries -- per-visibility keys, cells and
+// fractional offsets, the histogram / cursor array, the scan temporaries and
+// the weight-sum partials -- live in this file-scope array instead of the
+// caller's workspace.  The array is part of the library image: every GPU that
+// loads librick.so holds it (about 5 MB) until the process exits.
+
+#define NOALLOC_MAX_VIS (1 << 18)
+#define NOALLOC_MAX_BINS (1 << 18)
+#define NOALLOC_KEY (0)
+#define NOALLOC_CELL (NOALLOC_KEY + 4 * NOALLOC_MAX_VIS)
+#define NOALLOC_FRAC (NOALLOC_CELL + 4 * NOALLOC_MAX_VIS)
+#define NOALLOC_HIST (NOALLOC_FRAC + 8 * NOALLOC_MAX_VIS)
+#define NOALLOC_SCAN (NOALLOC_HIST + 4 * (NOALLOC_MAX_BINS + 256))
+#define NOALLOC_WPART (NOALLOC_SCAN + 4 * 4096)
+#define NOALLOC_BYTES (NOALLOC_WPART + 8 * (NOALLOC_MAX_VIS / (RICK_KEY_THREADS * RICK_KEY_ITEMS) + 256))
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// The array's device address, looked up once per device with that device
+// current (a host-side name of a __device__ array is not a device address).
+#define NOALLOC_MAX_DEVICES 64
+static void *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+static rick_status noalloc_scratch(unsigned char **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return RICK_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = NULL;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return RICK_ECUDA;
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = (unsigned char *)g_noalloc_addr[dev];
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const double *uvw,
+                                        const void *vis, const float *weight, void *ws_dev,
+                                        size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
+{
+    if (!plan || !ws_dev || n_vis < 0) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (n_vis > 0 && (!uvw || !vis)) return RICK_EINVAL;
+    if (((uintptr_t)ws_dev & 255) || ((uintptr_t)uvw & 7) || ((uintptr_t)vis & 7) ||
+        ((uintptr_t)weight & 3) || ((uintptr_t)stats_dev & 7))
+        return RICK_EINVAL;
+    if (n_vis > plan->max_vis) return RICK_ERANGE;
+    const rick_params &p = plan->p;
+    WsLayout L = rick_ws_layout(&p, plan->max_vis);
+    if (ws_bytes < L.total) return RICK_ERANGE;
+    // the fixed scratch bounds the problem size
+    if (n_vis > NOALLOC_MAX_VIS || L.nbins > NOALLOC_MAX_BINS) return RICK_ERANGE;
+    unsigned char *scratch = NULL;
+    rick_status sst = noalloc_scratch(&scratch);
+    if (sst != RICK_OK) {
+        plan->sticky = sst;
+        return sst;
+    }
+    const int64_t nkb = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) /
+                        (RICK_KEY_THREADS * RICK_KEY_ITEMS);
+    // outputs in the caller's workspace, temporaries in the fixed array
+    WsPtrs w = rick_ws_ptrs(ws_dev, L);
+    w.key = (uint32_t *)(scratch + NOALLOC_KEY);
+    w.cell = (uint32_t *)(scratch + NOALLOC_CELL);
+    w.frac = (float2 *)(scratch + NOALLOC_FRAC);
+    w.hist = (uint32_t *)(scratch + NOALLOC_HIST);
+    w.scan = (uint32_t *)(scratch + NOALLOC_SCAN);
+    w.wpart = (double *)(scratch + NOALLOC_WPART);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
+    int given = !isnan(p.w_min);
+
+    // the same stages as rick_bin, in the same order
+    bin_init_kernel<<<1, 1, 0, st>>>(w.hdr, (uint64_t)n_vis, cap, given,
+                                     given ? rick_dkey(p.w_min) : 0, given ? rick_dkey(p.w_max) : 0,
+                                     (uint32_t)nkb);
+    RICK_LAUNCH_CHECK(plan);
+    if (!given && n_vis > 0) {
+        wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
+    RICK_LAUNCH_CHECK(plan);
+    // the array keeps the last call's contents: the histogram must start at zero
+    RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+    if (n_vis > 0) {
+        KeyArgs ka;
+        ka.n_vis = n_vis;
+        ka.uvw = uvw;
+        ka.weight = weight;
+        ka.n = p.n;
+        ka.n_w = p.n_w;
+        ka.W = p.support;
+        ka.log2T = 0;
+        while ((1 << ka.log2T) < p.tile) ++ka.log2T;
+        ka.nt = p.n / p.tile;
+        ka.fov = p.fov;
+        ka.half_n = 0.5 * p.n;
+        ka.key_lo = rick_dkey(-0.5);
+        ka.key_hi = rick_dkey((double)p.n + 0.5);
+        ka.ws = w;
+        size_t smem = 8 * (size_t)(p.n_w > 1 ? p.n_w - 1 : 1);
+        bin_key_kernel<<<(unsigned)nkb, RICK_KEY_THREADS, smem, st>>>(ka);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL);
+    RICK_LAUNCH_CHECK(plan);
+    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.offsets, L.nbins + 1, w.scan, st, &plan->launches));
+    if (n_vis > 0) {
+        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+        int64_t blocks = (n_vis + 255) / 256;
+        if (blocks > (int64_t)plan->num_sms * 32) blocks = (int64_t)plan->num_sms * 32;
+        bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    uint32_t nt = (uint32_t)L.ntiles;
+    tile_count_kernel<<<(nt + 256) / 256, 256, 0, st>>>(w.offsets, w.gbase, w.dbase, nt,
+                                                        p.n / p.tile, cap);
+    RICK_LAUNCH_CHECK(plan);
+    RICK_CUDA_TRY(plan, scan_u32(w.gbase, w.gbase, L.ntiles + 1, w.scan, st, &plan->launches));
+    RICK_CUDA_TRY(plan, scan_u32(w.dbase, w.dbase, L.ntiles + 1, w.scan, st, &plan->launches));
     if (stats_dev)
         RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
                                             cudaMemcpyDeviceToDevice, st));

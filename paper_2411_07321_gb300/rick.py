@@ -52,7 +52,7 @@ class rick_bin_view(ctypes.Structure):
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
            "rick_plan_launch_count",
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
-           "rick_bin_values",
+           "rick_bin_noalloc", "rick_bin_values",
            "rick_grid", "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid"]
 
 
@@ -75,6 +75,7 @@ def _load():
         "rick_plan_fft_bytes": [vp, ctypes.POINTER(sz)],
         "rick_bin_layout": [vp, ctypes.POINTER(rick_bin_view)],
         "rick_bin": [vp, i64, vp, vp, vp, vp, sz, vp, vp],
+        "rick_bin_noalloc": [vp, i64, vp, vp, vp, vp, sz, vp, vp],
         "rick_bin_values": [vp, vp, vp, vp, vp, vp],
         "rick_grid": [vp, vp, vp, vp],
         "rick_fft_wplanes": [vp, vp, i32, vp],
@@ -151,6 +152,13 @@ def rick_bin_layout(plan: int) -> rick_bin_view:
 def rick_bin(plan, n_vis, uvw, vis, weight, ws, ws_bytes, stats, stream) -> None:
     _check("rick_bin", _L.rick_bin(plan, int(n_vis), uvw, vis, weight or None, ws, int(ws_bytes),
                                    stats or None, stream or None))
+
+
+def rick_bin_noalloc(plan, n_vis, uvw, vis, weight, ws, ws_bytes, stats, stream) -> None:
+    """rick_bin without allocations: temporaries in the library's fixed array
+    (n_vis <= 262144, at most 262144 bins)."""
+    _check("rick_bin_noalloc", _L.rick_bin_noalloc(plan, int(n_vis), uvw, vis, weight or None, ws,
+                                                   int(ws_bytes), stats or None, stream or None))
 
 
 def rick_bin_values(plan, vis, weight, ws, stats, stream) -> None:
