@@ -335,6 +335,115 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """The serving workload: 256 imaging requests with Poisson arrivals,
+    log-uniform 1e4..1e7 visibilities (prefixes of the LOFAR-like tracks), grids
+    512^2..4096^2, 4..16 w-planes, Gaussian or Kaiser-Bessel W=7.  The plain
+    per-request path (fresh plan and buffers per request) is run first,
+    back to back, to measure its mean service time; both paths then serve the
+    same arrival trace at 0.8 / (that mean)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2411_07321_gb300 import serve as S
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n_jobs = args.serve_jobs
+    d = synth.generate(synth.scaled("lofar", n_keep=10_000_000).obs)
+    host = {k: torch.from_numpy(d[k]).pin_memory() for k in ("uvw", "vis", "weight")}
+    rng = np.random.default_rng(5)
+    specs = []
+    for jid in range(n_jobs):
+        n_vis = int(np.exp(rng.uniform(np.log(1e4), np.log(1e7))))
+        n = int(rng.choice([512, 1024, 2048, 4096]))
+        specs.append(dict(n_vis=n_vis, n=n, n_w=int(rng.integers(4, 17)),
+                          kernel=str(rng.choice(["gauss", "kb"])), job_id=jid))
+
+    def job(sp, arrival=None):
+        nv = sp["n_vis"]
+        j = S.ImagingJob(host["uvw"][:nv], host["vis"][:nv], host["weight"][:nv], n=sp["n"],
+                         n_w=sp["n_w"], fov=S.fov_for(sp["n"], 7, 12000.0), kernel=sp["kernel"],
+                         support=7, tile=64, job_id=sp["job_id"])
+        if arrival is not None:
+            j.arrival = arrival
+        return j
+
+    # plain service times, back to back
+    S.run_plain(job(specs[0]))  # CUDA context, cuFFT and allocator warm-up
+    service, plain_imgs = [], {}
+    for sp in specs:
+        t0 = time.perf_counter()
+        img = S.run_plain(job(sp))
+        service.append(time.perf_counter() - t0)
+        if sp["job_id"] < 8:
+            plain_imgs[sp["job_id"]] = img
+    mean_service = float(np.mean(service))
+    rate = 0.8 / mean_service
+    offsets = S.poisson_arrivals(n_jobs, rate, seed=6)
+
+    # plain path on the arrival trace: one request at a time, in arrival order
+    t_base = time.perf_counter() + 0.2
+    lat_plain, done = [], t_base
+    for sp, off in zip(specs, offsets):
+        arrival = t_base + off
+        while time.perf_counter() < arrival:
+            time.sleep(2e-4)
+        S.run_plain(job(sp))
+        done = time.perf_counter()
+        lat_plain.append(done - arrival)
+    plain_wall = done - t_base
+
+    # served path on the same trace
+    with S.Server(dev, max_running=args.serve_slots) as srv:
+        for sp in specs[:4]:  # warm-up: resident slots of a few shapes
+            srv.submit(job(sp)).result()
+        t_base = time.perf_counter() + 0.2
+        futs = [None] * n_jobs
+
+        def feed():
+            for i, (sp, off) in enumerate(zip(specs, offsets)):
+                arrival = t_base + off
+                while time.perf_counter() < arrival:
+                    time.sleep(2e-4)
+                futs[i] = srv.submit(job(sp, arrival))
+
+        th = threading.Thread(target=feed)
+        th.start()
+        th.join()
+        res = [f.result() for f in futs]
+        served_wall = max(t_base + off + r.latency_s for off, r in zip(offsets, res)) - t_base
+        peak_used = srv.peak_used
+    lat_served = [r.latency_s for r in res]
+    err = 0.0  # inner region |l|, |m| < fov/4: clear of the taper's corner amplification
+    for jid, img in plain_imgs.items():
+        n = img.shape[0]
+        inner = (slice(n // 4, 3 * n // 4),) * 2
+        ref = img[inner].astype(np.float64)
+        err = max(err, float(np.abs(res[jid].image[inner] - ref).max() / np.abs(ref).max()))
+    total_vis = sum(sp["n_vis"] for sp in specs)
+
+    def summary(lat, wall):
+        return {"jobs_per_s": n_jobs / wall, "vis_per_s": total_vis / wall,
+                "p50_ms": 1e3 * S.percentile(lat, 50), "p99_ms": 1e3 * S.percentile(lat, 99),
+                "mean_ms": 1e3 * float(np.mean(lat)), "wall_s": wall}
+
+    print(json.dumps({
+        "metric": METRIC, "mode": "serve", "unit": "jobs/s", "n_gpus": 1, "n_jobs": n_jobs,
+        "value": n_jobs / served_wall, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "256 requests, Poisson arrivals at 0.8 / mean plain service "
+                               "time; n_vis log-uniform 1e4..1e7 (LOFAR-like tracks); grids "
+                               "512..4096; 4..16 w-planes; Gaussian or KB W=7",
+                   "arrival_rate_hz": rate, "slots": args.serve_slots},
+        "served": summary(lat_served, served_wall), "plain": summary(lat_plain, plain_wall),
+        "plain_mean_service_ms": 1e3 * mean_service, "served_peak_hbm_bytes": peak_used,
+        "max_rel_diff_served_vs_plain_inner": err,
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +454,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the serving workload instead (its own JSON line)")
+    ap.add_argument("--serve-jobs", type=int, default=256)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--n-vis", type=int, default=None,
                     help="profiling aid: image only the first N visibilities (not a bench line)")
     args = ap.parse_args()
@@ -354,7 +467,9 @@ def main():
 
     wl = synth.WORKLOADS[args.workload] if args.n_vis is None else \
         synth.scaled(args.workload, n_keep=args.n_vis)
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args, wl)
     else:
         run_ours(args, wl)

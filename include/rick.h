@@ -101,6 +101,14 @@ rick_status rick_plan_destroy(rick_plan *plan);
 /* Sticky error of a plan (RICK_OK if none). */
 rick_status rick_plan_last_error(const rick_plan *plan);
 
+/* Change a plan's sky geometry -- fov and the w range (NaN, NaN: from the
+ * data) -- without rebuilding it: the cuFFT plan, the taper table (which
+ * depends only on n and the kernel) and the kernel-weight fits stay.  Lets a
+ * resident plan serve jobs with different fields of view.  Host-only: calls
+ * already enqueued keep the geometry they were enqueued with.  RICK_EINVAL if
+ * the new geometry is invalid (the plan is then unchanged). */
+rick_status rick_plan_set_geometry(rick_plan *plan, double fov, double w_min, double w_max);
+
 /* Number of library kernels this plan has enqueued since it was created
  * (cuFFT's kernels are not included), for launch accounting. */
 rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count);

@@ -241,6 +241,20 @@ extern "C" rick_status rick_plan_last_error(const rick_plan *plan)
     return plan ? plan->sticky : RICK_EINVAL;
 }
 
+extern "C" rick_status rick_plan_set_geometry(rick_plan *plan, double fov, double w_min,
+                                              double w_max)
+{
+    if (!plan) return RICK_EINVAL;
+    rick_params q = plan->p;
+    q.fov = fov;
+    q.w_min = w_min;
+    q.w_max = w_max;
+    rick_status st = check_params(&q);
+    if (st != RICK_OK) return st;
+    plan->p = q;
+    return RICK_OK;
+}
+
 extern "C" rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count)
 {
     if (!plan || !count) return RICK_EINVAL;

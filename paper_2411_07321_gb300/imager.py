@@ -162,6 +162,12 @@ class Imager:
         out_host.copy_(self._out_img, non_blocking=True)
         return out_host
 
+    def set_geometry(self, fov: float, w_range: tuple[float, float] | None = None):
+        """Re-target the resident plan to another field of view / w range."""
+        wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)
+        R.rick_plan_set_geometry(self.plan, fov, wmin, wmax)
+        self.params.fov, self.params.w_min, self.params.w_max = float(fov), wmin, wmax
+
     def launches(self) -> int:
         """Library kernels this imager's plan has enqueued so far."""
         return R.rick_plan_launch_count(self.plan)

@@ -50,7 +50,7 @@ class rick_bin_view(ctypes.Structure):
 
 
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
-           "rick_plan_launch_count",
+           "rick_plan_launch_count", "rick_plan_set_geometry",
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
            "rick_bin_noalloc", "rick_bin_values",
            "rick_grid", "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid"]
@@ -71,6 +71,7 @@ def _load():
         "rick_plan_destroy": [vp],
         "rick_plan_last_error": [vp],
         "rick_plan_launch_count": [vp, ctypes.POINTER(ctypes.c_uint64)],
+        "rick_plan_set_geometry": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
         "rick_workspace_bytes": [P, i64, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "rick_plan_fft_bytes": [vp, ctypes.POINTER(sz)],
         "rick_bin_layout": [vp, ctypes.POINTER(rick_bin_view)],
@@ -128,6 +129,12 @@ def rick_plan_launch_count(plan: int) -> int:
     c = ctypes.c_uint64()
     _check("rick_plan_launch_count", _L.rick_plan_launch_count(plan, ctypes.byref(c)))
     return c.value
+
+
+def rick_plan_set_geometry(plan: int, fov: float, w_min: float = math.nan,
+                           w_max: float = math.nan) -> None:
+    _check("rick_plan_set_geometry", _L.rick_plan_set_geometry(plan, float(fov), float(w_min),
+                                                               float(w_max)))
 
 
 def rick_workspace_bytes(params: rick_params, n_vis: int) -> tuple[int, int]:

@@ -1,0 +1,332 @@
+"""Continuous-batching imaging server.
+
+Imaging requests (visibilities + imaging parameters) arrive at any time.  The
+server keeps a pool of resident *slots*.  Each slot is an ``Imager``:
+  - a plan with its cuFFT plan, taper table and kernel fits;
+  - a binning workspace and the w-planes;
+  - device input buffers and a pinned host output buffer;
+  - its own CUDA stream.
+
+A scheduler thread admits queued requests as soon as a compatible slot is idle,
+or HBM budget can be freed for a new one.  It enqueues each request's whole
+path (host->device copy, bin, grid, FFT, w-correct, device->host copy) on the
+slot's stream, and completes the request when the stream's event fires.  Work of
+requests admitted while others run overlaps on the device.
+
+Admission is by HBM footprint: a request needs a slot with the same grid size,
+plane count, kernel and tile, and a visibility capacity at least its own.  If no
+idle one exists, a new slot is created when budget - used >= its footprint, after
+evicting idle slots least-recently-used first.  A request larger than the whole
+budget is rejected with an error, and only that request fails.
+
+``run_plain`` is the per-request baseline: a fresh plan and fresh allocations
+for every request, run to completion before the next.
+"""
+from __future__ import annotations
+
+import collections
+import itertools
+import math
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .imager import IMAGE_FLAGS, Imager
+
+MIN_CAPACITY = 1 << 14
+
+
+def capacity_class(n_vis: int) -> int:
+    """Visibility capacity of the slot serving n_vis (powers of two)."""
+    c = MIN_CAPACITY
+    while c < n_vis:
+        c <<= 1
+    return c
+
+
+@dataclass
+class ImagingJob:
+    """One imaging request.  uvw [n,3] f64, vis [n] c64, weight [n] f32 (or
+    None) are host tensors (pinned memory lets the copies run asynchronously)."""
+    uvw: object
+    vis: object
+    weight: object
+    n: int
+    n_w: int
+    fov: float
+    kernel: str = "kb"
+    support: int = 7
+    tile: int = 64
+    precision: str = "fp32"
+    w_range: tuple | None = None
+    flags: int = IMAGE_FLAGS
+    job_id: int = -1
+    arrival: float = field(default_factory=time.perf_counter)
+
+    @property
+    def n_vis(self) -> int:
+        return int(self.uvw.shape[0])
+
+    def key(self):
+        return (self.n, self.n_w, self.kernel, self.support, self.tile, self.precision,
+                capacity_class(self.n_vis))
+
+
+@dataclass
+class JobResult:
+    job_id: int
+    image: np.ndarray
+    latency_s: float
+    queued_s: float
+    slot: int
+
+
+class AdmissionError(RuntimeError):
+    """The request can never fit the server's HBM budget."""
+
+
+class Admission:
+    """Footprint accounting of resident slots (host-only logic)."""
+
+    def __init__(self, budget_bytes: int):
+        self.budget = int(budget_bytes)
+        self.slots = {}  # id -> dict(key, bytes, busy, last)
+        self._ids = itertools.count()
+
+    def used(self) -> int:
+        return sum(s["bytes"] for s in self.slots.values())
+
+    def plan(self, key, bytes_needed: int):
+        """('reuse', id) | ('new', [ids to evict]) | None (wait).  Raises
+        AdmissionError if bytes_needed exceeds the whole budget."""
+        if bytes_needed > self.budget:
+            raise AdmissionError(f"request needs {bytes_needed} B, budget is {self.budget} B")
+        idle_same = [i for i, s in self.slots.items() if s["key"] == key and not s["busy"]]
+        if idle_same:
+            return ("reuse", min(idle_same, key=lambda i: self.slots[i]["last"]))
+        free = self.budget - self.used()
+        evict = []
+        for i in sorted((i for i, s in self.slots.items() if not s["busy"]),
+                        key=lambda i: self.slots[i]["last"]):
+            if free >= bytes_needed:
+                break
+            evict.append(i)
+            free += self.slots[i]["bytes"]
+        return ("new", evict) if free >= bytes_needed else None
+
+    def add(self, key, nbytes: int, now: float) -> int:
+        i = next(self._ids)
+        self.slots[i] = dict(key=key, bytes=int(nbytes), busy=True, last=now)
+        assert self.used() <= self.budget
+        return i
+
+    def acquire(self, i: int, now: float):
+        self.slots[i]["busy"] = True
+        self.slots[i]["last"] = now
+
+    def release(self, i: int, now: float):
+        self.slots[i]["busy"] = False
+        self.slots[i]["last"] = now
+
+    def remove(self, i: int):
+        del self.slots[i]
+
+
+def slot_footprint(job: ImagingJob) -> int:
+    """Device bytes of a slot for job's key (without creating it)."""
+    from . import rick as R
+    from .imager import KERNELS, PRECISIONS
+    p = R.make_params(job.n, job.n_w, job.fov, KERNELS[job.kernel], job.support, tile=job.tile,
+                      precision=PRECISIONS[job.precision])
+    cap = capacity_class(job.n_vis)
+    ws, planes = R.rick_workspace_bytes(p, cap)
+    # planes + workspace + cuFFT area (bounded by the planes' size for in-place
+    # C2C) + image + resident input buffers (uvw, vis, weight)
+    return ws + 2 * planes + job.n * job.n * 4 + cap * (24 + 8 + 4)
+
+
+class _Slot:
+    def __init__(self, job: ImagingJob, device):
+        import torch
+        self.key = job.key()
+        self.imager = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
+                             tile=job.tile, precision=job.precision,
+                             max_vis=capacity_class(job.n_vis), device=device)
+        self.stream = torch.cuda.Stream(device=device)
+        self.out = torch.empty((job.n, job.n), dtype=torch.float32).pin_memory()
+        self.event = None
+        self.job = None
+        self.future = None
+        self.t_start = 0.0
+
+
+class Server:
+    """Continuous-batching server on one device (see the module docstring)."""
+
+    def __init__(self, device="cuda:0", budget_bytes: int | None = None, max_running: int = 8):
+        import torch
+        self.device = torch.device(device)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(0.8 * free)
+        self.admission = Admission(budget_bytes)
+        self.max_running = max_running
+        self._pending = collections.deque()
+        self._slots = {}  # admission id -> _Slot
+        self._cv = threading.Condition()
+        self._stop = False
+        self.peak_used = 0
+        self._thread = threading.Thread(target=self._loop, name="rick-server", daemon=True)
+        self._thread.start()
+
+    # ---------------------------------------------------------------- API
+    def submit(self, job: ImagingJob) -> Future:
+        fut = Future()
+        with self._cv:
+            if self._stop:
+                raise RuntimeError("server is closed")
+            self._pending.append((job, fut))
+            self._cv.notify()
+        return fut
+
+    def close(self):
+        with self._cv:
+            self._stop = True
+            self._cv.notify()
+        self._thread.join()
+        for s in self._slots.values():
+            s.imager.close()
+        self._slots.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- scheduler
+    def _running(self):
+        return [i for i, s in self._slots.items() if s.job is not None]
+
+    def _admit(self) -> bool:
+        """Admit pending jobs in arrival order; a job that must wait for memory
+        does not hold back later jobs that fit now."""
+        progressed = False
+        waiting = collections.deque()
+        while self._pending and len(self._running()) < self.max_running:
+            job, fut = self._pending.popleft()
+            try:
+                need = slot_footprint(job)
+                decision = self.admission.plan(job.key(), need)
+            except Exception as e:  # invalid request or larger than the budget
+                fut.set_exception(e)
+                progressed = True
+                continue
+            if decision is None:
+                waiting.append((job, fut))
+                continue
+            now = time.perf_counter()
+            try:
+                if decision[0] == "reuse":
+                    sid = decision[1]
+                    self.admission.acquire(sid, now)
+                    slot = self._slots[sid]
+                else:
+                    for sid in decision[1]:
+                        self._slots.pop(sid).imager.close()
+                        self.admission.remove(sid)
+                    slot = _Slot(job, self.device)
+                    sid = self.admission.add(job.key(), need, now)
+                    self._slots[sid] = slot
+                    self.peak_used = max(self.peak_used, self.admission.used())
+                self._launch(sid, slot, job, fut)
+            except Exception as e:
+                fut.set_exception(e)
+                if decision[0] == "reuse":
+                    self.admission.release(decision[1], time.perf_counter())
+            progressed = True
+        self._pending.extendleft(reversed(waiting))
+        return progressed
+
+    def _launch(self, sid, slot, job, fut):
+        import torch
+        slot.job, slot.future, slot.t_start = job, fut, time.perf_counter()
+        with torch.cuda.stream(slot.stream):
+            slot.imager.set_geometry(job.fov, job.w_range)
+            slot.imager.image_from_host(job.uvw, job.vis, job.weight, slot.out, job.flags)
+            slot.event = torch.cuda.Event()
+            slot.event.record(slot.stream)
+
+    def _complete(self) -> bool:
+        progressed = False
+        for sid in self._running():
+            slot = self._slots[sid]
+            if not slot.event.query():
+                continue
+            now = time.perf_counter()
+            job, fut = slot.job, slot.future
+            res = JobResult(job.job_id, slot.out.numpy().copy(), now - job.arrival,
+                            slot.t_start - job.arrival, sid)
+            slot.job = slot.future = slot.event = None
+            self.admission.release(sid, now)
+            fut.set_result(res)
+            progressed = True
+        return progressed
+
+    def _loop(self):
+        import torch
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._cv:
+                if self._stop and not self._pending and not self._running():
+                    return
+                if not self._pending and not self._running():
+                    self._cv.wait(timeout=0.05)
+            try:
+                busy = self._complete()
+                with self._cv:
+                    busy = self._admit() or busy
+            except Exception as e:  # fail every outstanding request, keep serving
+                for sid in self._running():
+                    s = self._slots[sid]
+                    if s.future and not s.future.done():
+                        s.future.set_exception(e)
+                    s.job = s.future = s.event = None
+                    self.admission.release(sid, time.perf_counter())
+                busy = True
+            if not busy:
+                time.sleep(50e-6)
+
+
+def run_plain(job: ImagingJob, device="cuda:0") -> np.ndarray:
+    """The per-request baseline: fresh plan and allocations, run, tear down."""
+    import torch
+    with torch.cuda.device(device):
+        im = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
+                    tile=job.tile, precision=job.precision, w_range=job.w_range,
+                    max_vis=max(job.n_vis, 1), device=device)
+        out = torch.empty((job.n, job.n), dtype=torch.float32).pin_memory()
+        im.image_from_host(job.uvw, job.vis, job.weight, out, job.flags)
+        torch.cuda.current_stream().synchronize()
+        img = out.numpy().copy()
+        im.close()
+        del im
+    return img
+
+
+def fov_for(n: int, support: int, uv_max: float) -> float:
+    """Field of view whose uv cell keeps every footprint of |u|,|v| <= uv_max on
+    an n-cell grid: (n/2 - W - 1) / uv_max."""
+    return (n / 2 - support - 1) / uv_max
+
+
+def poisson_arrivals(n_jobs: int, rate: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else math.nan

@@ -1,0 +1,99 @@
+"""Host-side admission logic of the imaging server (no GPU needed).
+
+Admission keeps the sum of resident slot footprints within the HBM budget,
+reuses an idle slot of the same key, evicts idle slots least recently used
+first, never evicts a busy slot, and rejects a request larger than the whole
+budget -- a failure that touches no other request.
+"""
+import importlib
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_serve():
+    return importlib.import_module("paper_2411_07321_gb300.serve")
+
+
+@pytest.fixture(scope="module")
+def S():
+    pytest.importorskip("torch")
+    from paper_2411_07321_gb300 import build
+    build.build()  # serve.py loads the binding (no GPU work is done here)
+    return load_serve()
+
+
+def test_capacity_classes(S):
+    assert S.capacity_class(1) == 1 << 14
+    assert S.capacity_class(1 << 14) == 1 << 14
+    assert S.capacity_class((1 << 14) + 1) == 1 << 15
+    assert S.capacity_class(10_000_000) == 1 << 24
+
+
+def test_reuse_idle_slot_of_same_key(S):
+    a = S.Admission(1000)
+    k = ("A",)
+    assert a.plan(k, 300) == ("new", [])
+    i = a.add(k, 300, now=0.0)
+    a.release(i, now=1.0)
+    assert a.plan(k, 300) == ("reuse", i)
+    a.acquire(i, now=2.0)
+    # the only slot of that key is busy: a new one is planned
+    assert a.plan(k, 300) == ("new", [])
+
+
+def test_lru_eviction_and_busy_slots_never_evicted(S):
+    a = S.Admission(1000)
+    s1 = a.add(("A",), 400, now=0.0)
+    s2 = a.add(("B",), 400, now=1.0)
+    a.release(s1, now=5.0)   # s1 idle, used later than s2
+    a.release(s2, now=3.0)   # s2 idle, least recently used
+    # needs 500: 200 free, evict s2 (LRU) first -> 600 free
+    assert a.plan(("C",), 500) == ("new", [s2])
+    # with s1 busy, only s2 can go
+    a.acquire(s1, now=6.0)
+    assert a.plan(("C",), 500) == ("new", [s2])
+    # needs 700: even evicting s2 leaves 600 free -> wait
+    assert a.plan(("C",), 700) is None
+
+
+def test_budget_never_exceeded(S):
+    a = S.Admission(1000)
+    import random
+    rnd = random.Random(0)
+    live = []
+    for step in range(500):
+        key = (rnd.randrange(4),)
+        need = rnd.randrange(50, 400)
+        d = a.plan(key, need)
+        if d is None:
+            if live:
+                a.release(live.pop(rnd.randrange(len(live))), now=step)
+            continue
+        if d[0] == "reuse":
+            a.acquire(d[1], now=step)
+            live.append(d[1])
+        else:
+            for i in d[1]:
+                assert not a.slots[i]["busy"]
+                a.remove(i)
+            live.append(a.add(key, need, now=step))
+        assert a.used() <= a.budget
+        if len(live) > 3:
+            a.release(live.pop(0), now=step)
+
+
+def test_request_larger_than_budget_is_rejected(S):
+    a = S.Admission(1000)
+    with pytest.raises(S.AdmissionError):
+        a.plan(("A",), 1001)
+    assert a.plan(("A",), 1000) == ("new", [])
+
+
+def test_poisson_arrivals(S):
+    t = S.poisson_arrivals(20000, rate=50.0, seed=3)
+    import numpy as np
+    assert np.all(np.diff(t) > 0)
+    assert abs(np.mean(np.diff(t)) - 1 / 50.0) < 0.05 / 50.0
