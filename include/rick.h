@@ -90,12 +90,17 @@ const char *rick_status_string(rick_status s);
 
 /* Create a plan for `params` on the current CUDA device: validates params,
  * creates the batched cuFFT plan (n_w transforms of n x n, complex64), and
- * precomputes the taper table.  max_vis bounds n_vis in later calls.
+ * precomputes the taper table and the kernel-weight fits.  max_vis bounds
+ * n_vis in later calls.  Does not synchronise the device: the plan's own
+ * allocations are stream-ordered on a private stream, and only that stream is
+ * waited for, so work already running on other streams is not stalled.
  * Errors: RICK_EINVAL (bad params or max_vis < 0 or >= 2^31), RICK_ENOMEM,
  * RICK_ECUFFT, RICK_ECUDA.  *out is set only on success. */
 rick_status rick_plan_create(const rick_params *params, int64_t max_vis, rick_plan **out);
 
-/* Release a plan (NULL is accepted).  Synchronises the device first. */
+/* Release a plan (NULL is accepted).  The caller must make sure that no work
+ * enqueued with the plan is still pending (e.g. synchronise its streams); the
+ * device as a whole is not synchronised. */
 rick_status rick_plan_destroy(rick_plan *plan);
 
 /* Sticky error of a plan (RICK_OK if none). */

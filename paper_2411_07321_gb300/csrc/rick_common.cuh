@@ -75,6 +75,8 @@ struct rick_plan {
     int num_sms;
     cufftHandle fft;
     size_t fft_bytes;
+    void *fft_work;     // cuFFT work area (ours: stream-ordered allocation)
+    cudaStream_t own;   // the plan's private stream for its own allocations
     float *taper_inv;  // device [n]: 1 / C(nu_p), nu_p = (p - n/2) / n
     double beta, sigma, i0_beta;
     KernelPoly poly;   // kernel-weight polynomials (host copy, passed to kernels)

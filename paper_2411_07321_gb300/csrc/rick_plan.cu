@@ -162,6 +162,22 @@ static double bessel_i0_host(double x)
     return sum;
 }
 
+// Plan creation and destruction do not synchronise the device: the plan gets
+// its own non-blocking stream, its tables and the cuFFT work area are
+// allocated stream-ordered on it, and only that stream is waited for.  Work of
+// other plans on other streams keeps running meanwhile.
+static void plan_release(rick_plan *pl)
+{
+    if (pl->fft) cufftDestroy(pl->fft);
+    if (pl->own) {
+        if (pl->taper_inv) cudaFreeAsync(pl->taper_inv, pl->own);
+        if (pl->fft_work) cudaFreeAsync(pl->fft_work, pl->own);
+        cudaStreamSynchronize(pl->own);
+        cudaStreamDestroy(pl->own);
+    }
+    free(pl);
+}
+
 extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_vis, rick_plan **out)
 {
     if (!out) return RICK_EINVAL;
@@ -172,10 +188,10 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
     if (!pl) return RICK_ENOMEM;
     pl->p = *params;
     pl->max_vis = max_vis;
-    pl->fft = 0;
     if (cudaGetDevice(&pl->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&pl->own, cudaStreamNonBlocking) != cudaSuccess) {
         free(pl);
         return RICK_ECUDA;
     }
@@ -183,42 +199,50 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
     pl->sigma = isnan(params->gauss_sigma) ? params->support / 6.0 : params->gauss_sigma;
     pl->i0_beta = bessel_i0_host(pl->beta);
 
+    // batched 2D C2C plan; the work area is ours (stream-ordered allocation)
     int n = params->n;
     long long dims[2] = {n, n}, dist = (long long)n * n;
     cufftResult fr = cufftCreate(&pl->fft);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetAutoAllocation(pl->fft, 0);
     if (fr == CUFFT_SUCCESS)
         fr = cufftMakePlanMany64(pl->fft, 2, dims, NULL, 1, dist, NULL, 1, dist, CUFFT_C2C,
                                  params->n_w, &pl->fft_bytes);
     if (fr != CUFFT_SUCCESS) {
-        cufftDestroy(pl->fft);
-        free(pl);
+        plan_release(pl);
         return fr == CUFFT_ALLOC_FAILED ? RICK_ENOMEM : RICK_ECUFFT;
     }
-    if (cudaMalloc(&pl->taper_inv, sizeof(float) * n) != cudaSuccess) {
-        cufftDestroy(pl->fft);
-        free(pl);
+    if ((pl->fft_bytes && cudaMallocAsync(&pl->fft_work, pl->fft_bytes, pl->own) != cudaSuccess) ||
+        cudaMallocAsync((void **)&pl->taper_inv, sizeof(float) * n, pl->own) != cudaSuccess) {
+        plan_release(pl);
         return RICK_ENOMEM;
     }
-    pl->launches = 2;
-    taper_kernel<<<(n + 255) / 256, 256>>>(pl->taper_inv, n, params->support, params->kernel,
-                                           pl->beta, pl->i0_beta, pl->sigma);
-    float *coef = NULL;
-    bool ok = cudaGetLastError() == cudaSuccess &&
-              cudaMalloc(&coef, sizeof(float) * RICK_MAX_W * RICK_POLY_N) == cudaSuccess;
-    if (ok) {
-        cudaMemset(coef, 0, sizeof(float) * RICK_MAX_W * RICK_POLY_N);
-        kernel_poly_kernel<<<1, RICK_MAX_W>>>(coef, params->support, params->kernel, pl->beta,
-                                              pl->i0_beta, pl->sigma);
-        ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
-             cudaMemcpy(pl->poly.c, coef, sizeof(pl->poly.c), cudaMemcpyDeviceToHost) ==
-                 cudaSuccess;
+    if (pl->fft_bytes && cufftSetWorkArea(pl->fft, pl->fft_work) != CUFFT_SUCCESS) {
+        plan_release(pl);
+        return RICK_ECUFFT;
     }
-    if (coef) cudaFree(coef);
+    float *coef = NULL;
+    bool ok = cudaMallocAsync((void **)&coef, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
+              cudaSuccess;
+    if (ok) {
+        pl->launches = 2;
+        taper_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(
+            pl->taper_inv, n, params->support, params->kernel, pl->beta, pl->i0_beta, pl->sigma);
+        ok = cudaGetLastError() == cudaSuccess &&
+             cudaMemsetAsync(coef, 0, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
+                 cudaSuccess;
+        if (ok) {
+            kernel_poly_kernel<<<1, RICK_MAX_W, 0, pl->own>>>(coef, params->support, params->kernel,
+                                                             pl->beta, pl->i0_beta, pl->sigma);
+            ok = cudaGetLastError() == cudaSuccess &&
+                 cudaMemcpyAsync(pl->poly.c, coef, sizeof(pl->poly.c), cudaMemcpyDeviceToHost,
+                                 pl->own) == cudaSuccess;
+        }
+        cudaFreeAsync(coef, pl->own);
+        ok = ok && cudaStreamSynchronize(pl->own) == cudaSuccess;
+    }
     pl->poly.fc = (params->support & 1) ? 0.0f : 0.5f;
     if (!ok) {
-        cudaFree(pl->taper_inv);
-        cufftDestroy(pl->fft);
-        free(pl);
+        plan_release(pl);
         return RICK_ECUDA;
     }
     pl->sticky = RICK_OK;
@@ -226,13 +250,11 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
     return RICK_OK;
 }
 
+// The caller guarantees that no work enqueued with the plan is still pending.
 extern "C" rick_status rick_plan_destroy(rick_plan *plan)
 {
     if (!plan) return RICK_OK;
-    cudaDeviceSynchronize();
-    cufftDestroy(plan->fft);
-    cudaFree(plan->taper_inv);
-    free(plan);
+    plan_release(plan);
     return RICK_OK;
 }
 

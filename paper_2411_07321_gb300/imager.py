@@ -193,7 +193,10 @@ class Imager:
                     rec_cell=take(v.rec_cell, 4 * nb).view(np.uint32), stats=st)
 
     def close(self):
+        """Release the plan.  Work this imager enqueued must be complete (its
+        stream synchronised) -- the server only closes idle slots."""
         if getattr(self, "plan", None):
+            torch.cuda.current_stream(self.device).synchronize()
             R.rick_plan_destroy(self.plan)
             self.plan = None
 

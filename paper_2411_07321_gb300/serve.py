@@ -149,18 +149,35 @@ def slot_footprint(job: ImagingJob) -> int:
 
 
 class _Slot:
-    def __init__(self, job: ImagingJob, device):
+    def __init__(self, job: ImagingJob, device, out_host):
         import torch
         self.key = job.key()
         self.imager = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
                              tile=job.tile, precision=job.precision,
                              max_vis=capacity_class(job.n_vis), device=device)
         self.stream = torch.cuda.Stream(device=device)
-        self.out = torch.empty((job.n, job.n), dtype=torch.float32).pin_memory()
+        self.out = out_host  # pinned image buffer, from the server's pool
         self.event = None
         self.job = None
         self.future = None
         self.t_start = 0.0
+
+
+class _PinnedPool:
+    """Pinned host image buffers by grid size, reused across slots
+    (pinning host memory is slow; a new slot should not pay for it)."""
+
+    def __init__(self):
+        self.free = collections.defaultdict(list)
+
+    def get(self, n: int):
+        import torch
+        if self.free[n]:
+            return self.free[n].pop()
+        return torch.empty((n, n), dtype=torch.float32).pin_memory()
+
+    def put(self, buf):
+        self.free[buf.shape[0]].append(buf)
 
 
 class Server:
@@ -176,6 +193,7 @@ class Server:
         self.max_running = max_running
         self._pending = collections.deque()
         self._slots = {}  # admission id -> _Slot
+        self._pinned = _PinnedPool()
         self._cv = threading.Condition()
         self._stop = False
         self.peak_used = 0
@@ -197,9 +215,8 @@ class Server:
             self._stop = True
             self._cv.notify()
         self._thread.join()
-        for s in self._slots.values():
-            s.imager.close()
-        self._slots.clear()
+        for sid in list(self._slots):
+            self._evict(sid)
 
     def __enter__(self):
         return self
@@ -236,9 +253,8 @@ class Server:
                     slot = self._slots[sid]
                 else:
                     for sid in decision[1]:
-                        self._slots.pop(sid).imager.close()
-                        self.admission.remove(sid)
-                    slot = _Slot(job, self.device)
+                        self._evict(sid)
+                    slot = _Slot(job, self.device, self._pinned.get(job.n))
                     sid = self.admission.add(job.key(), need, now)
                     self._slots[sid] = slot
                     self.peak_used = max(self.peak_used, self.admission.used())
@@ -250,6 +266,13 @@ class Server:
             progressed = True
         self._pending.extendleft(reversed(waiting))
         return progressed
+
+    def _evict(self, sid):
+        slot = self._slots.pop(sid)
+        slot.stream.synchronize()  # idle already; the plan's work is complete
+        slot.imager.close()
+        self._pinned.put(slot.out)
+        self.admission.remove(sid)
 
     def _launch(self, sid, slot, job, fut):
         import torch
