@@ -422,6 +422,7 @@ def run_serve(args):
         res = [f.result() for f in futs]
         served_wall = max(t_base + off + r.latency_s for off, r in zip(offsets, res)) - t_base
         peak_used = srv.peak_used
+        counters = dict(srv.counters)
     lat_served = [r.latency_s for r in res]
     err = 0.0  # inner region |l|, |m| < fov/4: clear of the taper's corner amplification
     for jid, img in plain_imgs.items():
@@ -446,7 +447,7 @@ def run_serve(args):
         "served": summary(lat_served, served_wall), "plain": summary(lat_plain, plain_wall),
         "saturated_jobs_per_s": {"served": served_saturated, "plain": plain_saturated},
         "plain_mean_service_ms": 1e3 * mean_service, "served_peak_hbm_bytes": peak_used,
-        "max_rel_diff_served_vs_plain_inner": err,
+        "max_rel_diff_served_vs_plain_inner": err, "server_counters": counters,
     }), flush=True)
 
 

@@ -91,8 +91,9 @@ class AdmissionError(RuntimeError):
 class Admission:
     """Footprint accounting of resident slots (host-only logic)."""
 
-    def __init__(self, budget_bytes: int):
+    def __init__(self, budget_bytes: int, max_slots: int | None = None):
         self.budget = int(budget_bytes)
+        self.max_slots = max_slots  # resident slots at most (None: budget only)
         self.slots = {}  # id -> dict(key, bytes, busy, last)
         self._ids = itertools.count()
 
@@ -108,14 +109,17 @@ class Admission:
         if idle_same:
             return ("reuse", min(idle_same, key=lambda i: self.slots[i]["last"]))
         free = self.budget - self.used()
+        count = len(self.slots)
         evict = []
         for i in sorted((i for i, s in self.slots.items() if not s["busy"]),
                         key=lambda i: self.slots[i]["last"]):
-            if free >= bytes_needed:
+            if free >= bytes_needed and (self.max_slots is None or count < self.max_slots):
                 break
             evict.append(i)
             free += self.slots[i]["bytes"]
-        return ("new", evict) if free >= bytes_needed else None
+            count -= 1
+        fits = free >= bytes_needed and (self.max_slots is None or count < self.max_slots)
+        return ("new", evict) if fits else None
 
     def add(self, key, nbytes: int, now: float) -> int:
         i = next(self._ids)
@@ -169,28 +173,40 @@ class _PinnedPool:
 
     def __init__(self):
         self.free = collections.defaultdict(list)
+        self.lock = threading.Lock()
 
     def get(self, n: int):
         import torch
-        if self.free[n]:
-            return self.free[n].pop()
+        with self.lock:
+            if self.free[n]:
+                return self.free[n].pop()
         return torch.empty((n, n), dtype=torch.float32).pin_memory()
 
     def put(self, buf):
-        self.free[buf.shape[0]].append(buf)
+        with self.lock:
+            self.free[buf.shape[0]].append(buf)
 
 
 class Server:
     """Continuous-batching server on one device (see the module docstring)."""
 
-    def __init__(self, device="cuda:0", budget_bytes: int | None = None, max_running: int = 8):
+    def __init__(self, device="cuda:0", budget_bytes: int | None = None, max_running: int = 8,
+                 max_slots: int | None = None):
         import torch
+        from concurrent.futures import ThreadPoolExecutor
         self.device = torch.device(device)
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(0.8 * free)
-        self.admission = Admission(budget_bytes)
+        # resident slots beyond the running ones are kept for reuse; past the
+        # cap the least recently used idle slot gives its memory back first
+        self.admission = Admission(budget_bytes, max_slots or 2 * max_running)
         self.max_running = max_running
+        self.counters = dict(new_slots=0, reused=0, evicted=0, host_create_s=0.0,
+                             host_launch_s=0.0)
+        # finished images leave the pinned buffers on worker threads, so the
+        # scheduler never waits on a host copy
+        self._copier = ThreadPoolExecutor(max_workers=4, thread_name_prefix="rick-copy")
         self._pending = collections.deque()
         self._slots = {}  # admission id -> _Slot
         self._pinned = _PinnedPool()
@@ -215,6 +231,7 @@ class Server:
             self._stop = True
             self._cv.notify()
         self._thread.join()
+        self._copier.shutdown(wait=True)
         for sid in list(self._slots):
             self._evict(sid)
 
@@ -251,6 +268,7 @@ class Server:
                     sid = decision[1]
                     self.admission.acquire(sid, now)
                     slot = self._slots[sid]
+                    self.counters["reused"] += 1
                 else:
                     for sid in decision[1]:
                         self._evict(sid)
@@ -258,7 +276,11 @@ class Server:
                     sid = self.admission.add(job.key(), need, now)
                     self._slots[sid] = slot
                     self.peak_used = max(self.peak_used, self.admission.used())
+                    self.counters["new_slots"] += 1
+                    self.counters["host_create_s"] += time.perf_counter() - now
+                t0 = time.perf_counter()
                 self._launch(sid, slot, job, fut)
+                self.counters["host_launch_s"] += time.perf_counter() - t0
             except Exception as e:
                 fut.set_exception(e)
                 if decision[0] == "reuse":
@@ -271,12 +293,16 @@ class Server:
         slot = self._slots.pop(sid)
         slot.stream.synchronize()  # idle already; the plan's work is complete
         slot.imager.close()
-        self._pinned.put(slot.out)
+        if slot.out is not None:
+            self._pinned.put(slot.out)
         self.admission.remove(sid)
+        self.counters["evicted"] += 1
 
     def _launch(self, sid, slot, job, fut):
         import torch
         slot.job, slot.future, slot.t_start = job, fut, time.perf_counter()
+        if slot.out is None:
+            slot.out = self._pinned.get(job.n)
         with torch.cuda.stream(slot.stream):
             slot.imager.set_geometry(job.fov, job.w_range)
             slot.imager.image_from_host(job.uvw, job.vis, job.weight, slot.out, job.flags)
@@ -289,15 +315,19 @@ class Server:
             slot = self._slots[sid]
             if not slot.event.query():
                 continue
-            now = time.perf_counter()
-            job, fut = slot.job, slot.future
-            res = JobResult(job.job_id, slot.out.numpy().copy(), now - job.arrival,
-                            slot.t_start - job.arrival, sid)
+            job, fut, buf = slot.job, slot.future, slot.out
             slot.job = slot.future = slot.event = None
-            self.admission.release(sid, now)
-            fut.set_result(res)
+            slot.out = None  # the next job on this slot takes another pooled buffer
+            self.admission.release(sid, time.perf_counter())
+            self._copier.submit(self._deliver, job, fut, buf, slot.t_start, sid)
             progressed = True
         return progressed
+
+    def _deliver(self, job, fut, buf, t_start, sid):
+        img = buf.numpy().copy()
+        self._pinned.put(buf)
+        now = time.perf_counter()
+        fut.set_result(JobResult(job.job_id, img, now - job.arrival, t_start - job.arrival, sid))
 
     def _loop(self):
         import torch

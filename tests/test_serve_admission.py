@@ -97,3 +97,15 @@ def test_poisson_arrivals(S):
     import numpy as np
     assert np.all(np.diff(t) > 0)
     assert abs(np.mean(np.diff(t)) - 1 / 50.0) < 0.05 / 50.0
+
+
+def test_slot_cap_evicts_idle_lru_first(S):
+    a = S.Admission(10_000, max_slots=2)
+    s1 = a.add(("A",), 100, now=0.0)
+    s2 = a.add(("B",), 100, now=1.0)
+    # both busy: a third key must wait even though the budget has room
+    assert a.plan(("C",), 100) is None
+    a.release(s2, now=2.0)
+    a.release(s1, now=3.0)
+    assert a.plan(("C",), 100) == ("new", [s2])  # s2 is least recently used
+    assert a.plan(("A",), 100) == ("reuse", s1)
