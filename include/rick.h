@@ -174,11 +174,11 @@ rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out);
  * computes -- into the same workspace layout, which the later calls read --
  * but keeps its temporaries (per-visibility keys, cells and offsets, the
  * histogram, scan temporaries, weight-sum partials) in a fixed array compiled
- * into the library (about 5 MB, held on every GPU that loads the library until
+ * into the library (about 12 MB, held on every GPU that loads the library until
  * the process exits) instead of in ws_dev's scratch regions.  It calls no
  * cudaMalloc, cudaFree or allocating library routine.
  * The paper has no counterpart; this is an interface convenience.
- *   Limits: n_vis <= 262144 and 4 n_w (n/T)^2 <= 262144 bins, else
+ *   Limits: n_vis <= 262144 and 4 n_w (n/T)^2 <= 131072 bins, else
  *   RICK_ERANGE.  Arguments as for rick_bin.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream

@@ -143,6 +143,9 @@ __global__ void bin_setup_kernel(WsHeader *hdr, unsigned long long *bkey, float4
         ff s = ff_from_double(wk);
         wplane[k] = make_float4(s.hi, s.lo, (float)wk, 0.0f);
     }
+    // one more entry: the plane spacing, for the phase step between planes
+    ff d = ff_from_double(dw);
+    wplane[n_w] = make_float4(d.hi, d.lo, (float)dw, 0.0f);
 }
 
 // ------------------------------------------------------------------------
@@ -225,21 +228,25 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
             }
             a.ws.key[i] = key;
         }
-        // histogram: one atomic per distinct key of the warp
+        // histogram: one atomic per distinct key of the warp, on this block's
+        // sub-counter of the bin
         unsigned peers = __match_any_sync(FULL, key);
         if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
-            atomicAdd(&a.ws.hist[key], (uint32_t)__popc(peers));
+            atomicAdd(&a.ws.hist[key * RICK_BIN_SUBS + (blockIdx.x & (RICK_BIN_SUBS - 1))],
+                      (uint32_t)__popc(peers));
     }
-    // deterministic block reduction of the weight sum and the drop counts
-    double ws = (double)wsum - (double)wcomp;
+    // deterministic block reduction of the weight sum (double-single pairs in
+    // the warp: GB300 issues FP64 slowly) and of the drop counts
+    ff ws = ff_fast_two_sum(wsum, -wcomp);
     for (int o = 16; o > 0; o >>= 1) {
-        ws += __shfl_xor_sync(FULL, ws, o);
+        ff other = {__shfl_xor_sync(FULL, ws.hi, o), __shfl_xor_sync(FULL, ws.lo, o)};
+        ws = ff_add(ws, other);
         du += __shfl_xor_sync(FULL, du, o);
         dwn += __shfl_xor_sync(FULL, dwn, o);
     }
     int wid = threadIdx.x >> 5;
     if (lane == 0) {
-        s_wsum[wid] = ws;
+        s_wsum[wid] = (double)ws.hi + (double)ws.lo;
         s_drop[0][wid] = du;
         s_drop[1][wid] = dwn;
     }
@@ -293,11 +300,15 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
         uint32_t key = i < n_vis ? ws.key[i] : 0xFFFFFFFFu;
         unsigned peers = __match_any_sync(FULL, key);
         int leader = __ffs(peers) - 1;
+        // the sub-counter of the key pass's block that held this input
+        const uint32_t sub =
+            (uint32_t)((i0 / (RICK_KEY_THREADS * RICK_KEY_ITEMS)) & (RICK_BIN_SUBS - 1));
+        const uint32_t slot = key * RICK_BIN_SUBS + sub;
         uint32_t b = 0;
-        if (key != 0xFFFFFFFFu && lane == leader) b = atomicAdd(&ws.hist[key], (uint32_t)__popc(peers));
+        if (key != 0xFFFFFFFFu && lane == leader) b = atomicAdd(&ws.hist[slot], (uint32_t)__popc(peers));
         b = __shfl_sync(FULL, b, leader);
         if (key != 0xFFFFFFFFu) {
-            uint32_t pos = ws.offsets[key] + b + __popc(peers & ((1u << lane) - 1));
+            uint32_t pos = ws.suboff[slot] + b + __popc(peers & ((1u << lane) - 1));
             float2 v = vis[i];
             float wt = weight ? weight[i] : 1.0f;
             ws.perm[pos] = (uint32_t)i;
@@ -306,6 +317,15 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
             ws.rcell[pos] = ws.cell[i];
         }
     }
+}
+
+// Bin offsets from the sub-counter offsets: bin b starts where its first
+// sub-range starts.
+__global__ void bin_offsets_kernel(const uint32_t *suboff, uint32_t *offsets, int64_t nbins)
+{
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nbins;
+         b += (int64_t)gridDim.x * blockDim.x)
+        offsets[b] = suboff[b * RICK_BIN_SUBS];
 }
 
 // Re-pack record values for new visibilities through an existing permutation.
@@ -400,7 +420,7 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
     RICK_LAUNCH_CHECK(plan);
-    RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+    RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
 
     if (n_vis > 0) {
         KeyArgs ka;
@@ -424,9 +444,13 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
     }
     bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL);
     RICK_LAUNCH_CHECK(plan);
-    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.offsets, L.nbins + 1, w.scan, st, &plan->launches));
+    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.suboff, RICK_BIN_SUBS * L.nbins + 1, w.scan, st,
+                                 &plan->launches));
+    bin_offsets_kernel<<<(unsigned)((L.nbins + 256) / 256), 256, 0, st>>>(w.suboff, w.offsets,
+                                                                          L.nbins);
+    RICK_LAUNCH_CHECK(plan);
     if (n_vis > 0) {
-        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
         int64_t blocks = (n_vis + 255) / 256;
         if (blocks > (int64_t)plan->num_sms * 32) blocks = (int64_t)plan->num_sms * 32;
         bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
@@ -471,15 +495,16 @@ extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const f
 // fractional offsets, the histogram / cursor array, the scan temporaries and
 // the weight-sum partials -- live in this file-scope array instead of the
 // caller's workspace.  The array is part of the library image: every GPU that
-// loads librick.so holds it (about 5 MB) until the process exits.
+// loads librick.so holds it (about 12 MB) until the process exits.
 
 #define NOALLOC_MAX_VIS (1 << 18)
-#define NOALLOC_MAX_BINS (1 << 18)
+#define NOALLOC_MAX_BINS (1 << 17)
 #define NOALLOC_KEY (0)
 #define NOALLOC_CELL (NOALLOC_KEY + 4 * NOALLOC_MAX_VIS)
 #define NOALLOC_FRAC (NOALLOC_CELL + 4 * NOALLOC_MAX_VIS)
 #define NOALLOC_HIST (NOALLOC_FRAC + 8 * NOALLOC_MAX_VIS)
-#define NOALLOC_SCAN (NOALLOC_HIST + 4 * (NOALLOC_MAX_BINS + 256))
+#define NOALLOC_SUBOFF (NOALLOC_HIST + 4 * (RICK_BIN_SUBS * NOALLOC_MAX_BINS + 256))
+#define NOALLOC_SCAN (NOALLOC_SUBOFF + 4 * (RICK_BIN_SUBS * NOALLOC_MAX_BINS + 256))
 #define NOALLOC_WPART (NOALLOC_SCAN + 4 * 4096)
 #define NOALLOC_BYTES (NOALLOC_WPART + 8 * (NOALLOC_MAX_VIS / (RICK_KEY_THREADS * RICK_KEY_ITEMS) + 256))
 
@@ -536,6 +561,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     w.cell = (uint32_t *)(scratch + NOALLOC_CELL);
     w.frac = (float2 *)(scratch + NOALLOC_FRAC);
     w.hist = (uint32_t *)(scratch + NOALLOC_HIST);
+    w.suboff = (uint32_t *)(scratch + NOALLOC_SUBOFF);
     w.scan = (uint32_t *)(scratch + NOALLOC_SCAN);
     w.wpart = (double *)(scratch + NOALLOC_WPART);
     cudaStream_t st = (cudaStream_t)stream;
@@ -554,7 +580,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
     RICK_LAUNCH_CHECK(plan);
     // the array keeps the last call's contents: the histogram must start at zero
-    RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+    RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
     if (n_vis > 0) {
         KeyArgs ka;
         ka.n_vis = n_vis;
@@ -577,9 +603,13 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     }
     bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL);
     RICK_LAUNCH_CHECK(plan);
-    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.offsets, L.nbins + 1, w.scan, st, &plan->launches));
+    RICK_CUDA_TRY(plan, scan_u32(w.hist, w.suboff, RICK_BIN_SUBS * L.nbins + 1, w.scan, st,
+                                 &plan->launches));
+    bin_offsets_kernel<<<(unsigned)((L.nbins + 256) / 256), 256, 0, st>>>(w.suboff, w.offsets,
+                                                                          L.nbins);
+    RICK_LAUNCH_CHECK(plan);
     if (n_vis > 0) {
-        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(L.nbins + 1), st));
+        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
         int64_t blocks = (n_vis + 255) / 256;
         if (blocks > (int64_t)plan->num_sms * 32) blocks = (int64_t)plan->num_sms * 32;
         bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);

@@ -101,13 +101,18 @@ struct WsHeader {
 };
 
 struct WsLayout {
-    size_t header, key, cell, frac, perm, rec, rcell, hist, offsets, gbase, dbase, scan,
+    size_t header, key, cell, frac, perm, rec, rcell, hist, suboff, offsets, gbase, dbase, scan,
         wpart, bkey, wplane, total;
     int64_t n_vis, nbins, ntiles, nscan, nkeyblocks;
 };
 
 #define RICK_KEY_THREADS 256
 #define RICK_KEY_ITEMS 8
+// Each bin's histogram counter and scatter cursor is split into RICK_BIN_SUBS
+// sub-counters, chosen by the input's block of RICK_KEY_THREADS * RICK_KEY_ITEMS
+// visibilities: the densest bins (the array core) then take their atomics on
+// several addresses instead of one.
+#define RICK_BIN_SUBS 8
 
 RICK_HD size_t rick_align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -130,8 +135,7 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
     L.ntiles = (int64_t)p->n_w * nt * nt;
     L.nbins = 4 * L.ntiles;
     L.nkeyblocks = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) / (RICK_KEY_THREADS * RICK_KEY_ITEMS);
-    int64_t longest = L.nbins + 1 > L.ntiles + 1 ? L.nbins + 1 : L.ntiles + 1;
-    L.nscan = rick_scan_tmp(longest);
+    L.nscan = rick_scan_tmp(RICK_BIN_SUBS * L.nbins + 1);
     int64_t nv = n_vis > 0 ? n_vis : 1;
     size_t o = 0;
     L.header = o; o += rick_align256(sizeof(WsHeader));
@@ -141,7 +145,8 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
     L.perm = o;   o += rick_align256(4 * (size_t)nv);
     L.rec = o;    o += rick_align256(16 * (size_t)nv);
     L.rcell = o;  o += rick_align256(4 * (size_t)nv);
-    L.hist = o;   o += rick_align256(4 * (size_t)(L.nbins + 1));
+    L.hist = o;   o += rick_align256(4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1));
+    L.suboff = o; o += rick_align256(4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1));
     L.offsets = o; o += rick_align256(4 * (size_t)(L.nbins + 1));
     L.gbase = o;  o += rick_align256(4 * (size_t)(L.ntiles + 1));
     L.dbase = o;  o += rick_align256(4 * (size_t)(L.ntiles + 1));
@@ -156,7 +161,7 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
 // Device pointers into a workspace.
 struct WsPtrs {
     WsHeader *hdr;
-    uint32_t *key, *cell, *perm, *rcell, *hist, *offsets, *gbase, *dbase, *scan;
+    uint32_t *key, *cell, *perm, *rcell, *hist, *suboff, *offsets, *gbase, *dbase, *scan;
     float2 *frac;
     float4 *rec;  // per record: vis*weight (re, im), fractional offsets (fx, fy)
     double *wpart;
@@ -176,6 +181,7 @@ static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
     w.rec = (float4 *)(b + L.rec);
     w.rcell = (uint32_t *)(b + L.rcell);
     w.hist = (uint32_t *)(b + L.hist);
+    w.suboff = (uint32_t *)(b + L.suboff);
     w.offsets = (uint32_t *)(b + L.offsets);
     w.gbase = (uint32_t *)(b + L.gbase);
     w.dbase = (uint32_t *)(b + L.dbase);
@@ -261,6 +267,28 @@ RICK_HD float rick_scaled_int_to_float(int64_t s, int sh)
     return f;
 }
 
+// -0.5 <= x < 1 (the first grid cell; x < 0 only with W odd).  Kept out of
+// line so that its FP64 conversions stay on this rare path instead of being
+// predicated into every call.
+#if defined(__CUDACC__)
+static __host__ __device__ __noinline__
+#else
+static inline
+#endif
+bool rick_footprint_first_cell(double x, bool odd, int32_t *c, float *f)
+{
+    uint64_t b = rick_dbits(x);
+    if (b >> 63) {  // -0.5 <= x < 0: only W odd can have c = 0
+        if (!odd) return false;
+        *c = 0;
+        *f = (float)x;
+        return true;
+    }
+    *c = (odd && b >= 0x3FE0000000000000ull) ? 1 : 0;
+    *f = (float)(x - (double)*c);
+    return true;
+}
+
 // Footprint of one axis (see rick_bin in rick.h): from the FP64 grid
 // coordinate x, the corner a and the offset x - c rounded to float.  Returns
 // false when the footprint is not inside [0, n-1] or x is not finite.
@@ -276,13 +304,8 @@ RICK_HD bool rick_footprint(double x, int n, int W, uint64_t key_lo, uint64_t ke
     uint64_t b = rick_dbits(x);
     int32_t c;
     float f;
-    if (b >> 63) {  // -0.5 <= x < 0: only W odd can have c = 0
-        if (!odd) return false;
-        c = 0;
-        f = (float)x;
-    } else if (b < 0x3FF0000000000000ull) {  // 0 <= x < 1
-        c = (odd && b >= 0x3FE0000000000000ull) ? 1 : 0;
-        f = (float)(x - (double)c);
+    if (b < 0x3FF0000000000000ull || (b >> 63)) {  // -0.5 <= x < 1: the first cell, rare
+        if (!rick_footprint_first_cell(x, odd, &c, &f)) return false;
     } else {
         int e = (int)(b >> 52) - 1023;  // 0 <= e <= 15
         int sh = 52 - e;

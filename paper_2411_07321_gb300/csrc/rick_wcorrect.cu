@@ -65,11 +65,44 @@ __device__ __forceinline__ void wphase(const WcArgs &a, const float4 &wk, const 
     sincospif(2.0f * f, s, c);
 }
 
+// Phase factors e^{2 pi i w_k (n - 1)} of one pixel for k = 0 .. n_w - 1.  The
+// plane centres are equally spaced, w_k = w_0 + k dw, so the factor of plane k
+// is the previous one times the step e^{2 pi i dw (n - 1)}: one complex
+// multiply per plane.  Every RICK_PHASE_ANCHOR planes the factor is recomputed
+// exactly from w_k (double-single phase, sincospif), which bounds the FP32
+// drift of the recurrence to a few ulps.
+#define RICK_PHASE_ANCHOR 8
+
+struct PhaseWalker {
+    float c, s, cd, sd;
+    __device__ __forceinline__ void start(const WcArgs &a, const float4 *w, int n_w,
+                                          const PixelGeom &g)
+    {
+        if (a.flags & RICK_PHASE_FP32) {
+            cd = 1.0f;
+            sd = 0.0f;
+            return;
+        }
+        float fd = ff_frac(ff_mul(ff{w[n_w].x, w[n_w].y}, g.nm1));
+        sincospif(2.0f * fd, &sd, &cd);
+    }
+    __device__ __forceinline__ void at(const WcArgs &a, const float4 *w, int k, const PixelGeom &g)
+    {
+        if ((a.flags & RICK_PHASE_FP32) || k % RICK_PHASE_ANCHOR == 0) {
+            wphase(a, w[k], g, &c, &s);
+        } else {
+            float c2 = c * cd - s * sd;
+            s = s * cd + c * sd;
+            c = c2;
+        }
+    }
+};
+
 __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
 {
     extern __shared__ float4 s_w[];
     __shared__ float s_inv_sumw;
-    for (int k = threadIdx.x; k < a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
+    for (int k = threadIdx.x; k <= a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
     if (threadIdx.x == 0) {
         double sw = a.hdr->stats.sum_weight;  // nothing gridded: no normalisation
         s_inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
@@ -82,12 +115,13 @@ __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
     PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
     float acc = 0.0f;
     const float2 *src = a.planes_in + idx;
+    PhaseWalker ph;
+    ph.start(a, s_w, a.n_w, g);
 #pragma unroll 4
     for (int k = 0; k < a.n_w; ++k) {
         float2 F = src[(size_t)k * nn];
-        float c, s;
-        wphase(a, s_w[k], g, &c, &s);
-        acc = fmaf(F.x, c, fmaf(-F.y, s, acc));
+        ph.at(a, s_w, k, g);
+        acc = fmaf(F.x, ph.c, fmaf(-F.y, ph.s, acc));
     }
     a.image_out[idx] = acc * g.scale;
 }
@@ -96,7 +130,7 @@ __global__ void __launch_bounds__(256) wspread_kernel(WcArgs a)
 {
     extern __shared__ float4 s_w[];
     __shared__ float s_inv_sumw;
-    for (int k = threadIdx.x; k < a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
+    for (int k = threadIdx.x; k <= a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
     if (threadIdx.x == 0) {
         double sw = a.hdr->stats.sum_weight;  // nothing gridded: no normalisation
         s_inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
@@ -109,11 +143,12 @@ __global__ void __launch_bounds__(256) wspread_kernel(WcArgs a)
     PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
     float v = a.image_in[idx] * g.scale;
     float2 *dst = a.planes_out + idx;
+    PhaseWalker ph;
+    ph.start(a, s_w, a.n_w, g);
 #pragma unroll 4
     for (int k = 0; k < a.n_w; ++k) {
-        float c, s;
-        wphase(a, s_w[k], g, &c, &s);
-        dst[(size_t)k * nn] = make_float2(v * c, -v * s);
+        ph.at(a, s_w, k, g);
+        dst[(size_t)k * nn] = make_float2(v * ph.c, -v * ph.s);
     }
 }
 
@@ -156,7 +191,7 @@ extern "C" rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_d
     a.planes_in = (const float2 *)planes_dev;
     a.image_out = image_dev;
     size_t nn = (size_t)a.n * a.n;
-    wcorrect_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * a.n_w,
+    wcorrect_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
                       (cudaStream_t)stream>>>(a);
     RICK_LAUNCH_CHECK(plan);
     return RICK_OK;
@@ -173,7 +208,7 @@ extern "C" rick_status rick_wspread(rick_plan *plan, const float *image_dev, con
     a.image_in = image_dev;
     a.planes_out = (float2 *)planes_dev;
     size_t nn = (size_t)a.n * a.n;
-    wspread_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * a.n_w,
+    wspread_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
                      (cudaStream_t)stream>>>(a);
     RICK_LAUNCH_CHECK(plan);
     return RICK_OK;

@@ -163,7 +163,7 @@ def rick_bin(plan, n_vis, uvw, vis, weight, ws, ws_bytes, stats, stream) -> None
 
 def rick_bin_noalloc(plan, n_vis, uvw, vis, weight, ws, ws_bytes, stats, stream) -> None:
     """rick_bin without allocations: temporaries in the library's fixed array
-    (n_vis <= 262144, at most 262144 bins)."""
+    (n_vis <= 262144, at most 131072 bins)."""
     _check("rick_bin_noalloc", _L.rick_bin_noalloc(plan, int(n_vis), uvw, vis, weight or None, ws,
                                                    int(ws_bytes), stats or None, stream or None))
 

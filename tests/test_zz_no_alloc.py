@@ -85,7 +85,7 @@ def test_noalloc_rejects_sizes_beyond_its_array(P):
     assert e.value.status == R.RICK_ERANGE
     im.close()
     big = P.Imager(1024, 5, 0.05, kernel="kb", support=7, tile=8, max_vis=1000, device=dev)
-    with pytest.raises(R.RickError) as e:  # 4 * 5 * 128^2 = 327680 bins > 262144
+    with pytest.raises(R.RickError) as e:  # 4 * 5 * 128^2 = 327680 bins > 131072
         R.rick_bin_noalloc(big.plan, 10, uvw.data_ptr(), vis.data_ptr(), None, big.ws.data_ptr(),
                            big.ws_bytes, None, torch.cuda.current_stream().cuda_stream)
     assert e.value.status == R.RICK_ERANGE
