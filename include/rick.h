@@ -206,6 +206,16 @@ rick_status rick_bin_values(rick_plan *plan, const void *vis_dev, const float *w
  * overlap on the device. */
 rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream);
 
+/* rick_grid that adds into planes_dev instead of overwriting it: planes_dev
+ * must already hold planes (a rick_grid result, or zeros) of the same plan
+ * geometry and w range.  Gridding is linear in the records, so gridding the
+ * chunks of a visibility set one after another -- rick_bin + rick_grid for
+ * the first, rick_bin + rick_grid_accumulate for the rest, all binned with the
+ * same w range -- gives the planes of the whole set (up to FP32 summation
+ * order).  Tiles written by one work item are read, added to and written;
+ * tiles of several work items add with float atomics. */
+rick_status rick_grid_accumulate(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream);
+
 /* Per-plane 2D FFT (§2 step 3, §3.1): cuFFT complex64, unnormalised, in place,
  * batched over the n_w planes.  direction +1: inverse (e^{+2 pi i}), used for
  * imaging; -1: forward, used by degridding. */
@@ -235,6 +245,47 @@ rick_status rick_wspread(rick_plan *plan, const float *image_dev, const void *ws
  *   vis_out_dev: complex64 [n_vis] */
 rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
                         const float *weight_dev, void *vis_out_dev, void *stream);
+
+/* Imaging a visibility set held in HOST memory, streamed through the GPU in
+ * chunks (§4: visibilities are read in sequential chunks; §3.2 counts the
+ * offload to the GPU in the gridding time).  The set is cut into chunks of at
+ * most the plan's max_vis visibilities.  A copy stream owned by the plan
+ * moves chunk c + 1 into one of two staging buffers while `stream` bins chunk
+ * c and grids it into planes_dev (rick_grid for the first chunk,
+ * rick_grid_accumulate after); rick_fft_wplanes and rick_wcorrect_stack then
+ * run once.  The image is that of rick_bin + rick_grid + rick_fft_wplanes +
+ * rick_wcorrect_stack over the whole set, up to FP32 summation order; the weight
+ * sum and drop counts are totals over the chunks, added in chunk order.
+ * The w range is the plan's; if it is (NaN, NaN), the exact range of the
+ * whole set: uvw is then first copied, in chunks, into a device-resident
+ * array in the staging buffer, each chunk's range folded in as it lands, and
+ * every chunk is binned with that range (so nothing is dropped that the
+ * range-from-data binning keeps).  With a given range nothing of the set stays
+ * resident, so the set may be larger than device memory.
+ *   uvw_host, vis_host, weight_host: host arrays laid out as for rick_bin
+ *               (weight NULL: unit weights).  Page-locked memory
+ *               (cudaHostAlloc, cudaHostRegister) lets copies overlap compute;
+ *               pageable memory is accepted and copied without overlap.  They
+ *               must not change until the work is complete.
+ *   ws_dev, ws_bytes:       workspace of rick_workspace_bytes(params, max_vis)
+ *   stage_dev, stage_bytes: staging area of rick_stream_bytes(params, max_vis,
+ *               n_vis) bytes, 256-byte aligned
+ *   planes_dev: complex64 [n_w][n][n], overwritten
+ *   image_dev:  float32 [n][n]; flags as for rick_wcorrect_stack
+ *   stats_dev:  device rick_bin_stats of the whole set, or NULL
+ * Work is enqueued on `stream` and on the plan's copy stream, which waits for
+ * earlier work on `stream` before it touches the staging area; the call is
+ * complete when `stream` is.  Afterwards ws_dev holds the last chunk's binning
+ * with the whole set's stats.  Errors: RICK_EINVAL (NULL pointer,
+ * misalignment), RICK_ERANGE (stage_bytes or ws_bytes too small, max_vis ==
+ * 0 with n_vis > 0), RICK_ECUDA, RICK_ECUFFT. */
+rick_status rick_stream_bytes(const rick_params *params, int64_t max_vis, int64_t n_vis,
+                              size_t *bytes);
+rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_host,
+                            const void *vis_host, const float *weight_host, void *ws_dev,
+                            size_t ws_bytes, void *stage_dev, size_t stage_bytes,
+                            void *planes_dev, float *image_dev, uint32_t flags,
+                            rick_bin_stats *stats_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -86,18 +86,30 @@ static cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32
 // ------------------------------------------------------------------------
 // Pass 1: w range
 
+// range_src (optional): a header whose w-range keys stand in for a given
+// range (the exact range of a larger set, found by an earlier pass).
 __global__ void bin_init_kernel(WsHeader *hdr, uint64_t n_vis, uint32_t chunk_cap, int given,
-                                uint64_t wmin_key, uint64_t wmax_key, uint32_t n_key_blocks)
+                                uint64_t wmin_key, uint64_t wmax_key, uint32_t n_key_blocks,
+                                const WsHeader *range_src)
 {
     hdr->n_vis = n_vis;
     hdr->drop_uv = 0;
     hdr->drop_w = 0;
     hdr->chunk_cap = chunk_cap;
-    hdr->range_given = given;
     hdr->n_key_blocks = n_key_blocks;
+    if (range_src) {
+        given = 1;
+        wmin_key = range_src->wmin_key;
+        wmax_key = range_src->wmax_key;
+    }
+    hdr->range_given = given;
     hdr->wmin_key = given ? wmin_key : ~0ull;
     hdr->wmax_key = given ? wmax_key : 0ull;
 }
+
+// Launch the w-range reduction of uvw[0, n) into hdr's range keys.
+void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
+                        cudaStream_t st);
 
 __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr)
 {
@@ -119,6 +131,12 @@ __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr)
         if (lo != ~0ull) atomicMin(&hdr->wmin_key, (unsigned long long)lo);
         if (hi != 0ull) atomicMax(&hdr->wmax_key, (unsigned long long)hi);
     }
+}
+
+void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
+                        cudaStream_t st)
+{
+    wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr);
 }
 
 // ------------------------------------------------------------------------
@@ -388,9 +406,9 @@ __global__ void tile_count_kernel(const uint32_t *off, uint32_t *gcnt, uint32_t 
 
 // ------------------------------------------------------------------------
 
-extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw,
-                                const void *vis, const float *weight, void *ws_dev,
-                                size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
+rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, const void *vis,
+                          const float *weight, void *ws_dev, size_t ws_bytes,
+                          rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src)
 {
     if (!plan || !ws_dev || n_vis < 0) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
@@ -406,12 +424,13 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
                         (RICK_KEY_THREADS * RICK_KEY_ITEMS);
     WsPtrs w = rick_ws_ptrs(ws_dev, L);
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
-    int given = !isnan(p.w_min);
+    uint32_t cap = rick_chunk_cap(n_vis, plan->num_sms);
+    int given = !isnan(p.w_min) || range_src != NULL;
 
     bin_init_kernel<<<1, 1, 0, st>>>(w.hdr, (uint64_t)n_vis, cap, given,
-                                     given ? rick_dkey(p.w_min) : 0, given ? rick_dkey(p.w_max) : 0,
-                                     (uint32_t)nkb);
+                                     isnan(p.w_min) ? 0 : rick_dkey(p.w_min),
+                                     isnan(p.w_min) ? 0 : rick_dkey(p.w_max), (uint32_t)nkb,
+                                     range_src);
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
         int blocks = plan->num_sms * 4;
@@ -466,6 +485,13 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
         RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
                                             cudaMemcpyDeviceToDevice, st));
     return RICK_OK;
+}
+
+extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw,
+                                const void *vis, const float *weight, void *ws_dev,
+                                size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
+{
+    return rick_bin_impl(plan, n_vis, uvw, vis, weight, ws_dev, ws_bytes, stats_dev, stream, NULL);
 }
 
 extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const float *weight,
@@ -565,13 +591,13 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     w.scan = (uint32_t *)(scratch + NOALLOC_SCAN);
     w.wpart = (double *)(scratch + NOALLOC_WPART);
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
+    uint32_t cap = rick_chunk_cap(n_vis, plan->num_sms);
     int given = !isnan(p.w_min);
 
     // the same stages as rick_bin, in the same order
     bin_init_kernel<<<1, 1, 0, st>>>(w.hdr, (uint64_t)n_vis, cap, given,
                                      given ? rick_dkey(p.w_min) : 0, given ? rick_dkey(p.w_max) : 0,
-                                     (uint32_t)nkb);
+                                     (uint32_t)nkb, NULL);
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
         wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr);

@@ -82,6 +82,15 @@ struct rick_plan {
     KernelPoly poly;   // kernel-weight polynomials (host copy, passed to kernels)
     rick_status sticky;
     unsigned long long launches;  // library kernels enqueued so far (cuFFT's not included)
+    // streaming from host memory (created on first use): the copy stream and
+    // its events -- start of a call, chunk copied into staging buffer b,
+    // staging buffer b free again, uvw chunk resident, resident uvw area a
+    // free again -- and the staging area of the last call with its parity
+    cudaStream_t copy;
+    cudaEvent_t ev_start, ev_ready[2], ev_free[2], ev_uvw, ev_area_free[2];
+    void *stage_prev;
+    size_t stage_prev_bytes;
+    int parity;
 };
 
 // ------------------------------------------------------------------------
@@ -192,8 +201,9 @@ static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
     return w;
 }
 
-// Records per work item of the tile kernels: about 16 items per SM in total,
-// at least 1024.
+// Records per work item of the tile kernels for a binning of n_vis
+// visibilities: about 16 items per SM in total, at least 1024.  Set by the
+// binning in the workspace header, where the tile kernels read it.
 static inline uint32_t rick_chunk_cap(int64_t n_vis, int num_sms)
 {
     int64_t c = (n_vis + (int64_t)num_sms * 16 - 1) / ((int64_t)num_sms * 16);
@@ -438,9 +448,24 @@ __device__ __forceinline__ float ff_frac(ff t)
 // Launch arguments shared by the tile kernels.
 struct TileArgs {
     int n, n_w, T, nt, W;
-    uint32_t ntiles, chunk_cap;
+    uint32_t ntiles;
     const uint32_t *offsets, *base, *perm, *rcell;
     const float4 *rec;
     WsHeader *hdr;
     KernelPoly kp;
 };
+
+// ------------------------------------------------------------------------
+// Internal entry points shared by the translation units
+
+// rick_bin; range_src (device, optional) supplies the w range in place of the
+// plan's (a range found over a larger set by an earlier pass).
+rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, const void *vis,
+                          const float *weight, void *ws_dev, size_t ws_bytes,
+                          rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src);
+// Min/max keys of the finite w of uvw[0, n) folded into hdr->wmin_key / wmax_key.
+void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
+                        cudaStream_t st);
+// rick_grid (accumulate = 0) or rick_grid_accumulate (1).
+rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int accumulate,
+                           void *stream);

@@ -22,6 +22,7 @@ struct GridArgs {
     TileArgs t;
     float2 *planes;
     int log2T;
+    int accumulate;  // add into the planes instead of overwriting them
 };
 
 struct DegridArgs {
@@ -180,8 +181,9 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
         rl[3] = off[4 * (t - nt - 1) + 3] - rs[3];
     }
     const uint32_t Ltot = rl[0] + rl[1] + rl[2] + rl[3];
-    const uint32_t vbeg = chunk * ta.chunk_cap;
-    const uint32_t vend = min(Ltot, vbeg + ta.chunk_cap);
+    const uint32_t cap = ta.hdr->chunk_cap;
+    const uint32_t vbeg = chunk * cap;
+    const uint32_t vend = min(Ltot, vbeg + cap);
 
     // accumulators with padded rows (stride T + 1): the lanes of a group own
     // different rows, which then fall in different banks
@@ -240,8 +242,11 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
             im = -im;
         }
         float2 *dst = plane + (size_t)gj * n + gi;
-        if (nch == 1) {
+        if (nch == 1 && !a.accumulate) {
             *dst = make_float2(re, im);
+        } else if (nch == 1) {  // the only writer of this tile in this launch
+            float2 o = *dst;
+            *dst = make_float2(o.x + re, o.y + im);
         } else if (re != 0.0f || im != 0.0f) {
             atomicAdd(dst, make_float2(re, im));
         }
@@ -280,12 +285,14 @@ __global__ void __launch_bounds__(256, 3) grid_kernel(GridArgs a)
 
 // Zero every tile that is not written by exactly one grid work item: tiles
 // without records (no work item) and tiles whose chunks add into them with
-// atomics.  Grid-stride, one warp per tile, 16-byte stores.
+// atomics.  Grid-stride, one warp per tile, 16-byte stores.  When gridding
+// adds into existing planes only the work counter is reset.
 __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, uint32_t ntiles,
                                                          int nt, int log2T, int n, float2 *planes,
-                                                         WsHeader *hdr)
+                                                         WsHeader *hdr, int accumulate)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->grid_next = 0;
+    if (accumulate) return;
     int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -311,8 +318,9 @@ __device__ __forceinline__ void degrid_item(const DegridArgs &a, uint32_t b, uin
     const int T = 1 << a.log2T, S = T + W - 1, nt = ta.nt, n = ta.n;
     const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
     const int x0 = tx << a.log2T, y0 = ty << a.log2T;
-    const uint32_t r0 = ta.offsets[4 * t] + chunk * ta.chunk_cap;
-    const uint32_t r1 = min(ta.offsets[4 * t + 4], r0 + ta.chunk_cap);
+    const uint32_t cap = ta.hdr->chunk_cap;
+    const uint32_t r0 = ta.offsets[4 * t] + chunk * cap;
+    const uint32_t r1 = min(ta.offsets[4 * t + 4], r0 + cap);
 
     const float2 *plane = a.planes + (size_t)k * n * n;
     for (int i = threadIdx.x; i < S * S; i += blockDim.x) {
@@ -389,8 +397,7 @@ __global__ void degrid_zero_dropped_kernel(WsHeader *hdr, const uint32_t *key, f
 
 // ------------------------------------------------------------------------
 
-static TileArgs make_tile_args(const rick_plan *plan, const WsPtrs &w, const uint32_t *base,
-                               uint32_t cap)
+static TileArgs make_tile_args(const rick_plan *plan, const WsPtrs &w, const uint32_t *base)
 {
     const rick_params &p = plan->p;
     TileArgs t;
@@ -400,7 +407,6 @@ static TileArgs make_tile_args(const rick_plan *plan, const WsPtrs &w, const uin
     t.nt = p.n / p.tile;
     t.W = p.support;
     t.ntiles = (uint32_t)p.n_w * t.nt * t.nt;
-    t.chunk_cap = cap;
     t.offsets = w.offsets;
     t.base = base;
     t.perm = w.perm;
@@ -476,8 +482,8 @@ static cudaError_t launch_degrid(const DegridArgs &a, int num_sms, cudaStream_t 
     default: err = cudaErrorInvalidValue; \
     }
 
-extern "C" rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev,
-                                 void *stream)
+rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int accumulate,
+                           void *stream)
 {
     if (!plan || !ws_dev || !planes_dev) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
@@ -485,14 +491,14 @@ extern "C" rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev
     const rick_params &p = plan->p;
     WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&p, plan->max_vis));
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
     GridArgs a;
-    a.t = make_tile_args(plan, w, w.gbase, cap);
+    a.t = make_tile_args(plan, w, w.gbase);
     a.planes = (float2 *)planes_dev;
     a.log2T = ilog2(p.tile);
+    a.accumulate = accumulate;
     cudaError_t err = cudaSuccess;
-    zero_tiles_kernel<<<plan->num_sms * 8, 256, 0, st>>>(w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n,
-                                                          a.planes, w.hdr);
+    zero_tiles_kernel<<<accumulate ? 1 : plan->num_sms * 8, 256, 0, st>>>(
+        w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate);
     RICK_LAUNCH_CHECK(plan);
     bool comp = p.precision == RICK_PREC_FP32_COMPENSATED;
 #define CALL_GRID(WW) err = launch_grid<WW>(a, comp, plan->num_sms, st)
@@ -501,6 +507,17 @@ extern "C" rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev
     ++plan->launches;
     RICK_CUDA_TRY(plan, err);
     return RICK_OK;
+}
+
+extern "C" rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream)
+{
+    return rick_grid_impl(plan, ws_dev, planes_dev, 0, stream);
+}
+
+extern "C" rick_status rick_grid_accumulate(rick_plan *plan, void *ws_dev, void *planes_dev,
+                                            void *stream)
+{
+    return rick_grid_impl(plan, ws_dev, planes_dev, 1, stream);
 }
 
 extern "C" rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
@@ -514,9 +531,8 @@ extern "C" rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *pl
     const rick_params &p = plan->p;
     WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&p, plan->max_vis));
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t cap = rick_chunk_cap(plan->max_vis, plan->num_sms);
     DegridArgs a;
-    a.t = make_tile_args(plan, w, w.dbase, cap);
+    a.t = make_tile_args(plan, w, w.dbase);
     a.planes = (const float2 *)planes_dev;
     a.weight = weight_dev;
     a.vis_out = (float2 *)vis_out_dev;

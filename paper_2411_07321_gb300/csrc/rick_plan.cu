@@ -169,6 +169,12 @@ static double bessel_i0_host(double x)
 static void plan_release(rick_plan *pl)
 {
     if (pl->fft) cufftDestroy(pl->fft);
+    cudaEvent_t evs[8] = {pl->ev_start,   pl->ev_ready[0],     pl->ev_ready[1],
+                          pl->ev_free[0],  pl->ev_free[1],      pl->ev_uvw,
+                          pl->ev_area_free[0], pl->ev_area_free[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (pl->copy) cudaStreamDestroy(pl->copy);
     if (pl->own) {
         if (pl->taper_inv) cudaFreeAsync(pl->taper_inv, pl->own);
         if (pl->fft_work) cudaFreeAsync(pl->fft_work, pl->own);

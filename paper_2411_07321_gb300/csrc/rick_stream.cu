@@ -1,0 +1,234 @@
+// rick_stream.cu -- imaging a visibility set that sits in host memory,
+// streamed through the GPU in chunks (§4 reads the visibilities in
+// sequential chunks; §3.2 counts the offload to the GPU as part of gridding).
+//
+// The set is cut into chunks of at most the plan's max_vis visibilities.  A
+// copy stream of the plan moves chunk c + 1 into one of two staging buffers
+// while the caller's stream bins chunk c and grids it into the planes: the
+// first chunk with rick_grid (every plane cell written), the later ones with
+// rick_grid_accumulate (gridding is linear in the records, so the sum over
+// chunks is the gridding of the whole set).  The plane FFT and the
+// w-correction then run once.  Gridded weight sums and drop counts are added
+// up over the chunks in chunk order, so the normalisation is that of the
+// whole set.
+//
+// The w-planes must be the same for every chunk.  With a given w range (the
+// plan's) every chunk uses it.  Without one, the range of the whole set is
+// needed before the first chunk is binned: uvw is then copied first, in
+// chunks, into a device-resident array, each chunk's w range folded in as it
+// lands, and only the visibilities and weights go through the staging
+// buffers.  Every chunk is binned with that exact range as a given range,
+// which drops nothing that the range-from-data binning keeps.  Calls
+// alternate between two such areas, so the uvw of the next call can land
+// while this call's chunks are still being binned.
+//
+// Calls of one plan that pass the same staging area overlap: the copy stream
+// waits only for the binnings that read a buffer before refilling it, so a
+// call's copies run under the previous call's gridding, FFT and w-correction.
+#include <math.h>
+
+#include "rick_common.cuh"
+
+struct StageLayout {
+    size_t range, total, vis, weight, uvw, bytes;
+    size_t uvw_buf, vis_buf, weight_buf;  // bytes of one staging buffer / resident area
+    int64_t chunk;
+    int resident_uvw;
+};
+
+// The staging area: the range header and stats totals, two chunk buffers of
+// vis and of weight, then either two chunk buffers of uvw (given w range) or
+// two resident uvw areas (range from the data), used by alternate calls.
+// The resident area size is fixed by stage_bytes (0: the size that holds
+// n_vis), so that calls with the same staging area agree on its layout.
+static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n_vis,
+                                size_t stage_bytes)
+{
+    StageLayout S;
+    S.chunk = max_vis > 0 ? max_vis : 1;
+    S.resident_uvw = isnan(p->w_min) ? 1 : 0;
+    S.vis_buf = rick_align256(8 * (size_t)S.chunk);
+    S.weight_buf = rick_align256(4 * (size_t)S.chunk);
+    size_t o = 0;
+    S.range = o;  o += rick_align256(sizeof(WsHeader));
+    S.total = o;  o += rick_align256(sizeof(rick_bin_stats));
+    S.vis = o;    o += 2 * S.vis_buf;
+    S.weight = o; o += 2 * S.weight_buf;
+    S.uvw = o;
+    if (!S.resident_uvw) {
+        S.uvw_buf = rick_align256(24 * (size_t)S.chunk);
+    } else if (stage_bytes == 0) {
+        S.uvw_buf = rick_align256(24 * (size_t)(n_vis > 0 ? n_vis : 1));
+    } else {
+        S.uvw_buf = stage_bytes > o ? (stage_bytes - o) / 2 / 256 * 256 : 0;
+    }
+    S.bytes = o + 2 * S.uvw_buf;
+    return S;
+}
+
+__global__ void range_init_kernel(WsHeader *rh)
+{
+    rh->wmin_key = ~0ull;
+    rh->wmax_key = 0ull;
+}
+
+// Running totals of the chunk binnings (first: start them).
+__global__ void stats_add_kernel(const WsHeader *hdr, rick_bin_stats *tot, int first)
+{
+    const rick_bin_stats &s = hdr->stats;
+    if (first) {
+        *tot = s;
+        return;
+    }
+    tot->n_binned += s.n_binned;
+    tot->n_dropped_uv += s.n_dropped_uv;
+    tot->n_dropped_w += s.n_dropped_w;
+    tot->sum_weight += s.sum_weight;
+    tot->w_min = s.w_min;
+    tot->w_max = s.w_max;
+}
+
+// The whole set's stats into the workspace header (read by the w-correction
+// for the weight sum) and to the caller.
+__global__ void stats_finish_kernel(WsHeader *hdr, const rick_bin_stats *tot, rick_bin_stats *out)
+{
+    hdr->stats = *tot;
+    if (out) *out = *tot;
+}
+
+extern "C" rick_status rick_stream_bytes(const rick_params *params, int64_t max_vis,
+                                         int64_t n_vis, size_t *bytes)
+{
+    if (!params || !bytes || max_vis < 0 || n_vis < 0) return RICK_EINVAL;
+    *bytes = stage_layout(params, max_vis, n_vis, 0).bytes;
+    return RICK_OK;
+}
+
+static rick_status stream_resources(rick_plan *plan)
+{
+    if (plan->copy) return RICK_OK;
+    cudaEvent_t *evs[8] = {&plan->ev_start,  &plan->ev_ready[0], &plan->ev_ready[1],
+                           &plan->ev_free[0], &plan->ev_free[1],  &plan->ev_uvw,
+                           &plan->ev_area_free[0], &plan->ev_area_free[1]};
+    for (cudaEvent_t *e : evs)
+        RICK_CUDA_TRY(plan, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    RICK_CUDA_TRY(plan, cudaStreamCreateWithFlags(&plan->copy, cudaStreamNonBlocking));
+    return RICK_OK;
+}
+
+#define RICK_TRY(expr)                      \
+    do {                                    \
+        rick_status s_ = (expr);            \
+        if (s_ != RICK_OK) return s_;       \
+    } while (0)
+
+extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_host,
+                                       const void *vis_host, const float *weight_host,
+                                       void *ws_dev, size_t ws_bytes, void *stage_dev,
+                                       size_t stage_bytes, void *planes_dev, float *image_dev,
+                                       uint32_t flags, rick_bin_stats *stats_dev, void *stream)
+{
+    if (!plan || !ws_dev || !stage_dev || !planes_dev || !image_dev || n_vis < 0)
+        return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (n_vis > 0 && (!uvw_host || !vis_host)) return RICK_EINVAL;
+    if (((uintptr_t)stage_dev & 255) || ((uintptr_t)ws_dev & 255) ||
+        ((uintptr_t)planes_dev & 15) || ((uintptr_t)image_dev & 3) ||
+        ((uintptr_t)stats_dev & 7) || ((uintptr_t)uvw_host & 7) || ((uintptr_t)vis_host & 7) ||
+        ((uintptr_t)weight_host & 3))
+        return RICK_EINVAL;
+    if (n_vis > 0 && plan->max_vis < 1) return RICK_ERANGE;
+    const StageLayout S = stage_layout(&plan->p, plan->max_vis, n_vis, stage_bytes);
+    if (stage_bytes < S.bytes || (S.resident_uvw && S.uvw_buf < 24 * (size_t)n_vis))
+        return RICK_ERANGE;
+    if (ws_bytes < rick_ws_layout(&plan->p, plan->max_vis).total) return RICK_ERANGE;
+    RICK_TRY(stream_resources(plan));
+
+    cudaStream_t st = (cudaStream_t)stream, cp = plan->copy;
+    char *sb = (char *)stage_dev;
+    WsHeader *rh = (WsHeader *)(sb + S.range);
+    rick_bin_stats *tot = (rick_bin_stats *)(sb + S.total);
+    WsHeader *hdr = rick_ws_ptrs(ws_dev, rick_ws_layout(&plan->p, plan->max_vis)).hdr;
+    const int64_t chunk = S.chunk;
+    const int64_t nchunks = n_vis > 0 ? (n_vis + chunk - 1) / chunk : 1;  // one empty chunk
+    const float2 *vh = (const float2 *)vis_host;
+
+    // Before the copy stream writes the staging area: for a staging area new
+    // to this plan, everything enqueued earlier on the caller's stream (the
+    // memory may have had other uses); for the same area as the plan's last
+    // call, only the binnings that read its buffers -- so the copies of this
+    // call overlap the previous call's gridding, FFT and w-correction.
+    if (stage_dev != plan->stage_prev || stage_bytes != plan->stage_prev_bytes) {
+        RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_start, st));
+        RICK_CUDA_TRY(plan, cudaStreamWaitEvent(cp, plan->ev_start, 0));
+        plan->stage_prev = stage_dev;
+        plan->stage_prev_bytes = stage_bytes;
+        plan->parity = 0;
+    }
+    const int area = plan->parity;
+    plan->parity ^= 1;
+
+    double *uvw_res = (double *)(sb + S.uvw + area * S.uvw_buf);
+    if (S.resident_uvw) {
+        // the call before last binned from this area
+        RICK_CUDA_TRY(plan, cudaStreamWaitEvent(cp, plan->ev_area_free[area], 0));
+        range_init_kernel<<<1, 1, 0, st>>>(rh);
+        RICK_LAUNCH_CHECK(plan);
+        for (int64_t c = 0; c < nchunks && n_vis > 0; ++c) {
+            const int64_t off = c * chunk, nc = n_vis - off < chunk ? n_vis - off : chunk;
+            RICK_CUDA_TRY(plan, cudaMemcpyAsync(uvw_res + 3 * off, uvw_host + 3 * off, 24 * nc,
+                                                cudaMemcpyHostToDevice, cp));
+            RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_uvw, cp));
+            RICK_CUDA_TRY(plan, cudaStreamWaitEvent(st, plan->ev_uvw, 0));
+            rick_launch_wrange(plan, uvw_res + 3 * off, nc, rh, st);
+            RICK_LAUNCH_CHECK(plan);
+        }
+    }
+
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int b = (int)(c & 1);
+        const int64_t off = c * chunk;
+        const int64_t nc = n_vis - off < chunk ? n_vis - off : chunk;
+        const double *uvw_c = NULL;
+        const void *vis_c = NULL;
+        const float *wt_c = NULL;
+        if (nc > 0) {
+            // staging buffer b was last read by the binning of chunk c - 2, or
+            // of one of the last two chunks of the previous call
+            RICK_CUDA_TRY(plan, cudaStreamWaitEvent(cp, plan->ev_free[b], 0));
+            if (S.resident_uvw) {
+                uvw_c = uvw_res + 3 * off;
+            } else {
+                double *ub = (double *)(sb + S.uvw + b * S.uvw_buf);
+                RICK_CUDA_TRY(plan, cudaMemcpyAsync(ub, uvw_host + 3 * off, 24 * nc,
+                                                    cudaMemcpyHostToDevice, cp));
+                uvw_c = ub;
+            }
+            float2 *vb = (float2 *)(sb + S.vis + b * S.vis_buf);
+            RICK_CUDA_TRY(plan, cudaMemcpyAsync(vb, vh + off, 8 * nc, cudaMemcpyHostToDevice, cp));
+            vis_c = vb;
+            if (weight_host) {
+                float *wb = (float *)(sb + S.weight + b * S.weight_buf);
+                RICK_CUDA_TRY(plan, cudaMemcpyAsync(wb, weight_host + off, 4 * nc,
+                                                    cudaMemcpyHostToDevice, cp));
+                wt_c = wb;
+            }
+            RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_ready[b], cp));
+            RICK_CUDA_TRY(plan, cudaStreamWaitEvent(st, plan->ev_ready[b], 0));
+        }
+        RICK_TRY(rick_bin_impl(plan, nc > 0 ? nc : 0, uvw_c, vis_c, wt_c, ws_dev, ws_bytes, NULL,
+                               st, S.resident_uvw ? rh : NULL));
+        // the binning has read staging buffer b (the records are in ws now)
+        RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_free[b], st));
+        stats_add_kernel<<<1, 1, 0, st>>>(hdr, tot, c == 0);
+        RICK_LAUNCH_CHECK(plan);
+        RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev, c > 0, st));
+    }
+    // every binning of this call has read its resident uvw area
+    RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_area_free[area], st));
+    stats_finish_kernel<<<1, 1, 0, st>>>(hdr, tot, stats_dev);
+    RICK_LAUNCH_CHECK(plan);
+    RICK_TRY(rick_fft_wplanes(plan, planes_dev, 1, st));
+    RICK_TRY(rick_wcorrect_stack(plan, planes_dev, ws_dev, image_dev, flags, st));
+    return RICK_OK;
+}

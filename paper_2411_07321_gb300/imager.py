@@ -162,6 +162,39 @@ class Imager:
         out_host.copy_(self._out_img, non_blocking=True)
         return out_host
 
+    def image_streamed(self, uvw_host: torch.Tensor, vis_host: torch.Tensor,
+                       weight_host: torch.Tensor | None, out_host: torch.Tensor | None = None,
+                       flags: int = IMAGE_FLAGS) -> torch.Tensor:
+        """The image of a visibility set in host memory, of any size, streamed
+        through the GPU in chunks of this imager's ``max_vis`` (copies of the
+        next chunk overlap binning and gridding of the current one; pinned
+        host tensors give the overlap).  Returns the device image, also copied
+        into ``out_host`` if given, all ordered on the current stream."""
+        n = uvw_host.shape[0]
+        for t, dt, shape, name in ((uvw_host, torch.float64, (n, 3), "uvw"),
+                                   (vis_host, torch.complex64, (n,), "vis"),
+                                   (weight_host, torch.float32, (n,), "weight")):
+            if t is None:
+                continue
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or \
+                    tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a contiguous {dt} host tensor of shape {shape}")
+        need = R.rick_stream_bytes(self.params, self.max_vis, n)
+        if getattr(self, "_stage", None) is None or self._stage.numel() < need:
+            self._stage = None
+            self._stage = torch.empty(need, dtype=torch.uint8, device=self.device)
+        if getattr(self, "_out_img", None) is None:
+            self._out_img = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
+        R.rick_image_host(self.plan, n, uvw_host.data_ptr(), vis_host.data_ptr(),
+                          _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
+                          self._stage.data_ptr(), self._stage.numel(), self.planes.data_ptr(),
+                          self._out_img.data_ptr(), flags, self.stats_buf.data_ptr(),
+                          self._stream())
+        self.n_vis = n - (n - 1) // self.max_vis * self.max_vis if n else 0  # the last chunk
+        if out_host is not None:
+            out_host.copy_(self._out_img, non_blocking=True)
+        return self._out_img
+
     def set_geometry(self, fov: float, w_range: tuple[float, float] | None = None):
         """Re-target the resident plan to another field of view / w range."""
         wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)

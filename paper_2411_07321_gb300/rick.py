@@ -52,8 +52,9 @@ class rick_bin_view(ctypes.Structure):
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
            "rick_plan_launch_count", "rick_plan_set_geometry",
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
-           "rick_bin_noalloc", "rick_bin_values",
-           "rick_grid", "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid"]
+           "rick_bin_noalloc", "rick_bin_values", "rick_grid", "rick_grid_accumulate",
+           "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
+           "rick_stream_bytes", "rick_image_host"]
 
 
 def _load():
@@ -79,6 +80,9 @@ def _load():
         "rick_bin_noalloc": [vp, i64, vp, vp, vp, vp, sz, vp, vp],
         "rick_bin_values": [vp, vp, vp, vp, vp, vp],
         "rick_grid": [vp, vp, vp, vp],
+        "rick_grid_accumulate": [vp, vp, vp, vp],
+        "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
+        "rick_image_host": [vp, i64, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32, vp, vp],
         "rick_fft_wplanes": [vp, vp, i32, vp],
         "rick_wcorrect_stack": [vp, vp, vp, vp, u32, vp],
         "rick_wspread": [vp, vp, vp, vp, u32, vp],
@@ -175,6 +179,26 @@ def rick_bin_values(plan, vis, weight, ws, stats, stream) -> None:
 
 def rick_grid(plan, ws, planes, stream) -> None:
     _check("rick_grid", _L.rick_grid(plan, ws, planes, stream or None))
+
+
+def rick_grid_accumulate(plan, ws, planes, stream) -> None:
+    _check("rick_grid_accumulate", _L.rick_grid_accumulate(plan, ws, planes, stream or None))
+
+
+def rick_stream_bytes(params: rick_params, max_vis: int, n_vis: int) -> int:
+    b = ctypes.c_size_t()
+    _check("rick_stream_bytes", _L.rick_stream_bytes(ctypes.byref(params), int(max_vis),
+                                                     int(n_vis), ctypes.byref(b)))
+    return b.value
+
+
+def rick_image_host(plan, n_vis, uvw_host, vis_host, weight_host, ws, ws_bytes, stage,
+                    stage_bytes, planes, image, flags, stats, stream) -> None:
+    """Streamed imaging from host arrays (host addresses for the inputs)."""
+    _check("rick_image_host", _L.rick_image_host(plan, int(n_vis), uvw_host, vis_host,
+                                                 weight_host or None, ws, int(ws_bytes), stage,
+                                                 int(stage_bytes), planes, image, int(flags),
+                                                 stats or None, stream or None))
 
 
 def rick_fft_wplanes(plan, planes, direction, stream) -> None:

@@ -77,3 +77,23 @@ def test_null_plan_rejected(R):
     assert R._L.rick_plan_last_error(None) == R.RICK_EINVAL
     v = R.rick_bin_view()
     assert R._L.rick_bin_layout(None, ctypes.byref(v)) == R.RICK_EINVAL
+
+
+def test_stream_bytes(R):
+    """Staging area of the streamed path: two chunk buffers of vis and weight,
+    plus two of uvw (given w range) or two areas holding the whole set's uvw,
+    resident while its w range is found and used by alternate calls (range
+    from the data)."""
+    al = lambda x: (x + 255) // 256 * 256
+    chunk, n = 100_000, 1_234_567
+    given = R.make_params(256, 8, 0.035, 1, 7, w_min=-10.0, w_max=10.0, tile=32)
+    data = R.make_params(256, 8, 0.035, 1, 7, tile=32)
+    head = R.rick_stream_bytes(given, chunk, n) - 2 * (al(24 * chunk) + al(8 * chunk) +
+                                                       al(4 * chunk))
+    assert 0 < head <= 4096
+    assert R.rick_stream_bytes(data, chunk, n) == head + 2 * (al(24 * n) + al(8 * chunk) +
+                                                              al(4 * chunk))
+    # a given range keeps nothing of the set resident: independent of n
+    assert R.rick_stream_bytes(given, chunk, 10 * n) == R.rick_stream_bytes(given, chunk, n)
+    with pytest.raises(R.RickError):
+        R.rick_stream_bytes(given, -1, n)
