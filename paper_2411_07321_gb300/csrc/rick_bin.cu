@@ -308,31 +308,58 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
 // ------------------------------------------------------------------------
 // Pass 5: scatter records into their bins
 
+// Each thread takes RICK_SCATTER_U inputs per pass (256 apart), so that the
+// dependent chain of one input -- key load, cursor atomic, sub-offset load,
+// record stores -- overlaps those of the others.
+#define RICK_SCATTER_U 4
+
 __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const float2 *vis,
                                                           const float *weight, WsPtrs ws)
 {
-    int lane = threadIdx.x & 31;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n_vis;
-         i0 += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
-        uint32_t key = i < n_vis ? ws.key[i] : 0xFFFFFFFFu;
-        unsigned peers = __match_any_sync(FULL, key);
-        int leader = __ffs(peers) - 1;
-        // the sub-counter of the key pass's block that held this input
-        const uint32_t sub =
-            (uint32_t)((i0 / (RICK_KEY_THREADS * RICK_KEY_ITEMS)) & (RICK_BIN_SUBS - 1));
-        const uint32_t slot = key * RICK_BIN_SUBS + sub;
-        uint32_t b = 0;
-        if (key != 0xFFFFFFFFu && lane == leader) b = atomicAdd(&ws.hist[slot], (uint32_t)__popc(peers));
-        b = __shfl_sync(FULL, b, leader);
-        if (key != 0xFFFFFFFFu) {
-            uint32_t pos = ws.suboff[slot] + b + __popc(peers & ((1u << lane) - 1));
-            float2 v = vis[i];
-            float wt = weight ? weight[i] : 1.0f;
-            ws.perm[pos] = (uint32_t)i;
-            float2 fr = ws.frac[i];
-            ws.rec[pos] = make_float4(v.x * wt, v.y * wt, fr.x, fr.y);
-            ws.rcell[pos] = ws.cell[i];
+    constexpr int U = RICK_SCATTER_U;
+    const int lane = threadIdx.x & 31;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * U;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * U; i0 < n_vis; i0 += step) {
+        int64_t idx[U];
+        uint32_t key[U], slot[U], cl[U], b[U];
+        unsigned peers[U];
+        float2 v[U], fr[U];
+        float wt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            idx[u] = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+            key[u] = idx[u] < n_vis ? ws.key[idx[u]] : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (key[u] != 0xFFFFFFFFu) {
+                v[u] = vis[idx[u]];
+                wt[u] = weight ? weight[idx[u]] : 1.0f;
+                fr[u] = ws.frac[idx[u]];
+                cl[u] = ws.cell[idx[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            // the sub-counter of the key pass's block that held this input
+            const uint32_t sub =
+                (uint32_t)((idx[u] / (RICK_KEY_THREADS * RICK_KEY_ITEMS)) & (RICK_BIN_SUBS - 1));
+            slot[u] = key[u] * RICK_BIN_SUBS + sub;
+            peers[u] = __match_any_sync(FULL, key[u]);
+            b[u] = 0;
+            if (key[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
+                b[u] = atomicAdd(&ws.hist[slot[u]], (uint32_t)__popc(peers[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t bb = __shfl_sync(FULL, b[u], __ffs(peers[u]) - 1);
+            if (key[u] != 0xFFFFFFFFu) {
+                const uint32_t pos =
+                    ws.suboff[slot[u]] + bb + __popc(peers[u] & ((1u << lane) - 1));
+                ws.perm[pos] = (uint32_t)idx[u];
+                ws.rec[pos] = make_float4(v[u].x * wt[u], v[u].y * wt[u], fr[u].x, fr[u].y);
+                ws.rcell[pos] = cl[u];
+            }
         }
     }
 }
@@ -470,8 +497,8 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     RICK_LAUNCH_CHECK(plan);
     if (n_vis > 0) {
         RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
-        int64_t blocks = (n_vis + 255) / 256;
-        if (blocks > (int64_t)plan->num_sms * 32) blocks = (int64_t)plan->num_sms * 32;
+        int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
+        if (blocks > (int64_t)plan->num_sms * 16) blocks = (int64_t)plan->num_sms * 16;
         bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
         RICK_LAUNCH_CHECK(plan);
     }
@@ -636,8 +663,8 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     RICK_LAUNCH_CHECK(plan);
     if (n_vis > 0) {
         RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
-        int64_t blocks = (n_vis + 255) / 256;
-        if (blocks > (int64_t)plan->num_sms * 32) blocks = (int64_t)plan->num_sms * 32;
+        int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
+        if (blocks > (int64_t)plan->num_sms * 16) blocks = (int64_t)plan->num_sms * 16;
         bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
         RICK_LAUNCH_CHECK(plan);
     }

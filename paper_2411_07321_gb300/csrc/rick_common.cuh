@@ -152,8 +152,9 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
     L.cell = o;   o += rick_align256(4 * (size_t)nv);
     L.frac = o;   o += rick_align256(8 * (size_t)nv);
     L.perm = o;   o += rick_align256(4 * (size_t)nv);
-    L.rec = o;    o += rick_align256(16 * (size_t)nv);
-    L.rcell = o;  o += rick_align256(4 * (size_t)nv);
+    // one record of padding: the gridding loop reads one record ahead
+    L.rec = o;    o += rick_align256(16 * (size_t)(nv + 1));
+    L.rcell = o;  o += rick_align256(4 * (size_t)(nv + 1));
     L.hist = o;   o += rick_align256(4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1));
     L.suboff = o; o += rick_align256(4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1));
     L.offsets = o; o += rick_align256(4 * (size_t)(L.nbins + 1));
@@ -255,8 +256,27 @@ RICK_HD int rick_clz64(uint64_t x)
 
 // Round the exact value s * 2^-sh (|s| < 2^53, s != 0, 0 <= sh <= 60) to the
 // nearest float, ties to even, with integer operations only.
+//
+// Device path: normalise |s| so that its top bit is bit 63, keep the upper 32
+// bits with every lower bit ORed into their lowest bit (a sticky bit), and let
+// the hardware round that 32-bit integer to float.  The kept integer has 32
+// significant bits, so the rounding position is bit 8 and the round bit bit 7;
+// folding the discarded bits into bit 0 changes neither, and keeps "exactly
+// half way" and "above half way" apart -- the result is the correctly rounded
+// value of s.  Scaling by the power of two 2^(32 - lz - sh) is exact.
 RICK_HD float rick_scaled_int_to_float(int64_t s, int sh)
 {
+#if defined(__CUDA_ARCH__)
+    {
+        const uint64_t mag = s < 0 ? (uint64_t)(-s) : (uint64_t)s;
+        const int lz = __clzll((long long)mag);
+        const uint64_t norm = mag << lz;
+        const uint32_t top = (uint32_t)(norm >> 32) | ((uint32_t)norm != 0u ? 1u : 0u);
+        const float f = __uint2float_rn(top) * __int_as_float((32 - lz - sh + 127) << 23);
+        return s < 0 ? -f : f;
+    }
+#endif
+
     uint32_t sign = s < 0 ? 0x80000000u : 0u;
     uint64_t mag = s < 0 ? (uint64_t)(-s) : (uint64_t)s;
     int lz = rick_clz64(mag);

@@ -113,12 +113,9 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
     float4 q = rec[0];
     uint32_t cell = cur;
     for (uint32_t i = 0; i < n; ++i) {
-        float4 nq = q;
-        uint32_t ncell = cell;
-        if (i + 1 < n) {  // prefetch the next record
-            nq = rec[i + 1];
-            ncell = rcell[i + 1];
-        }
+        // prefetch the next record (the record arrays end with one of padding)
+        const float4 nq = rec[i + 1];
+        const uint32_t ncell = rcell[i + 1];
         if (cell != cur) {
             group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
                            (int)(cur >> 16) - y0 + j, live, ar, ai);
@@ -181,6 +178,13 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
         rl[3] = off[4 * (t - nt - 1) + 3] - rs[3];
     }
     const uint32_t Ltot = rl[0] + rl[1] + rl[2] + rl[3];
+    // the ranges in shared memory, for a loop over them that is not unrolled
+    // (one copy of the record loop keeps the kernel small)
+    __shared__ uint32_t s_rs[4], s_rl[4];
+    if (threadIdx.x < 4) {
+        s_rs[threadIdx.x] = rs[threadIdx.x];
+        s_rl[threadIdx.x] = rl[threadIdx.x];
+    }
     const uint32_t cap = ta.hdr->chunk_cap;
     const uint32_t vbeg = chunk * cap;
     const uint32_t vend = min(Ltot, vbeg + cap);
@@ -208,13 +212,14 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
         const uint32_t per = (re - rb + nstreams - 1) / nstreams;
         uint32_t v0 = min(rb + stream * per, re), v1 = min(v0 + per, re);
         uint32_t base = 0;
-#pragma unroll
+#pragma unroll 1
         for (int g = 0; g < 4; ++g) {
-            uint32_t a0 = max(v0, base), a1 = min(v1, base + rl[g]);
+            const uint32_t lg = s_rl[g];
+            uint32_t a0 = max(v0, base), a1 = min(v1, base + lg);
             if (a0 < a1)
-                grid_stream<W>(ta, rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
+                grid_stream<W>(ta, s_rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
                                coef);
-            base += rl[g];
+            base += lg;
         }
         if (COMP) {
             __syncthreads();
@@ -255,8 +260,11 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
 
 // Persistent: one wave of CTAs takes work items (tile, chunk) from a counter
 // in the workspace header (reset by zero_tiles_kernel, launched just before).
+// Four CTAs per SM for W <= 8 (64 registers a thread): the record loop is
+// latency-bound, and the extra warps hide more of it than the few spilled
+// registers cost.
 template <int W, bool COMP>
-__global__ void __launch_bounds__(256, 3) grid_kernel(GridArgs a)
+__global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(GridArgs a)
 {
     extern __shared__ float sm[];
     __shared__ uint32_t s_b, s_tile;
