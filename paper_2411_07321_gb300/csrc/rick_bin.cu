@@ -179,6 +179,27 @@ struct KeyArgs {
     WsPtrs ws;
 };
 
+// Lanes that start a run of equal keys (lane 0, or a key unlike the previous
+// lane's), as a warp ballot.
+__device__ __forceinline__ unsigned run_starts(uint32_t key, int lane)
+{
+    const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+    return __ballot_sync(FULL, lane == 0 || key != prev);
+}
+
+// One past the last lane of the run that starts at or before `lane`.
+__device__ __forceinline__ int run_end(unsigned starts, int lane)
+{
+    const unsigned after = lane == 31 ? 0u : starts & (0xFFFFFFFFu << (lane + 1));
+    return after ? __ffs(after) - 1 : 32;
+}
+
+// First lane of the run that holds `lane`.
+__device__ __forceinline__ int run_begin(unsigned starts, int lane)
+{
+    return 31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
+}
+
 __device__ __forceinline__ uint32_t plane_of(uint64_t kw, const unsigned long long *sb, int nb)
 {
     int lo = 0, hi = nb;  // number of boundaries <= w
@@ -246,12 +267,13 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
             }
             a.ws.key[i] = key;
         }
-        // histogram: one atomic per distinct key of the warp, on this block's
-        // sub-counter of the bin
-        unsigned peers = __match_any_sync(FULL, key);
-        if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+        // histogram, on this block's sub-counter of the bin: one atomic per run
+        // of equal keys in consecutive lanes (consecutive inputs -- the
+        // channels of one baseline and time -- mostly share a key)
+        const unsigned starts = run_starts(key, lane);
+        if (key != 0xFFFFFFFFu && ((starts >> lane) & 1u))
             atomicAdd(&a.ws.hist[key * RICK_BIN_SUBS + (blockIdx.x & (RICK_BIN_SUBS - 1))],
-                      (uint32_t)__popc(peers));
+                      (uint32_t)(run_end(starts, lane) - lane));
     }
     // deterministic block reduction of the weight sum (double-single pairs in
     // the warp: GB300 issues FP64 slowly) and of the drop counts
@@ -322,7 +344,7 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * U; i0 < n_vis; i0 += step) {
         int64_t idx[U];
         uint32_t key[U], slot[U], cl[U], b[U];
-        unsigned peers[U];
+        unsigned starts[U];
         float2 v[U], fr[U];
         float wt[U];
 #pragma unroll
@@ -345,17 +367,18 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
             const uint32_t sub =
                 (uint32_t)((idx[u] / (RICK_KEY_THREADS * RICK_KEY_ITEMS)) & (RICK_BIN_SUBS - 1));
             slot[u] = key[u] * RICK_BIN_SUBS + sub;
-            peers[u] = __match_any_sync(FULL, key[u]);
+            // one cursor atomic per run of equal keys in consecutive lanes
+            starts[u] = run_starts(key[u], lane);
             b[u] = 0;
-            if (key[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
-                b[u] = atomicAdd(&ws.hist[slot[u]], (uint32_t)__popc(peers[u]));
+            if (key[u] != 0xFFFFFFFFu && ((starts[u] >> lane) & 1u))
+                b[u] = atomicAdd(&ws.hist[slot[u]], (uint32_t)(run_end(starts[u], lane) - lane));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint32_t bb = __shfl_sync(FULL, b[u], __ffs(peers[u]) - 1);
+            const int first = run_begin(starts[u], lane);
+            const uint32_t bb = __shfl_sync(FULL, b[u], first);
             if (key[u] != 0xFFFFFFFFu) {
-                const uint32_t pos =
-                    ws.suboff[slot[u]] + bb + __popc(peers[u] & ((1u << lane) - 1));
+                const uint32_t pos = ws.suboff[slot[u]] + bb + (uint32_t)(lane - first);
                 ws.perm[pos] = (uint32_t)idx[u];
                 ws.rec[pos] = make_float4(v[u].x * wt[u], v[u].y * wt[u], fr[u].x, fr[u].y);
                 ws.rcell[pos] = cl[u];

@@ -329,11 +329,55 @@ RICK_HD bool rick_footprint(double x, int n, int W, uint64_t key_lo, uint64_t ke
 {
     const bool odd = W & 1;
     const int h = odd ? (W - 1) / 2 : W / 2 - 1;
-    uint64_t kx = rick_dkey(x);
-    if (kx < key_lo || kx >= key_hi) return false;
     uint64_t b = rick_dbits(x);
     int32_t c;
     float f;
+#if defined(__CUDA_ARCH__)
+    // Device path for the common case 1 <= x < n + 1/2 (n <= 2^15): the
+    // integer part of x lies in the high word of its bit pattern, so the split
+    // runs on 32-bit words.  The mantissa is mh 2^32 + lw with mh holding the
+    // implicit one and k = 20 - e fraction bits; the fraction is
+    // (fh 2^32 + lw) 2^-(k+32).
+    const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+    if (hw >= 0x3FF00000u && hw < 0x80000000u) {
+        if (b >= (key_hi ^ 0x8000000000000000ull)) return false;  // x >= n + 1/2, inf, NaN
+        const int k = 20 - ((int)(hw >> 20) - 1023);
+        const uint32_t mh = (hw & 0xFFFFFu) | 0x100000u;
+        uint32_t fh = mh & ((1u << k) - 1u), fo = lw;
+        const uint32_t up = odd ? (fh >> (k - 1)) & 1u : 0u;
+        c = (int32_t)((mh >> k) + up);
+        if (up) {  // x - c = fraction - 1: magnitude 2^(k+32) - (fh 2^32 + lw)
+            fh = (1u << k) - fh - (lw != 0u ? 1u : 0u);
+            fo = 0u - lw;
+        }
+        if ((fh | fo) == 0u) {
+            f = 0.0f;
+        } else {
+            // the top 32 bits of the normalised magnitude, lower bits folded
+            // into a sticky bit, rounded by the hardware (see
+            // rick_scaled_int_to_float), times 2^sc
+            uint32_t top;
+            int sc;
+            if (fh != 0u) {
+                const int lz = __clz((int)fh);
+                top = __funnelshift_l(fo, fh, lz) | ((fo << lz) != 0u ? 1u : 0u);
+                sc = -lz - k;
+            } else {
+                const int lz = __clz((int)fo);
+                top = fo << lz;
+                sc = -lz - k - 32;
+            }
+            f = __uint2float_rn(top) * __int_as_float((sc + 127) << 23);
+            if (up) f = -f;
+        }
+    } else {
+        const uint64_t kx = rick_dkey(x);
+        if (kx < key_lo || kx >= key_hi) return false;
+        if (!rick_footprint_first_cell(x, odd, &c, &f)) return false;  // -1/2 <= x < 1
+    }
+#else
+    uint64_t kx = rick_dkey(x);
+    if (kx < key_lo || kx >= key_hi) return false;
     if (b < 0x3FF0000000000000ull || (b >> 63)) {  // -0.5 <= x < 1: the first cell, rare
         if (!rick_footprint_first_cell(x, odd, &c, &f)) return false;
     } else {
@@ -347,6 +391,7 @@ RICK_HD bool rick_footprint(double x, int n, int W, uint64_t key_lo, uint64_t ke
         int64_t s = up ? (int64_t)fb - (int64_t)(1ull << sh) : (int64_t)fb;
         f = s == 0 ? 0.0f : rick_scaled_int_to_float(s, sh);
     }
+#endif
     int32_t a0 = c - h;
     if (a0 < 0 || a0 + W - 1 > n - 1) return false;
     *a = a0;
