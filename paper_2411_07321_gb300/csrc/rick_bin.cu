@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
     const int T = 1 << a.log2T, tmask = T - 1;
     int lane = threadIdx.x & 31;
 
-    float wsum = 0.0f, wcomp = 0.0f;  // Kahan sum of this thread's weights
+    ff ws = {0.0f, 0.0f};  // this thread's weight sum in double-single arithmetic
     unsigned long long du = 0, dwn = 0;
     int64_t base = (int64_t)blockIdx.x * RICK_KEY_THREADS * RICK_KEY_ITEMS + threadIdx.x;
 #pragma unroll 2
@@ -260,9 +260,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
                     a.ws.cell[i] = (uint32_t)ax | ((uint32_t)ay << 16);
                     a.ws.frac[i] = make_float2(fx, fy);
                     float wt = a.weight ? a.weight[i] : 1.0f;
-                    float y = wt - wcomp, t = wsum + y;
-                    wcomp = (t - wsum) - y;
-                    wsum = t;
+                    ws = ff_add(ws, ff{wt, 0.0f});
                 }
             }
             a.ws.key[i] = key;
@@ -277,7 +275,6 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
     }
     // deterministic block reduction of the weight sum (double-single pairs in
     // the warp: GB300 issues FP64 slowly) and of the drop counts
-    ff ws = ff_fast_two_sum(wsum, -wcomp);
     for (int o = 16; o > 0; o >>= 1) {
         ff other = {__shfl_xor_sync(FULL, ws.hi, o), __shfl_xor_sync(FULL, ws.lo, o)};
         ws = ff_add(ws, other);

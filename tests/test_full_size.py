@@ -1,0 +1,119 @@
+"""Parity at the bench workload's full size, in the launch configuration that
+bench.py times: the LOFAR-like set of 5e7 visibilities, a 4096^2 grid with 16
+w-planes, Kaiser-Bessel W=7, uv-tile 64.
+
+- Binning: the bin offsets (histogram and scan over all 262,144 bins), the drop
+  counts and the w range bit for bit against the oracle's counting sort of the
+  whole set; the bin, cell, fractional offsets and value of a random sample of
+  200,000 records bit for bit against the oracle's per-visibility geometry.
+- Image: the device-resident path and the streamed host path (chunks of 2^24
+  visibilities from pinned host memory, as bench.py's e2e) against the FP64
+  oracle's image of the whole set, 1e-5 of peak on the tapered image and on
+  the inner region (as in test_gpu_parity).
+
+The oracle images the full set in well under a minute on the host cores.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2411_07321_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def full():
+    wl = synth.WORKLOADS["lofar"]
+    d = synth.generate(wl.obs)
+    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov, kernel=oracle.KB, support=wl.support,
+                       tile=wl.tile)
+    ref, st = oracle.image(op, d["uvw"], d["vis"], d["weight"])
+    # the weight sum correctly rounded: the oracle's running FP64 sum of 5e7
+    # terms carries ~1e-12 relative rounding of its own
+    st["sum_weight_exact"] = math.fsum(d["weight"].astype(np.float64))
+    return wl, d, op, ref, st
+
+
+def errors(img, ref, op):
+    c = np.array([oracle.taper(op, (i - op.n // 2) / op.n) for i in range(op.n)])
+    cc = (c / oracle.taper(op, 0.0))[:, None] * (c / oracle.taper(op, 0.0))[None, :]
+    d = img.astype(np.float64) - ref
+    q = op.n // 4
+    inner = (slice(op.n // 2 - q, op.n // 2 + q),) * 2
+    return dict(tapered=np.abs(d * cc).max() / np.abs(ref * cc).max(),
+                inner=np.abs(d[inner]).max() / np.abs(ref[inner]).max(),
+                full=np.abs(d).max() / np.abs(ref).max())
+
+
+def test_full_size_binning_and_image(P, full):
+    wl, d, op, ref, ost = full
+    dev = torch.device("cuda:0")
+    n = len(d["vis"])
+    t = {k: torch.from_numpy(d[k]).to(dev) for k in ("uvw", "vis", "weight")}
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                  max_vis=n, device=dev)
+    img = im.image(t["uvw"], t["vis"], t["weight"]).cpu().numpy()
+    g = im.binned()
+    st = g["stats"]
+    ob = oracle.bin(op, d["uvw"])
+    kept = ob["status"] == 0
+    assert st["n_binned"] == int(kept.sum()) == ost["n_binned"]
+    assert st["n_dropped_uv"] == int((ob["status"] == 1).sum())
+    assert st["n_dropped_w"] == int((ob["status"] == 2).sum())
+    assert (st["w_min"], st["w_max"]) == (ob["w_min"], ob["w_max"])
+    assert st["sum_weight"] == pytest.approx(ost["sum_weight_exact"], rel=1e-13)
+    assert np.array_equal(g["offsets"].astype(np.int64), ob["offsets"])
+    # a random sample of records: bin, cell, offsets and value bit for bit
+    rng = np.random.default_rng(12)
+    r = rng.choice(st["n_binned"], size=200_000, replace=False)
+    idx = g["perm"][r].astype(np.int64)
+    b = np.searchsorted(ob["offsets"], r, side="right") - 1
+    assert np.array_equal(b, ob["key"][idx])
+    assert np.array_equal(g["rec_cell"][r] & 0xFFFF, ob["ax"][idx])
+    assert np.array_equal(g["rec_cell"][r] >> 16, ob["ay"][idx])
+    assert np.array_equal(g["rec_frac"][r, 0], ob["fx"][idx].astype(np.float32))
+    assert np.array_equal(g["rec_frac"][r, 1], ob["fy"][idx].astype(np.float32))
+    v, w = d["vis"][idx], d["weight"][idx].astype(np.float64)
+    want = (v.real.astype(np.float64) * w).astype(np.float32) + \
+        1j * (v.imag.astype(np.float64) * w).astype(np.float32)
+    assert np.array_equal(g["rec_val"][r], want.astype(np.complex64))
+    # every input index appears once
+    assert np.array_equal(np.sort(g["perm"].astype(np.int64)), np.flatnonzero(kept))
+    e = errors(img, ref, op)
+    print(f"full-size image error vs FP64 oracle: full {e['full']:.2e}, tapered "
+          f"{e['tapered']:.2e}, inner {e['inner']:.2e} (of peak)")
+    assert e["tapered"] <= TOL and e["inner"] <= TOL
+    im.close()
+
+
+def test_full_size_streamed_image(P, full):
+    wl, d, op, ref, ost = full
+    dev = torch.device("cuda:0")
+    h = {k: torch.from_numpy(d[k]).pin_memory() for k in ("uvw", "vis", "weight")}
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                  max_vis=1 << 24, device=dev)
+    out = torch.empty((wl.n, wl.n), dtype=torch.float32).pin_memory()
+    for _ in range(2):  # the second call reuses the staging area (overlapped copies)
+        im.image_streamed(h["uvw"], h["vis"], h["weight"], out)
+    torch.cuda.synchronize()
+    e = errors(out.numpy(), ref, op)
+    print(f"full-size streamed image error: tapered {e['tapered']:.2e}, inner {e['inner']:.2e}")
+    assert e["tapered"] <= TOL and e["inner"] <= TOL
+    st = im.stats()
+    assert st["n_binned"] == ost["n_binned"]
+    assert st["sum_weight"] == pytest.approx(ost["sum_weight_exact"], rel=1e-13)
+    im.close()
