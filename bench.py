@@ -107,23 +107,29 @@ def algorithmic_bytes(n_vis: int, n_binned: int, n: int, n_w: int) -> dict:
     }
 
 
-def traffic_of(kernel: str, n_vis: int):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            rec = json.load(f)[kernel]
-    except Exception:
-        return None
-    src = os.path.join(ROOT, rec["source"])
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
-        return None
-    if h != rec["source_sha256_16"]:
-        return None
-    return rec["bytes_per_vis"] * n_vis if "bytes_per_vis" in rec else rec["bytes_per_launch"]
+def traffic_of(stage: str, n_vis: int):
+    """DRAM bytes per launch of a stage's kernels from the committed ncu summary
+    (a "traffic <stage> <bytes> bytes n_vis <n> sources <file>=<sha256[:16]> ..."
+    line under profiles/), if it was taken on this workload size and none of the
+    named sources changed since (else None)."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            f = line.split()
+            if len(f) < 7 or f[0] != "traffic" or f[1] != stage or f[3] != "bytes":
+                continue
+            if f[4] != "n_vis" or int(f[5]) != int(n_vis) or f[6] != "sources":
+                continue
+            for item in f[7:]:
+                src, _, digest = item.partition("=")
+                try:
+                    h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+                except OSError:
+                    return None
+                if h[:16] != digest:
+                    return None
+            return int(f[2])
+    return None
 
 
 def dist_env():

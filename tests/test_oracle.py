@@ -5,6 +5,7 @@ rational arithmetic, the brute-force transform of Eq. 1, or an invariant the
 mathematics guarantees, chosen so that a dropped term, a wrong sign, an
 off-by-one shift or a transposed axis fails at least one of them.
 """
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -25,6 +26,15 @@ def rng(seed):
 @pytest.mark.parametrize("x", [0.0, 1e-3, 0.5, 3.75, 9.0, 16.25, 21.0, 30.0])
 def test_i0_series_matches_scipy(x):
     assert oracle.i0(x) == pytest.approx(float(sp.i0(x)), rel=1e-13, abs=0)
+
+
+def test_i0_matches_tabulated_values():
+    """I0 against the published table in tests/golden/bessel_i0.txt (10 digits)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bessel_i0.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 5
+    for x, v in rows:
+        assert oracle.i0(float(x)) == pytest.approx(float(v), rel=5e-10)
 
 
 @pytest.mark.parametrize("W", [3, 5, 7, 9])
