@@ -173,8 +173,8 @@ rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out);
  * from a fixed budget.  This entry point computes exactly what rick_bin
  * computes -- into the same workspace layout, which the later calls read --
  * but keeps its temporaries (per-visibility keys, cells and offsets, the
- * histogram, scan temporaries, weight-sum partials) in a fixed array compiled
- * into the library (about 12 MB, held on every GPU that loads the library until
+ * ranks, histogram, scan temporaries, weight-sum partials) in a fixed array compiled
+ * into the library (about 13 MB, held on every GPU that loads the library until
  * the process exits) instead of in ws_dev's scratch regions.  It calls no
  * cudaMalloc, cudaFree or allocating library routine.
  * The paper has no counterpart; this is an interface convenience.

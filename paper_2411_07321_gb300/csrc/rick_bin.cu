@@ -267,11 +267,17 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
         }
         // histogram, on this block's sub-counter of the bin: one atomic per run
         // of equal keys in consecutive lanes (consecutive inputs -- the
-        // channels of one baseline and time -- mostly share a key)
+        // channels of one baseline and time -- mostly share a key).  The
+        // counter's old value ranks the run inside the (bin, sub-counter)
+        // range, so the scatter needs no atomics of its own.
         const unsigned starts = run_starts(key, lane);
+        uint32_t base = 0;
         if (key != 0xFFFFFFFFu && ((starts >> lane) & 1u))
-            atomicAdd(&a.ws.hist[key * RICK_BIN_SUBS + (blockIdx.x & (RICK_BIN_SUBS - 1))],
-                      (uint32_t)(run_end(starts, lane) - lane));
+            base = atomicAdd(&a.ws.hist[key * RICK_BIN_SUBS + (blockIdx.x & (RICK_BIN_SUBS - 1))],
+                             (uint32_t)(run_end(starts, lane) - lane));
+        const int first = run_begin(starts, lane);
+        base = __shfl_sync(FULL, base, first);
+        if (i < a.n_vis) a.ws.rank[i] = base + (uint32_t)(lane - first);
     }
     // deterministic block reduction of the weight sum (double-single pairs in
     // the warp: GB300 issues FP64 slowly) and of the drop counts
@@ -327,31 +333,29 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
 // ------------------------------------------------------------------------
 // Pass 5: scatter records into their bins
 
-// Each thread takes RICK_SCATTER_U inputs per pass (256 apart), so that the
-// dependent chain of one input -- key load, cursor atomic, sub-offset load,
-// record stores -- overlaps those of the others.
+// Each thread takes RICK_SCATTER_U inputs per pass (256 apart), so that their
+// load chains -- key and rank, then the (bin, sub-counter) offset, then the
+// record stores -- overlap.  Positions come from the ranks the key pass took
+// from the histogram counters: no atomics here.
 #define RICK_SCATTER_U 4
 
 __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const float2 *vis,
                                                           const float *weight, WsPtrs ws)
 {
     constexpr int U = RICK_SCATTER_U;
-    const int lane = threadIdx.x & 31;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * U;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * U; i0 < n_vis; i0 += step) {
         int64_t idx[U];
-        uint32_t key[U], slot[U], cl[U], b[U];
-        unsigned starts[U];
+        uint32_t key[U], rk[U], cl[U];
         float2 v[U], fr[U];
         float wt[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             idx[u] = i0 + (int64_t)u * blockDim.x + threadIdx.x;
-            key[u] = idx[u] < n_vis ? ws.key[idx[u]] : 0xFFFFFFFFu;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (key[u] != 0xFFFFFFFFu) {
+            key[u] = 0xFFFFFFFFu;
+            if (idx[u] < n_vis) {
+                key[u] = ws.key[idx[u]];
+                rk[u] = ws.rank[idx[u]];
                 v[u] = vis[idx[u]];
                 wt[u] = weight ? weight[idx[u]] : 1.0f;
                 fr[u] = ws.frac[idx[u]];
@@ -360,22 +364,11 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            // the sub-counter of the key pass's block that held this input
-            const uint32_t sub =
-                (uint32_t)((idx[u] / (RICK_KEY_THREADS * RICK_KEY_ITEMS)) & (RICK_BIN_SUBS - 1));
-            slot[u] = key[u] * RICK_BIN_SUBS + sub;
-            // one cursor atomic per run of equal keys in consecutive lanes
-            starts[u] = run_starts(key[u], lane);
-            b[u] = 0;
-            if (key[u] != 0xFFFFFFFFu && ((starts[u] >> lane) & 1u))
-                b[u] = atomicAdd(&ws.hist[slot[u]], (uint32_t)(run_end(starts[u], lane) - lane));
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int first = run_begin(starts[u], lane);
-            const uint32_t bb = __shfl_sync(FULL, b[u], first);
             if (key[u] != 0xFFFFFFFFu) {
-                const uint32_t pos = ws.suboff[slot[u]] + bb + (uint32_t)(lane - first);
+                // the sub-counter of the key pass's block that held this input
+                const uint32_t sub = (uint32_t)((idx[u] / (RICK_KEY_THREADS * RICK_KEY_ITEMS)) &
+                                                (RICK_BIN_SUBS - 1));
+                const uint32_t pos = ws.suboff[key[u] * RICK_BIN_SUBS + sub] + rk[u];
                 ws.perm[pos] = (uint32_t)idx[u];
                 ws.rec[pos] = make_float4(v[u].x * wt[u], v[u].y * wt[u], fr[u].x, fr[u].y);
                 ws.rcell[pos] = cl[u];
@@ -516,9 +509,8 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
                                                                           L.nbins);
     RICK_LAUNCH_CHECK(plan);
     if (n_vis > 0) {
-        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
-        if (blocks > (int64_t)plan->num_sms * 16) blocks = (int64_t)plan->num_sms * 16;
+        if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
         bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
         RICK_LAUNCH_CHECK(plan);
     }
@@ -568,14 +560,15 @@ extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const f
 // fractional offsets, the histogram / cursor array, the scan temporaries and
 // the weight-sum partials -- live in this file-scope array instead of the
 // caller's workspace.  The array is part of the library image: every GPU that
-// loads librick.so holds it (about 12 MB) until the process exits.
+// loads librick.so holds it (about 13 MB) until the process exits.
 
 #define NOALLOC_MAX_VIS (1 << 18)
 #define NOALLOC_MAX_BINS (1 << 17)
 #define NOALLOC_KEY (0)
 #define NOALLOC_CELL (NOALLOC_KEY + 4 * NOALLOC_MAX_VIS)
 #define NOALLOC_FRAC (NOALLOC_CELL + 4 * NOALLOC_MAX_VIS)
-#define NOALLOC_HIST (NOALLOC_FRAC + 8 * NOALLOC_MAX_VIS)
+#define NOALLOC_RANK (NOALLOC_FRAC + 8 * NOALLOC_MAX_VIS)
+#define NOALLOC_HIST (NOALLOC_RANK + 4 * NOALLOC_MAX_VIS)
 #define NOALLOC_SUBOFF (NOALLOC_HIST + 4 * (RICK_BIN_SUBS * NOALLOC_MAX_BINS + 256))
 #define NOALLOC_SCAN (NOALLOC_SUBOFF + 4 * (RICK_BIN_SUBS * NOALLOC_MAX_BINS + 256))
 #define NOALLOC_WPART (NOALLOC_SCAN + 4 * 4096)
@@ -632,6 +625,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     WsPtrs w = rick_ws_ptrs(ws_dev, L);
     w.key = (uint32_t *)(scratch + NOALLOC_KEY);
     w.cell = (uint32_t *)(scratch + NOALLOC_CELL);
+    w.rank = (uint32_t *)(scratch + NOALLOC_RANK);
     w.frac = (float2 *)(scratch + NOALLOC_FRAC);
     w.hist = (uint32_t *)(scratch + NOALLOC_HIST);
     w.suboff = (uint32_t *)(scratch + NOALLOC_SUBOFF);
@@ -682,9 +676,8 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
                                                                           L.nbins);
     RICK_LAUNCH_CHECK(plan);
     if (n_vis > 0) {
-        RICK_CUDA_TRY(plan, cudaMemsetAsync(w.hist, 0, 4 * (size_t)(RICK_BIN_SUBS * L.nbins + 1), st));
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
-        if (blocks > (int64_t)plan->num_sms * 16) blocks = (int64_t)plan->num_sms * 16;
+        if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
         bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
         RICK_LAUNCH_CHECK(plan);
     }

@@ -110,17 +110,18 @@ struct WsHeader {
 };
 
 struct WsLayout {
-    size_t header, key, cell, frac, perm, rec, rcell, hist, suboff, offsets, gbase, dbase, scan,
+    size_t header, key, rank, cell, frac, perm, rec, rcell, hist, suboff, offsets, gbase, dbase, scan,
         wpart, bkey, wplane, total;
     int64_t n_vis, nbins, ntiles, nscan, nkeyblocks;
 };
 
 #define RICK_KEY_THREADS 256
 #define RICK_KEY_ITEMS 8
-// Each bin's histogram counter and scatter cursor is split into RICK_BIN_SUBS
-// sub-counters, chosen by the input's block of RICK_KEY_THREADS * RICK_KEY_ITEMS
-// visibilities: the densest bins (the array core) then take their atomics on
-// several addresses instead of one.
+// Each bin's histogram counter is split into RICK_BIN_SUBS sub-counters, chosen
+// by the input's block of RICK_KEY_THREADS * RICK_KEY_ITEMS visibilities: the
+// densest bins (the array core) then take their atomics on several addresses
+// instead of one.  The value a counter held before an input's atomic is the
+// input's rank within its (bin, sub-counter) range.
 #define RICK_BIN_SUBS 8
 
 RICK_HD size_t rick_align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -149,6 +150,7 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
     size_t o = 0;
     L.header = o; o += rick_align256(sizeof(WsHeader));
     L.key = o;    o += rick_align256(4 * (size_t)nv);
+    L.rank = o;   o += rick_align256(4 * (size_t)nv);
     L.cell = o;   o += rick_align256(4 * (size_t)nv);
     L.frac = o;   o += rick_align256(8 * (size_t)nv);
     L.perm = o;   o += rick_align256(4 * (size_t)nv);
@@ -171,7 +173,7 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
 // Device pointers into a workspace.
 struct WsPtrs {
     WsHeader *hdr;
-    uint32_t *key, *cell, *perm, *rcell, *hist, *suboff, *offsets, *gbase, *dbase, *scan;
+    uint32_t *key, *rank, *cell, *perm, *rcell, *hist, *suboff, *offsets, *gbase, *dbase, *scan;
     float2 *frac;
     float4 *rec;  // per record: vis*weight (re, im), fractional offsets (fx, fy)
     double *wpart;
@@ -185,6 +187,7 @@ static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
     WsPtrs w;
     w.hdr = (WsHeader *)(b + L.header);
     w.key = (uint32_t *)(b + L.key);
+    w.rank = (uint32_t *)(b + L.rank);
     w.cell = (uint32_t *)(b + L.cell);
     w.frac = (float2 *)(b + L.frac);
     w.perm = (uint32_t *)(b + L.perm);
