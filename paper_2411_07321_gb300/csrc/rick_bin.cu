@@ -93,6 +93,7 @@ __global__ void bin_init_kernel(WsHeader *hdr, uint64_t n_vis, uint32_t chunk_ca
                                 const WsHeader *range_src)
 {
     hdr->n_vis = n_vis;
+    hdr->fault = 0;
     hdr->drop_uv = 0;
     hdr->drop_w = 0;
     hdr->chunk_cap = chunk_cap;
@@ -176,8 +177,16 @@ struct KeyArgs {
     int n, n_w, W, log2T, nt;
     double fov, half_n;
     uint64_t key_lo, key_hi;  // rick_dkey(-0.5), rick_dkey(n + 0.5)
+    int bulk;                 // uvw (and weight) 16-byte aligned: blocks stage them by bulk copy
     WsPtrs ws;
 };
+
+// Dynamic shared memory of the key pass: the block's uvw and weights, then the
+// plane boundary keys.
+static inline size_t key_pass_smem(int n_w)
+{
+    return 28 * (size_t)(RICK_KEY_THREADS * RICK_KEY_ITEMS) + 8 * (size_t)(n_w > 1 ? n_w - 1 : 1);
+}
 
 // Lanes that start a run of equal keys (lane 0, or a key unlike the previous
 // lane's), as a warp ballot.
@@ -215,13 +224,51 @@ __device__ __forceinline__ uint32_t plane_of(uint64_t kw, const unsigned long lo
 
 __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
 {
-    extern __shared__ unsigned long long s_bkey[];
+    constexpr int NI = RICK_KEY_THREADS * RICK_KEY_ITEMS;
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    double *s_uvw = (double *)s_dyn;
+    float *s_wt = (float *)(s_dyn + 24 * NI);
+    unsigned long long *s_bkey = (unsigned long long *)(s_dyn + 28 * NI);
+    __shared__ unsigned long long s_bar;
     __shared__ double s_wsum[RICK_KEY_THREADS / 32];
     __shared__ unsigned long long s_drop[2][RICK_KEY_THREADS / 32];
     const WsHeader *hdr = a.ws.hdr;
+    const int64_t blk0 = (int64_t)blockIdx.x * NI;
+    const int nitems = (int)(a.n_vis - blk0 < NI ? a.n_vis - blk0 : NI);
+    // The block's 2048 uvw rows and weights are contiguous: one bulk copy each
+    // (TMA) into shared memory, while the plane keys load; a ragged last block
+    // or unaligned inputs take plain loads instead.
+    const bool bulk = a.bulk && nitems == NI;
+    if (bulk && threadIdx.x == 0) {
+        rick_mbar_init(&s_bar, 1);
+        rick_mbar_expect_tx(&s_bar, 24 * NI + (a.weight ? 4 * NI : 0));
+        rick_bulk_g2s(s_uvw, a.uvw + 3 * blk0, 24 * NI, &s_bar);
+        if (a.weight) rick_bulk_g2s(s_wt, a.weight + blk0, 4 * NI, &s_bar);
+    }
     int nb = a.n_w - 1;
     for (int j = threadIdx.x; j < nb; j += blockDim.x) s_bkey[j] = a.ws.bkey[j];
+    if (!bulk) {
+        for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+            s_uvw[3 * i] = a.uvw[3 * (blk0 + i)];
+            s_uvw[3 * i + 1] = a.uvw[3 * (blk0 + i) + 1];
+            s_uvw[3 * i + 2] = a.uvw[3 * (blk0 + i) + 2];
+            if (a.weight) s_wt[i] = a.weight[blk0 + i];
+        }
+    }
     __syncthreads();
+    const bool landed = !bulk || rick_mbar_wait(&s_bar, 0, 1u << 24);
+    if (!__syncthreads_and(landed)) {
+        // the copy did not complete in time (never expected): leave this block's
+        // inputs out of the binning, flag the fault (reported as n_binned < 0),
+        // and let the copy land before the block's shared memory is released
+        if (threadIdx.x == 0) {
+            atomicExch(&a.ws.hdr->fault, 1u);
+            a.ws.wpart[blockIdx.x] = 0.0;
+        }
+        for (int i = threadIdx.x; i < nitems; i += blockDim.x) a.ws.key[blk0 + i] = 0xFFFFFFFFu;
+        rick_mbar_wait(&s_bar, 0, 1u << 24);
+        return;
+    }
     const bool degenerate = rick_dbits(hdr->dw) == 0;
     const bool given = hdr->range_given;
     const uint64_t wlo = hdr->wmin_key, whi = hdr->wmax_key;
@@ -230,13 +277,14 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
 
     ff ws = {0.0f, 0.0f};  // this thread's weight sum in double-single arithmetic
     unsigned long long du = 0, dwn = 0;
-    int64_t base = (int64_t)blockIdx.x * RICK_KEY_THREADS * RICK_KEY_ITEMS + threadIdx.x;
+    int64_t base = blk0 + threadIdx.x;
 #pragma unroll 2
     for (int it = 0; it < RICK_KEY_ITEMS; ++it) {
         int64_t i = base + (int64_t)it * RICK_KEY_THREADS;
         uint32_t key = 0xFFFFFFFFu;
+        const int li = it * RICK_KEY_THREADS + threadIdx.x;  // index inside the block
         if (i < a.n_vis) {
-            double u = a.uvw[3 * i], v = a.uvw[3 * i + 1], w = a.uvw[3 * i + 2];
+            double u = s_uvw[3 * li], v = s_uvw[3 * li + 1], w = s_uvw[3 * li + 2];
             int32_t ax, ay;
             float fx, fy;
             bool ok = rick_footprint(fma(u, a.fov, a.half_n), a.n, a.W, a.key_lo, a.key_hi, &ax,
@@ -259,7 +307,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
                             (uint32_t)(ax >> a.log2T)) << 2) | cls;
                     a.ws.cell[i] = (uint32_t)ax | ((uint32_t)ay << 16);
                     a.ws.frac[i] = make_float2(fx, fy);
-                    float wt = a.weight ? a.weight[i] : 1.0f;
+                    float wt = a.weight ? s_wt[li] : 1.0f;
                     ws = ff_add(ws, ff{wt, 0.0f});
                 }
             }
@@ -323,6 +371,7 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
     }
     if (threadIdx.x == 0) {
         long long binned = (long long)hdr->n_vis - (long long)hdr->drop_uv - (long long)hdr->drop_w;
+        if (hdr->fault) binned = -1;  // a bounded wait ran out: the binning is incomplete
         hdr->stats.n_binned = binned;
         hdr->stats.n_dropped_uv = (long long)hdr->drop_uv;
         hdr->stats.n_dropped_w = (long long)hdr->drop_w;
@@ -497,7 +546,11 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
         ka.key_lo = rick_dkey(-0.5);
         ka.key_hi = rick_dkey((double)p.n + 0.5);
         ka.ws = w;
-        size_t smem = 8 * (size_t)(p.n_w > 1 ? p.n_w - 1 : 1);
+        ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
+        const size_t smem = key_pass_smem(p.n_w);
+        RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
         bin_key_kernel<<<(unsigned)nkb, RICK_KEY_THREADS, smem, st>>>(ka);
         RICK_LAUNCH_CHECK(plan);
     }
@@ -664,7 +717,11 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         ka.key_lo = rick_dkey(-0.5);
         ka.key_hi = rick_dkey((double)p.n + 0.5);
         ka.ws = w;
-        size_t smem = 8 * (size_t)(p.n_w > 1 ? p.n_w - 1 : 1);
+        ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
+        const size_t smem = key_pass_smem(p.n_w);
+        RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
         bin_key_kernel<<<(unsigned)nkb, RICK_KEY_THREADS, smem, st>>>(ka);
         RICK_LAUNCH_CHECK(plan);
     }

@@ -107,6 +107,7 @@ struct WsHeader {
     uint32_t range_given;
     uint32_t n_key_blocks;
     uint32_t grid_next, degrid_next;    // work counters of the persistent tile kernels
+    uint32_t fault;                     // a bounded device-side wait ran out (never expected)
 };
 
 struct WsLayout {
@@ -485,6 +486,61 @@ __device__ __forceinline__ ff ff_nm1(ff l, ff m, ff *r2_out)
     ff q = ff_div(r2, den);
     *r2_out = r2;
     return {-q.hi, -q.lo};
+}
+
+// ------------------------------------------------------------------------
+// Bulk (TMA) copies from global into shared memory, completed on an mbarrier
+
+__device__ __forceinline__ uint32_t rick_smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One-phase barrier for `count` arrivals, made visible to the async proxy.
+__device__ __forceinline__ void rick_mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(rick_smem_addr(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive once, announcing `bytes` of bulk copies that complete on the barrier.
+__device__ __forceinline__ void rick_mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     rick_smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
+// shared memory; completion is counted on `bar`.
+__device__ __forceinline__ void rick_bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                              unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(rick_smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(rick_smem_addr(bar))
+        : "memory");
+}
+
+// Wait for phase `parity` of `bar`, polling at most `limit` times; false if it
+// did not complete.
+__device__ __forceinline__ bool rick_mbar_wait(unsigned long long *bar, uint32_t parity,
+                                               uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(rick_smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 // Fraction of a double-single phase in cycles: (hi - rint(hi)) + lo, in
