@@ -76,7 +76,9 @@ typedef struct rick_params {
 
 /* Geometry and counts of the last rick_bin, written to device memory. */
 typedef struct rick_bin_stats {
-    int64_t n_binned;     /* visibilities kept                                        */
+    int64_t n_binned;     /* visibilities kept; -1 if a bounded device-side wait of    */
+                          /*   the binning ran out (never expected; the binning is    */
+                          /*   then incomplete and must not be used)                  */
     int64_t n_dropped_uv; /* footprint not inside the grid (or non-finite u, v)       */
     int64_t n_dropped_w;  /* w outside a given range                                  */
     double sum_weight;    /* sum of the kept visibilities' weights                    */
@@ -146,6 +148,9 @@ rick_status rick_plan_fft_bytes(const rick_plan *plan, size_t *fft_bytes);
  *               bytes, 256-byte aligned; overwritten; the later calls of
  *               this binning (grid, wcorrect, wspread, degrid) read it
  *   stats_dev:  device rick_bin_stats, or NULL
+ * uvw_dev and weight_dev aligned to 16 bytes let each block of the key pass
+ * fetch its 2048 rows with one bulk (TMA) copy; 8-byte alignment is enough for
+ * correctness.
  * Errors: RICK_EINVAL (NULL pointer, misalignment), RICK_ERANGE (n_vis >
  * max_vis or ws_bytes too small), RICK_ECUDA. */
 rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw_dev, const void *vis_dev,
