@@ -62,10 +62,12 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float a)
 // Record streams.  A group of G = next_pow2(W) lanes walks a contiguous run of
 // records; lane j of the group owns footprint row j (W cells).  Per record,
 // lane j evaluates kernel segment j at both offsets -- gx[j] = G((j - h) - fx)
-// and gy[j] = G((j - h) - fy), Horner with the segment's coefficients held in
-// the lane's registers -- so it already has its row's v weight, scales the
+// and gy[j] = G((j - h) - fy), one Horner chain on (x, y) pairs with packed
+// two-wide FP32 FMAs and the segment's coefficients held (duplicated) in the
+// lane's registers -- so it already has its row's v weight, scales the
 // visibility by it, and takes the W u weights from its group with shuffles:
-// W shuffles and 2W FMAs per record and lane.  While consecutive records share
+// W shuffles and W packed FMAs per record and lane (re and im of two cells per
+// instruction pair).  While consecutive records share
 // the footprint corner (the channels of one baseline-time land on the same
 // cells) the row sums stay in registers; when the corner changes the group
 // adds its rows to the tile accumulator at once -- one row per lane, so the
@@ -96,7 +98,7 @@ __device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T,
 template <int W>
 __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n, int x0,
                                             int y0, float *acc_re, float *acc_im, int T, int TP,
-                                            const float *coef)
+                                            const float2 *coef2)
 {
     constexpr int G = StreamShape<W>::G;
     const int j = threadIdx.x & (G - 1);  // this lane's row / kernel segment
@@ -125,21 +127,29 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         }
         float gx = 1.0f, gy = 1.0f;
         if (W > 1) {
-            const float sx = 2.0f * (q.z - ta.kp.fc), sy = 2.0f * (q.w - ta.kp.fc);
-            gx = coef[RICK_POLY_DEG];
-            gy = coef[RICK_POLY_DEG];
+            const float2 s2 = make_float2(2.0f * (q.z - ta.kp.fc), 2.0f * (q.w - ta.kp.fc));
+            float2 g2 = coef2[RICK_POLY_DEG];
 #pragma unroll
-            for (int k = RICK_POLY_DEG - 1; k >= 0; --k) {
-                gx = __fmaf_rn(gx, sx, coef[k]);
-                gy = __fmaf_rn(gy, sy, coef[k]);
-            }
+            for (int k = RICK_POLY_DEG - 1; k >= 0; --k) g2 = __ffma2_rn(g2, s2, coef2[k]);
+            gx = g2.x;
+            gy = g2.y;
         }
-        const float vr = q.x * gy, vi = q.y * gy;
+        const float2 vv = __fmul2_rn(make_float2(q.x, q.y), make_float2(gy, gy));
+        const float2 vr2 = make_float2(vv.x, vv.x), vi2 = make_float2(vv.y, vv.y);
+        float wv[W];
 #pragma unroll
-        for (int jx = 0; jx < W; ++jx) {
-            const float w = G == 1 ? gx : __shfl_sync(gmask, gx, jx, G);
-            ar[jx] = __fmaf_rn(vr, w, ar[jx]);
-            ai[jx] = __fmaf_rn(vi, w, ai[jx]);
+        for (int jx = 0; jx < W; ++jx) wv[jx] = G == 1 ? gx : __shfl_sync(gmask, gx, jx, G);
+#pragma unroll
+        for (int jx = 0; jx + 1 < W; jx += 2) {
+            const float2 w2 = make_float2(wv[jx], wv[jx + 1]);
+            const float2 a2 = __ffma2_rn(vr2, w2, make_float2(ar[jx], ar[jx + 1]));
+            const float2 b2 = __ffma2_rn(vi2, w2, make_float2(ai[jx], ai[jx + 1]));
+            ar[jx] = a2.x; ar[jx + 1] = a2.y;
+            ai[jx] = b2.x; ai[jx + 1] = b2.y;
+        }
+        if (W & 1) {
+            ar[W - 1] = __fmaf_rn(vv.x, wv[W - 1], ar[W - 1]);
+            ai[W - 1] = __fmaf_rn(vv.y, wv[W - 1], ai[W - 1]);
         }
         q = nq;
         cell = ncell;
@@ -150,7 +160,7 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
 
 template <int W, bool COMP>
 __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm,
-                                          const float *coef)
+                                          const float2 *coef2)
 {
     const TileArgs &ta = a.t;
     const uint32_t chunk = b - ta.base[t], nch = ta.base[t + 1] - ta.base[t];
@@ -218,7 +228,7 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
             uint32_t a0 = max(v0, base), a1 = min(v1, base + lg);
             if (a0 < a1)
                 grid_stream<W>(ta, s_rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
-                               coef);
+                               coef2);
             base += lg;
         }
         if (COMP) {
@@ -274,9 +284,9 @@ __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(Gr
     // this lane's kernel segment (= its footprint row within its group)
     constexpr int G = StreamShape<W>::G;
     const int seg = min((int)(threadIdx.x & (G - 1)), W - 1);
-    float coef[RICK_POLY_N];
+    float2 coef2[RICK_POLY_N];
 #pragma unroll
-    for (int k = 0; k < RICK_POLY_N; ++k) coef[k] = a.t.kp.c[seg][k];
+    for (int k = 0; k < RICK_POLY_N; ++k) coef2[k] = make_float2(a.t.kp.c[seg][k], a.t.kp.c[seg][k]);
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(Gr
         __syncthreads();
         const uint32_t b = s_b, t = s_tile;
         if (b >= total) break;
-        grid_item<W, COMP>(a, b, t, sm, coef);
+        grid_item<W, COMP>(a, b, t, sm, coef2);
         __syncthreads();  // the accumulator is reused by the next item
     }
 }
