@@ -107,6 +107,7 @@ struct WsHeader {
     uint32_t range_given;
     uint32_t n_key_blocks;
     uint32_t grid_next, degrid_next;    // work counters of the persistent tile kernels
+    uint32_t zero_next;                 // counter of the grid kernel's tile-clearing items
     uint32_t fault;                     // a bounded device-side wait ran out (never expected)
 };
 

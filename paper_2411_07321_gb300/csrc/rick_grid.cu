@@ -9,9 +9,9 @@
 // tile, then writes the tile once with plain coalesced stores.  The
 // checkerboard (-1)^(i+j) of the centred FFT is applied in that write.  A tile
 // with more than one chunk is zeroed first and its chunks add their sums with
-// float2 atomics.  Tiles without records are not work items: a light
-// grid-stride kernel writes their zeros, so the register-heavy gridding CTAs
-// only run where there are records.
+// float2 atomics.  Tiles without records are not gridding items: the
+// persistent gridding CTAs clear them in groups between their gridding items,
+// so the stores of zeros overlap the gridding of the other tiles.
 //
 // Degridding: one CTA per chunk of a non-empty tile's own bin; the CTA stages
 // the (T + W - 1)^2 plane region its records can touch into shared memory and
@@ -23,7 +23,11 @@ struct GridArgs {
     float2 *planes;
     int log2T;
     int accumulate;  // add into the planes instead of overwriting them
+    uint32_t nzero;  // tile-clearing items (RICK_ZERO_GROUP tiles each); 0 when accumulating
 };
+
+// Tiles per clearing item of the grid kernel.
+#define RICK_ZERO_GROUP 16
 
 struct DegridArgs {
     TileArgs t;
@@ -268,19 +272,38 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     }
 }
 
+// Clear the tiles of group z that have no work item (no records reach them):
+// 16-byte stores, the CTA's threads striding over the tile.
+__device__ __forceinline__ void zero_group(const GridArgs &a, uint32_t z)
+{
+    const TileArgs &ta = a.t;
+    const int T = 1 << a.log2T, half = T >> 1, nt = ta.nt, n = ta.n;
+    const uint32_t t1 = min(ta.ntiles, (z + 1) * RICK_ZERO_GROUP);
+    for (uint32_t t = z * RICK_ZERO_GROUP; t < t1; ++t) {
+        if (ta.base[t + 1] != ta.base[t]) continue;
+        const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
+        float4 *plane = (float4 *)(a.planes + (size_t)k * n * n);
+        for (int i = threadIdx.x; i < T * half; i += blockDim.x) {
+            const int row = i / half, col2 = i - row * half;
+            plane[((size_t)((ty << a.log2T) + row) * n + (tx << a.log2T)) / 2 + col2] =
+                make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
 // Persistent: one wave of CTAs takes work items (tile, chunk) from a counter
-// in the workspace header (reset by zero_tiles_kernel, launched just before).
-// Four CTAs per SM for W <= 8 (64 registers a thread): the record loop is
-// latency-bound, and the extra warps hide more of it than the few spilled
-// registers cost.
+// in the workspace header (reset by zero_tiles_kernel, launched just before),
+// and with each a clearing item for a group of tiles without records, so that
+// the HBM-bound clearing of the empty tiles runs under the issue-bound
+// gridding of the others.  Four CTAs per SM for W <= 8 (64 registers a
+// thread): the record loop is latency-bound, and the extra warps hide more of
+// it than the few spilled registers cost.
 template <int W, bool COMP>
 __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(GridArgs a)
 {
     extern __shared__ float sm[];
-    __shared__ uint32_t s_b, s_tile;
+    __shared__ uint32_t s_b, s_tile, s_z;
     const uint32_t total = a.t.base[a.t.ntiles];
-    // this lane's kernel segment (u weights on the first half of its group, v
-    // weights on the second) and the footprint cells it accumulates
     // this lane's kernel segment (= its footprint row within its group)
     constexpr int G = StreamShape<W>::G;
     const int seg = min((int)(threadIdx.x & (G - 1)), W - 1);
@@ -289,34 +312,43 @@ __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(Gr
     for (int k = 0; k < RICK_POLY_N; ++k) coef2[k] = make_float2(a.t.kp.c[seg][k], a.t.kp.c[seg][k]);
     for (;;) {
         if (threadIdx.x == 0) {
-            uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
+            const uint32_t b = atomicAdd(&a.t.hdr->grid_next, 1u);
             s_b = b;
             s_tile = b < total ? find_tile(a.t.base, a.t.ntiles, b) : 0u;
+            s_z = a.nzero ? atomicAdd(&a.t.hdr->zero_next, 1u) : 0u;
         }
         __syncthreads();
-        const uint32_t b = s_b, t = s_tile;
-        if (b >= total) break;
-        grid_item<W, COMP>(a, b, t, sm, coef2);
-        __syncthreads();  // the accumulator is reused by the next item
+        const uint32_t b = s_b, t = s_tile, z = s_z;
+        __syncthreads();  // everyone has the item before thread 0 takes the next
+        if (b >= total && z >= a.nzero) break;
+        if (b < total) {
+            grid_item<W, COMP>(a, b, t, sm, coef2);
+            __syncthreads();  // the accumulator is reused by the next item
+        }
+        if (z < a.nzero) zero_group(a, z);
     }
 }
 
-// Zero every tile that is not written by exactly one grid work item: tiles
-// without records (no work item) and tiles whose chunks add into them with
-// atomics.  Grid-stride, one warp per tile, 16-byte stores.  When gridding
-// adds into existing planes only the work counter is reset.
+// Zero the tiles whose chunks add into them with atomics (more than one work
+// item) before the grid kernel runs, and reset the grid kernel's counters.
+// Grid-stride, one warp per tile, 16-byte stores.  Tiles without records are
+// cleared by the grid kernel itself; when gridding adds into existing planes
+// nothing is cleared.
 __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, uint32_t ntiles,
                                                          int nt, int log2T, int n, float2 *planes,
                                                          WsHeader *hdr, int accumulate)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->grid_next = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        hdr->grid_next = 0;
+        hdr->zero_next = 0;
+    }
     if (accumulate) return;
     int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const int T = 1 << log2T, half = T >> 1;  // float4 = two cells
     for (uint32_t t = warp; t < ntiles; t += nwarps) {
-        if (base[t + 1] - base[t] == 1) continue;
+        if (base[t + 1] - base[t] <= 1) continue;
         uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
         float4 *plane = (float4 *)(planes + (size_t)k * n * n);
         for (int i = lane; i < T * half; i += 32) {
@@ -514,6 +546,7 @@ rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int 
     a.planes = (float2 *)planes_dev;
     a.log2T = ilog2(p.tile);
     a.accumulate = accumulate;
+    a.nzero = accumulate ? 0u : (a.t.ntiles + RICK_ZERO_GROUP - 1) / RICK_ZERO_GROUP;
     cudaError_t err = cudaSuccess;
     zero_tiles_kernel<<<accumulate ? 1 : plan->num_sms * 8, 256, 0, st>>>(
         w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate);
