@@ -157,6 +157,24 @@ rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw_dev, cons
                      const float *weight_dev, void *ws_dev, size_t ws_bytes,
                      rick_bin_stats *stats_dev, void *stream);
 
+/* rick_bin for multi-channel input (SURVEY f-2): visibilities in rows of
+ * n_chan channels, as a measurement set stores them, with uvw given once per
+ * row and a factor per channel -- the uvw of channel c of row r is
+ * uvw_rows[r] * chan_scale[c], one FP64 product per coordinate (e.g. metres
+ * times nu_c / c, or wavelengths at a reference frequency times nu_c / nu_0).
+ * The result is exactly that of rick_bin on the expanded uvw
+ * [n_rows n_chan][3]; the device reads 24 bytes of uvw per row instead of per
+ * visibility.
+ *   uvw_rows_dev:   float64 [n_rows][3]
+ *   chan_scale_dev: float64 [n_chan]
+ *   vis_dev, weight_dev: [n_rows][n_chan], channel fastest, as for rick_bin
+ * Errors: as rick_bin; RICK_EINVAL for n_chan < 1; RICK_ERANGE if
+ * n_rows n_chan > max_vis. */
+rick_status rick_bin_channels(rick_plan *plan, int64_t n_rows, int32_t n_chan,
+                              const double *uvw_rows_dev, const double *chan_scale_dev,
+                              const void *vis_dev, const float *weight_dev, void *ws_dev,
+                              size_t ws_bytes, rick_bin_stats *stats_dev, void *stream);
+
 /* Where the binning arrays sit inside a workspace (byte offsets from ws_dev),
  * for callers that read the binned records directly:
  *   offsets  uint32 [n_bins + 1]   bin b holds records [offsets[b], offsets[b+1])
@@ -291,6 +309,20 @@ rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_ho
                             size_t ws_bytes, void *stage_dev, size_t stage_bytes,
                             void *planes_dev, float *image_dev, uint32_t flags,
                             rick_bin_stats *stats_dev, void *stream);
+
+/* rick_image_host for multi-channel input held in host memory: rows of n_chan
+ * channels with uvw once per row and a factor per channel, as for
+ * rick_bin_channels (1 <= n_chan <= 4096).  Chunks are whole rows, at most
+ * the plan's max_vis visibilities each; the staging area is that of
+ * rick_stream_bytes(params, max_vis, n_rows n_chan).  Only 24 bytes of uvw per
+ * row cross to the device.  The image equals rick_image_host's on the expanded
+ * uvw. */
+rick_status rick_image_host_channels(rick_plan *plan, int64_t n_rows, int32_t n_chan,
+                                     const double *uvw_rows_host, const double *chan_scale_host,
+                                     const void *vis_host, const float *weight_host,
+                                     void *ws_dev, size_t ws_bytes, void *stage_dev,
+                                     size_t stage_bytes, void *planes_dev, float *image_dev,
+                                     uint32_t flags, rick_bin_stats *stats_dev, void *stream);
 
 #ifdef __cplusplus
 }

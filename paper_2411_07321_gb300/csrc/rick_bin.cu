@@ -108,16 +108,27 @@ __global__ void bin_init_kernel(WsHeader *hdr, uint64_t n_vis, uint32_t chunk_ca
     hdr->wmax_key = given ? wmax_key : 0ull;
 }
 
-// Launch the w-range reduction of uvw[0, n) into hdr's range keys.
+// Launch the w-range reduction of visibilities [0, n) into hdr's range keys.
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
-                        cudaStream_t st);
+                        cudaStream_t st, int n_chan, const double *scale);
 
-__global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr)
+// w of visibility i: uvw[i][2], or for multi-channel input (n_chan > 0) the
+// row's w times the channel factor, one FP64 product.
+__device__ __forceinline__ double vis_w(const double *uvw, int64_t i, int n_chan,
+                                        const double *scale)
+{
+    if (n_chan <= 0) return uvw[3 * i + 2];
+    const int64_t r = i / n_chan;
+    return uvw[3 * r + 2] * scale[i - r * n_chan];
+}
+
+__global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n_chan,
+                              const double *scale)
 {
     uint64_t lo = ~0ull, hi = 0ull;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t b = rick_dbits(uvw[3 * i + 2]);
+        uint64_t b = rick_dbits(vis_w(uvw, i, n_chan, scale));
         if (((b >> 52) & 0x7FF) == 0x7FF) continue;  // not finite
         uint64_t k = rick_dkey(rick_bitsd(b));
         lo = k < lo ? k : lo;
@@ -135,9 +146,9 @@ __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr)
 }
 
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
-                        cudaStream_t st)
+                        cudaStream_t st, int n_chan, const double *scale)
 {
-    wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr);
+    wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr, n_chan, scale);
 }
 
 // ------------------------------------------------------------------------
@@ -178,6 +189,8 @@ struct KeyArgs {
     double fov, half_n;
     uint64_t key_lo, key_hi;  // rick_dkey(-0.5), rick_dkey(n + 0.5)
     int bulk;                 // uvw (and weight) 16-byte aligned: blocks stage them by bulk copy
+    int n_chan;               // > 0: uvw holds rows of n_chan visibilities, scaled per channel
+    const double *chan_scale;
     WsPtrs ws;
 };
 
@@ -247,7 +260,21 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
     }
     int nb = a.n_w - 1;
     for (int j = threadIdx.x; j < nb; j += blockDim.x) s_bkey[j] = a.ws.bkey[j];
-    if (!bulk) {
+    if (!bulk && a.n_chan > 0) {
+        // multi-channel input: the uvw of channel c of row r is the row's uvw
+        // times the channel factor (one FP64 product per coordinate)
+        const int64_t row0 = blk0 / a.n_chan;
+        const int ch0 = (int)(blk0 - row0 * a.n_chan);
+        for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+            const int t = ch0 + i;
+            const int64_t r = row0 + t / a.n_chan;
+            const double f = a.chan_scale[t % a.n_chan];
+            s_uvw[3 * i] = a.uvw[3 * r] * f;
+            s_uvw[3 * i + 1] = a.uvw[3 * r + 1] * f;
+            s_uvw[3 * i + 2] = a.uvw[3 * r + 2] * f;
+            if (a.weight) s_wt[i] = a.weight[blk0 + i];
+        }
+    } else if (!bulk) {
         for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
             s_uvw[3 * i] = a.uvw[3 * (blk0 + i)];
             s_uvw[3 * i + 1] = a.uvw[3 * (blk0 + i) + 1];
@@ -495,16 +522,24 @@ __global__ void tile_count_kernel(const uint32_t *off, uint32_t *gcnt, uint32_t 
 
 // ------------------------------------------------------------------------
 
+// Rows of n_chan channels that fit a plan's capacity.
+static int64_t plan_max_rows(const rick_plan *plan, int32_t n_chan)
+{
+    return plan && n_chan > 0 ? plan->max_vis / n_chan : 0;
+}
+
 rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, const void *vis,
                           const float *weight, void *ws_dev, size_t ws_bytes,
-                          rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src)
+                          rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src,
+                          int n_chan, const double *chan_scale)
 {
     if (!plan || !ws_dev || n_vis < 0) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (n_vis > 0 && (!uvw || !vis)) return RICK_EINVAL;
     if (((uintptr_t)ws_dev & 255) || ((uintptr_t)uvw & 7) || ((uintptr_t)vis & 7) ||
-        ((uintptr_t)weight & 3) || ((uintptr_t)stats_dev & 7))
+        ((uintptr_t)weight & 3) || ((uintptr_t)stats_dev & 7) || ((uintptr_t)chan_scale & 7))
         return RICK_EINVAL;
+    if (n_chan < 0 || (n_chan > 0 && n_vis > 0 && !chan_scale)) return RICK_EINVAL;
     if (n_vis > plan->max_vis) return RICK_ERANGE;
     const rick_params &p = plan->p;
     WsLayout L = rick_ws_layout(&p, plan->max_vis);
@@ -523,7 +558,7 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
         int blocks = plan->num_sms * 4;
-        wrange_kernel<<<blocks, 256, 0, st>>>(uvw, n_vis, w.hdr);
+        wrange_kernel<<<blocks, 256, 0, st>>>(uvw, n_vis, w.hdr, n_chan, chan_scale);
         RICK_LAUNCH_CHECK(plan);
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
@@ -546,7 +581,9 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
         ka.key_lo = rick_dkey(-0.5);
         ka.key_hi = rick_dkey((double)p.n + 0.5);
         ka.ws = w;
-        ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
+        ka.n_chan = n_chan;
+        ka.chan_scale = chan_scale;
+        ka.bulk = n_chan == 0 && ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
         RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -583,7 +620,20 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
                                 const void *vis, const float *weight, void *ws_dev,
                                 size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
 {
-    return rick_bin_impl(plan, n_vis, uvw, vis, weight, ws_dev, ws_bytes, stats_dev, stream, NULL);
+    return rick_bin_impl(plan, n_vis, uvw, vis, weight, ws_dev, ws_bytes, stats_dev, stream, NULL,
+                         0, NULL);
+}
+
+extern "C" rick_status rick_bin_channels(rick_plan *plan, int64_t n_rows, int32_t n_chan,
+                                         const double *uvw_rows, const double *chan_scale,
+                                         const void *vis, const float *weight, void *ws_dev,
+                                         size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
+{
+    if (!plan || n_rows < 0 || n_chan < 1) return RICK_EINVAL;
+    if (n_rows > 0 && !chan_scale) return RICK_EINVAL;
+    if (n_rows > plan_max_rows(plan, n_chan)) return RICK_ERANGE;
+    return rick_bin_impl(plan, n_rows * n_chan, uvw_rows, vis, weight, ws_dev, ws_bytes, stats_dev,
+                         stream, NULL, n_chan, chan_scale);
 }
 
 extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const float *weight,
@@ -694,7 +744,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
                                      (uint32_t)nkb, NULL);
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
-        wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr);
+        wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr, 0, NULL);
         RICK_LAUNCH_CHECK(plan);
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
@@ -717,6 +767,8 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         ka.key_lo = rick_dkey(-0.5);
         ka.key_hi = rick_dkey((double)p.n + 0.5);
         ka.ws = w;
+        ka.n_chan = 0;
+        ka.chan_scale = NULL;
         ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
         RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,

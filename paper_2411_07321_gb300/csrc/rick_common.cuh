@@ -585,12 +585,15 @@ struct TileArgs {
 
 // rick_bin; range_src (device, optional) supplies the w range in place of the
 // plan's (a range found over a larger set by an earlier pass).
+// With n_chan > 0, uvw holds rows of n_chan visibilities and the uvw of
+// visibility i is uvw[i / n_chan] * chan_scale[i % n_chan] (multi-channel input).
 rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, const void *vis,
                           const float *weight, void *ws_dev, size_t ws_bytes,
-                          rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src);
-// Min/max keys of the finite w of uvw[0, n) folded into hdr->wmin_key / wmax_key.
+                          rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src,
+                          int n_chan, const double *chan_scale);
+// Min/max keys of the finite w of visibilities [0, n) folded into hdr->wmin_key / wmax_key.
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
-                        cudaStream_t st);
+                        cudaStream_t st, int n_chan, const double *scale);
 // rick_grid (accumulate = 0) or rick_grid_accumulate (1).
 rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int accumulate,
                            void *stream);

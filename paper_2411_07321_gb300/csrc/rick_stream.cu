@@ -29,8 +29,12 @@
 
 #include "rick_common.cuh"
 
+// Channels of multi-channel input the streamed call accepts (their factors
+// are staged in the staging area).
+#define RICK_STREAM_MAX_CHAN 4096
+
 struct StageLayout {
-    size_t range, total, vis, weight, uvw, bytes;
+    size_t range, total, scale, vis, weight, uvw, bytes;
     size_t uvw_buf, vis_buf, weight_buf;  // bytes of one staging buffer / resident area
     int64_t chunk;
     int resident_uvw;
@@ -52,6 +56,7 @@ static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n
     size_t o = 0;
     S.range = o;  o += rick_align256(sizeof(WsHeader));
     S.total = o;  o += rick_align256(sizeof(rick_bin_stats));
+    S.scale = o;  o += 2 * 8 * (size_t)RICK_STREAM_MAX_CHAN;  // channel factors, per area
     S.vis = o;    o += 2 * S.vis_buf;
     S.weight = o; o += 2 * S.weight_buf;
     S.uvw = o;
@@ -122,24 +127,31 @@ static rick_status stream_resources(rick_plan *plan)
         if (s_ != RICK_OK) return s_;       \
     } while (0)
 
-extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_host,
-                                       const void *vis_host, const float *weight_host,
-                                       void *ws_dev, size_t ws_bytes, void *stage_dev,
-                                       size_t stage_bytes, void *planes_dev, float *image_dev,
-                                       uint32_t flags, rick_bin_stats *stats_dev, void *stream)
+// The streamed path over "units": visibilities (n_chan == 0) or rows of n_chan
+// visibilities whose uvw is the row's times a per-channel factor.
+static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
+                               const double *uvw_host, const double *scale_host,
+                               const void *vis_host, const float *weight_host, void *ws_dev,
+                               size_t ws_bytes, void *stage_dev, size_t stage_bytes,
+                               void *planes_dev, float *image_dev, uint32_t flags,
+                               rick_bin_stats *stats_dev, void *stream)
 {
-    if (!plan || !ws_dev || !stage_dev || !planes_dev || !image_dev || n_vis < 0)
+    if (!plan || !ws_dev || !stage_dev || !planes_dev || !image_dev || n_units < 0)
         return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
-    if (n_vis > 0 && (!uvw_host || !vis_host)) return RICK_EINVAL;
+    if (n_chan < 0 || n_chan > RICK_STREAM_MAX_CHAN) return n_chan < 0 ? RICK_EINVAL : RICK_ERANGE;
+    if (n_units > 0 && (!uvw_host || !vis_host || (n_chan > 0 && !scale_host)))
+        return RICK_EINVAL;
     if (((uintptr_t)stage_dev & 255) || ((uintptr_t)ws_dev & 255) ||
         ((uintptr_t)planes_dev & 15) || ((uintptr_t)image_dev & 3) ||
         ((uintptr_t)stats_dev & 7) || ((uintptr_t)uvw_host & 7) || ((uintptr_t)vis_host & 7) ||
-        ((uintptr_t)weight_host & 3))
+        ((uintptr_t)weight_host & 3) || ((uintptr_t)scale_host & 7))
         return RICK_EINVAL;
-    if (n_vis > 0 && plan->max_vis < 1) return RICK_ERANGE;
+    const int64_t per = n_chan > 0 ? n_chan : 1;  // visibilities per unit
+    const int64_t n_vis = n_units * per;
+    if (n_units > 0 && plan->max_vis < per) return RICK_ERANGE;
     const StageLayout S = stage_layout(&plan->p, plan->max_vis, n_vis, stage_bytes);
-    if (stage_bytes < S.bytes || (S.resident_uvw && S.uvw_buf < 24 * (size_t)n_vis))
+    if (stage_bytes < S.bytes || (S.resident_uvw && S.uvw_buf < 24 * (size_t)n_units))
         return RICK_ERANGE;
     if (ws_bytes < rick_ws_layout(&plan->p, plan->max_vis).total) return RICK_ERANGE;
     RICK_TRY(stream_resources(plan));
@@ -149,8 +161,8 @@ extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const dou
     WsHeader *rh = (WsHeader *)(sb + S.range);
     rick_bin_stats *tot = (rick_bin_stats *)(sb + S.total);
     WsHeader *hdr = rick_ws_ptrs(ws_dev, rick_ws_layout(&plan->p, plan->max_vis)).hdr;
-    const int64_t chunk = S.chunk;
-    const int64_t nchunks = n_vis > 0 ? (n_vis + chunk - 1) / chunk : 1;  // one empty chunk
+    const int64_t chunk = plan->max_vis / per;  // units per chunk (whole rows)
+    const int64_t nchunks = n_units > 0 ? (n_units + chunk - 1) / chunk : 1;  // one empty chunk
     const float2 *vh = (const float2 *)vis_host;
 
     // Before the copy stream writes the staging area: for a staging area new
@@ -167,20 +179,26 @@ extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const dou
     }
     const int area = plan->parity;
     plan->parity ^= 1;
+    // the call before last binned from this area (resident uvw, channel factors)
+    RICK_CUDA_TRY(plan, cudaStreamWaitEvent(cp, plan->ev_area_free[area], 0));
+
+    double *scale_dev = (double *)(sb + S.scale + area * 8 * (size_t)RICK_STREAM_MAX_CHAN);
+    if (n_chan > 0 && n_units > 0)
+        RICK_CUDA_TRY(plan, cudaMemcpyAsync(scale_dev, scale_host, 8 * (size_t)n_chan,
+                                            cudaMemcpyHostToDevice, cp));
+    const double *scale_c = n_chan > 0 ? scale_dev : NULL;
 
     double *uvw_res = (double *)(sb + S.uvw + area * S.uvw_buf);
     if (S.resident_uvw) {
-        // the call before last binned from this area
-        RICK_CUDA_TRY(plan, cudaStreamWaitEvent(cp, plan->ev_area_free[area], 0));
         range_init_kernel<<<1, 1, 0, st>>>(rh);
         RICK_LAUNCH_CHECK(plan);
-        for (int64_t c = 0; c < nchunks && n_vis > 0; ++c) {
-            const int64_t off = c * chunk, nc = n_vis - off < chunk ? n_vis - off : chunk;
+        for (int64_t c = 0; c < nchunks && n_units > 0; ++c) {
+            const int64_t off = c * chunk, nc = n_units - off < chunk ? n_units - off : chunk;
             RICK_CUDA_TRY(plan, cudaMemcpyAsync(uvw_res + 3 * off, uvw_host + 3 * off, 24 * nc,
                                                 cudaMemcpyHostToDevice, cp));
             RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_uvw, cp));
             RICK_CUDA_TRY(plan, cudaStreamWaitEvent(st, plan->ev_uvw, 0));
-            rick_launch_wrange(plan, uvw_res + 3 * off, nc, rh, st);
+            rick_launch_wrange(plan, uvw_res + 3 * off, nc * per, rh, st, n_chan, scale_c);
             RICK_LAUNCH_CHECK(plan);
         }
     }
@@ -188,7 +206,7 @@ extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const dou
     for (int64_t c = 0; c < nchunks; ++c) {
         const int b = (int)(c & 1);
         const int64_t off = c * chunk;
-        const int64_t nc = n_vis - off < chunk ? n_vis - off : chunk;
+        const int64_t nc = n_units - off < chunk ? n_units - off : chunk;
         const double *uvw_c = NULL;
         const void *vis_c = NULL;
         const float *wt_c = NULL;
@@ -205,30 +223,56 @@ extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const dou
                 uvw_c = ub;
             }
             float2 *vb = (float2 *)(sb + S.vis + b * S.vis_buf);
-            RICK_CUDA_TRY(plan, cudaMemcpyAsync(vb, vh + off, 8 * nc, cudaMemcpyHostToDevice, cp));
+            RICK_CUDA_TRY(plan, cudaMemcpyAsync(vb, vh + off * per, 8 * nc * per,
+                                                cudaMemcpyHostToDevice, cp));
             vis_c = vb;
             if (weight_host) {
                 float *wb = (float *)(sb + S.weight + b * S.weight_buf);
-                RICK_CUDA_TRY(plan, cudaMemcpyAsync(wb, weight_host + off, 4 * nc,
+                RICK_CUDA_TRY(plan, cudaMemcpyAsync(wb, weight_host + off * per, 4 * nc * per,
                                                     cudaMemcpyHostToDevice, cp));
                 wt_c = wb;
             }
             RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_ready[b], cp));
             RICK_CUDA_TRY(plan, cudaStreamWaitEvent(st, plan->ev_ready[b], 0));
         }
-        RICK_TRY(rick_bin_impl(plan, nc > 0 ? nc : 0, uvw_c, vis_c, wt_c, ws_dev, ws_bytes, NULL,
-                               st, S.resident_uvw ? rh : NULL));
+        RICK_TRY(rick_bin_impl(plan, nc > 0 ? nc * per : 0, uvw_c, vis_c, wt_c, ws_dev, ws_bytes,
+                               NULL, st, S.resident_uvw ? rh : NULL, n_chan, scale_c));
         // the binning has read staging buffer b (the records are in ws now)
         RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_free[b], st));
         stats_add_kernel<<<1, 1, 0, st>>>(hdr, tot, c == 0);
         RICK_LAUNCH_CHECK(plan);
         RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev, c > 0, st));
     }
-    // every binning of this call has read its resident uvw area
+    // every binning of this call has read its resident uvw area and factors
     RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_area_free[area], st));
     stats_finish_kernel<<<1, 1, 0, st>>>(hdr, tot, stats_dev);
     RICK_LAUNCH_CHECK(plan);
     RICK_TRY(rick_fft_wplanes(plan, planes_dev, 1, st));
     RICK_TRY(rick_wcorrect_stack(plan, planes_dev, ws_dev, image_dev, flags, st));
     return RICK_OK;
+}
+
+extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_host,
+                                       const void *vis_host, const float *weight_host,
+                                       void *ws_dev, size_t ws_bytes, void *stage_dev,
+                                       size_t stage_bytes, void *planes_dev, float *image_dev,
+                                       uint32_t flags, rick_bin_stats *stats_dev, void *stream)
+{
+    return stream_impl(plan, n_vis, 0, uvw_host, NULL, vis_host, weight_host, ws_dev, ws_bytes,
+                       stage_dev, stage_bytes, planes_dev, image_dev, flags, stats_dev, stream);
+}
+
+extern "C" rick_status rick_image_host_channels(rick_plan *plan, int64_t n_rows, int32_t n_chan,
+                                                const double *uvw_rows_host,
+                                                const double *chan_scale_host,
+                                                const void *vis_host, const float *weight_host,
+                                                void *ws_dev, size_t ws_bytes, void *stage_dev,
+                                                size_t stage_bytes, void *planes_dev,
+                                                float *image_dev, uint32_t flags,
+                                                rick_bin_stats *stats_dev, void *stream)
+{
+    if (n_chan < 1) return RICK_EINVAL;
+    return stream_impl(plan, n_rows, n_chan, uvw_rows_host, chan_scale_host, vis_host, weight_host,
+                       ws_dev, ws_bytes, stage_dev, stage_bytes, planes_dev, image_dev, flags,
+                       stats_dev, stream);
 }

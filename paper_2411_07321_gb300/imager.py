@@ -78,6 +78,21 @@ class Imager:
                    self.ws_bytes, self.stats_buf.data_ptr(), self._stream())
         self.n_vis = n
 
+    def bin_channels(self, uvw_rows: torch.Tensor, chan_scale: torch.Tensor, vis: torch.Tensor,
+                     weight: torch.Tensor | None = None):
+        """Binning of rows of n_chan channels: uvw once per row, times a factor per
+        channel (vis and weight hold n_rows * n_chan values, channel fastest)."""
+        n_rows, n_chan = uvw_rows.shape[0], chan_scale.shape[0]
+        self._check(uvw_rows, torch.float64, (n_rows, 3), "uvw_rows")
+        self._check(chan_scale, torch.float64, (n_chan,), "chan_scale")
+        self._check(vis.reshape(-1), torch.complex64, (n_rows * n_chan,), "vis")
+        if weight is not None:
+            self._check(weight.reshape(-1), torch.float32, (n_rows * n_chan,), "weight")
+        R.rick_bin_channels(self.plan, n_rows, n_chan, uvw_rows.data_ptr(), chan_scale.data_ptr(),
+                            vis.data_ptr(), _ptr(weight), self.ws.data_ptr(), self.ws_bytes,
+                            self.stats_buf.data_ptr(), self._stream())
+        self.n_vis = n_rows * n_chan
+
     def bin_values(self, vis: torch.Tensor, weight: torch.Tensor | None = None):
         self._check(vis, torch.complex64, (self.n_vis,), "vis")
         if weight is not None:
@@ -164,16 +179,25 @@ class Imager:
 
     def image_streamed(self, uvw_host: torch.Tensor, vis_host: torch.Tensor,
                        weight_host: torch.Tensor | None, out_host: torch.Tensor | None = None,
-                       flags: int = IMAGE_FLAGS) -> torch.Tensor:
+                       flags: int = IMAGE_FLAGS,
+                       chan_scale: torch.Tensor | None = None) -> torch.Tensor:
         """The image of a visibility set in host memory, of any size, streamed
         through the GPU in chunks of this imager's ``max_vis`` (copies of the
         next chunk overlap binning and gridding of the current one; pinned
-        host tensors give the overlap).  Returns the device image, also copied
-        into ``out_host`` if given, all ordered on the current stream."""
-        n = uvw_host.shape[0]
-        for t, dt, shape, name in ((uvw_host, torch.float64, (n, 3), "uvw"),
+        host tensors give the overlap).  With ``chan_scale`` (float64
+        [n_chan]) the input is multi-channel: ``uvw_host`` holds one row per
+        n_chan visibilities, scaled per channel.  Returns the device image,
+        also copied into ``out_host`` if given, all ordered on the current
+        stream."""
+        n_units = uvw_host.shape[0]
+        n_chan = 0 if chan_scale is None else chan_scale.shape[0]
+        n = n_units * max(n_chan, 1)
+        vis_host = vis_host.reshape(-1)
+        weight_host = None if weight_host is None else weight_host.reshape(-1)
+        for t, dt, shape, name in ((uvw_host, torch.float64, (n_units, 3), "uvw"),
                                    (vis_host, torch.complex64, (n,), "vis"),
-                                   (weight_host, torch.float32, (n,), "weight")):
+                                   (weight_host, torch.float32, (n,), "weight"),
+                                   (chan_scale, torch.float64, (n_chan,), "chan_scale")):
             if t is None:
                 continue
             if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or \
@@ -185,12 +209,23 @@ class Imager:
             self._stage = torch.empty(need, dtype=torch.uint8, device=self.device)
         if getattr(self, "_out_img", None) is None:
             self._out_img = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
-        R.rick_image_host(self.plan, n, uvw_host.data_ptr(), vis_host.data_ptr(),
-                          _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
-                          self._stage.data_ptr(), self._stage.numel(), self.planes.data_ptr(),
-                          self._out_img.data_ptr(), flags, self.stats_buf.data_ptr(),
-                          self._stream())
-        self.n_vis = n - (n - 1) // self.max_vis * self.max_vis if n else 0  # the last chunk
+        if n_chan:
+            R.rick_image_host_channels(self.plan, n_units, n_chan, uvw_host.data_ptr(),
+                                       chan_scale.data_ptr(), vis_host.data_ptr(),
+                                       _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
+                                       self._stage.data_ptr(), self._stage.numel(),
+                                       self.planes.data_ptr(), self._out_img.data_ptr(), flags,
+                                       self.stats_buf.data_ptr(), self._stream())
+            rows = max(self.max_vis // n_chan, 1)
+            last = n_units - (n_units - 1) // rows * rows if n_units else 0
+            self.n_vis = last * n_chan  # the last chunk
+        else:
+            R.rick_image_host(self.plan, n, uvw_host.data_ptr(), vis_host.data_ptr(),
+                              _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
+                              self._stage.data_ptr(), self._stage.numel(), self.planes.data_ptr(),
+                              self._out_img.data_ptr(), flags, self.stats_buf.data_ptr(),
+                              self._stream())
+            self.n_vis = n - (n - 1) // self.max_vis * self.max_vis if n else 0  # the last chunk
         if out_host is not None:
             out_host.copy_(self._out_img, non_blocking=True)
         return self._out_img

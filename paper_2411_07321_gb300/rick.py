@@ -54,7 +54,8 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
            "rick_bin_noalloc", "rick_bin_values", "rick_grid", "rick_grid_accumulate",
            "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
-           "rick_stream_bytes", "rick_image_host"]
+           "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
+           "rick_image_host_channels"]
 
 
 def _load():
@@ -83,6 +84,9 @@ def _load():
         "rick_grid_accumulate": [vp, vp, vp, vp],
         "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
         "rick_image_host": [vp, i64, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32, vp, vp],
+        "rick_bin_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, vp],
+        "rick_image_host_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32,
+                                     vp, vp],
         "rick_fft_wplanes": [vp, vp, i32, vp],
         "rick_wcorrect_stack": [vp, vp, vp, vp, u32, vp],
         "rick_wspread": [vp, vp, vp, vp, u32, vp],
@@ -170,6 +174,24 @@ def rick_bin_noalloc(plan, n_vis, uvw, vis, weight, ws, ws_bytes, stats, stream)
     (n_vis <= 262144, at most 131072 bins)."""
     _check("rick_bin_noalloc", _L.rick_bin_noalloc(plan, int(n_vis), uvw, vis, weight or None, ws,
                                                    int(ws_bytes), stats or None, stream or None))
+
+
+def rick_bin_channels(plan, n_rows, n_chan, uvw_rows, chan_scale, vis, weight, ws, ws_bytes, stats,
+                      stream) -> None:
+    """rick_bin for rows of n_chan channels with per-row uvw and per-channel factors."""
+    _check("rick_bin_channels", _L.rick_bin_channels(plan, int(n_rows), int(n_chan), uvw_rows,
+                                                     chan_scale, vis, weight or None, ws,
+                                                     int(ws_bytes), stats or None, stream or None))
+
+
+def rick_image_host_channels(plan, n_rows, n_chan, uvw_rows_host, chan_scale_host, vis_host,
+                             weight_host, ws, ws_bytes, stage, stage_bytes, planes, image, flags,
+                             stats, stream) -> None:
+    """Streamed imaging of multi-channel rows held in host memory."""
+    _check("rick_image_host_channels", _L.rick_image_host_channels(
+        plan, int(n_rows), int(n_chan), uvw_rows_host, chan_scale_host, vis_host,
+        weight_host or None, ws, int(ws_bytes), stage, int(stage_bytes), planes, image, int(flags),
+        stats or None, stream or None))
 
 
 def rick_bin_values(plan, vis, weight, ws, stats, stream) -> None:

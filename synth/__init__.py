@@ -117,15 +117,20 @@ def lib():
         L.sx_observation.restype = ctypes.c_int64
         D = ctypes.POINTER(ctypes.c_double)
         F = ctypes.POINTER(ctypes.c_float)
-        L.sx_observation.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, D, F, F, D, D, D]
+        L.sx_observation.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, D, F, F, D, D, D, D, D]
         _lib = L
     return _lib
 
 
-def generate(obs: Observation):
-    """Returns dict(uvw f64 [n,3], vis c64 [n], weight f32 [n], src_l, src_m, src_flux)."""
+def generate(obs: Observation, rows: bool = False):
+    """Returns dict(uvw f64 [n,3], vis c64 [n], weight f32 [n], src_l, src_m, src_flux);
+    with rows=True also uvw_rows f64 [ceil(n / n_chan), 3] and chan_scale f64
+    [n_chan], with uvw[r * n_chan + c] = uvw_rows[r] * chan_scale[c] exactly."""
     n = obs.n_keep
     uvw = np.empty((n, 3), np.float64)
+    n_rows = (n + obs.n_chan - 1) // obs.n_chan
+    ur = np.empty((n_rows, 3), np.float64) if rows else None
+    cf = np.empty(obs.n_chan, np.float64) if rows else None
     vis = np.empty(n, np.complex64)
     wt = np.empty(n, np.float32)
     k = max(obs.n_src, 1)
@@ -134,9 +139,14 @@ def generate(obs: Observation):
     F = ctypes.POINTER(ctypes.c_float)
     got = lib().sx_observation(ctypes.byref(obs.c()), n, uvw.ctypes.data_as(D),
                                vis.ctypes.data_as(F), wt.ctypes.data_as(F), sl.ctypes.data_as(D),
-                               sm.ctypes.data_as(D), ss.ctypes.data_as(D))
-    return dict(uvw=uvw[:got], vis=vis[:got], weight=wt[:got], src_l=sl[:obs.n_src],
-                src_m=sm[:obs.n_src], src_flux=ss[:obs.n_src])
+                               sm.ctypes.data_as(D), ss.ctypes.data_as(D),
+                               ur.ctypes.data_as(D) if rows else None,
+                               cf.ctypes.data_as(D) if rows else None)
+    out = dict(uvw=uvw[:got], vis=vis[:got], weight=wt[:got], src_l=sl[:obs.n_src],
+               src_m=sm[:obs.n_src], src_flux=ss[:obs.n_src])
+    if rows:
+        out.update(uvw_rows=ur[:(got + obs.n_chan - 1) // obs.n_chan], chan_scale=cf)
+    return out
 
 
 # The five workloads.  Sizes follow the paper's Table 2 shapes scaled to one GPU.

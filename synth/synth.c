@@ -131,9 +131,13 @@ static void sx_row_uvw(const sx_config *c, const double *xyz, const int *bl_a, c
 /* Full observation: uvw [n_keep][3] (f64, lambda), vis [n_keep] as (re, im)
  * f32 pairs, weight [n_keep] f32, and the sky (l, m, flux) [n_src].
  * Rows are (time, baseline); each row holds n_chan channels with uvw scaled by
- * nu_c / nu0.  Only the first n_keep visibilities are produced. */
+ * f_c = nu_c / nu0: uvw[row n_chan + c] = uvw_rows[row] * f_c, one FP64
+ * product per coordinate.  uvw_rows [ceil(n_keep / n_chan)][3] and chan_f
+ * [n_chan] receive those factors if not NULL.  Only the first n_keep
+ * visibilities are produced. */
 int64_t sx_observation(const sx_config *c, int64_t n_keep, double *uvw, float *vis, float *weight,
-                       double *src_l, double *src_m, double *src_s)
+                       double *src_l, double *src_m, double *src_s, double *uvw_rows,
+                       double *chan_f)
 {
     int n_ant = c->n_ant;
     int64_t n_bl = (int64_t)n_ant * (n_ant - 1) / 2;
@@ -170,6 +174,8 @@ int64_t sx_observation(const sx_config *c, int64_t n_keep, double *uvw, float *v
     double s_uv = max_uv > 0 ? c->uv_max / max_uv : 1.0, s_w = max_w > 0 ? c->w_max / max_w : 1.0;
 
     sx_sources(c, src_l, src_m, src_s);
+    if (chan_f)
+        for (int ch = 0; ch < c->n_chan; ++ch) chan_f[ch] = (c->nu0 + ch * c->dnu) / c->nu0;
     double *src_amp = malloc(sizeof(double) * (c->n_src > 0 ? c->n_src : 1));
     double *src_nm1 = malloc(sizeof(double) * (c->n_src > 0 ? c->n_src : 1));
     for (int k = 0; k < c->n_src; ++k) {
@@ -186,6 +192,11 @@ int64_t sx_observation(const sx_config *c, int64_t n_keep, double *uvw, float *v
             double q[3];
             sx_row_uvw(c, xyz, bl_a, bl_b, n_bl, r, q);
             double u0 = q[0] * s_uv, v0 = q[1] * s_uv, w0 = q[2] * s_w;
+            if (uvw_rows) {
+                uvw_rows[3 * r] = u0;
+                uvw_rows[3 * r + 1] = v0;
+                uvw_rows[3 * r + 2] = w0;
+            }
             int64_t i0 = r * c->n_chan;
             int nc = (int)((n_keep - i0) < c->n_chan ? (n_keep - i0) : c->n_chan);
             for (int ch = 0; ch < nc; ++ch) {

@@ -6,8 +6,9 @@ w-planes, Kaiser-Bessel W=7, uv-tile 64.
   counts and the w range bit for bit against the oracle's counting sort of the
   whole set; the bin, cell, fractional offsets and value of a random sample of
   200,000 records bit for bit against the oracle's per-visibility geometry.
-- Image: the device-resident path and the streamed host path (chunks of 2^24
-  visibilities from pinned host memory, as bench.py's e2e) against the FP64
+- Image: the device-resident path, the streamed host path (chunks of 2^24
+  visibilities from pinned host memory, as bench.py's e2e) and the streamed
+  multi-channel path (uvw once per row of 16 channels) against the FP64
   oracle's image of the whole set, 1e-5 of peak on the tapered image and on
   the inner region (as in test_gpu_parity).
 
@@ -38,7 +39,7 @@ def P():
 @pytest.fixture(scope="module")
 def full():
     wl = synth.WORKLOADS["lofar"]
-    d = synth.generate(wl.obs)
+    d = synth.generate(wl.obs, rows=True)
     op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov, kernel=oracle.KB, support=wl.support,
                        tile=wl.tile)
     ref, st = oracle.image(op, d["uvw"], d["vis"], d["weight"])
@@ -112,6 +113,27 @@ def test_full_size_streamed_image(P, full):
     torch.cuda.synchronize()
     e = errors(out.numpy(), ref, op)
     print(f"full-size streamed image error: tapered {e['tapered']:.2e}, inner {e['inner']:.2e}")
+    assert e["tapered"] <= TOL and e["inner"] <= TOL
+    st = im.stats()
+    assert st["n_binned"] == ost["n_binned"]
+    assert st["sum_weight"] == pytest.approx(ost["sum_weight_exact"], rel=1e-13)
+    im.close()
+
+
+def test_full_size_streamed_channel_image(P, full):
+    wl, d, op, ref, ost = full
+    dev = torch.device("cuda:0")
+    h = {k: torch.from_numpy(d[k]).pin_memory()
+         for k in ("uvw_rows", "chan_scale", "vis", "weight")}
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                  max_vis=1 << 24, device=dev)
+    out = torch.empty((wl.n, wl.n), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        im.image_streamed(h["uvw_rows"], h["vis"], h["weight"], out, chan_scale=h["chan_scale"])
+    torch.cuda.synchronize()
+    e = errors(out.numpy(), ref, op)
+    print(f"full-size streamed channel image error: tapered {e['tapered']:.2e}, "
+          f"inner {e['inner']:.2e}")
     assert e["tapered"] <= TOL and e["inner"] <= TOL
     st = im.stats()
     assert st["n_binned"] == ost["n_binned"]

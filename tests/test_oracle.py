@@ -13,6 +13,7 @@ import pytest
 import scipy.special as sp
 
 import oracle
+import synth
 
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 
@@ -381,3 +382,22 @@ def test_single_plane_zero_w_is_plain_2d_imaging():
     assert np.abs(img1 - ref).max() <= 1e-12 * np.abs(ref).max()
     img4, _ = oracle.image(oracle.Params(**{**p.__dict__, "n_w": 4}), uvw, vis, wt, flags=0)
     assert np.abs(img4 - img1).max() <= 1e-13 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- the input generator
+
+@pytest.mark.parametrize("name,n_keep", [("small", 5000), ("lofar", 20000), ("lofar", 16 * 1000 + 5)])
+def test_generator_rows_times_channel_factors(name, n_keep):
+    """The per-visibility uvw of the generator is the per-row uvw times the
+    channel factor, one FP64 product per coordinate: the multi-channel input
+    form (rows and factors) describes exactly the same visibilities."""
+    obs = synth.scaled(name, n_keep=n_keep).obs
+    d = synth.generate(obs, rows=True)
+    nc = obs.n_chan
+    assert d["uvw_rows"].shape == ((n_keep + nc - 1) // nc, 3)
+    assert np.array_equal(d["chan_scale"], (obs.nu0 + np.arange(nc) * obs.dnu) / obs.nu0)
+    full = (d["uvw_rows"][:, None, :] * d["chan_scale"][None, :, None]).reshape(-1, 3)[:n_keep]
+    assert np.array_equal(full, d["uvw"])
+    # the visibilities are those of the per-visibility call
+    d2 = synth.generate(obs)
+    assert np.array_equal(d2["vis"], d["vis"]) and np.array_equal(d2["uvw"], d["uvw"])
