@@ -220,7 +220,7 @@ def run_ours(args, wl):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    data = synth.generate(wl.obs)
+    data = synth.generate(wl.obs, rows=True)
     n_vis = len(data["vis"])
     uvw_h = torch.from_numpy(data["uvw"]).pin_memory()
     vis_h = torch.from_numpy(data["vis"]).pin_memory()
@@ -307,8 +307,24 @@ def run_ours(args, wl):
             dist.barrier()
         return t
 
-    e2e_ms = timed(lambda: ims.image_streamed(uvw_h, vis_h, wt_h, out_h))
+    e2e_vis_ms = timed(lambda: ims.image_streamed(uvw_h, vis_h, wt_h, out_h))
     e2e_resident_ms = timed(lambda: im.image_from_host(uvw_h, vis_h, wt_h, out_h))
+    # the same visibilities as rows of n_chan channels (a measurement set's
+    # layout): uvw once per row and a factor per channel
+    n_chan = wl.obs.n_chan
+    rows_ok = n_vis % n_chan == 0
+    if rows_ok:
+        rows_h = torch.from_numpy(data["uvw_rows"]).pin_memory()
+        scale_h = torch.from_numpy(data["chan_scale"]).pin_memory()
+        e2e_ms = timed(lambda: ims.image_streamed(rows_h, vis_h, wt_h, out_h, chan_scale=scale_h))
+        h2d = rows_h.numel() * 8 + scale_h.numel() * 8 + n_vis * (8 + 4)
+        call = (f"Imager.image_streamed with chan_scale (rick_image_host_channels): rows of "
+                f"{n_chan} channels with uvw once per row, chunks of {min(args.chunk, n_vis)} "
+                f"visibilities, w range from the data")
+    else:
+        e2e_ms, h2d = e2e_vis_ms, n_vis * (24 + 8 + 4)
+        call = (f"Imager.image_streamed (rick_image_host), chunks of {min(args.chunk, n_vis)} "
+                f"visibilities, w range from the data")
     ims.close()
     e2e_value = n_vis * args.steps * world / (e2e_ms / 1e3)
 
@@ -338,10 +354,14 @@ def run_ours(args, wl):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**config_of(wl), "parallelism": f"replicas{world}"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_vis * (24 + 8 + 4),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": wl.n * wl.n * 4, "ms_per_step": e2e_ms / args.steps,
-                "call": f"Imager.image_streamed (rick_image_host), chunks of "
-                        f"{min(args.chunk, n_vis)} visibilities, w range from the data",
+                "call": call,
+                "per_visibility_uvw": {
+                    "value": n_vis * args.steps * world / (e2e_vis_ms / 1e3),
+                    "ms_per_step": e2e_vis_ms / args.steps,
+                    "h2d_bytes_per_step": n_vis * (24 + 8 + 4),
+                    "call": "Imager.image_streamed (rick_image_host), uvw per visibility"},
                 "resident_call_ms_per_step": e2e_resident_ms / args.steps},
         "roofline": roofline,
         "stages": {"ms": stage_ms, "gbps": gbps, "algorithmic_bytes": alg,
