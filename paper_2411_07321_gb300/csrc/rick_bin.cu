@@ -112,34 +112,79 @@ __global__ void bin_init_kernel(WsHeader *hdr, uint64_t n_vis, uint32_t chunk_ca
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
                         cudaStream_t st, int n_chan, const double *scale);
 
-// w of visibility i: uvw[i][2], or for multi-channel input (n_chan > 0) the
-// row's w times the channel factor, one FP64 product.
-__device__ __forceinline__ double vis_w(const double *uvw, int64_t i, int n_chan,
-                                        const double *scale)
+
+// Fold the key of w into [lo, hi] unless w is not finite.
+__device__ __forceinline__ void wrange_fold(double w, uint64_t &lo, uint64_t &hi)
 {
-    if (n_chan <= 0) return uvw[3 * i + 2];
-    const int64_t r = i / n_chan;
-    return uvw[3 * r + 2] * scale[i - r * n_chan];
+    const uint64_t b = rick_dbits(w);
+    if (((b >> 52) & 0x7FF) == 0x7FF) return;  // not finite
+    const uint64_t k = rick_dkey(w);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
 }
 
+// w range of visibilities [0, n).  Multi-channel input (n_chan > 0): rows of
+// n_chan visibilities, w = the row's w times the channel factor.  When every
+// factor is positive and finite, rounding is monotone in the factor, so a
+// row's extremes are its products with the smallest and the largest factor
+// (unless one of those overflows, when every channel is folded).
 __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n_chan,
                               const double *scale)
 {
+    __shared__ double s_min[32], s_max[32];
+    __shared__ int s_ok[32];
     uint64_t lo = ~0ull, hi = 0ull;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t b = rick_dbits(vis_w(uvw, i, n_chan, scale));
-        if (((b >> 52) & 0x7FF) == 0x7FF) continue;  // not finite
-        uint64_t k = rick_dkey(rick_bitsd(b));
-        lo = k < lo ? k : lo;
-        hi = k > hi ? k : hi;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (n_chan <= 0) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            wrange_fold(uvw[3 * i + 2], lo, hi);
+    } else {
+        // smallest and largest factor, and whether all are positive and finite
+        double fmin = INFINITY, fmax = 0.0;
+        int ok = 1;
+        for (int c = threadIdx.x; c < n_chan; c += blockDim.x) {
+            const double f = scale[c];
+            ok &= (f > 0.0 && f < INFINITY) ? 1 : 0;
+            fmin = fmin < f ? fmin : f;
+            fmax = fmax > f ? fmax : f;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double a = __shfl_xor_sync(FULL, fmin, o), b = __shfl_xor_sync(FULL, fmax, o);
+            fmin = fmin < a ? fmin : a;
+            fmax = fmax > b ? fmax : b;
+            ok &= __shfl_xor_sync(FULL, ok, o);
+        }
+        if (lane == 0) {
+            s_min[wid] = fmin;
+            s_max[wid] = fmax;
+            s_ok[wid] = ok;
+        }
+        __syncthreads();
+        for (int k = 0; k < nw; ++k) {
+            fmin = fmin < s_min[k] ? fmin : s_min[k];
+            fmax = fmax > s_max[k] ? fmax : s_max[k];
+            ok &= s_ok[k];
+        }
+        const int64_t n_rows = n / n_chan;  // whole rows (callers pass n = rows * n_chan)
+        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows;
+             r += (int64_t)gridDim.x * blockDim.x) {
+            const double w0 = uvw[3 * r + 2];
+            const double a = w0 * fmin, b = w0 * fmax;
+            if (ok && isfinite(a) && isfinite(b)) {
+                wrange_fold(a, lo, hi);
+                wrange_fold(b, lo, hi);
+            } else {
+                for (int c = 0; c < n_chan; ++c) wrange_fold(w0 * scale[c], lo, hi);
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         uint64_t l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
         lo = l2 < lo ? l2 : lo;
         hi = h2 > hi ? h2 : hi;
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (lo != ~0ull) atomicMin(&hdr->wmin_key, (unsigned long long)lo);
         if (hi != 0ull) atomicMax(&hdr->wmax_key, (unsigned long long)hi);
     }

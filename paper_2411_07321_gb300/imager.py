@@ -187,8 +187,11 @@ class Imager:
         host tensors give the overlap).  With ``chan_scale`` (float64
         [n_chan]) the input is multi-channel: ``uvw_host`` holds one row per
         n_chan visibilities, scaled per channel.  Returns the device image,
-        also copied into ``out_host`` if given, all ordered on the current
-        stream."""
+        ordered on the current stream.  If ``out_host`` is given the image is
+        also copied there on this imager's copy-out stream, so that the copy
+        overlaps the next call's work: synchronise the device (or call
+        ``wait_out()``) before reading it.  Consecutive calls alternate between
+        two device image buffers."""
         n_units = uvw_host.shape[0]
         n_chan = 0 if chan_scale is None else chan_scale.shape[0]
         n = n_units * max(n_chan, 1)
@@ -207,14 +210,24 @@ class Imager:
         if getattr(self, "_stage", None) is None or self._stage.numel() < need:
             self._stage = None
             self._stage = torch.empty(need, dtype=torch.uint8, device=self.device)
-        if getattr(self, "_out_img", None) is None:
-            self._out_img = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
+        if getattr(self, "_out_imgs", None) is None:
+            self._out_imgs = [torch.empty((self.n, self.n), dtype=torch.float32,
+                                          device=self.device) for _ in range(2)]
+            self._out_done = [None, None]
+            self._out_i = 0
+            self._copy_out = torch.cuda.Stream(device=self.device)
+        i = self._out_i
+        self._out_i ^= 1
+        img = self._out_imgs[i]
+        cur = torch.cuda.current_stream(self.device)
+        if self._out_done[i] is not None:  # the copy-out of this buffer two calls ago
+            cur.wait_event(self._out_done[i])
         if n_chan:
             R.rick_image_host_channels(self.plan, n_units, n_chan, uvw_host.data_ptr(),
                                        chan_scale.data_ptr(), vis_host.data_ptr(),
                                        _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
                                        self._stage.data_ptr(), self._stage.numel(),
-                                       self.planes.data_ptr(), self._out_img.data_ptr(), flags,
+                                       self.planes.data_ptr(), img.data_ptr(), flags,
                                        self.stats_buf.data_ptr(), self._stream())
             rows = max(self.max_vis // n_chan, 1)
             last = n_units - (n_units - 1) // rows * rows if n_units else 0
@@ -223,12 +236,25 @@ class Imager:
             R.rick_image_host(self.plan, n, uvw_host.data_ptr(), vis_host.data_ptr(),
                               _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
                               self._stage.data_ptr(), self._stage.numel(), self.planes.data_ptr(),
-                              self._out_img.data_ptr(), flags, self.stats_buf.data_ptr(),
-                              self._stream())
+                              img.data_ptr(), flags, self.stats_buf.data_ptr(), self._stream())
             self.n_vis = n - (n - 1) // self.max_vis * self.max_vis if n else 0  # the last chunk
         if out_host is not None:
-            out_host.copy_(self._out_img, non_blocking=True)
-        return self._out_img
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            self._copy_out.wait_event(ready)
+            with torch.cuda.stream(self._copy_out):
+                out_host.copy_(img, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(self._copy_out)
+            self._out_done[i] = done
+        else:
+            self._out_done[i] = None
+        return img
+
+    def wait_out(self):
+        """Wait until the copies into ``out_host`` of ``image_streamed`` are done."""
+        if getattr(self, "_copy_out", None) is not None:
+            self._copy_out.synchronize()
 
     def set_geometry(self, fov: float, w_range: tuple[float, float] | None = None):
         """Re-target the resident plan to another field of view / w range."""
@@ -265,6 +291,7 @@ class Imager:
         stream synchronised) -- the server only closes idle slots."""
         if getattr(self, "plan", None):
             torch.cuda.current_stream(self.device).synchronize()
+            self.wait_out()
             R.rick_plan_destroy(self.plan)
             self.plan = None
 
