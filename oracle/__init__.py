@@ -124,6 +124,8 @@ def lib():
         L.or_dft.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _D,
                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_double,
                              _D]
+        L.or_density_weights.argtypes = [P, ctypes.c_int64, _D, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_double, _D]
         L.or_max_threads.restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -280,6 +282,19 @@ def dft(n: int, fov: float, uvw, vis, weight=None, flags: int = 0, sum_weight: f
     lib().or_dft(int(n), float(fov), uvw.shape[0], _p(uvw, ctypes.c_double), _vp(vis), _vp(wt),
                  int(flags), float(sum_weight), _p(img, ctypes.c_double))
     return img
+
+
+WEIGHT_UNIFORM, WEIGHT_BRIGGS = 1, 2
+
+
+def density_weights(p: Params, uvw, weight=None, scheme: int = WEIGHT_BRIGGS,
+                    robust: float = 0.0) -> np.ndarray:
+    """Uniform or Briggs-robust imaging weights (FP64), 0 for dropped visibilities."""
+    uvw, wt = _uvw(uvw), _wt(weight)
+    out = np.empty(uvw.shape[0], np.float64)
+    lib().or_density_weights(ctypes.byref(p.c()), uvw.shape[0], _p(uvw, ctypes.c_double),
+                             _vp(wt), int(scheme), float(robust), _p(out, ctypes.c_double))
+    return out
 
 
 def max_threads() -> int:

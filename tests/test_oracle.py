@@ -401,3 +401,46 @@ def test_generator_rows_times_channel_factors(name, n_keep):
     # the visibilities are those of the per-visibility call
     d2 = synth.generate(obs)
     assert np.array_equal(d2["vis"], d["vis"]) and np.array_equal(d2["uvw"], d["uvw"])
+
+
+# ---------------------------------------------------------------- imaging weights
+
+def test_density_weights_hand_example():
+    """Three visibilities, two in one cell (weights 1 and 2) and one alone
+    (weight 4): densities 3 and 4.  Uniform: 1/3, 2/3, 1.  Briggs R = 0:
+    f^2 = 25 / ((3^2 + 4^2) / 7) = 7, weights 1/22, 2/22, 4/29."""
+    n, fov = 64, 0.01
+    p = oracle.Params(n=n, n_w=1, fov=fov, kernel=oracle.KB, support=1, tile=16)
+    cell = 1.0 / fov
+    uvw = np.array([[3 * cell, 2 * cell, 0.0], [3.2 * cell, 1.9 * cell, 0.0],
+                    [-5 * cell, 7 * cell, 0.0]])
+    wt = np.array([1.0, 2.0, 4.0])
+    u = oracle.density_weights(p, uvw, wt, oracle.WEIGHT_UNIFORM)
+    assert u == pytest.approx([1 / 3, 2 / 3, 1.0], rel=1e-15)
+    b = oracle.density_weights(p, uvw, wt, oracle.WEIGHT_BRIGGS, 0.0)
+    assert b == pytest.approx([1 / 22, 2 / 22, 4 / 29], rel=1e-15)
+
+
+def test_density_weights_limits_and_cell_sums():
+    """Uniform: the new weights of every occupied cell sum to 1.  Briggs tends
+    to natural weighting as R grows and to uniform (up to one factor f^2) as R
+    falls.  Dropped visibilities get 0."""
+    d = synth.generate(synth.scaled("small", n_keep=20000).obs)
+    wl = synth.WORKLOADS["small"]
+    n = 64  # the outer uv tracks leave this grid: some visibilities are dropped
+    p = oracle.Params(n=n, n_w=wl.n_w, fov=1.0 * np.pi / 180, kernel=oracle.KB, support=7,
+                      tile=16)
+    wt = 0.5 + rng(3).random(len(d["vis"]))
+    g = oracle.coords(p, d["uvw"])
+    kept = g["status"] == 0
+    assert (~kept).any() and kept.any()
+    uni = oracle.density_weights(p, d["uvw"], wt, oracle.WEIGHT_UNIFORM)
+    assert np.all(uni[~kept] == 0.0)
+    cells = (g["ay"][kept] + 3) * n + g["ax"][kept] + 3
+    sums = np.bincount(cells, weights=uni[kept])
+    assert np.allclose(sums[np.unique(cells)], 1.0, rtol=1e-12)
+    nat = oracle.density_weights(p, d["uvw"], wt, oracle.WEIGHT_BRIGGS, 8.0)
+    assert np.allclose(nat[kept], wt[kept], rtol=1e-6)
+    rob = oracle.density_weights(p, d["uvw"], wt, oracle.WEIGHT_BRIGGS, -8.0)
+    ratio = rob[kept] / uni[kept]
+    assert np.allclose(ratio, ratio[0], rtol=1e-6)
