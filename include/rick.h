@@ -59,6 +59,10 @@ typedef int32_t rick_status;
 #define RICK_PHASE_FP32 8u /* ablation: w-phase argument in plain FP32 instead of       */
                            /* double-single (~48-bit) arithmetic                         */
 
+/* Imaging-weight schemes of rick_density_weights. */
+#define RICK_WEIGHT_UNIFORM 1 /* w / D                                           */
+#define RICK_WEIGHT_BRIGGS 2  /* w / (1 + f^2 D), Briggs' robust weighting        */
+
 typedef struct rick_params {
     int32_t n;          /* grid side = image side, power of two, 16 ... 32768           */
     int32_t n_w;        /* number of w-planes, >= 1                                     */
@@ -309,6 +313,28 @@ rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_ho
                             size_t ws_bytes, void *stage_dev, size_t stage_bytes,
                             void *planes_dev, float *image_dev, uint32_t flags,
                             rick_bin_stats *stats_dev, void *stream);
+
+/* Imaging weights from the uv-cell density (SURVEY f-3; the paper's §2 names
+ * Briggs 1995 for the weighting).  The density D of a uv cell is the sum of the
+ * natural weights of the kept visibilities whose centre cell c (the cell
+ * nearest to (x, y), as in rick_bin) it is, over all w-planes.
+ *   RICK_WEIGHT_UNIFORM: w' = w / D
+ *   RICK_WEIGHT_BRIGGS:  w' = w / (1 + f^2 D),
+ *                        f^2 = (5 10^-robust)^2 / (sum_cells D^2 / sum w)
+ * Dropped visibilities get w' = 0.  The pass reads the corners and keys that
+ * the last rick_bin / rick_bin_channels of these n_vis visibilities left in
+ * ws_dev, and their weights weight_dev (NULL: unit, as given to the binning).
+ * To image with the new weights, pass them to rick_bin_values, then grid as
+ * usual.  D is accumulated in FP32 with float atomics (order unspecified),
+ * sum D^2 in FP64.
+ *   scratch_dev: rick_density_scratch_bytes(params) bytes, 256-byte aligned
+ *   weight_out_dev: float32 [n_vis], input order
+ * Errors: RICK_EINVAL (NULL pointer, misalignment, unknown scheme, robust not
+ * finite), RICK_ERANGE (n_vis > max_vis, scratch too small). */
+rick_status rick_density_scratch_bytes(const rick_params *params, size_t *bytes);
+rick_status rick_density_weights(rick_plan *plan, int64_t n_vis, const float *weight_dev,
+                                 void *ws_dev, int32_t scheme, double robust, void *scratch_dev,
+                                 size_t scratch_bytes, float *weight_out_dev, void *stream);
 
 /* rick_image_host for multi-channel input held in host memory: rows of n_chan
  * channels with uvw once per row and a factor per channel, as for

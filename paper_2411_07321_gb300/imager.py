@@ -100,6 +100,32 @@ class Imager:
         R.rick_bin_values(self.plan, vis.data_ptr(), _ptr(weight), self.ws.data_ptr(),
                           self.stats_buf.data_ptr(), self._stream())
 
+    def density_weights(self, scheme: str = "briggs", robust: float = 0.0,
+                        weight: torch.Tensor | None = None) -> torch.Tensor:
+        """Uniform or Briggs-robust imaging weights (float32, input order) from the
+        uv-cell density of the last binning; ``weight`` are the weights that
+        binning was given (None: unit)."""
+        schemes = {"uniform": R.RICK_WEIGHT_UNIFORM, "briggs": R.RICK_WEIGHT_BRIGGS}
+        if weight is not None:
+            self._check(weight, torch.float32, (self.n_vis,), "weight")
+        need = R.rick_density_scratch_bytes(self.params)
+        if getattr(self, "_dens", None) is None or self._dens.numel() < need:
+            self._dens = torch.empty(need, dtype=torch.uint8, device=self.device)
+        out = torch.empty(self.n_vis, dtype=torch.float32, device=self.device)
+        R.rick_density_weights(self.plan, self.n_vis, _ptr(weight), self.ws.data_ptr(),
+                               schemes[scheme], robust, self._dens.data_ptr(), self._dens.numel(),
+                               out.data_ptr(), self._stream())
+        return out
+
+    def image_weighted(self, uvw, vis, weight=None, scheme: str = "briggs", robust: float = 0.0,
+                       flags: int = IMAGE_FLAGS, out=None) -> torch.Tensor:
+        """The image with uniform or Briggs-robust weighting: bin, density
+        weights, re-weight the records, grid, FFT, w-correct."""
+        self.bin(uvw, vis, weight)
+        w2 = self.density_weights(scheme, robust, weight)
+        self.bin_values(vis, w2)
+        return self.image_from_binned(flags, out)
+
     def grid(self):
         R.rick_grid(self.plan, self.ws.data_ptr(), self.planes.data_ptr(), self._stream())
 

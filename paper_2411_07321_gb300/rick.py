@@ -21,6 +21,7 @@ RICK_OK, RICK_EINVAL, RICK_ENOMEM, RICK_ECUDA, RICK_ECUFFT, RICK_ERANGE = 0, -1,
 RICK_KERNEL_GAUSS, RICK_KERNEL_KB = 0, 1
 RICK_PREC_FP32, RICK_PREC_FP32_COMPENSATED = 0, 1
 RICK_N_CORRECT, RICK_NORMALIZE, RICK_N_DIVIDE, RICK_PHASE_FP32 = 1, 2, 4, 8
+RICK_WEIGHT_UNIFORM, RICK_WEIGHT_BRIGGS = 1, 2
 
 
 class RickError(RuntimeError):
@@ -55,7 +56,7 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_bin_noalloc", "rick_bin_values", "rick_grid", "rick_grid_accumulate",
            "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
            "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
-           "rick_image_host_channels"]
+           "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights"]
 
 
 def _load():
@@ -85,6 +86,8 @@ def _load():
         "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
         "rick_image_host": [vp, i64, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32, vp, vp],
         "rick_bin_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, vp],
+        "rick_density_scratch_bytes": [P, ctypes.POINTER(sz)],
+        "rick_density_weights": [vp, i64, vp, vp, i32, ctypes.c_double, vp, sz, vp, vp],
         "rick_image_host_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32,
                                      vp, vp],
         "rick_fft_wplanes": [vp, vp, i32, vp],
@@ -192,6 +195,22 @@ def rick_image_host_channels(plan, n_rows, n_chan, uvw_rows_host, chan_scale_hos
         plan, int(n_rows), int(n_chan), uvw_rows_host, chan_scale_host, vis_host,
         weight_host or None, ws, int(ws_bytes), stage, int(stage_bytes), planes, image, int(flags),
         stats or None, stream or None))
+
+
+def rick_density_scratch_bytes(params: rick_params) -> int:
+    b = ctypes.c_size_t()
+    _check("rick_density_scratch_bytes", _L.rick_density_scratch_bytes(ctypes.byref(params),
+                                                                       ctypes.byref(b)))
+    return b.value
+
+
+def rick_density_weights(plan, n_vis, weight, ws, scheme, robust, scratch, scratch_bytes,
+                         weight_out, stream) -> None:
+    """Uniform / Briggs imaging weights from the uv-cell density of the last binning."""
+    _check("rick_density_weights", _L.rick_density_weights(plan, int(n_vis), weight or None, ws,
+                                                           int(scheme), float(robust), scratch,
+                                                           int(scratch_bytes), weight_out,
+                                                           stream or None))
 
 
 def rick_bin_values(plan, vis, weight, ws, stats, stream) -> None:
