@@ -307,6 +307,16 @@ def run_ours(args, wl):
             dist.barrier()
         return t
 
+    # Briggs-robust weighting (SURVEY f-3): the extra passes per image, after a
+    # binning of the same visibilities -- density weights, then re-weighting
+    # the records
+    im.bin(uvw, vis, wt)
+
+    def reweight():
+        w2 = im.density_weights("briggs", 0.0, wt)
+        im.bin_values(vis, w2)
+
+    weighting_ms = timed(reweight)
     e2e_vis_ms = timed(lambda: ims.image_streamed(uvw_h, vis_h, wt_h, out_h))
     e2e_resident_ms = timed(lambda: im.image_from_host(uvw_h, vis_h, wt_h, out_h))
     # the same visibilities as rows of n_chan channels (a measurement set's
@@ -366,6 +376,8 @@ def run_ours(args, wl):
         "roofline": roofline,
         "stages": {"ms": stage_ms, "gbps": gbps, "algorithmic_bytes": alg,
                    "n_binned": n_binned},
+        "weighting": {"scheme": "briggs, robust 0", "ms_per_image": weighting_ms / args.steps,
+                      "passes": "rick_density_weights + rick_bin_values, after a binning"},
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": launches,

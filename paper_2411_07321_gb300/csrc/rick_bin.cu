@@ -507,37 +507,52 @@ __global__ void bin_offsets_kernel(const uint32_t *suboff, uint32_t *offsets, in
         offsets[b] = suboff[b * RICK_BIN_SUBS];
 }
 
-// Re-pack record values for new visibilities through an existing permutation.
-__global__ void bin_values_kernel(const float2 *vis, const float *weight, WsPtrs ws)
+// Re-pack record values for new visibilities through an existing permutation,
+// and sum the new weights: double-single per thread and warp, FP64 per block,
+// block partials in wpart (summed in a fixed order by values_finalize_kernel).
+__global__ void __launch_bounds__(256) bin_values_kernel(const float2 *vis, const float *weight,
+                                                         WsPtrs ws)
 {
+    __shared__ double s_part[8];
     const WsHeader *hdr = ws.hdr;
-    int64_t nb = hdr->stats.n_binned;
+    const int64_t nb = hdr->stats.n_binned;
+    ff acc = {0.0f, 0.0f};
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb;
          r += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t i = ws.perm[r];
-        float2 v = vis[i];
-        float wt = weight ? weight[i] : 1.0f;
+        const uint32_t i = ws.perm[r];
+        const float2 v = vis[i];
+        const float wt = weight ? weight[i] : 1.0f;
         float2 *val = (float2 *)&ws.rec[r];  // the value half of the record
         *val = make_float2(v.x * wt, v.y * wt);
+        acc = ff_add(acc, ff{wt, 0.0f});
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff other = {__shfl_xor_sync(FULL, acc.hi, o), __shfl_xor_sync(FULL, acc.lo, o)};
+        acc = ff_add(acc, other);
+    }
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = (double)acc.hi + (double)acc.lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_part[k];
+        ws.wpart[blockIdx.x] = t;
     }
 }
 
-__global__ void __launch_bounds__(1024) values_wsum_kernel(const float *weight, WsPtrs ws)
+__global__ void __launch_bounds__(1024) values_finalize_kernel(const double *wpart, int nparts,
+                                                               int unit_weights, WsHeader *hdr)
 {
     __shared__ double s[1024];
-    WsHeader *hdr = ws.hdr;
-    int64_t nb = hdr->stats.n_binned;
     double t = 0.0;
-    if (weight) {
-        for (int64_t r = threadIdx.x; r < nb; r += 1024) t += (double)weight[ws.perm[r]];
-    }
+    for (int i = threadIdx.x; i < nparts; i += 1024) t += wpart[i];
     s[threadIdx.x] = t;
     __syncthreads();
     for (int o = 512; o > 0; o >>= 1) {
         if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) hdr->stats.sum_weight = weight ? s[0] : (double)nb;
+    if (threadIdx.x == 0)
+        hdr->stats.sum_weight = unit_weights ? (double)hdr->stats.n_binned : s[0];
 }
 
 // ------------------------------------------------------------------------
@@ -690,11 +705,14 @@ extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const f
         ((uintptr_t)stats_dev & 7))
         return RICK_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&plan->p, plan->max_vis));
+    const WsLayout L = rick_ws_layout(&plan->p, plan->max_vis);
+    WsPtrs w = rick_ws_ptrs(ws_dev, L);
+    // one weight partial per block: the workspace holds nkeyblocks + 1 of them
     int blocks = plan->num_sms * 8;
+    if (blocks > (int)L.nkeyblocks + 1) blocks = (int)L.nkeyblocks + 1;
     bin_values_kernel<<<blocks, 256, 0, st>>>((const float2 *)vis, weight, w);
     RICK_LAUNCH_CHECK(plan);
-    values_wsum_kernel<<<1, 1024, 0, st>>>(weight, w);
+    values_finalize_kernel<<<1, 1024, 0, st>>>(w.wpart, blocks, weight == NULL, w.hdr);
     RICK_LAUNCH_CHECK(plan);
     if (stats_dev)
         RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
