@@ -124,6 +124,8 @@ def lib():
         L.or_dft.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _D,
                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_double,
                              _D]
+        L.or_image_pixels.argtypes = [P, ctypes.c_int64, _D, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_uint32, ctypes.c_int32, _I32, _I32, _D]
         L.or_density_weights.argtypes = [P, ctypes.c_int64, _D, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_double, _D]
         L.or_max_threads.restype = ctypes.c_int32
@@ -282,6 +284,19 @@ def dft(n: int, fov: float, uvw, vis, weight=None, flags: int = 0, sum_weight: f
     lib().or_dft(int(n), float(fov), uvw.shape[0], _p(uvw, ctypes.c_double), _vp(vis), _vp(wt),
                  int(flags), float(sum_weight), _p(img, ctypes.c_double))
     return img
+
+
+def image_pixels(p: Params, uvw, vis, weight, pixels, flags: int = N_CORRECT | NORMALIZE):
+    """The w-stacked image at the given (p, q) pixels, evaluated per visibility
+    (no FFT): for checking a few pixels of a large image."""
+    uvw, vis, wt = _uvw(uvw), _vis(vis), _wt(weight)
+    pix = np.asarray(pixels, np.int32).reshape(-1, 2)
+    px, py = np.ascontiguousarray(pix[:, 0]), np.ascontiguousarray(pix[:, 1])
+    out = np.empty(len(pix), np.float64)
+    lib().or_image_pixels(ctypes.byref(p.c()), uvw.shape[0], _p(uvw, ctypes.c_double), _vp(vis),
+                          _vp(wt), int(flags), len(pix), _p(px, ctypes.c_int32),
+                          _p(py, ctypes.c_int32), _p(out, ctypes.c_double))
+    return out
 
 
 WEIGHT_UNIFORM, WEIGHT_BRIGGS = 1, 2

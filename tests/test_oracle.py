@@ -444,3 +444,21 @@ def test_density_weights_limits_and_cell_sums():
     rob = oracle.density_weights(p, d["uvw"], wt, oracle.WEIGHT_BRIGGS, -8.0)
     ratio = rob[kept] / uni[kept]
     assert np.allclose(ratio, ratio[0], rtol=1e-6)
+
+
+# ---------------------------------------------------------------- sampled pixels
+
+@pytest.mark.parametrize("W,n_w,kern", [(7, 8, oracle.KB), (4, 3, oracle.GAUSS), (1, 1, oracle.KB)])
+def test_image_pixels_equal_fft_image(W, n_w, kern):
+    """The per-visibility evaluation of chosen pixels equals the FFT image there
+    (the two routes compute the same sums in a different order)."""
+    d = synth.generate(synth.scaled("small", n_keep=3000).obs)
+    wl = synth.WORKLOADS["small"]
+    n = 64
+    p = oracle.Params(n=n, n_w=n_w, fov=wl.fov / 4, kernel=kern, support=W, tile=16)
+    wt = 0.5 + rng(9).random(len(d["vis"]))
+    img, _ = oracle.image(p, d["uvw"], d["vis"], wt)
+    pix = [(n // 2, n // 2), (0, 0), (n - 1, 3), (17, 40), (n // 2 + 5, n // 2 - 9), (63, 63)]
+    got = oracle.image_pixels(p, d["uvw"], d["vis"], wt, pix)
+    want = np.array([img[q, pp] for pp, q in pix])
+    assert got == pytest.approx(want, rel=1e-10, abs=1e-12 * np.abs(img).max())
