@@ -63,7 +63,7 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float a)
 }
 
 // ------------------------------------------------------------------------
-// Record streams.  A group of G = next_pow2(W) lanes walks a contiguous run of
+// Record streams.  A group of W consecutive lanes walks a contiguous run of
 // records; lane j of the group owns footprint row j (W cells).  Per record,
 // lane j evaluates kernel segment j at both offsets -- gx[j] = G((j - h) - fx)
 // and gy[j] = G((j - h) - fy), one Horner chain on (x, y) pairs with packed
@@ -77,9 +77,18 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float a)
 // adds its rows to the tile accumulator at once -- one row per lane, so the
 // group's atomics never collide.
 
+// A record stream is a group of G consecutive lanes, lane j owning footprint
+// row j < W.  G is the power of two next to W when that packs as many groups
+// into a warp as W lanes would (W = 7: four groups either way, and the lane
+// arithmetic is shifts), else W itself (W = 9: three groups of nine instead of
+// two of sixteen).  A warp holds NG = 32 / G groups; its last 32 - NG G lanes
+// stay idle.
 template <int W>
 struct StreamShape {
-    static constexpr int G = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : 16;
+    static constexpr int P2 = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : 16;
+    static constexpr int G = (32 / P2 == 32 / W) ? P2 : W;
+    static constexpr int NG = 32 / G;
+    static constexpr int LIVE = NG * G;  // lanes of a warp that carry a stream
 };
 
 template <int W>
@@ -105,10 +114,10 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
                                             const float2 *coef2)
 {
     constexpr int G = StreamShape<W>::G;
-    const int j = threadIdx.x & (G - 1);  // this lane's row / kernel segment
+    const int lane = threadIdx.x & 31, grp = lane / G;
+    const int j = lane - grp * G;  // this lane's row / kernel segment
     const bool live = j < W;
-    const unsigned gmask = G == 32 ? 0xffffffffu
-                                   : (((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1)));
+    const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
     if (n == 0) return;
     float ar[W], ai[W];
 #pragma unroll
@@ -142,7 +151,13 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         const float2 vr2 = make_float2(vv.x, vv.x), vi2 = make_float2(vv.y, vv.y);
         float wv[W];
 #pragma unroll
-        for (int jx = 0; jx < W; ++jx) wv[jx] = G == 1 ? gx : __shfl_sync(gmask, gx, jx, G);
+        for (int jx = 0; jx < W; ++jx) {
+            // power-of-two groups: the lane inside the group is an immediate
+            // (width form); groups of W lanes: the absolute lane
+            wv[jx] = W == 1 ? gx
+                   : (G & (G - 1)) == 0 ? __shfl_sync(gmask, gx, jx, G)
+                                        : __shfl_sync(gmask, gx, grp * G + jx);
+        }
 #pragma unroll
         for (int jx = 0; jx + 1 < W; jx += 2) {
             const float2 w2 = make_float2(wv[jx], wv[jx + 1]);
@@ -218,8 +233,11 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     // each folded into the (sum, compensation) pair of every cell.  Each round
     // is split into one contiguous run per record stream, and each run into
     // its pieces of the four ranges.
-    constexpr int G = StreamShape<W>::G;
-    const uint32_t nstreams = blockDim.x / G, stream = threadIdx.x / G;
+    constexpr int NG = StreamShape<W>::NG;
+    const int lane = threadIdx.x & 31;
+    const bool streaming = lane < StreamShape<W>::LIVE;
+    const uint32_t nstreams = (blockDim.x >> 5) * NG;
+    const uint32_t stream = (threadIdx.x >> 5) * NG + (streaming ? lane / StreamShape<W>::G : 0);
     const uint32_t round = COMP ? 4096u : max(vend - vbeg, 1u);
     for (uint32_t rb = vbeg; rb < vend; rb += round) {
         const uint32_t re = min(vend, rb + round);
@@ -230,7 +248,7 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
         for (int g = 0; g < 4; ++g) {
             const uint32_t lg = s_rl[g];
             uint32_t a0 = max(v0, base), a1 = min(v1, base + lg);
-            if (a0 < a1)
+            if (streaming && a0 < a1)
                 grid_stream<W>(ta, s_rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
                                coef2);
             base += lg;
@@ -305,8 +323,7 @@ __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(Gr
     __shared__ uint32_t s_b, s_tile, s_z;
     const uint32_t total = a.t.base[a.t.ntiles];
     // this lane's kernel segment (= its footprint row within its group)
-    constexpr int G = StreamShape<W>::G;
-    const int seg = min((int)(threadIdx.x & (G - 1)), W - 1);
+    const int seg = min((int)((threadIdx.x & 31) % StreamShape<W>::G), W - 1);
     float2 coef2[RICK_POLY_N];
 #pragma unroll
     for (int k = 0; k < RICK_POLY_N; ++k) coef2[k] = make_float2(a.t.kp.c[seg][k], a.t.kp.c[seg][k]);
