@@ -120,6 +120,16 @@ rick_status rick_plan_last_error(const rick_plan *plan);
  * the new geometry is invalid (the plan is then unchanged). */
 rick_status rick_plan_set_geometry(rick_plan *plan, double fov, double w_min, double w_max);
 
+/* Change a plan's gridding kernel -- kernel, support, kb_beta, gauss_sigma as
+ * in rick_params -- without rebuilding it: the taper table and the
+ * kernel-weight fits are recomputed (a few microseconds of device work on the
+ * plan's own stream, waited for), the cuFFT plan stays.  Lets a resident plan
+ * serve jobs with different kernels.  Work enqueued with the plan must be
+ * complete (the taper table is rewritten).  RICK_EINVAL if the kernel is
+ * invalid for the plan (e.g. support > tile); the plan is then unchanged. */
+rick_status rick_plan_set_kernel(rick_plan *plan, int32_t kernel, int32_t support, double kb_beta,
+                                 double gauss_sigma);
+
 /* Number of library kernels this plan has enqueued since it was created
  * (cuFFT's kernels are not included), for launch accounting. */
 rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count);

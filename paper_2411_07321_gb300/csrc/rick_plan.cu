@@ -184,6 +184,38 @@ static void plan_release(rick_plan *pl)
     free(pl);
 }
 
+// The kernel-dependent tables of a plan: 1/C(nu) on the device and the
+// kernel-weight polynomial coefficients (fitted on the device in FP64, kept on
+// the host for the kernels' parameter space).  Waits for the plan's own
+// stream, which holds nothing but this work.
+static bool kernel_tables(rick_plan *pl)
+{
+    const rick_params *params = &pl->p;
+    const int n = params->n;
+    float *coef = NULL;
+    bool ok = cudaMallocAsync((void **)&coef, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
+              cudaSuccess;
+    if (ok) {
+        pl->launches += 2;
+        taper_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(
+            pl->taper_inv, n, params->support, params->kernel, pl->beta, pl->i0_beta, pl->sigma);
+        ok = cudaGetLastError() == cudaSuccess &&
+             cudaMemsetAsync(coef, 0, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
+                 cudaSuccess;
+        if (ok) {
+            kernel_poly_kernel<<<1, RICK_MAX_W, 0, pl->own>>>(coef, params->support, params->kernel,
+                                                             pl->beta, pl->i0_beta, pl->sigma);
+            ok = cudaGetLastError() == cudaSuccess &&
+                 cudaMemcpyAsync(pl->poly.c, coef, sizeof(pl->poly.c), cudaMemcpyDeviceToHost,
+                                 pl->own) == cudaSuccess;
+        }
+        cudaFreeAsync(coef, pl->own);
+        ok = ok && cudaStreamSynchronize(pl->own) == cudaSuccess;
+    }
+    pl->poly.fc = (params->support & 1) ? 0.0f : 0.5f;
+    return ok;
+}
+
 extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_vis, rick_plan **out)
 {
     if (!out) return RICK_EINVAL;
@@ -226,33 +258,35 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
         plan_release(pl);
         return RICK_ECUFFT;
     }
-    float *coef = NULL;
-    bool ok = cudaMallocAsync((void **)&coef, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
-              cudaSuccess;
-    if (ok) {
-        pl->launches = 2;
-        taper_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(
-            pl->taper_inv, n, params->support, params->kernel, pl->beta, pl->i0_beta, pl->sigma);
-        ok = cudaGetLastError() == cudaSuccess &&
-             cudaMemsetAsync(coef, 0, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
-                 cudaSuccess;
-        if (ok) {
-            kernel_poly_kernel<<<1, RICK_MAX_W, 0, pl->own>>>(coef, params->support, params->kernel,
-                                                             pl->beta, pl->i0_beta, pl->sigma);
-            ok = cudaGetLastError() == cudaSuccess &&
-                 cudaMemcpyAsync(pl->poly.c, coef, sizeof(pl->poly.c), cudaMemcpyDeviceToHost,
-                                 pl->own) == cudaSuccess;
-        }
-        cudaFreeAsync(coef, pl->own);
-        ok = ok && cudaStreamSynchronize(pl->own) == cudaSuccess;
-    }
-    pl->poly.fc = (params->support & 1) ? 0.0f : 0.5f;
-    if (!ok) {
+    if (!kernel_tables(pl)) {
         plan_release(pl);
         return RICK_ECUDA;
     }
     pl->sticky = RICK_OK;
     *out = pl;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_plan_set_kernel(rick_plan *plan, int32_t kernel, int32_t support,
+                                            double kb_beta, double gauss_sigma)
+{
+    if (!plan) return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    rick_params q = plan->p;
+    q.kernel = kernel;
+    q.support = support;
+    q.kb_beta = kb_beta;
+    q.gauss_sigma = gauss_sigma;
+    rick_status st = check_params(&q);
+    if (st != RICK_OK) return st;
+    plan->p = q;
+    plan->beta = kb_beta_of(&q);
+    plan->sigma = isnan(q.gauss_sigma) ? q.support / 6.0 : q.gauss_sigma;
+    plan->i0_beta = bessel_i0_host(plan->beta);
+    if (!kernel_tables(plan)) {
+        plan->sticky = RICK_ECUDA;
+        return RICK_ECUDA;
+    }
     return RICK_OK;
 }
 

@@ -288,6 +288,15 @@ class Imager:
         R.rick_plan_set_geometry(self.plan, fov, wmin, wmax)
         self.params.fov, self.params.w_min, self.params.w_max = float(fov), wmin, wmax
 
+    def set_kernel(self, kernel: str, support: int, kb_beta: float = math.nan,
+                   gauss_sigma: float = math.nan):
+        """Re-target the resident plan to another gridding kernel (the taper
+        table and kernel fits are rebuilt, the cuFFT plan stays).  Work this
+        imager enqueued must be complete."""
+        R.rick_plan_set_kernel(self.plan, KERNELS[kernel], support, kb_beta, gauss_sigma)
+        self.params.kernel, self.params.support = KERNELS[kernel], int(support)
+        self.params.kb_beta, self.params.gauss_sigma = float(kb_beta), float(gauss_sigma)
+
     def launches(self) -> int:
         """Library kernels this imager's plan has enqueued so far."""
         return R.rick_plan_launch_count(self.plan)

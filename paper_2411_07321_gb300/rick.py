@@ -51,7 +51,7 @@ class rick_bin_view(ctypes.Structure):
 
 
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
-           "rick_plan_launch_count", "rick_plan_set_geometry",
+           "rick_plan_launch_count", "rick_plan_set_geometry", "rick_plan_set_kernel",
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
            "rick_bin_noalloc", "rick_bin_values", "rick_grid", "rick_grid_accumulate",
            "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
@@ -75,6 +75,7 @@ def _load():
         "rick_plan_last_error": [vp],
         "rick_plan_launch_count": [vp, ctypes.POINTER(ctypes.c_uint64)],
         "rick_plan_set_geometry": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+        "rick_plan_set_kernel": [vp, i32, i32, ctypes.c_double, ctypes.c_double],
         "rick_workspace_bytes": [P, i64, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "rick_plan_fft_bytes": [vp, ctypes.POINTER(sz)],
         "rick_bin_layout": [vp, ctypes.POINTER(rick_bin_view)],
@@ -146,6 +147,12 @@ def rick_plan_set_geometry(plan: int, fov: float, w_min: float = math.nan,
                            w_max: float = math.nan) -> None:
     _check("rick_plan_set_geometry", _L.rick_plan_set_geometry(plan, float(fov), float(w_min),
                                                                float(w_max)))
+
+
+def rick_plan_set_kernel(plan: int, kernel: int, support: int, kb_beta: float = math.nan,
+                         gauss_sigma: float = math.nan) -> None:
+    _check("rick_plan_set_kernel", _L.rick_plan_set_kernel(plan, int(kernel), int(support),
+                                                           float(kb_beta), float(gauss_sigma)))
 
 
 def rick_workspace_bytes(params: rick_params, n_vis: int) -> tuple[int, int]:

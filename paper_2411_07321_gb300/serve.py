@@ -14,10 +14,13 @@ slot's stream, and completes the request when the stream's event fires.  Work of
 requests admitted while others run overlaps on the device.
 
 Admission is by HBM footprint: a request needs a slot with the same grid size,
-plane count, kernel and tile, and a visibility capacity at least its own.  If no
-idle one exists, a new slot is created when budget - used >= its footprint, after
-evicting idle slots least-recently-used first.  A request larger than the whole
-budget is rejected with an error, and only that request fails.
+plane count, tile and precision, and a visibility capacity at least its own;
+the slot's plan is re-targeted to the request's field of view, w range and
+gridding kernel (rick_plan_set_geometry, rick_plan_set_kernel), so the cuFFT
+plan and the buffers are reused.  If no idle slot fits, a new one is created
+when budget - used >= its footprint, after evicting idle slots
+least-recently-used first.  A request larger than the whole budget is rejected
+with an error, and only that request fails.
 
 ``run_plain`` is the per-request baseline: a fresh plan and fresh allocations
 for every request, run to completion before the next.
@@ -71,8 +74,8 @@ class ImagingJob:
         return int(self.uvw.shape[0])
 
     def key(self):
-        return (self.n, self.n_w, self.kernel, self.support, self.tile, self.precision,
-                capacity_class(self.n_vis))
+        """What a slot must share with the request (its capacity may be larger)."""
+        return (self.n, self.n_w, self.tile, self.precision)
 
 
 @dataclass
@@ -100,14 +103,18 @@ class Admission:
     def used(self) -> int:
         return sum(s["bytes"] for s in self.slots.values())
 
-    def plan(self, key, bytes_needed: int):
-        """('reuse', id) | ('new', [ids to evict]) | None (wait).  Raises
-        AdmissionError if bytes_needed exceeds the whole budget."""
+    def plan(self, key, bytes_needed: int, cap: int = 0):
+        """('reuse', id) | ('new', [ids to evict]) | None (wait).  An idle slot
+        of the same key with capacity >= cap is reused (the smallest such, then
+        the least recently used).  Raises AdmissionError if bytes_needed
+        exceeds the whole budget."""
         if bytes_needed > self.budget:
             raise AdmissionError(f"request needs {bytes_needed} B, budget is {self.budget} B")
-        idle_same = [i for i, s in self.slots.items() if s["key"] == key and not s["busy"]]
+        idle_same = [i for i, s in self.slots.items()
+                     if s["key"] == key and not s["busy"] and s["cap"] >= cap]
         if idle_same:
-            return ("reuse", min(idle_same, key=lambda i: self.slots[i]["last"]))
+            return ("reuse", min(idle_same, key=lambda i: (self.slots[i]["cap"],
+                                                          self.slots[i]["last"])))
         free = self.budget - self.used()
         count = len(self.slots)
         evict = []
@@ -121,9 +128,9 @@ class Admission:
         fits = free >= bytes_needed and (self.max_slots is None or count < self.max_slots)
         return ("new", evict) if fits else None
 
-    def add(self, key, nbytes: int, now: float) -> int:
+    def add(self, key, nbytes: int, now: float, cap: int = 0) -> int:
         i = next(self._ids)
-        self.slots[i] = dict(key=key, bytes=int(nbytes), busy=True, last=now)
+        self.slots[i] = dict(key=key, bytes=int(nbytes), busy=True, last=now, cap=int(cap))
         assert self.used() <= self.budget
         return i
 
@@ -159,6 +166,7 @@ class _Slot:
         self.imager = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
                              tile=job.tile, precision=job.precision,
                              max_vis=capacity_class(job.n_vis), device=device)
+        self.kernel = (job.kernel, job.support)
         self.stream = torch.cuda.Stream(device=device)
         self.out = out_host  # pinned image buffer, from the server's pool
         self.event = None
@@ -254,7 +262,7 @@ class Server:
             job, fut = self._pending.popleft()
             try:
                 need = slot_footprint(job)
-                decision = self.admission.plan(job.key(), need)
+                decision = self.admission.plan(job.key(), need, capacity_class(job.n_vis))
             except Exception as e:  # invalid request or larger than the budget
                 fut.set_exception(e)
                 progressed = True
@@ -273,7 +281,7 @@ class Server:
                     for sid in decision[1]:
                         self._evict(sid)
                     slot = _Slot(job, self.device, self._pinned.get(job.n))
-                    sid = self.admission.add(job.key(), need, now)
+                    sid = self.admission.add(job.key(), need, now, capacity_class(job.n_vis))
                     self._slots[sid] = slot
                     self.peak_used = max(self.peak_used, self.admission.used())
                     self.counters["new_slots"] += 1
@@ -303,6 +311,9 @@ class Server:
         slot.job, slot.future, slot.t_start = job, fut, time.perf_counter()
         if slot.out is None:
             slot.out = self._pinned.get(job.n)
+        if slot.kernel != (job.kernel, job.support):  # the slot is idle: its work is done
+            slot.imager.set_kernel(job.kernel, job.support)
+            slot.kernel = (job.kernel, job.support)
         with torch.cuda.stream(slot.stream):
             slot.imager.set_geometry(job.fov, job.w_range)
             slot.imager.image_from_host(job.uvw, job.vis, job.weight, slot.out, job.flags)

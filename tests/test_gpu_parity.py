@@ -223,3 +223,32 @@ def test_empty_and_all_dropped(P):
     assert st["n_binned"] == 0 and st["n_dropped_uv"] == 3
     assert torch.count_nonzero(img).item() == 0
     im.close()
+
+
+def test_set_kernel_retargets_a_plan(P):
+    """A plan made for one kernel and re-targeted with rick_plan_set_kernel
+    images like a plan made for the new kernel."""
+    dev = torch.device("cuda:0")
+    d = small_data(30000)
+    wl = synth.WORKLOADS["small"]
+    t = {k: torch.from_numpy(d[k]).to(dev) for k in ("uvw", "vis", "weight")}
+    fresh = P.Imager(wl.n, wl.n_w, wl.fov, kernel="kb", support=9, tile=32, max_vis=30000,
+                     device=dev)
+    ref = fresh.image(t["uvw"], t["vis"], t["weight"]).cpu().numpy()
+    moved = P.Imager(wl.n, wl.n_w, wl.fov, kernel="gauss", support=5, tile=32, max_vis=30000,
+                     device=dev)
+    moved.image(t["uvw"], t["vis"], t["weight"])
+    torch.cuda.synchronize()
+    moved.set_kernel("kb", 9)
+    got = moved.image(t["uvw"], t["vis"], t["weight"]).cpu().numpy()
+    # FP32 record order differs between the two binnings; compare the tapered
+    # image (the taper division amplifies rounding at the corners)
+    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov, kernel=oracle.KB, support=9, tile=32)
+    cc = taper_2d(op)
+    assert np.abs((got - ref) * cc).max() <= 1e-6 * np.abs(ref * cc).max()
+    with pytest.raises(P.rick.RickError):
+        moved.set_kernel("kb", 33)  # invalid support: the plan is unchanged
+    again = moved.image(t["uvw"], t["vis"], t["weight"]).cpu().numpy()
+    assert np.abs((again - ref) * cc).max() <= 1e-6 * np.abs(ref * cc).max()
+    fresh.close()
+    moved.close()

@@ -109,3 +109,29 @@ def test_slot_cap_evicts_idle_lru_first(S):
     a.release(s1, now=3.0)
     assert a.plan(("C",), 100) == ("new", [s2])  # s2 is least recently used
     assert a.plan(("A",), 100) == ("reuse", s1)
+
+
+def test_reuse_prefers_the_smallest_idle_slot_with_enough_capacity(S):
+    a = S.Admission(10_000)
+    k = ("A",)
+    small = a.add(k, 100, now=0.0, cap=1 << 14)
+    big = a.add(k, 400, now=1.0, cap=1 << 20)
+    mid = a.add(k, 200, now=2.0, cap=1 << 16)
+    for i in (small, big, mid):
+        a.release(i, now=3.0)
+    assert a.plan(k, 100, cap=1 << 15) == ("reuse", mid)   # 2^16 is the smallest that holds it
+    assert a.plan(k, 100, cap=1 << 14) == ("reuse", small)
+    assert a.plan(k, 100, cap=1 << 21) == ("new", [])       # none is large enough
+    a.acquire(mid, now=4.0)
+    assert a.plan(k, 100, cap=1 << 15) == ("reuse", big)   # the next larger one
+
+
+def test_job_key_leaves_out_kernel_and_capacity(S):
+    import numpy as np
+    uvw = np.zeros((10, 3))
+    a = S.ImagingJob(uvw, None, None, n=512, n_w=8, fov=0.01, kernel="kb", support=7)
+    b = S.ImagingJob(np.zeros((100_000, 3)), None, None, n=512, n_w=8, fov=0.02,
+                     kernel="gauss", support=5)
+    assert a.key() == b.key()
+    c = S.ImagingJob(uvw, None, None, n=512, n_w=9, fov=0.01)
+    assert a.key() != c.key()
