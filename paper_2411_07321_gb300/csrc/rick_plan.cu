@@ -65,8 +65,40 @@ static rick_status check_params(const rick_params *p)
 // nu_p = (p - n/2)/n, stored as 1/C.  KB: closed form of Jackson (1991),
 // W sinh(sqrt(beta^2 - (pi W nu)^2)) / sqrt(...) / I0(beta); Gaussian:
 // composite Simpson rule on 4096 panels (the integrand is entire).  FP64.
+// Nodes and weights of the 48-point Gauss-Legendre rule on [-1, 1] (nodes in
+// decreasing order), by Newton's iteration on the Legendre polynomial P_48 from
+// the cosine initial guesses (the textbook method), in FP64 on the host.
+#define RICK_GL_N 48
+struct GaussLegendre {
+    double x[RICK_GL_N], w[RICK_GL_N];
+};
+
+static GaussLegendre gauss_legendre()
+{
+    GaussLegendre g;
+    const int N = RICK_GL_N;
+    for (int i = 0; i < N; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (N + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;  // P_0, P_1; recurrence up to P_N
+            for (int k = 2; k <= N; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = N * (x * p1 - p0) / (x * x - 1.0);  // P_N'(x)
+            const double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        g.x[i] = x;
+        g.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    return g;
+}
+
 __global__ void taper_kernel(float *taper_inv, int n, int W, int kind, double beta, double i0b,
-                             double sigma)
+                             double sigma, GaussLegendre gl)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -86,14 +118,16 @@ __global__ void taper_kernel(float *taper_inv, int n, int W, int kind, double be
         }
         c /= i0b;
     } else {
-        const int panels = 4096;
-        double h = (double)W / panels, s = 0.0;
-        for (int j = 0; j <= panels; ++j) {
-            double d = -0.5 * W + j * h;
-            double f = exp(-d * d / (2.0 * sigma * sigma)) * cos(2.0 * M_PI * nu * d);
-            s += f * ((j == 0 || j == panels) ? 1.0 : ((j & 1) ? 4.0 : 2.0));
+        // the even integrand e^{-d^2 / (2 sigma^2)} cos(2 pi nu d) is entire and
+        // at most a few oscillations long on [0, W/2]: twice its 48-point
+        // Gauss-Legendre sum there is exact to rounding
+        const double half = 0.25 * W;  // d = half (t + 1), t in [-1, 1]
+        double s = 0.0;
+        for (int i = 0; i < RICK_GL_N; ++i) {
+            const double d = half * (gl.x[i] + 1.0);
+            s += gl.w[i] * exp(-d * d / (2.0 * sigma * sigma)) * cos(2.0 * M_PI * nu * d);
         }
-        c = s * h / 3.0;
+        c = 2.0 * half * s;
     }
     taper_inv[p] = (float)(1.0 / c);
 }
@@ -197,8 +231,9 @@ static bool kernel_tables(rick_plan *pl)
               cudaSuccess;
     if (ok) {
         pl->launches += 2;
-        taper_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(
-            pl->taper_inv, n, params->support, params->kernel, pl->beta, pl->i0_beta, pl->sigma);
+        taper_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(pl->taper_inv, n, params->support,
+                                                           params->kernel, pl->beta, pl->i0_beta,
+                                                           pl->sigma, gauss_legendre());
         ok = cudaGetLastError() == cudaSuccess &&
              cudaMemsetAsync(coef, 0, sizeof(float) * RICK_MAX_W * RICK_POLY_N, pl->own) ==
                  cudaSuccess;
