@@ -307,7 +307,7 @@ def run_ours(args, wl):
             dist.barrier()
         return t
 
-    # Briggs-robust weighting (SURVEY f-3): the extra passes per image, after a
+    # Briggs-robust weighting: the extra passes per image, after a
     # binning of the same visibilities -- density weights, then re-weighting
     # the records
     im.bin(uvw, vis, wt)

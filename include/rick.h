@@ -14,7 +14,9 @@
  *  - Grid cell i <-> u = (i - n/2) / fov; image pixel p <-> l = (p - n/2) fov / n.
  *  - Planes are complex64 [n_w][n][n], row-major (v row, u fastest); after the
  *    inverse FFT the same buffer holds [n_w][m row q][l column p].
- *  - The image is float32 [n][n], row q (m) major, column p (l) fastest.
+ *  - The image is float32 [m][m], m = image_n (n unless the grid is padded),
+ *    row q (m) major, column p (l) fastest; its pixel (p', q') is the grid-frame
+ *    pixel (p' + (n - m)/2, q' + (n - m)/2).
  *  - Pointers named *_dev are device pointers, *_host host pointers.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Every call that takes a stream only enqueues work on it and returns;
@@ -64,7 +66,7 @@ typedef int32_t rick_status;
 #define RICK_WEIGHT_BRIGGS 2  /* w / (1 + f^2 D), Briggs' robust weighting        */
 
 typedef struct rick_params {
-    int32_t n;          /* grid side = image side, power of two, 16 ... 32768           */
+    int32_t n;          /* grid (mesh) side, power of two, 16 ... 32768                 */
     int32_t n_w;        /* number of w-planes, >= 1                                     */
     double fov;         /* image side in direction-cosine units (> 0); cell du = 1/fov */
     double w_min;       /* w range in wavelengths; both NaN: exact min/max over all    */
@@ -76,6 +78,13 @@ typedef struct rick_params {
     int32_t tile;       /* uv-tile side T: power of two, max(8, W) <= T <= min(128, n);  */
                         /*   T <= 64 with RICK_PREC_FP32_COMPENSATED                    */
     int32_t precision;  /* RICK_PREC_*                                                   */
+    int32_t image_n;    /* side m of the image: the central m x m pixels of the n x n    */
+                        /*   w-stacked image are kept (grid padding by n/m, which moves  */
+                        /*   the aliases of the kept field onto the kernel's stopband);  */
+                        /*   pixel p' of the image is pixel p' + (n - m)/2 of the grid   */
+                        /*   frame, so the pixel size stays fov/n and the phase centre   */
+                        /*   is pixel m/2.  Even, 16 <= m <= n; 0 means m = n (no crop)  */
+    int32_t reserved;   /* must be 0                                                     */
 } rick_params;
 
 /* Geometry and counts of the last rick_bin, written to device memory. */
@@ -130,6 +139,20 @@ rick_status rick_plan_set_geometry(rick_plan *plan, double fov, double w_min, do
 rick_status rick_plan_set_kernel(rick_plan *plan, int32_t kernel, int32_t support, double kb_beta,
                                  double gauss_sigma);
 
+/* Change a plan's image side image_n (as in rick_params; 0: the grid side)
+ * without rebuilding it: only the crop of the w-correction and its adjoint
+ * change.  Host-only, like rick_plan_set_geometry.  RICK_EINVAL if invalid
+ * (the plan is then unchanged). */
+rick_status rick_plan_set_image_n(rick_plan *plan, int32_t image_n);
+
+/* Kaiser-Bessel shape for a grid oversampling alpha = n / image_n (Beatty,
+ * Nishimura & Pauly 2005): beta = pi sqrt((W/alpha)^2 (alpha - 1/2)^2 - 0.8),
+ * which puts the first zero of the kernel's transform just beyond the first
+ * alias of the image edge.  The default kb_beta (NaN) is this value for
+ * alpha = 2.  Returns NaN if support < 2, alpha < 1 or the root's argument is
+ * not positive. */
+double rick_kb_beta(int32_t support, double alpha);
+
 /* Number of library kernels this plan has enqueued since it was created
  * (cuFFT's kernels are not included), for launch accounting. */
 rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count);
@@ -171,7 +194,7 @@ rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uvw_dev, cons
                      const float *weight_dev, void *ws_dev, size_t ws_bytes,
                      rick_bin_stats *stats_dev, void *stream);
 
-/* rick_bin for multi-channel input (SURVEY f-2): visibilities in rows of
+/* rick_bin for multi-channel input: visibilities in rows of
  * n_chan channels, as a measurement set stores them, with uvw given once per
  * row and a factor per channel -- the uvw of channel c of row r is
  * uvw_rows[r] * chan_scale[c], one FP64 product per coordinate (e.g. metres
@@ -264,13 +287,17 @@ rick_status rick_fft_wplanes(rick_plan *plan, void *planes_dev, int32_t directio
  * s = [n if RICK_N_CORRECT] [1/n if RICK_N_DIVIDE] [1/sum w if RICK_NORMALIZE]
  *     / (C(l) C(m)),  C the continuous transform of G (C == 1 for W == 1).
  * The phase w_k (n - 1) is formed in double-single arithmetic from FP64 inputs
- * (RICK_PHASE_FP32: plain FP32, for comparison).
+ * (RICK_PHASE_FP32: plain FP32, for comparison).  p, q are grid-frame pixels;
+ * only the central image_n x image_n are computed and written, to the m x m
+ * image_dev.
  * ws_dev supplies the w range and weight sum of the last rick_bin. */
 rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_dev, const void *ws_dev,
                                 float *image_dev, uint32_t flags, void *stream);
 
 /* Adjoint of rick_wcorrect_stack (same flags): for every plane k,
- * planes[k][q][p] = image[q][p] s(p,q) (-1)^(p+q) e^{-2 pi i w_k (n - 1)}. */
+ * planes[k][q][p] = image[q][p] s(p,q) (-1)^(p+q) e^{-2 pi i w_k (n - 1)},
+ * the m x m image zero-padded to the n x n grid frame (cells outside the
+ * central crop are written as 0). */
 rick_status rick_wspread(rick_plan *plan, const float *image_dev, const void *ws_dev,
                          void *planes_dev, uint32_t flags, void *stream);
 
@@ -308,7 +335,7 @@ rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
  *   stage_dev, stage_bytes: staging area of rick_stream_bytes(params, max_vis,
  *               n_vis) bytes, 256-byte aligned
  *   planes_dev: complex64 [n_w][n][n], overwritten
- *   image_dev:  float32 [n][n]; flags as for rick_wcorrect_stack
+ *   image_dev:  float32 [m][m]; flags as for rick_wcorrect_stack
  *   stats_dev:  device rick_bin_stats of the whole set, or NULL
  * Work is enqueued on `stream` and on the plan's copy stream, which waits for
  * earlier work on `stream` before it touches the staging area; the call is
@@ -324,7 +351,7 @@ rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_ho
                             void *planes_dev, float *image_dev, uint32_t flags,
                             rick_bin_stats *stats_dev, void *stream);
 
-/* Imaging weights from the uv-cell density (SURVEY f-3; the paper's §2 names
+/* Imaging weights from the uv-cell density (the paper's §2 names
  * Briggs 1995 for the weighting).  The density D of a uv cell is the sum of the
  * natural weights of the kept visibilities whose centre cell c (the cell
  * nearest to (x, y), as in rick_bin) it is, over all w-planes.

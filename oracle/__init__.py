@@ -16,8 +16,10 @@ Functions and the passage each follows:
   fft1d / fft2d         -- radix-2 Cooley-Tukey, the transform of §2 step 3
   coords / bin          -- §2 closest w-plane + gridding sub-step 1 (binning)
   grid                  -- Eq. 3
-  image                 -- §2 steps 2-4, Eq. 2
+  image                 -- §2 steps 2-4, Eq. 2 (optionally the central image_n x
+                           image_n pixels of a padded grid)
   adjoint               -- exact transpose of ``image`` (degridding)
+  kb_beta               -- KB shape for a grid oversampling (Beatty et al. 2005)
   dft                   -- brute-force inverse of Eq. 1 at pixel centres
 """
 from __future__ import annotations
@@ -62,7 +64,8 @@ class _Params(ctypes.Structure):
                 ("w_min", ctypes.c_double), ("w_max", ctypes.c_double),
                 ("kernel", ctypes.c_int32), ("support", ctypes.c_int32),
                 ("kb_beta", ctypes.c_double), ("gauss_sigma", ctypes.c_double),
-                ("tile", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("tile", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("image_n", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 @dataclass
@@ -78,10 +81,15 @@ class Params:
     kb_beta: float = float("nan")
     gauss_sigma: float = float("nan")
     tile: int = 64
+    image_n: int = 0  # side of the central crop kept (grid padding n / image_n); 0: n
+
+    def side(self) -> int:
+        return self.image_n if self.image_n > 0 else self.n
 
     def c(self) -> _Params:
         return _Params(self.n, self.n_w, self.fov, self.w_min, self.w_max, self.kernel,
-                       self.support, self.kb_beta, self.gauss_sigma, self.tile, 0)
+                       self.support, self.kb_beta, self.gauss_sigma, self.tile, 0,
+                       self.image_n, 0)
 
 
 _lib = None
@@ -99,6 +107,8 @@ def lib():
         L.or_i0.argtypes = [ctypes.c_double]
         L.or_kb_beta_default.restype = ctypes.c_double
         L.or_kb_beta_default.argtypes = [ctypes.c_int32]
+        L.or_kb_beta.restype = ctypes.c_double
+        L.or_kb_beta.argtypes = [ctypes.c_int32, ctypes.c_double]
         L.or_kernel.restype = ctypes.c_double
         L.or_kernel.argtypes = [P, ctypes.c_double]
         L.or_taper.restype = ctypes.c_double
@@ -159,6 +169,10 @@ def i0(x: float) -> float:
 
 def kb_beta_default(W: int) -> float:
     return lib().or_kb_beta_default(int(W))
+
+
+def kb_beta(W: int, alpha: float) -> float:
+    return lib().or_kb_beta(int(W), float(alpha))
 
 
 def kernel(p: Params, d: float) -> float:
@@ -237,9 +251,11 @@ def _stats(st):
 
 def image(p: Params, uvw, vis, weight=None, flags: int = N_CORRECT | NORMALIZE,
           want_acc: bool = False):
-    """The w-stacked image (FP64).  Returns (image, stats) or (image, acc, stats)."""
+    """The w-stacked image (FP64), image_n x image_n (the central crop of the n x n
+    grid's image).  Returns (image, stats) or (image, acc, stats); acc is the
+    n x n plane sum before scaling."""
     uvw, vis, wt = _uvw(uvw), _vis(vis), _wt(weight)
-    img = np.empty((p.n, p.n), np.float64)
+    img = np.empty((p.side(), p.side()), np.float64)
     acc = np.empty((p.n, p.n), np.complex128) if want_acc else None
     st = np.zeros(6, np.float64)
     lib().or_image(ctypes.byref(p.c()), uvw.shape[0], _p(uvw, ctypes.c_double), _vp(vis), _vp(wt),
@@ -260,10 +276,11 @@ def grid(p: Params, uvw, vis, weight=None):
 def adjoint(p: Params, uvw, image_in, weight=None, flags: int = N_CORRECT | NORMALIZE,
             w_min=None, w_max=None, sum_weight=None):
     """Transpose of ``image`` (weights applied) or, with weight=None and other
-    flags, the degridding predictor.  Geometry (w range, weight sum) defaults
-    to the forward operator's."""
+    flags, the degridding predictor.  image_in is image_n x image_n.  Geometry
+    (w range, weight sum) defaults to the forward operator's."""
     uvw, wt = _uvw(uvw), _wt(weight)
     y = np.ascontiguousarray(image_in, dtype=np.float64)
+    assert y.shape == (p.side(), p.side())
     if w_min is None or w_max is None:
         given = not (np.isnan(p.w_min) or np.isnan(p.w_max))
         w_min, w_max = (p.w_min, p.w_max) if given else wrange(uvw)
@@ -287,7 +304,8 @@ def dft(n: int, fov: float, uvw, vis, weight=None, flags: int = 0, sum_weight: f
 
 
 def image_pixels(p: Params, uvw, vis, weight, pixels, flags: int = N_CORRECT | NORMALIZE):
-    """The w-stacked image at the given (p, q) pixels, evaluated per visibility
+    """The w-stacked image at the given (p, q) pixels of the n x n grid frame
+    (a crop's pixel p' is p' + (n - image_n)/2 there), evaluated per visibility
     (no FFT): for checking a few pixels of a large image."""
     uvw, vis, wt = _uvw(uvw), _vis(vis), _wt(weight)
     pix = np.asarray(pixels, np.int32).reshape(-1, 2)

@@ -24,7 +24,11 @@
  *  - taper correction C(nu) = integral_{-W/2}^{W/2} G(d) cos(2 pi nu d) dd,
  *    nu = (p - n/2)/n, C == 1 for W == 1;
  *  - image = Re(sum_k F_k e^{2 pi i w_k (n-1)}) * [n] / (C C) / [sum w]  (Eq. 2,
- *    the w-integral becoming the sum over planes and (w_max - w_min) the weight sum).
+ *    the w-integral becoming the sum over planes and (w_max - w_min) the weight sum);
+ *  - grid padding (not in the paper, whose mesh equals the image): the n x n
+ *    image is computed as above and its central m x m pixels are kept, pixel
+ *    p' of the crop being pixel p' + (n - m)/2 of the grid frame (m even, so
+ *    the phase centre n/2 becomes m/2); the adjoint zero-pads.
  * Parity status: every function below is pinned by the CPU tests (closed forms,
  * the brute-force DFT of Eq. 1, Hermitian and weight-sum invariants, adjoint
  * identity); none is "parity unpinned".
@@ -53,6 +57,10 @@ typedef struct {
     double gauss_sigma;  /* Gaussian sigma in cells; NaN -> W/6                */
     int32_t tile;        /* uv-tile side T used for the binning key            */
     uint32_t flags;      /* unused by the oracle's geometry; kept for layout   */
+    int32_t image_n;     /* side m of the image kept: the central m x m pixels */
+                         /*   of the n x n w-stacked image (grid padding by    */
+                         /*   n/m); 0 -> n, no crop                            */
+    int32_t reserved_;   /* 0                                                  */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -71,11 +79,19 @@ double or_i0(double x)
     return sum;
 }
 
-/* Default KB shape: Beatty, Nishimura & Pauly (2005) with oversampling 2. */
+/* KB shape for grid oversampling alpha (Beatty, Nishimura & Pauly 2005):
+ * beta = pi sqrt((W / alpha)^2 (alpha - 1/2)^2 - 0.8), which puts the first zero
+ * of the kernel's transform just beyond the first alias of the image edge. */
+double or_kb_beta(int32_t W, double alpha)
+{
+    double t = (W / alpha) * (W / alpha) * (alpha - 0.5) * (alpha - 0.5) - 0.8;
+    return M_PI * sqrt(t);
+}
+
+/* Default KB shape: Beatty's choice for oversampling 2. */
 double or_kb_beta_default(int32_t W)
 {
-    double a = 2.0, t = (W / a) * (W / a) * (a - 0.5) * (a - 0.5) - 0.8;
-    return M_PI * sqrt(t);
+    return or_kb_beta(W, 2.0);
 }
 
 static double or_beta(const or_params *p)
@@ -372,6 +388,12 @@ static double or_nm1(double l, double m)
     return -r2 / (1.0 + sqrt(1.0 - r2));
 }
 
+/* Side m of the image kept and its offset (n - m)/2 in the grid frame. */
+static int or_image_side(const or_params *p)
+{
+    return p->image_n > 0 ? p->image_n : p->n;
+}
+
 /* Pixel scale s(p,q) = [n] [1/n] [1/sum w] / (C(nu_p) C(nu_q)). */
 static void or_scale_plane(const or_params *p, uint32_t flags, double sumw, double *scale)
 {
@@ -485,7 +507,8 @@ void or_grid_plane(const or_params *p, const or_geom *g, int64_t cnt, const int6
 /* The image (§2 steps 2-4, Eq. 2):                                          */
 /*   per plane k: grid -> x (-1)^{i+j} -> unnormalised inverse 2D DFT ->     */
 /*   x (-1)^{p+q} -> x e^{2 pi i w_k (n-1)} -> sum over planes;              */
-/*   image = Re(sum) * s(p,q).                                               */
+/*   image = Re(sum) * s(p,q), then the central m x m pixels are kept.       */
+/* image: m x m; acc_out (if given): the n x n plane sum before scaling.     */
 /* stats: kept, dropped_uv, dropped_w, sum_w, w_min, w_max.                  */
 
 void or_image(const or_params *p, int64_t nvis, const double *uvw, const double complex *vis,
@@ -521,7 +544,12 @@ void or_image(const or_params *p, int64_t nvis, const double *uvw, const double 
     }
     double *scale = malloc(sizeof(double) * nn);
     or_scale_plane(p, flags, g.sumw, scale);
-    for (size_t t = 0; t < nn; ++t) image[t] = creal(acc[t]) * scale[t];
+    int m = or_image_side(p), o = (n - m) / 2;
+    for (int q = 0; q < m; ++q)
+        for (int pp = 0; pp < m; ++pp) {
+            size_t t = (size_t)(q + o) * n + (pp + o);
+            image[(size_t)q * m + pp] = creal(acc[t]) * scale[t];
+        }
     if (stats) {
         int64_t du = 0, dw = 0;
         for (int64_t i = 0; i < nvis; ++i) {
@@ -572,6 +600,7 @@ void or_grid(const or_params *p, int64_t nvis, const double *uvw, const double c
 /*   y * s(p,q) -> x e^{-2 pi i w_k (n-1)} -> x (-1)^{p+q} ->                */
 /*   unnormalised forward 2D DFT -> x (-1)^{i+j} ->                          */
 /*   per visibility [w_m] sum G(d_x) G(d_y) P[a_y + jy][a_x + jx].           */
+/* The m x m image enters zero-padded to n x n (the transpose of the crop). */
 /* wmin/wmax/sumw are those of the forward operator (the binning geometry). */
 
 void or_adjoint(const or_params *p, int64_t nvis, const double *uvw, const double *weight,
@@ -591,6 +620,7 @@ void or_adjoint(const or_params *p, int64_t nvis, const double *uvw, const doubl
     or_scale_plane(p, flags, sumw, scale);
     double complex *plane = malloc(sizeof(double complex) * nn);
     double dl = p->fov / n;
+    int mside = or_image_side(p), o = (n - mside) / 2;
     for (int64_t i = 0; i < nvis; ++i) vis_out[i] = 0.0;
     for (int k = 0; k < p->n_w; ++k) {
         double wk = or_plane_centre(p, k, wmin, wmax);
@@ -599,8 +629,11 @@ void or_adjoint(const or_params *p, int64_t nvis, const double *uvw, const doubl
             for (int pp = 0; pp < n; ++pp) {
                 double l = (pp - n / 2) * dl, m = (qq - n / 2) * dl;
                 double ph = -2.0 * M_PI * wk * or_nm1(l, m);
-                double complex f = image[(size_t)qq * n + pp] * scale[(size_t)qq * n + pp] *
-                                   (cos(ph) + I * sin(ph));
+                int inside = pp >= o && pp < o + mside && qq >= o && qq < o + mside;
+                double complex f = 0.0; /* outside the crop (possibly off the unit circle) */
+                if (inside)
+                    f = image[(size_t)(qq - o) * mside + (pp - o)] * scale[(size_t)qq * n + pp] *
+                        (cos(ph) + I * sin(ph));
                 if ((pp + qq) & 1) f = -f;
                 plane[(size_t)qq * n + pp] = f;
             }

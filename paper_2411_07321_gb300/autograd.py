@@ -2,12 +2,13 @@
 
 Both functions run on an ``Imager`` whose geometry was set by ``Imager.bin``
 (uvw, weights); they change only the values gridded through that geometry.
+m is the imager's image side (its grid side n unless the grid is padded).
 
-GridFn   vis (complex64 [n_vis]) -> image (float32 [n, n]) = A vis, the
+GridFn   vis (complex64 [n_vis]) -> image (float32 [m, m]) = A vis, the
          w-stacked image (grid, inverse FFT per plane, w-correct, stack).
          backward: grad_vis = A^H grad_image -- w-spread, forward FFT,
          degrid, the hand-written adjoint (the oracle pins it).
-DegridFn image (float32 [n, n]) -> model visibilities (complex64 [n_vis]) = D x,
+DegridFn image (float32 [m, m]) -> model visibilities (complex64 [n_vis]) = D x,
          the degridding predictor of Eq. 1 (x / n / taper, forward FFT per plane,
          degrid, no weights).  backward: grad_image = Re(D^H grad_vis) --
          grid with unit weights, inverse FFT, w-correct with the same scaling.

@@ -23,14 +23,27 @@ extern "C" const char *rick_status_string(rick_status s)
 
 static bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// Beatty, Nishimura & Pauly (2005): the KB shape for oversampling alpha.
+extern "C" double rick_kb_beta(int32_t support, double alpha)
+{
+    if (support < 2 || !(alpha >= 1.0) || !isfinite(alpha)) return NAN;
+    const double t = (support / alpha) * (support / alpha) * (alpha - 0.5) * (alpha - 0.5) - 0.8;
+    return t > 0.0 ? M_PI * sqrt(t) : NAN;
+}
+
 static rick_status check_params(const rick_params *p)
 {
     if (!p) return RICK_EINVAL;
     if (!is_pow2(p->n) || p->n < 16 || p->n > 32768) return RICK_EINVAL;
     if (p->n_w < 1 || p->n_w > 1024) return RICK_EINVAL;
     if (!(p->fov > 0.0) || !isfinite(p->fov)) return RICK_EINVAL;
-    // the image must stay inside the unit circle of direction cosines
-    if (!(p->fov * 0.5 * sqrt(2.0) < 1.0)) return RICK_EINVAL;
+    if (p->reserved != 0) return RICK_EINVAL;
+    if (p->image_n != 0 && (p->image_n < 16 || p->image_n > p->n || (p->image_n & 1)))
+        return RICK_EINVAL;
+    // the image (the kept crop of a padded grid) must stay inside the unit
+    // circle of direction cosines; its corner pixel is at l = m = -(m/2) fov/n
+    const double kept = p->image_n ? (double)p->image_n / p->n : 1.0;
+    if (!(p->fov * kept * 0.5 * sqrt(2.0) < 1.0)) return RICK_EINVAL;
     if (isnan(p->w_min) != isnan(p->w_max)) return RICK_EINVAL;
     if (!isnan(p->w_min) && !(isfinite(p->w_min) && isfinite(p->w_max) && p->w_min <= p->w_max))
         return RICK_EINVAL;
@@ -49,8 +62,7 @@ static rick_status check_params(const rick_params *p)
     if (p->kernel == RICK_KERNEL_KB && p->support > 1) {
         double b = p->kb_beta;
         if (isnan(b)) {
-            double t = (p->support / 2.0) * (p->support / 2.0) * 2.25 - 0.8;
-            if (!(t > 0)) return RICK_EINVAL;
+            if (isnan(rick_kb_beta(p->support, 2.0))) return RICK_EINVAL;
         } else if (!(b > 0.0) || !isfinite(b)) {
             return RICK_EINVAL;
         }
@@ -63,8 +75,8 @@ static rick_status check_params(const rick_params *p)
 
 // Taper correction C(nu) = integral_{-W/2}^{W/2} G(d) cos(2 pi nu d) dd for
 // nu_p = (p - n/2)/n, stored as 1/C.  KB: closed form of Jackson (1991),
-// W sinh(sqrt(beta^2 - (pi W nu)^2)) / sqrt(...) / I0(beta); Gaussian:
-// composite Simpson rule on 4096 panels (the integrand is entire).  FP64.
+// W sinh(sqrt(beta^2 - (pi W nu)^2)) / sqrt(...) / I0(beta); Gaussian: a
+// 48-point Gauss-Legendre rule (the integrand is entire).  FP64.
 // Nodes and weights of the 48-point Gauss-Legendre rule on [-1, 1] (nodes in
 // decreasing order), by Newton's iteration on the Legendre polynomial P_48 from
 // the cosine initial guesses (the textbook method), in FP64 on the host.
@@ -179,11 +191,13 @@ __global__ void kernel_poly_kernel(float *coef, int W, int kind, double beta, do
     for (int k = 0; k < N; ++k) coef[j * N + k] = (float)c[k];
 }
 
+// The default KB shape is Beatty's for oversampling 2 (0 where that has no
+// real root: W == 1, which needs no shape).
 static double kb_beta_of(const rick_params *p)
 {
     if (!isnan(p->kb_beta)) return p->kb_beta;
-    double t = (p->support / 2.0) * (p->support / 2.0) * 2.25 - 0.8;
-    return M_PI * sqrt(t > 0 ? t : 0.0);
+    const double b = rick_kb_beta(p->support, 2.0);
+    return isnan(b) ? 0.0 : b;
 }
 
 static double bessel_i0_host(double x)
@@ -346,6 +360,17 @@ extern "C" rick_status rick_plan_set_geometry(rick_plan *plan, double fov, doubl
     q.fov = fov;
     q.w_min = w_min;
     q.w_max = w_max;
+    rick_status st = check_params(&q);
+    if (st != RICK_OK) return st;
+    plan->p = q;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_plan_set_image_n(rick_plan *plan, int32_t image_n)
+{
+    if (!plan) return RICK_EINVAL;
+    rick_params q = plan->p;
+    q.image_n = image_n;
     rick_status st = check_params(&q);
     if (st != RICK_OK) return st;
     plan->p = q;

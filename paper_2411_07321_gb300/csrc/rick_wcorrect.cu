@@ -12,10 +12,14 @@
 // itself is evaluated in double-single from l, m; only its fraction in cycles
 // goes to sincospif.  This keeps FP64-class accuracy without per-pixel FP64
 // instructions, which GB300 issues at a small fraction of the FP32 rate.
+//
+// On a padded grid only the kept m x m crop is corrected (m^2 n_w plane reads
+// instead of n^2 n_w); the adjoint writes zeros outside the crop.
 #include "rick_common.cuh"
 
 struct WcArgs {
     int n, n_w;
+    int m, off;  // image side and its offset (n - m)/2 in the grid frame
     const float2 *planes_in;
     float2 *planes_out;
     const float *image_in;
@@ -109,12 +113,12 @@ __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
     }
     __syncthreads();
     const size_t nn = (size_t)a.n * a.n;
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nn) return;
-    int p = (int)(idx % a.n), q = (int)(idx / a.n);
+    const size_t oidx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (oidx >= (size_t)a.m * a.m) return;
+    const int p = (int)(oidx % a.m) + a.off, q = (int)(oidx / a.m) + a.off;
     PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
     float acc = 0.0f;
-    const float2 *src = a.planes_in + idx;
+    const float2 *src = a.planes_in + ((size_t)q * a.n + p);
     PhaseWalker ph;
     ph.start(a, s_w, a.n_w, g);
 #pragma unroll 4
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
         ph.at(a, s_w, k, g);
         acc = fmaf(F.x, ph.c, fmaf(-F.y, ph.s, acc));
     }
-    a.image_out[idx] = acc * g.scale;
+    a.image_out[oidx] = acc * g.scale;
 }
 
 __global__ void __launch_bounds__(256) wspread_kernel(WcArgs a)
@@ -139,10 +143,15 @@ __global__ void __launch_bounds__(256) wspread_kernel(WcArgs a)
     const size_t nn = (size_t)a.n * a.n;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nn) return;
-    int p = (int)(idx % a.n), q = (int)(idx / a.n);
-    PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
-    float v = a.image_in[idx] * g.scale;
+    const int p = (int)(idx % a.n), q = (int)(idx / a.n);
     float2 *dst = a.planes_out + idx;
+    const int pi = p - a.off, qi = q - a.off;
+    if (pi < 0 || pi >= a.m || qi < 0 || qi >= a.m) {  // zero padding
+        for (int k = 0; k < a.n_w; ++k) dst[(size_t)k * nn] = make_float2(0.0f, 0.0f);
+        return;
+    }
+    PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
+    float v = a.image_in[(size_t)qi * a.m + pi] * g.scale;
     PhaseWalker ph;
     ph.start(a, s_w, a.n_w, g);
 #pragma unroll 4
@@ -159,6 +168,8 @@ static WcArgs make_args(rick_plan *plan, const void *ws_dev, uint32_t flags)
     WcArgs a;
     a.n = p.n;
     a.n_w = p.n_w;
+    a.m = p.image_n ? p.image_n : p.n;
+    a.off = (p.n - a.m) / 2;
     a.taper_inv = plan->taper_inv;
     a.hdr = w.hdr;
     a.wplane = w.wplane;
@@ -190,8 +201,8 @@ extern "C" rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_d
     WcArgs a = make_args(plan, ws_dev, flags);
     a.planes_in = (const float2 *)planes_dev;
     a.image_out = image_dev;
-    size_t nn = (size_t)a.n * a.n;
-    wcorrect_kernel<<<(unsigned)((nn + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
+    size_t mm = (size_t)a.m * a.m;
+    wcorrect_kernel<<<(unsigned)((mm + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
                       (cudaStream_t)stream>>>(a);
     RICK_LAUNCH_CHECK(plan);
     return RICK_OK;

@@ -35,14 +35,19 @@ class Imager:
     def __init__(self, n: int, n_w: int, fov: float, kernel: str = "kb", support: int = 7,
                  tile: int = 64, w_range: tuple[float, float] | None = None,
                  kb_beta: float = math.nan, gauss_sigma: float = math.nan,
-                 precision: str = "fp32", max_vis: int = 1 << 20, device=None):
+                 precision: str = "fp32", max_vis: int = 1 << 20, device=None,
+                 image_n: int | None = None):
+        """n is the grid side; the image is the central image_n x image_n crop
+        (default n: no padding), with pixel size fov / n."""
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("Imager runs on a CUDA device only")
         wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)
         self.params = R.make_params(n, n_w, fov, KERNELS[kernel], support, wmin, wmax, kb_beta,
-                                    gauss_sigma, tile, PRECISIONS[precision])
+                                    gauss_sigma, tile, PRECISIONS[precision],
+                                    0 if image_n is None else image_n)
         self.n, self.n_w, self.max_vis = int(n), int(n_w), int(max_vis)
+        self.m = int(image_n) if image_n else self.n
         with torch.cuda.device(self.device):
             self.plan = R.rick_plan_create(self.params, self.max_vis)
             self.ws_bytes, self.plane_bytes = R.rick_workspace_bytes(self.params, self.max_vis)
@@ -134,14 +139,14 @@ class Imager:
 
     def wcorrect(self, flags: int = IMAGE_FLAGS, out: torch.Tensor | None = None) -> torch.Tensor:
         if out is None:
-            out = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
-        self._check(out, torch.float32, (self.n, self.n), "image")
+            out = torch.empty((self.m, self.m), dtype=torch.float32, device=self.device)
+        self._check(out, torch.float32, (self.m, self.m), "image")
         R.rick_wcorrect_stack(self.plan, self.planes.data_ptr(), self.ws.data_ptr(),
                               out.data_ptr(), flags, self._stream())
         return out
 
     def wspread(self, image: torch.Tensor, flags: int = IMAGE_FLAGS):
-        self._check(image, torch.float32, (self.n, self.n), "image")
+        self._check(image, torch.float32, (self.m, self.m), "image")
         R.rick_wspread(self.plan, image.data_ptr(), self.ws.data_ptr(), self.planes.data_ptr(),
                        flags, self._stream())
 
@@ -191,7 +196,8 @@ class Imager:
             self._in_uvw = torch.empty((self.max_vis, 3), dtype=torch.float64, device=self.device)
             self._in_vis = torch.empty(self.max_vis, dtype=torch.complex64, device=self.device)
             self._in_wt = torch.empty(self.max_vis, dtype=torch.float32, device=self.device)
-            self._out_img = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
+        if getattr(self, "_out_img", None) is None or self._out_img.shape[0] != self.m:
+            self._out_img = torch.empty((self.m, self.m), dtype=torch.float32, device=self.device)
         uvw, vis = self._in_uvw[:n], self._in_vis[:n]
         uvw.copy_(uvw_host, non_blocking=True)
         vis.copy_(vis_host, non_blocking=True)
@@ -237,17 +243,19 @@ class Imager:
             self._stage = None
             self._stage = torch.empty(need, dtype=torch.uint8, device=self.device)
         if getattr(self, "_out_imgs", None) is None:
-            self._out_imgs = [torch.empty((self.n, self.n), dtype=torch.float32,
-                                          device=self.device) for _ in range(2)]
+            self._out_imgs = [None, None]
             self._out_done = [None, None]
             self._out_i = 0
             self._copy_out = torch.cuda.Stream(device=self.device)
         i = self._out_i
         self._out_i ^= 1
-        img = self._out_imgs[i]
         cur = torch.cuda.current_stream(self.device)
         if self._out_done[i] is not None:  # the copy-out of this buffer two calls ago
             cur.wait_event(self._out_done[i])
+        if self._out_imgs[i] is None or self._out_imgs[i].shape[0] != self.m:
+            self._out_imgs[i] = torch.empty((self.m, self.m), dtype=torch.float32,
+                                            device=self.device)
+        img = self._out_imgs[i]
         if n_chan:
             R.rick_image_host_channels(self.plan, n_units, n_chan, uvw_host.data_ptr(),
                                        chan_scale.data_ptr(), vis_host.data_ptr(),
@@ -287,6 +295,12 @@ class Imager:
         wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)
         R.rick_plan_set_geometry(self.plan, fov, wmin, wmax)
         self.params.fov, self.params.w_min, self.params.w_max = float(fov), wmin, wmax
+
+    def set_image_n(self, image_n: int | None):
+        """Re-target the resident plan to another crop of its grid (None: no crop)."""
+        R.rick_plan_set_image_n(self.plan, 0 if image_n is None else image_n)
+        self.params.image_n = 0 if image_n is None else int(image_n)
+        self.m = int(image_n) if image_n else self.n
 
     def set_kernel(self, kernel: str, support: int, kb_beta: float = math.nan,
                    gauss_sigma: float = math.nan):

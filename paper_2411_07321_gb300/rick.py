@@ -35,7 +35,8 @@ class rick_params(ctypes.Structure):
                 ("w_min", ctypes.c_double), ("w_max", ctypes.c_double),
                 ("kernel", ctypes.c_int32), ("support", ctypes.c_int32),
                 ("kb_beta", ctypes.c_double), ("gauss_sigma", ctypes.c_double),
-                ("tile", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("image_n", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class rick_bin_stats(ctypes.Structure):
@@ -52,6 +53,7 @@ class rick_bin_view(ctypes.Structure):
 
 EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_plan_last_error",
            "rick_plan_launch_count", "rick_plan_set_geometry", "rick_plan_set_kernel",
+           "rick_plan_set_image_n", "rick_kb_beta",
            "rick_workspace_bytes", "rick_plan_fft_bytes", "rick_bin_layout", "rick_bin",
            "rick_bin_noalloc", "rick_bin_values", "rick_grid", "rick_grid_accumulate",
            "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
@@ -69,6 +71,8 @@ def _load():
     P = ctypes.POINTER(rick_params)
     L.rick_status_string.restype = ctypes.c_char_p
     L.rick_status_string.argtypes = [i32]
+    L.rick_kb_beta.restype = ctypes.c_double
+    L.rick_kb_beta.argtypes = [i32, ctypes.c_double]
     for name, args in {
         "rick_plan_create": [P, i64, ctypes.POINTER(vp)],
         "rick_plan_destroy": [vp],
@@ -76,6 +80,7 @@ def _load():
         "rick_plan_launch_count": [vp, ctypes.POINTER(ctypes.c_uint64)],
         "rick_plan_set_geometry": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
         "rick_plan_set_kernel": [vp, i32, i32, ctypes.c_double, ctypes.c_double],
+        "rick_plan_set_image_n": [vp, i32],
         "rick_workspace_bytes": [P, i64, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "rick_plan_fft_bytes": [vp, ctypes.POINTER(sz)],
         "rick_bin_layout": [vp, ctypes.POINTER(rick_bin_view)],
@@ -116,10 +121,10 @@ def _check(fn: str, s: int) -> None:
 
 def make_params(n, n_w, fov, kernel=RICK_KERNEL_KB, support=7, w_min=math.nan, w_max=math.nan,
                 kb_beta=math.nan, gauss_sigma=math.nan, tile=64,
-                precision=RICK_PREC_FP32) -> rick_params:
+                precision=RICK_PREC_FP32, image_n=0) -> rick_params:
     return rick_params(int(n), int(n_w), float(fov), float(w_min), float(w_max), int(kernel),
                        int(support), float(kb_beta), float(gauss_sigma), int(tile),
-                       int(precision))
+                       int(precision), int(image_n), 0)
 
 
 def rick_plan_create(params: rick_params, max_vis: int) -> int:
@@ -153,6 +158,14 @@ def rick_plan_set_kernel(plan: int, kernel: int, support: int, kb_beta: float = 
                          gauss_sigma: float = math.nan) -> None:
     _check("rick_plan_set_kernel", _L.rick_plan_set_kernel(plan, int(kernel), int(support),
                                                            float(kb_beta), float(gauss_sigma)))
+
+
+def rick_plan_set_image_n(plan: int, image_n: int) -> None:
+    _check("rick_plan_set_image_n", _L.rick_plan_set_image_n(plan, int(image_n)))
+
+
+def rick_kb_beta(support: int, alpha: float) -> float:
+    return float(_L.rick_kb_beta(int(support), float(alpha)))
 
 
 def rick_workspace_bytes(params: rick_params, n_vis: int) -> tuple[int, int]:

@@ -15,9 +15,9 @@ requests admitted while others run overlaps on the device.
 
 Admission is by HBM footprint: a request needs a slot with the same grid size,
 plane count, tile and precision, and a visibility capacity at least its own;
-the slot's plan is re-targeted to the request's field of view, w range and
-gridding kernel (rick_plan_set_geometry, rick_plan_set_kernel), so the cuFFT
-plan and the buffers are reused.  If no idle slot fits, a new one is created
+the slot's plan is re-targeted to the request's field of view, w range, image
+crop and gridding kernel (rick_plan_set_geometry, rick_plan_set_image_n,
+rick_plan_set_kernel), so the cuFFT plan and the buffers are reused.  If no idle slot fits, a new one is created
 when budget - used >= its footprint, after evicting idle slots
 least-recently-used first.  A request larger than the whole budget is rejected
 with an error, and only that request fails.
@@ -68,10 +68,16 @@ class ImagingJob:
     flags: int = IMAGE_FLAGS
     job_id: int = -1
     arrival: float = field(default_factory=time.perf_counter)
+    image_n: int | None = None  # central crop of the n-cell grid (None: n)
 
     @property
     def n_vis(self) -> int:
         return int(self.uvw.shape[0])
+
+    @property
+    def side(self) -> int:
+        """Side of the returned image."""
+        return int(self.image_n) if self.image_n else self.n
 
     def key(self):
         """What a slot must share with the request (its capacity may be larger)."""
@@ -151,7 +157,7 @@ def slot_footprint(job: ImagingJob) -> int:
     from . import rick as R
     from .imager import KERNELS, PRECISIONS
     p = R.make_params(job.n, job.n_w, job.fov, KERNELS[job.kernel], job.support, tile=job.tile,
-                      precision=PRECISIONS[job.precision])
+                      precision=PRECISIONS[job.precision], image_n=job.image_n or 0)
     cap = capacity_class(job.n_vis)
     ws, planes = R.rick_workspace_bytes(p, cap)
     # planes + workspace + cuFFT area (bounded by the planes' size for in-place
@@ -165,7 +171,8 @@ class _Slot:
         self.key = job.key()
         self.imager = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
                              tile=job.tile, precision=job.precision,
-                             max_vis=capacity_class(job.n_vis), device=device)
+                             max_vis=capacity_class(job.n_vis), device=device,
+                             image_n=job.image_n)
         self.kernel = (job.kernel, job.support)
         self.stream = torch.cuda.Stream(device=device)
         self.out = out_host  # pinned image buffer, from the server's pool
@@ -176,7 +183,7 @@ class _Slot:
 
 
 class _PinnedPool:
-    """Pinned host image buffers by grid size, reused across slots
+    """Pinned host image buffers by image side, reused across slots
     (pinning host memory is slow; a new slot should not pay for it)."""
 
     def __init__(self):
@@ -280,7 +287,7 @@ class Server:
                 else:
                     for sid in decision[1]:
                         self._evict(sid)
-                    slot = _Slot(job, self.device, self._pinned.get(job.n))
+                    slot = _Slot(job, self.device, self._pinned.get(job.side))
                     sid = self.admission.add(job.key(), need, now, capacity_class(job.n_vis))
                     self._slots[sid] = slot
                     self.peak_used = max(self.peak_used, self.admission.used())
@@ -309,11 +316,15 @@ class Server:
     def _launch(self, sid, slot, job, fut):
         import torch
         slot.job, slot.future, slot.t_start = job, fut, time.perf_counter()
-        if slot.out is None:
-            slot.out = self._pinned.get(job.n)
+        if slot.out is None or slot.out.shape[0] != job.side:
+            if slot.out is not None:
+                self._pinned.put(slot.out)
+            slot.out = self._pinned.get(job.side)
         if slot.kernel != (job.kernel, job.support):  # the slot is idle: its work is done
             slot.imager.set_kernel(job.kernel, job.support)
             slot.kernel = (job.kernel, job.support)
+        if slot.imager.m != job.side:
+            slot.imager.set_image_n(job.image_n)
         with torch.cuda.stream(slot.stream):
             slot.imager.set_geometry(job.fov, job.w_range)
             slot.imager.image_from_host(job.uvw, job.vis, job.weight, slot.out, job.flags)
@@ -371,8 +382,8 @@ def run_plain(job: ImagingJob, device="cuda:0") -> np.ndarray:
     with torch.cuda.device(device):
         im = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
                     tile=job.tile, precision=job.precision, w_range=job.w_range,
-                    max_vis=max(job.n_vis, 1), device=device)
-        out = torch.empty((job.n, job.n), dtype=torch.float32).pin_memory()
+                    max_vis=max(job.n_vis, 1), device=device, image_n=job.image_n)
+        out = torch.empty((job.side, job.side), dtype=torch.float32).pin_memory()
         im.image_from_host(job.uvw, job.vis, job.weight, out, job.flags)
         torch.cuda.current_stream().synchronize()
         img = out.numpy().copy()

@@ -38,17 +38,42 @@ def test_status_strings(R):
         assert R.status_string(s) and R.status_string(s) != "unknown status"
 
 
-def test_struct_layout_matches_header(R):
+def test_struct_layout_matches_header(R, tmp_path):
+    """The binding's structs have the C compiler's size and field offsets."""
     import ctypes
-    assert ctypes.sizeof(R.rick_params) == 64
+    import subprocess
+    assert ctypes.sizeof(R.rick_params) == 72
     assert ctypes.sizeof(R.rick_bin_stats) == 48
+    structs = {"rick_params": R.rick_params, "rick_bin_stats": R.rick_bin_stats,
+               "rick_bin_view": R.rick_bin_view}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rick.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        name, field, v = line.split()
+        got[(name, field)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
 
 
 @pytest.mark.parametrize("bad", [
     dict(n=100), dict(n=8), dict(n_w=0), dict(fov=0.0), dict(fov=2.0), dict(support=0),
     dict(support=17), dict(tile=4), dict(tile=48), dict(tile=256), dict(kernel=7),
     dict(w_min=1.0), dict(w_min=2.0, w_max=1.0), dict(precision=3), dict(kb_beta=-1.0),
-    dict(gauss_sigma=0.0, kernel=0),
+    dict(gauss_sigma=0.0, kernel=0), dict(image_n=14), dict(image_n=101), dict(image_n=512),
+    dict(image_n=-2), dict(fov=2.0, image_n=192),
 ])
 def test_invalid_params_rejected_on_host(R, bad):
     kw = dict(n=256, n_w=8, fov=0.035, kernel=1, support=7, w_min=math.nan, w_max=math.nan,
@@ -60,7 +85,28 @@ def test_invalid_params_rejected_on_host(R, bad):
     assert e.value.status == R.RICK_EINVAL
 
 
-def test_workspace_bytes_scale_with_capacity(R):
+def test_crop_params(R):
+    """A crop relaxes the unit-circle bound to the kept field; reserved must be 0."""
+    kw = dict(n=256, n_w=8, fov=2.0, kernel=1, support=7, tile=32)
+    R.rick_workspace_bytes(R.make_params(**kw, image_n=128), 1000)  # 2 * 0.5 / sqrt 2 < 1
+    p = R.make_params(**dict(kw, fov=0.03))
+    p.reserved = 1
+    with pytest.raises(R.RickError):
+        R.rick_workspace_bytes(p, 1000)
+
+
+def test_kb_beta_for_oversampling(R):
+    import oracle
+    for W in (2, 4, 7, 9, 16):
+        for alpha in (1.25, 1.5, 2.0, 3.0):
+            want = oracle.kb_beta(W, alpha)
+            if math.isnan(want):
+                assert math.isnan(R.rick_kb_beta(W, alpha))
+            else:
+                assert R.rick_kb_beta(W, alpha) == pytest.approx(want, rel=1e-15)
+    assert math.isnan(R.rick_kb_beta(1, 2.0))
+    assert math.isnan(R.rick_kb_beta(7, 0.9))
+
     p = R.make_params(4096, 16, 0.1396, 1, 7, tile=64)
     b1, planes = R.rick_workspace_bytes(p, 1_000_000)
     b2, _ = R.rick_workspace_bytes(p, 2_000_000)

@@ -462,3 +462,87 @@ def test_image_pixels_equal_fft_image(W, n_w, kern):
     got = oracle.image_pixels(p, d["uvw"], d["vis"], wt, pix)
     want = np.array([img[q, pp] for pp, q in pix])
     assert got == pytest.approx(want, rel=1e-10, abs=1e-12 * np.abs(img).max())
+
+
+# ---------------------------------------------------------------- grid padding and crop
+
+def _padding_case(m_img=64, fov_img=2.0 ** -4, M=3000, seed=31):
+    """Three point sources, two near the edges of an m_img-pixel field, w = 0
+    (so that the only error left is the gridding's aliasing)."""
+    r = rng(seed)
+    lim = (m_img / 2 - 5) / fov_img
+    uvw = np.stack([r.uniform(-lim, lim, M), r.uniform(-lim, lim, M), np.zeros(M)], 1)
+    dl = fov_img / m_img
+    vis = sum(_point_source_vis(uvw, a * dl, b * dl, S)
+              for a, b, S in ((28.0, -27.0, 1.0), (3.0, -2.0, 0.5), (-31.3, 29.6, 0.7)))
+    return uvw, vis, fov_img
+
+
+@pytest.mark.parametrize("kern,W,alpha,tol", [(oracle.KB, 7, 2, 1e-6), (oracle.KB, 9, 2, 1e-8),
+                                              (oracle.KB, 7, 4, 1e-6), (oracle.GAUSS, 7, 2, 2e-3)])
+def test_padding_cuts_aliasing_against_dft(kern, W, alpha, tol):
+    """The central crop of a grid padded by alpha is the brute-force DFT of the
+    kept field to the kernel's aliasing level, where the unpadded grid of the
+    same pixel size is off by percents near the edges.  An offset crop, a wrong
+    pixel size or a wrong phase centre would miss the DFT by far more."""
+    uvw, vis, fov_img = _padding_case()
+    m = 64
+    f = oracle.N_CORRECT | oracle.NORMALIZE
+    ref = oracle.dft(m, fov_img, uvw, vis, None, flags=f, sum_weight=float(len(vis)))
+    peak = np.abs(ref).max()
+    n = m * alpha
+    p = oracle.Params(n=n, n_w=1, fov=fov_img * alpha, kernel=kern, support=W, tile=16, image_n=m)
+    img, st = oracle.image(p, uvw, vis, None, flags=f)
+    assert img.shape == (m, m) and st["n_binned"] == len(vis)
+    err = np.abs(img - ref).max() / peak
+    p1 = oracle.Params(n=m, n_w=1, fov=fov_img, kernel=kern, support=W, tile=16)
+    img1, _ = oracle.image(p1, uvw, vis, None, flags=f)
+    err1 = np.abs(img1 - ref).max() / peak
+    print(f"padding {alpha}: {err:.2e} (unpadded {err1:.2e})")
+    assert err <= tol and err1 >= 1e-2
+    # image_n == n is the uncropped image
+    p2 = oracle.Params(n=m, n_w=1, fov=fov_img, kernel=kern, support=W, tile=16, image_n=m)
+    assert np.array_equal(oracle.image(p2, uvw, vis, None, flags=f)[0], img1)
+
+
+@pytest.mark.parametrize("n,m", [(64, 32), (64, 46)])  # offsets 16 and 9 (odd)
+def test_crop_adjoint_dot_product(n, m):
+    """<A x, y> = Re <x, A^H y> with A the cropped image operator: the adjoint
+    zero-pads the m x m image into the n x n grid frame (P9)."""
+    fov, W = 0.06, 7
+    r = rng(32)
+    M = 600
+    lim = (n / 2 - 1) / fov
+    uvw = np.stack([r.uniform(-lim, lim, M), r.uniform(-lim, lim, M), r.uniform(-300, 300, M)], 1)
+    x = r.normal(size=M) + 1j * r.normal(size=M)
+    y = r.normal(size=(m, m))
+    wt = r.uniform(0.5, 1.5, M)
+    p = oracle.Params(n=n, n_w=5, fov=fov, kernel=oracle.KB, support=W, tile=16, image_n=m)
+    f = oracle.N_CORRECT | oracle.NORMALIZE
+    ax, st = oracle.image(p, uvw, x, wt, flags=f)
+    aty = oracle.adjoint(p, uvw, y, wt, flags=f, w_min=st["w_min"], w_max=st["w_max"],
+                         sum_weight=st["sum_weight"])
+    lhs = np.sum(ax * y)
+    rhs = np.real(np.sum(x * np.conj(aty)))
+    assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(ax * y))
+    # and the crop is the central block of the uncropped image at the same pixels
+    full, _ = oracle.image(oracle.Params(n=n, n_w=5, fov=fov, kernel=oracle.KB, support=W,
+                                         tile=16), uvw, x, wt, flags=f)
+    o = (n - m) // 2
+    assert np.array_equal(ax, full[o:o + m, o:o + m])
+
+
+@pytest.mark.parametrize("W,alpha", [(4, 1.5), (7, 1.5), (9, 1.5), (4, 2.0), (7, 2.0), (9, 2.0),
+                                     (4, 3.0), (7, 3.0)])
+def test_kb_beta_puts_first_taper_zero_past_the_alias_edge(W, alpha):
+    """Beatty et al.'s KB shape for oversampling alpha: the kernel's transform C
+    (here by quadrature of G, not its closed form) stays positive out to the
+    first alias of the image edge, nu = 1 - 1/(2 alpha) grid units, and turns
+    negative just beyond it."""
+    beta = oracle.kb_beta(W, alpha)
+    p = oracle.Params(n=64, n_w=1, fov=0.05, kernel=oracle.KB, support=W, kb_beta=beta, tile=16)
+    edge = 1.0 - 1.0 / (2.0 * alpha)
+    assert all(oracle.taper(p, nu) > 0 for nu in np.linspace(0.0, edge, 25))
+    assert oracle.taper(p, edge + 0.2 / W ** 2 + 0.01 / W) < 0
+    if alpha == 2.0:
+        assert beta == oracle.kb_beta_default(W)
