@@ -97,3 +97,24 @@ def test_failures_stay_with_their_request(S, data):
             futs[2].result(timeout=60)
         for f in (futs[0], futs[3], futs[4]):
             assert f.result(timeout=120).image.shape[0] in (256, 512, 1024)
+
+
+def test_crops_share_a_slot(S, data):
+    """Requests for different crops of one grid (image_n) run on one re-targeted
+    slot, each giving its plain per-request image."""
+    n = 512
+    fov = S.fov_for(n, 7, 12000.0)
+    jobs = [S.ImagingJob(data["uvw"][:200_000], data["vis"][:200_000], data["weight"][:200_000],
+                         n=n, n_w=8, fov=fov, kernel="kb", support=7, tile=32, job_id=i,
+                         image_n=m) for i, m in enumerate((None, 256, 384, 256, None))]
+    with S.Server("cuda:0", max_running=1) as srv:
+        res = [srv.submit(j).result(timeout=120) for j in jobs]
+        assert srv.counters["new_slots"] == 1 and srv.counters["reused"] == len(jobs) - 1
+    op = oracle.Params(n=n, n_w=1, fov=0.01, kernel=oracle.KB, support=7)
+    c = np.array([oracle.taper(op, (i - n // 2) / n) for i in range(n)])
+    for j, r in zip(jobs, res):
+        assert r.image.shape == (j.side, j.side)
+        ref = S.run_plain(j)
+        o = (n - j.side) // 2
+        cc = np.outer(c[o:o + j.side], c[o:o + j.side])
+        assert np.abs((r.image - ref) * cc).max() <= 1e-5 * np.abs(ref * cc).max()

@@ -135,3 +135,5 @@ def test_job_key_leaves_out_kernel_and_capacity(S):
     assert a.key() == b.key()
     c = S.ImagingJob(uvw, None, None, n=512, n_w=9, fov=0.01)
     assert a.key() != c.key()
+    d = S.ImagingJob(uvw, None, None, n=512, n_w=8, fov=0.01, image_n=300)
+    assert d.key() == a.key() and (d.side, a.side) == (300, 512)
