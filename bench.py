@@ -328,8 +328,8 @@ def run_ours(args, wl):
         scale_h = torch.from_numpy(data["chan_scale"]).pin_memory()
         e2e_ms = timed(lambda: ims.image_streamed(rows_h, vis_h, wt_h, out_h, chan_scale=scale_h))
         h2d = rows_h.numel() * 8 + scale_h.numel() * 8 + n_vis * (8 + 4)
-        call = (f"Imager.image_streamed with chan_scale (rick_image_host_channels): rows of "
-                f"{n_chan} channels with uvw once per row, chunks of {min(args.chunk, n_vis)} "
+        call = (f"Imager.image_streamed with chan_scale (rick_image_host_rows, one "
+                f"correlation): rows of {n_chan} channels with uvw once per row, chunks of {min(args.chunk, n_vis)} "
                 f"visibilities, w range from the data")
     else:
         e2e_ms, h2d = e2e_vis_ms, n_vis * (24 + 8 + 4)

@@ -212,6 +212,30 @@ rick_status rick_bin_channels(rick_plan *plan, int64_t n_rows, int32_t n_chan,
                               const void *vis_dev, const float *weight_dev, void *ws_dev,
                               size_t ws_bytes, rick_bin_stats *stats_dev, void *stream);
 
+/* Correlations per visibility that rick_bin_rows / rick_image_host_rows take. */
+#define RICK_MAX_CORR 4
+
+/* rick_bin_channels for rows whose visibilities carry n_corr correlations (a
+ * measurement set stores e.g. the XX and YY products of linear feeds; the
+ * paper's LOFAR counts include two).  Each (row, channel) is gridded once, as
+ * the weighted sum of its correlations: its record holds sum_c w_c V_c and its
+ * weight is sum_c w_c, so the normalised image is the weighted mean of the
+ * correlations (Stokes I for XX and YY) and equals, up to FP32 rounding, the
+ * image of the set with each correlation as its own visibility at the same
+ * uvw.  A correlation with weight 0 (flagged) drops out.
+ *   vis_dev:    complex64 [n_rows][n_chan][n_corr], correlation fastest
+ *   weight_dev: float32 [n_rows][n_chan][n_corr], or NULL: unit weight per
+ *               correlation (a visibility then weighs n_corr)
+ * The binning's visibilities are the (row, channel) pairs: rick_bin_values,
+ * rick_degrid and rick_density_weights then take one value or weight per pair,
+ * and the stats count pairs (sum_weight sums all correlation weights).
+ * n_corr == 1 is rick_bin_channels.  Errors: as rick_bin_channels;
+ * RICK_EINVAL for n_corr outside 1 ... RICK_MAX_CORR. */
+rick_status rick_bin_rows(rick_plan *plan, int64_t n_rows, int32_t n_chan, int32_t n_corr,
+                          const double *uvw_rows_dev, const double *chan_scale_dev,
+                          const void *vis_dev, const float *weight_dev, void *ws_dev,
+                          size_t ws_bytes, rick_bin_stats *stats_dev, void *stream);
+
 /* Where the binning arrays sit inside a workspace (byte offsets from ws_dev),
  * for callers that read the binned records directly:
  *   offsets  uint32 [n_bins + 1]   bin b holds records [offsets[b], offsets[b+1])
@@ -386,6 +410,17 @@ rick_status rick_image_host_channels(rick_plan *plan, int64_t n_rows, int32_t n_
                                      void *ws_dev, size_t ws_bytes, void *stage_dev,
                                      size_t stage_bytes, void *planes_dev, float *image_dev,
                                      uint32_t flags, rick_bin_stats *stats_dev, void *stream);
+
+/* rick_image_host_channels with n_corr correlations per visibility, folded as
+ * in rick_bin_rows (vis_host, weight_host [n_rows][n_chan][n_corr]).  A chunk
+ * holds at most max_vis values, i.e. max_vis / n_corr visibilities, so the
+ * staging area of rick_stream_bytes(params, max_vis, n_rows n_chan) serves it. */
+rick_status rick_image_host_rows(rick_plan *plan, int64_t n_rows, int32_t n_chan, int32_t n_corr,
+                                 const double *uvw_rows_host, const double *chan_scale_host,
+                                 const void *vis_host, const float *weight_host, void *ws_dev,
+                                 size_t ws_bytes, void *stage_dev, size_t stage_bytes,
+                                 void *planes_dev, float *image_dev, uint32_t flags,
+                                 rick_bin_stats *stats_dev, void *stream);
 
 #ifdef __cplusplus
 }

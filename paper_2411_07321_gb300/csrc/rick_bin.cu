@@ -235,6 +235,7 @@ struct KeyArgs {
     uint64_t key_lo, key_hi;  // rick_dkey(-0.5), rick_dkey(n + 0.5)
     int bulk;                 // uvw (and weight) 16-byte aligned: blocks stage them by bulk copy
     int n_chan;               // > 0: uvw holds rows of n_chan visibilities, scaled per channel
+    int n_corr;               // correlations per visibility (weights [n_vis][n_corr])
     const double *chan_scale;
     WsPtrs ws;
 };
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
             s_uvw[3 * i] = a.uvw[3 * r] * f;
             s_uvw[3 * i + 1] = a.uvw[3 * r + 1] * f;
             s_uvw[3 * i + 2] = a.uvw[3 * r + 2] * f;
-            if (a.weight) s_wt[i] = a.weight[blk0 + i];
+            if (a.weight && a.n_corr == 1) s_wt[i] = a.weight[blk0 + i];
         }
     } else if (!bulk) {
         for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
@@ -379,8 +380,14 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
                             (uint32_t)(ax >> a.log2T)) << 2) | cls;
                     a.ws.cell[i] = (uint32_t)ax | ((uint32_t)ay << 16);
                     a.ws.frac[i] = make_float2(fx, fy);
-                    float wt = a.weight ? s_wt[li] : 1.0f;
-                    ws = ff_add(ws, ff{wt, 0.0f});
+                    if (a.n_corr == 1) {
+                        float wt = a.weight ? s_wt[li] : 1.0f;
+                        ws = ff_add(ws, ff{wt, 0.0f});
+                    } else {  // the visibility's weight is the sum of its correlations'
+                        for (int c = 0; c < a.n_corr; ++c)
+                            ws = ff_add(ws, ff{a.weight ? a.weight[i * a.n_corr + c] : 1.0f,
+                                               0.0f});
+                    }
                 }
             }
             a.ws.key[i] = key;
@@ -429,6 +436,8 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
 }
 
 // Weight sum over the block partials in a fixed order; stats.
+// unit_weights > 0: no weights were given, and each kept visibility weighs
+// unit_weights (its number of correlations).
 __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const double *wpart,
                                                             int nparts, int unit_weights)
 {
@@ -447,7 +456,7 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
         hdr->stats.n_binned = binned;
         hdr->stats.n_dropped_uv = (long long)hdr->drop_uv;
         hdr->stats.n_dropped_w = (long long)hdr->drop_w;
-        hdr->stats.sum_weight = unit_weights ? (double)binned : s[0];
+        hdr->stats.sum_weight = unit_weights ? (double)binned * unit_weights : s[0];
     }
 }
 
@@ -460,8 +469,13 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
 // from the histogram counters: no atomics here.
 #define RICK_SCATTER_U 4
 
+//
+// With CORR, each visibility has n_corr correlations (vis and weight
+// [n_vis][n_corr]) and its record carries their weighted sum, sum_c w_c V_c.
+template <bool CORR>
 __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const float2 *vis,
-                                                          const float *weight, WsPtrs ws)
+                                                          const float *weight, WsPtrs ws,
+                                                          int n_corr)
 {
     constexpr int U = RICK_SCATTER_U;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * U;
@@ -477,8 +491,20 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
             if (idx[u] < n_vis) {
                 key[u] = ws.key[idx[u]];
                 rk[u] = ws.rank[idx[u]];
-                v[u] = vis[idx[u]];
-                wt[u] = weight ? weight[idx[u]] : 1.0f;
+                if (CORR) {
+                    float2 acc = make_float2(0.0f, 0.0f);
+                    for (int c = 0; c < n_corr; ++c) {
+                        const float2 vc = vis[idx[u] * n_corr + c];
+                        const float wc = weight ? weight[idx[u] * n_corr + c] : 1.0f;
+                        acc.x = __fmaf_rn(vc.x, wc, acc.x);
+                        acc.y = __fmaf_rn(vc.y, wc, acc.y);
+                    }
+                    v[u] = acc;
+                    wt[u] = 1.0f;
+                } else {
+                    v[u] = vis[idx[u]];
+                    wt[u] = weight ? weight[idx[u]] : 1.0f;
+                }
                 fr[u] = ws.frac[idx[u]];
                 cl[u] = ws.cell[idx[u]];
             }
@@ -591,9 +617,9 @@ static int64_t plan_max_rows(const rick_plan *plan, int32_t n_chan)
 rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, const void *vis,
                           const float *weight, void *ws_dev, size_t ws_bytes,
                           rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src,
-                          int n_chan, const double *chan_scale)
+                          int n_chan, const double *chan_scale, int n_corr)
 {
-    if (!plan || !ws_dev || n_vis < 0) return RICK_EINVAL;
+    if (!plan || !ws_dev || n_vis < 0 || n_corr < 1 || n_corr > RICK_MAX_CORR) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (n_vis > 0 && (!uvw || !vis)) return RICK_EINVAL;
     if (((uintptr_t)ws_dev & 255) || ((uintptr_t)uvw & 7) || ((uintptr_t)vis & 7) ||
@@ -642,8 +668,10 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
         ka.key_hi = rick_dkey((double)p.n + 0.5);
         ka.ws = w;
         ka.n_chan = n_chan;
+        ka.n_corr = n_corr;
         ka.chan_scale = chan_scale;
-        ka.bulk = n_chan == 0 && ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
+        ka.bulk = n_chan == 0 && n_corr == 1 && ((uintptr_t)uvw & 15) == 0 &&
+                  ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
         RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -651,7 +679,7 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
         bin_key_kernel<<<(unsigned)nkb, RICK_KEY_THREADS, smem, st>>>(ka);
         RICK_LAUNCH_CHECK(plan);
     }
-    bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL);
+    bin_finalize_kernel<<<1, 1024, 0, st>>>(w.hdr, w.wpart, (int)nkb, weight == NULL ? n_corr : 0);
     RICK_LAUNCH_CHECK(plan);
     RICK_CUDA_TRY(plan, scan_u32(w.hist, w.suboff, RICK_BIN_SUBS * L.nbins + 1, w.scan, st,
                                  &plan->launches));
@@ -661,7 +689,12 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     if (n_vis > 0) {
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
         if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
-        bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
+        if (n_corr == 1)
+            bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
+                                                                        weight, w, 1);
+        else
+            bin_scatter_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
+                                                                       weight, w, n_corr);
         RICK_LAUNCH_CHECK(plan);
     }
     uint32_t nt = (uint32_t)L.ntiles;
@@ -681,7 +714,7 @@ extern "C" rick_status rick_bin(rick_plan *plan, int64_t n_vis, const double *uv
                                 size_t ws_bytes, rick_bin_stats *stats_dev, void *stream)
 {
     return rick_bin_impl(plan, n_vis, uvw, vis, weight, ws_dev, ws_bytes, stats_dev, stream, NULL,
-                         0, NULL);
+                         0, NULL, 1);
 }
 
 extern "C" rick_status rick_bin_channels(rick_plan *plan, int64_t n_rows, int32_t n_chan,
@@ -693,7 +726,21 @@ extern "C" rick_status rick_bin_channels(rick_plan *plan, int64_t n_rows, int32_
     if (n_rows > 0 && !chan_scale) return RICK_EINVAL;
     if (n_rows > plan_max_rows(plan, n_chan)) return RICK_ERANGE;
     return rick_bin_impl(plan, n_rows * n_chan, uvw_rows, vis, weight, ws_dev, ws_bytes, stats_dev,
-                         stream, NULL, n_chan, chan_scale);
+                         stream, NULL, n_chan, chan_scale, 1);
+}
+
+extern "C" rick_status rick_bin_rows(rick_plan *plan, int64_t n_rows, int32_t n_chan,
+                                     int32_t n_corr, const double *uvw_rows,
+                                     const double *chan_scale, const void *vis,
+                                     const float *weight, void *ws_dev, size_t ws_bytes,
+                                     rick_bin_stats *stats_dev, void *stream)
+{
+    if (!plan || n_rows < 0 || n_chan < 1 || n_corr < 1 || n_corr > RICK_MAX_CORR)
+        return RICK_EINVAL;
+    if (n_rows > 0 && !chan_scale) return RICK_EINVAL;
+    if (n_rows > plan_max_rows(plan, n_chan)) return RICK_ERANGE;
+    return rick_bin_impl(plan, n_rows * n_chan, uvw_rows, vis, weight, ws_dev, ws_bytes, stats_dev,
+                         stream, NULL, n_chan, chan_scale, n_corr);
 }
 
 extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const float *weight,
@@ -831,6 +878,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         ka.key_hi = rick_dkey((double)p.n + 0.5);
         ka.ws = w;
         ka.n_chan = 0;
+        ka.n_corr = 1;
         ka.chan_scale = NULL;
         ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
@@ -850,7 +898,8 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     if (n_vis > 0) {
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
         if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
-        bin_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis, weight, w);
+        bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
+                                                                    weight, w, 1);
         RICK_LAUNCH_CHECK(plan);
     }
     uint32_t nt = (uint32_t)L.ntiles;

@@ -590,7 +590,7 @@ struct TileArgs {
 rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, const void *vis,
                           const float *weight, void *ws_dev, size_t ws_bytes,
                           rick_bin_stats *stats_dev, void *stream, const WsHeader *range_src,
-                          int n_chan, const double *chan_scale);
+                          int n_chan, const double *chan_scale, int n_corr);
 // Min/max keys of the finite w of visibilities [0, n) folded into hdr->wmin_key / wmax_key.
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
                         cudaStream_t st, int n_chan, const double *scale);

@@ -128,8 +128,11 @@ static rick_status stream_resources(rick_plan *plan)
     } while (0)
 
 // The streamed path over "units": visibilities (n_chan == 0) or rows of n_chan
-// visibilities whose uvw is the row's times a per-channel factor.
-static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
+// visibilities whose uvw is the row's times a per-channel factor, each
+// visibility with n_corr correlations (values and weights [unit][chan][corr]).
+// A chunk holds at most max_vis values, so with several correlations it holds
+// max_vis / n_corr visibilities: the staging buffers keep their size.
+static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan, int32_t n_corr,
                                const double *uvw_host, const double *scale_host,
                                const void *vis_host, const float *weight_host, void *ws_dev,
                                size_t ws_bytes, void *stage_dev, size_t stage_bytes,
@@ -140,6 +143,7 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (n_chan < 0 || n_chan > RICK_STREAM_MAX_CHAN) return n_chan < 0 ? RICK_EINVAL : RICK_ERANGE;
+    if (n_corr < 1 || n_corr > RICK_MAX_CORR || (n_corr > 1 && n_chan < 1)) return RICK_EINVAL;
     if (n_units > 0 && (!uvw_host || !vis_host || (n_chan > 0 && !scale_host)))
         return RICK_EINVAL;
     if (((uintptr_t)stage_dev & 255) || ((uintptr_t)ws_dev & 255) ||
@@ -148,8 +152,9 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         ((uintptr_t)weight_host & 3) || ((uintptr_t)scale_host & 7))
         return RICK_EINVAL;
     const int64_t per = n_chan > 0 ? n_chan : 1;  // visibilities per unit
+    const int64_t vals = per * n_corr;              // values (and weights) per unit
     const int64_t n_vis = n_units * per;
-    if (n_units > 0 && plan->max_vis < per) return RICK_ERANGE;
+    if (n_units > 0 && plan->max_vis < vals) return RICK_ERANGE;
     const StageLayout S = stage_layout(&plan->p, plan->max_vis, n_vis, stage_bytes);
     if (stage_bytes < S.bytes || (S.resident_uvw && S.uvw_buf < 24 * (size_t)n_units))
         return RICK_ERANGE;
@@ -161,7 +166,7 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
     WsHeader *rh = (WsHeader *)(sb + S.range);
     rick_bin_stats *tot = (rick_bin_stats *)(sb + S.total);
     WsHeader *hdr = rick_ws_ptrs(ws_dev, rick_ws_layout(&plan->p, plan->max_vis)).hdr;
-    const int64_t chunk = plan->max_vis / per;  // units per chunk (whole rows)
+    const int64_t chunk = plan->max_vis / vals;  // units per chunk (whole rows)
     const int64_t nchunks = n_units > 0 ? (n_units + chunk - 1) / chunk : 1;  // one empty chunk
     const float2 *vh = (const float2 *)vis_host;
 
@@ -223,12 +228,12 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
                 uvw_c = ub;
             }
             float2 *vb = (float2 *)(sb + S.vis + b * S.vis_buf);
-            RICK_CUDA_TRY(plan, cudaMemcpyAsync(vb, vh + off * per, 8 * nc * per,
+            RICK_CUDA_TRY(plan, cudaMemcpyAsync(vb, vh + off * vals, 8 * nc * vals,
                                                 cudaMemcpyHostToDevice, cp));
             vis_c = vb;
             if (weight_host) {
                 float *wb = (float *)(sb + S.weight + b * S.weight_buf);
-                RICK_CUDA_TRY(plan, cudaMemcpyAsync(wb, weight_host + off * per, 4 * nc * per,
+                RICK_CUDA_TRY(plan, cudaMemcpyAsync(wb, weight_host + off * vals, 4 * nc * vals,
                                                     cudaMemcpyHostToDevice, cp));
                 wt_c = wb;
             }
@@ -236,7 +241,7 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
             RICK_CUDA_TRY(plan, cudaStreamWaitEvent(st, plan->ev_ready[b], 0));
         }
         RICK_TRY(rick_bin_impl(plan, nc > 0 ? nc * per : 0, uvw_c, vis_c, wt_c, ws_dev, ws_bytes,
-                               NULL, st, S.resident_uvw ? rh : NULL, n_chan, scale_c));
+                               NULL, st, S.resident_uvw ? rh : NULL, n_chan, scale_c, n_corr));
         // the binning has read staging buffer b (the records are in ws now)
         RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_free[b], st));
         stats_add_kernel<<<1, 1, 0, st>>>(hdr, tot, c == 0);
@@ -258,7 +263,7 @@ extern "C" rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const dou
                                        size_t stage_bytes, void *planes_dev, float *image_dev,
                                        uint32_t flags, rick_bin_stats *stats_dev, void *stream)
 {
-    return stream_impl(plan, n_vis, 0, uvw_host, NULL, vis_host, weight_host, ws_dev, ws_bytes,
+    return stream_impl(plan, n_vis, 0, 1, uvw_host, NULL, vis_host, weight_host, ws_dev, ws_bytes,
                        stage_dev, stage_bytes, planes_dev, image_dev, flags, stats_dev, stream);
 }
 
@@ -272,7 +277,21 @@ extern "C" rick_status rick_image_host_channels(rick_plan *plan, int64_t n_rows,
                                                 rick_bin_stats *stats_dev, void *stream)
 {
     if (n_chan < 1) return RICK_EINVAL;
-    return stream_impl(plan, n_rows, n_chan, uvw_rows_host, chan_scale_host, vis_host, weight_host,
-                       ws_dev, ws_bytes, stage_dev, stage_bytes, planes_dev, image_dev, flags,
-                       stats_dev, stream);
+    return stream_impl(plan, n_rows, n_chan, 1, uvw_rows_host, chan_scale_host, vis_host,
+                       weight_host, ws_dev, ws_bytes, stage_dev, stage_bytes, planes_dev, image_dev,
+                       flags, stats_dev, stream);
+}
+
+extern "C" rick_status rick_image_host_rows(rick_plan *plan, int64_t n_rows, int32_t n_chan,
+                                            int32_t n_corr, const double *uvw_rows_host,
+                                            const double *chan_scale_host, const void *vis_host,
+                                            const float *weight_host, void *ws_dev,
+                                            size_t ws_bytes, void *stage_dev, size_t stage_bytes,
+                                            void *planes_dev, float *image_dev, uint32_t flags,
+                                            rick_bin_stats *stats_dev, void *stream)
+{
+    if (n_chan < 1) return RICK_EINVAL;
+    return stream_impl(plan, n_rows, n_chan, n_corr, uvw_rows_host, chan_scale_host, vis_host,
+                       weight_host, ws_dev, ws_bytes, stage_dev, stage_bytes, planes_dev, image_dev,
+                       flags, stats_dev, stream);
 }

@@ -84,18 +84,21 @@ class Imager:
         self.n_vis = n
 
     def bin_channels(self, uvw_rows: torch.Tensor, chan_scale: torch.Tensor, vis: torch.Tensor,
-                     weight: torch.Tensor | None = None):
+                     weight: torch.Tensor | None = None, n_corr: int = 1):
         """Binning of rows of n_chan channels: uvw once per row, times a factor per
-        channel (vis and weight hold n_rows * n_chan values, channel fastest)."""
+        channel (vis and weight hold n_rows * n_chan * n_corr values, correlation
+        fastest, then channel).  With n_corr > 1 each (row, channel) is gridded
+        as the weighted sum of its correlations (rick_bin_rows)."""
         n_rows, n_chan = uvw_rows.shape[0], chan_scale.shape[0]
+        nv = n_rows * n_chan * n_corr
         self._check(uvw_rows, torch.float64, (n_rows, 3), "uvw_rows")
         self._check(chan_scale, torch.float64, (n_chan,), "chan_scale")
-        self._check(vis.reshape(-1), torch.complex64, (n_rows * n_chan,), "vis")
+        self._check(vis.reshape(-1), torch.complex64, (nv,), "vis")
         if weight is not None:
-            self._check(weight.reshape(-1), torch.float32, (n_rows * n_chan,), "weight")
-        R.rick_bin_channels(self.plan, n_rows, n_chan, uvw_rows.data_ptr(), chan_scale.data_ptr(),
-                            vis.data_ptr(), _ptr(weight), self.ws.data_ptr(), self.ws_bytes,
-                            self.stats_buf.data_ptr(), self._stream())
+            self._check(weight.reshape(-1), torch.float32, (nv,), "weight")
+        R.rick_bin_rows(self.plan, n_rows, n_chan, n_corr, uvw_rows.data_ptr(),
+                        chan_scale.data_ptr(), vis.data_ptr(), _ptr(weight), self.ws.data_ptr(),
+                        self.ws_bytes, self.stats_buf.data_ptr(), self._stream())
         self.n_vis = n_rows * n_chan
 
     def bin_values(self, vis: torch.Tensor, weight: torch.Tensor | None = None):
@@ -212,13 +215,15 @@ class Imager:
     def image_streamed(self, uvw_host: torch.Tensor, vis_host: torch.Tensor,
                        weight_host: torch.Tensor | None, out_host: torch.Tensor | None = None,
                        flags: int = IMAGE_FLAGS,
-                       chan_scale: torch.Tensor | None = None) -> torch.Tensor:
+                       chan_scale: torch.Tensor | None = None, n_corr: int = 1) -> torch.Tensor:
         """The image of a visibility set in host memory, of any size, streamed
         through the GPU in chunks of this imager's ``max_vis`` (copies of the
         next chunk overlap binning and gridding of the current one; pinned
         host tensors give the overlap).  With ``chan_scale`` (float64
         [n_chan]) the input is multi-channel: ``uvw_host`` holds one row per
-        n_chan visibilities, scaled per channel.  Returns the device image,
+        n_chan visibilities, scaled per channel, and each visibility may carry
+        ``n_corr`` correlations (vis and weight [rows][chan][corr], folded into
+        one record as in ``bin_channels``).  Returns the device image,
         ordered on the current stream.  If ``out_host`` is given the image is
         also copied there on this imager's copy-out stream, so that the copy
         overlaps the next call's work: synchronise the device (or call
@@ -226,12 +231,15 @@ class Imager:
         two device image buffers."""
         n_units = uvw_host.shape[0]
         n_chan = 0 if chan_scale is None else chan_scale.shape[0]
+        if n_corr != 1 and not n_chan:
+            raise ValueError("correlations need the row form (chan_scale)")
         n = n_units * max(n_chan, 1)
+        nv = n * n_corr
         vis_host = vis_host.reshape(-1)
         weight_host = None if weight_host is None else weight_host.reshape(-1)
         for t, dt, shape, name in ((uvw_host, torch.float64, (n_units, 3), "uvw"),
-                                   (vis_host, torch.complex64, (n,), "vis"),
-                                   (weight_host, torch.float32, (n,), "weight"),
+                                   (vis_host, torch.complex64, (nv,), "vis"),
+                                   (weight_host, torch.float32, (nv,), "weight"),
                                    (chan_scale, torch.float64, (n_chan,), "chan_scale")):
             if t is None:
                 continue
@@ -257,13 +265,13 @@ class Imager:
                                             device=self.device)
         img = self._out_imgs[i]
         if n_chan:
-            R.rick_image_host_channels(self.plan, n_units, n_chan, uvw_host.data_ptr(),
-                                       chan_scale.data_ptr(), vis_host.data_ptr(),
-                                       _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
-                                       self._stage.data_ptr(), self._stage.numel(),
-                                       self.planes.data_ptr(), img.data_ptr(), flags,
-                                       self.stats_buf.data_ptr(), self._stream())
-            rows = max(self.max_vis // n_chan, 1)
+            R.rick_image_host_rows(self.plan, n_units, n_chan, n_corr, uvw_host.data_ptr(),
+                                   chan_scale.data_ptr(), vis_host.data_ptr(),
+                                   _ptr(weight_host), self.ws.data_ptr(), self.ws_bytes,
+                                   self._stage.data_ptr(), self._stage.numel(),
+                                   self.planes.data_ptr(), img.data_ptr(), flags,
+                                   self.stats_buf.data_ptr(), self._stream())
+            rows = max(self.max_vis // (n_chan * n_corr), 1)
             last = n_units - (n_units - 1) // rows * rows if n_units else 0
             self.n_vis = last * n_chan  # the last chunk
         else:

@@ -22,6 +22,7 @@ RICK_KERNEL_GAUSS, RICK_KERNEL_KB = 0, 1
 RICK_PREC_FP32, RICK_PREC_FP32_COMPENSATED = 0, 1
 RICK_N_CORRECT, RICK_NORMALIZE, RICK_N_DIVIDE, RICK_PHASE_FP32 = 1, 2, 4, 8
 RICK_WEIGHT_UNIFORM, RICK_WEIGHT_BRIGGS = 1, 2
+RICK_MAX_CORR = 4
 
 
 class RickError(RuntimeError):
@@ -58,7 +59,8 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_bin_noalloc", "rick_bin_values", "rick_grid", "rick_grid_accumulate",
            "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
            "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
-           "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights"]
+           "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
+           "rick_bin_rows", "rick_image_host_rows"]
 
 
 def _load():
@@ -92,6 +94,9 @@ def _load():
         "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
         "rick_image_host": [vp, i64, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32, vp, vp],
         "rick_bin_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, vp],
+        "rick_bin_rows": [vp, i64, i32, i32, vp, vp, vp, vp, vp, sz, vp, vp],
+        "rick_image_host_rows": [vp, i64, i32, i32, vp, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32,
+                                 vp, vp],
         "rick_density_scratch_bytes": [P, ctypes.POINTER(sz)],
         "rick_density_weights": [vp, i64, vp, vp, i32, ctypes.c_double, vp, sz, vp, vp],
         "rick_image_host_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32,
@@ -213,6 +218,24 @@ def rick_image_host_channels(plan, n_rows, n_chan, uvw_rows_host, chan_scale_hos
     """Streamed imaging of multi-channel rows held in host memory."""
     _check("rick_image_host_channels", _L.rick_image_host_channels(
         plan, int(n_rows), int(n_chan), uvw_rows_host, chan_scale_host, vis_host,
+        weight_host or None, ws, int(ws_bytes), stage, int(stage_bytes), planes, image, int(flags),
+        stats or None, stream or None))
+
+
+def rick_bin_rows(plan, n_rows, n_chan, n_corr, uvw_rows, chan_scale, vis, weight, ws, ws_bytes,
+                  stats, stream) -> None:
+    """rick_bin_channels with n_corr correlations per visibility, folded into one record."""
+    _check("rick_bin_rows", _L.rick_bin_rows(plan, int(n_rows), int(n_chan), int(n_corr), uvw_rows,
+                                             chan_scale, vis, weight or None, ws, int(ws_bytes),
+                                             stats or None, stream or None))
+
+
+def rick_image_host_rows(plan, n_rows, n_chan, n_corr, uvw_rows_host, chan_scale_host, vis_host,
+                         weight_host, ws, ws_bytes, stage, stage_bytes, planes, image, flags,
+                         stats, stream) -> None:
+    """Streamed imaging of rows of channels with n_corr correlations, in host memory."""
+    _check("rick_image_host_rows", _L.rick_image_host_rows(
+        plan, int(n_rows), int(n_chan), int(n_corr), uvw_rows_host, chan_scale_host, vis_host,
         weight_host or None, ws, int(ws_bytes), stage, int(stage_bytes), planes, image, int(flags),
         stats or None, stream or None))
 

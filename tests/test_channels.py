@@ -6,7 +6,11 @@ for bit (bin offsets, stats, and every bin's records matched through their
 input index); the streamed multi-channel image (rick_image_host_channels) must
 be the FP64 oracle's image of the expanded set within 1e-5 of peak on the
 tapered image and the inner region, for a range from the data, a given range,
-ragged chunks of whole rows and pageable host memory.
+ragged chunks of whole rows and pageable host memory.  With several
+correlations per visibility (rick_bin_rows, rick_image_host_rows) each (row,
+channel) is gridded once as the weighted sum of its correlations: the image
+must be the oracle's image of the set with every correlation as its own
+visibility, and the weight sum that set's, correctly rounded to 1e-13.
 """
 import math
 
@@ -105,5 +109,76 @@ def test_streamed_channel_image_matches_oracle(P, chunk, w_range, pinned):
     got = im.stats()
     assert got["n_binned"] == st["n_binned"]
     assert got["n_dropped_w"] == st["n_dropped_w"]
+    assert got["sum_weight"] == pytest.approx(st["sum_weight"], rel=1e-12)
+    im.close()
+
+
+def corr_data(n_rows, n_corr, seed_shift=5, flag_frac=0.05):
+    """Rows of 16 channels whose visibilities carry n_corr correlations: the
+    generator's visibility plus independent noise per correlation, weights in
+    [0.5, 1.5) per correlation with a few correlations flagged (weight 0)."""
+    obs, d = rows_data(n_rows, seed_shift)
+    n = len(d["vis"])
+    r = np.random.default_rng(7)
+    noise = 0.05 * (r.normal(size=(n, n_corr)) + 1j * r.normal(size=(n, n_corr)))
+    vis = (d["vis"][:, None] + noise).astype(np.complex64)
+    wt = (0.5 + r.random((n, n_corr))).astype(np.float32)
+    wt[r.random((n, n_corr)) < flag_frac] = 0.0
+    return d, vis, wt
+
+
+def expanded(d, vis, wt):
+    """The set with every correlation as its own visibility at the same uvw."""
+    n_corr = vis.shape[1]
+    return np.repeat(d["uvw"], n_corr, axis=0), vis.reshape(-1), wt.reshape(-1)
+
+
+@pytest.mark.parametrize("n_corr,weighted", [(2, True), (4, True), (2, False)])
+def test_correlations_fold_into_one_record(P, n_corr, weighted):
+    d, vis, wt = corr_data(1500, n_corr)
+    n, n_w, W = 512, 8, 7
+    fov = (n / 2 - W - 1) / 12000.0
+    dev = torch.device("cuda:0")
+    im = P.Imager(n, n_w, fov, kernel="kb", support=W, tile=32, max_vis=len(d["vis"]), device=dev)
+    t = {k: torch.from_numpy(d[k]).to(dev) for k in ("uvw_rows", "chan_scale")}
+    tv = torch.from_numpy(vis).to(dev)
+    tw = torch.from_numpy(wt).to(dev) if weighted else None
+    im.bin_channels(t["uvw_rows"], t["chan_scale"], tv, tw, n_corr=n_corr)
+    img = im.image_from_binned().cpu().numpy()
+    got = im.stats()
+    uvw_x, vis_x, wt_x = expanded(d, vis, wt if weighted else np.ones_like(wt))
+    op = oracle.Params(n=n, n_w=n_w, fov=fov, kernel=oracle.KB, support=W, tile=32)
+    ref, st = oracle.image(op, uvw_x, vis_x, wt_x)
+    tap, inner = taper_errors(img, ref, op)
+    print(f"correlations {n_corr} weighted={weighted}: tapered {tap:.2e} inner {inner:.2e}")
+    assert tap <= TOL and inner <= TOL
+    assert got["n_binned"] * n_corr == st["n_binned"]
+    kept = np.repeat(oracle.coords(op, d["uvw"])["status"] == 0, n_corr)
+    exact = math.fsum(wt_x[kept].astype(np.float64))
+    assert got["sum_weight"] == pytest.approx(exact, rel=1e-13)
+    with pytest.raises(P.rick.RickError):
+        im.bin_channels(t["uvw_rows"], t["chan_scale"], tv, tw, n_corr=P.rick.RICK_MAX_CORR + 1)
+    im.close()
+
+
+def test_streamed_correlations(P):
+    n_corr = 2
+    d, vis, wt = corr_data(2500, n_corr, seed_shift=9)
+    n, n_w, W = 512, 8, 7
+    fov = (n / 2 - W - 1) / 12000.0
+    im = P.Imager(n, n_w, fov, kernel="kb", support=W, tile=32, max_vis=16 * 600,
+                  device=torch.device("cuda:0"))  # 300 rows per chunk, ragged last chunk
+    h = {k: torch.from_numpy(d[k]).pin_memory() for k in ("uvw_rows", "chan_scale")}
+    hv = torch.from_numpy(vis).pin_memory()
+    hw = torch.from_numpy(wt).pin_memory()
+    img = im.image_streamed(h["uvw_rows"], hv, hw, chan_scale=h["chan_scale"], n_corr=n_corr)
+    torch.cuda.synchronize()
+    op = oracle.Params(n=n, n_w=n_w, fov=fov, kernel=oracle.KB, support=W, tile=32)
+    ref, st = oracle.image(op, *expanded(d, vis, wt))
+    tap, inner = taper_errors(img.cpu().numpy(), ref, op)
+    print(f"streamed correlations: tapered {tap:.2e} inner {inner:.2e}")
+    assert tap <= TOL and inner <= TOL
+    got = im.stats()
+    assert got["n_binned"] * n_corr == st["n_binned"]
     assert got["sum_weight"] == pytest.approx(st["sum_weight"], rel=1e-12)
     im.close()
