@@ -156,8 +156,10 @@ def test_correlations_fold_into_one_record(P, n_corr, weighted):
     kept = np.repeat(oracle.coords(op, d["uvw"])["status"] == 0, n_corr)
     exact = math.fsum(wt_x[kept].astype(np.float64))
     assert got["sum_weight"] == pytest.approx(exact, rel=1e-13)
-    with pytest.raises(P.rick.RickError):
-        im.bin_channels(t["uvw_rows"], t["chan_scale"], tv, tw, n_corr=P.rick.RICK_MAX_CORR + 1)
+    with pytest.raises(P.rick.RickError):  # checked on the host before any launch
+        P.rick.rick_bin_rows(im.plan, 1500, 16, P.rick.RICK_MAX_CORR + 1,
+                             t["uvw_rows"].data_ptr(), t["chan_scale"].data_ptr(), tv.data_ptr(),
+                             None, im.ws.data_ptr(), im.ws_bytes, None, None)
     im.close()
 
 
