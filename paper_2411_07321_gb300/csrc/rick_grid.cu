@@ -230,9 +230,12 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     __syncthreads();
 
     // plain: one round over the chunk; compensated: rounds of 4096 records,
-    // each folded into the (sum, compensation) pair of every cell.  Each round
-    // is split into one contiguous run per record stream, and each run into
-    // its pieces of the four ranges.
+    // each folded into the (sum, compensation) pair of every cell.  The
+    // round's piece of each of the four ranges is split evenly into one
+    // contiguous run per record stream, so the streams of a warp always walk
+    // the same range with runs of equal length (a split of the whole round
+    // would let a warp's streams straddle a range boundary, and the warp then
+    // walks both ranges one after the other).
     constexpr int NG = StreamShape<W>::NG;
     const int lane = threadIdx.x & 31;
     const bool streaming = lane < StreamShape<W>::LIVE;
@@ -241,16 +244,18 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     const uint32_t round = COMP ? 4096u : max(vend - vbeg, 1u);
     for (uint32_t rb = vbeg; rb < vend; rb += round) {
         const uint32_t re = min(vend, rb + round);
-        const uint32_t per = (re - rb + nstreams - 1) / nstreams;
-        uint32_t v0 = min(rb + stream * per, re), v1 = min(v0 + per, re);
         uint32_t base = 0;
 #pragma unroll 1
         for (int g = 0; g < 4; ++g) {
             const uint32_t lg = s_rl[g];
-            uint32_t a0 = max(v0, base), a1 = min(v1, base + lg);
-            if (streaming && a0 < a1)
-                grid_stream<W>(ta, s_rs[g] + (a0 - base), a1 - a0, x0, y0, acc_re, acc_im, T, TP,
-                               coef2);
+            const uint32_t a0 = max(rb, base), a1 = min(re, base + lg);
+            if (a0 < a1) {
+                const uint32_t per = (a1 - a0 + nstreams - 1) / nstreams;
+                const uint32_t v0 = min(a0 + stream * per, a1), v1 = min(v0 + per, a1);
+                if (streaming && v0 < v1)
+                    grid_stream<W>(ta, s_rs[g] + (v0 - base), v1 - v0, x0, y0, acc_re, acc_im, T,
+                                   TP, coef2);
+            }
             base += lg;
         }
         if (COMP) {
