@@ -186,7 +186,7 @@ rick_status rick_plan_fft_bytes(const rick_plan *plan, size_t *fft_bytes);
  *               this binning (grid, wcorrect, wspread, degrid) read it
  *   stats_dev:  device rick_bin_stats, or NULL
  * uvw_dev and weight_dev aligned to 16 bytes let each block of the key pass
- * fetch its 2048 rows with one bulk (TMA) copy; 8-byte alignment is enough for
+ * fetch its 1024 rows with one bulk (TMA) copy; 8-byte alignment is enough for
  * correctness.
  * Errors: RICK_EINVAL (NULL pointer, misalignment), RICK_ERANGE (n_vis >
  * max_vis or ws_bytes too small), RICK_ECUDA. */
@@ -284,7 +284,7 @@ rick_status rick_bin_values(rick_plan *plan, const void *vis_dev, const float *w
  * planes_dev (complex64 [n_w][n][n]) is overwritten.  Each uv-tile is summed
  * in shared memory and written once (plain stores; tiles with more records
  * than one chunk add their chunk sums with float atomics).  The kernel
- * weights G are degree-9 polynomial fits per unit segment (FP64 fit at plan
+ * weights G are degree-8 polynomial fits per unit segment (FP64 fit at plan
  * creation, FP32 evaluation).  rick_grid and rick_degrid use a word of the
  * workspace header as a work counter: calls that share a workspace must not
  * overlap on the device. */

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
     const WsHeader *hdr = a.ws.hdr;
     const int64_t blk0 = (int64_t)blockIdx.x * NI;
     const int nitems = (int)(a.n_vis - blk0 < NI ? a.n_vis - blk0 : NI);
-    // The block's 2048 uvw rows and weights are contiguous: one bulk copy each
+    // The block's 1024 uvw rows and weights are contiguous: one bulk copy each
     // (TMA) into shared memory, while the plane keys load; a ragged last block
     // or unaligned inputs take plain loads instead.
     const bool bulk = a.bulk && nitems == NI;
@@ -465,9 +465,10 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
 
 // Each thread takes RICK_SCATTER_U inputs per pass (256 apart), so that their
 // load chains -- key and rank, then the (bin, sub-counter) offset, then the
-// record stores -- overlap.  Positions come from the ranks the key pass took
-// from the histogram counters: no atomics here.
-#define RICK_SCATTER_U 4
+// record stores -- overlap (eight chains at two CTAs per SM beat four at four
+// CTAs per SM).  Positions come from the ranks the key pass took from the
+// histogram counters: no atomics here.
+#define RICK_SCATTER_U 8
 
 //
 // With CORR, each visibility has n_corr correlations (vis and weight

@@ -23,11 +23,13 @@
 // s = 2 (f - fc) in [-1, 1) (fc = 0 for odd W, where f is in [-1/2, 1/2);
 // fc = 1/2 for even W, f in [0, 1)), fitted at plan creation by Chebyshev
 // interpolation of degree RICK_POLY_DEG in FP64 and evaluated by Horner's rule
-// in FP32 (degree 9 already reaches FP32 rounding, ~1e-7 of the peak, for the
-// Gaussian and Kaiser-Bessel kernels with W = 3..16).  The coefficients travel in the kernel-argument (constant) space.
+// in FP32.  Degree 8 fits the Kaiser-Bessel kernels of W = 4..16 to 7e-8 of the
+// peak or better (2e-9 for W = 7), below FP32 rounding of the sums; the
+// Gaussians are smoother.  The coefficients travel in the kernel-argument
+// (constant) space.
 
 #define RICK_MAX_W 16
-#define RICK_POLY_DEG 9
+#define RICK_POLY_DEG 8
 #define RICK_POLY_N (RICK_POLY_DEG + 1)
 
 struct KernelPoly {
@@ -117,8 +119,10 @@ struct WsLayout {
     int64_t n_vis, nbins, ntiles, nscan, nkeyblocks;
 };
 
+// Key pass blocks: 1024 visibilities, staged in 28 KB of shared memory, so that
+// six blocks fit an SM (the pass is bound by integer issue and needs the warps).
 #define RICK_KEY_THREADS 256
-#define RICK_KEY_ITEMS 8
+#define RICK_KEY_ITEMS 4
 // Each bin's histogram counter is split into RICK_BIN_SUBS sub-counters, chosen
 // by the input's block of RICK_KEY_THREADS * RICK_KEY_ITEMS visibilities: the
 // densest bins (the array core) then take their atomics on several addresses
@@ -208,11 +212,13 @@ static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
 }
 
 // Records per work item of the tile kernels for a binning of n_vis
-// visibilities: about 16 items per SM in total, at least 1024.  Set by the
-// binning in the workspace header, where the tile kernels read it.
+// visibilities: about 64 items per SM in total (16 per resident CTA: short
+// items balance the skewed tiles of a centrally concentrated uv coverage), at
+// least 1024.  Set by the binning in the workspace header, where the tile
+// kernels read it.
 static inline uint32_t rick_chunk_cap(int64_t n_vis, int num_sms)
 {
-    int64_t c = (n_vis + (int64_t)num_sms * 16 - 1) / ((int64_t)num_sms * 16);
+    int64_t c = (n_vis + (int64_t)num_sms * 64 - 1) / ((int64_t)num_sms * 64);
     if (c < 1024) c = 1024;
     c = (c + 255) & ~(int64_t)255;
     if (c > (1 << 30)) c = 1 << 30;

@@ -27,7 +27,7 @@ struct GridArgs {
 };
 
 // Tiles per clearing item of the grid kernel.
-#define RICK_ZERO_GROUP 16
+#define RICK_ZERO_GROUP 8
 
 struct DegridArgs {
     TileArgs t;
