@@ -14,7 +14,9 @@
 // instructions, which GB300 issues at a small fraction of the FP32 rate.
 //
 // On a padded grid only the kept m x m crop is corrected (m^2 n_w plane reads
-// instead of n^2 n_w); the adjoint writes zeros outside the crop.
+// instead of n^2 n_w); the adjoint writes zeros outside the crop.  Where the
+// crop offset is even, a thread corrects two adjacent pixels (16-byte plane
+// loads: 0.36 instead of 0.41 ms for 16 planes of 4096^2).
 #include "rick_common.cuh"
 
 struct WcArgs {
@@ -130,6 +132,43 @@ __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
     a.image_out[oidx] = acc * g.scale;
 }
 
+// The same for two adjacent pixels per thread: one 16-byte load per plane
+// brings both pixels' values.  Needs an even crop offset (16-byte aligned
+// pairs) and an 8-byte aligned image.
+__global__ void __launch_bounds__(256) wcorrect2_kernel(WcArgs a)
+{
+    extern __shared__ float4 s_w[];
+    __shared__ float s_inv_sumw;
+    for (int k = threadIdx.x; k <= a.n_w; k += blockDim.x) s_w[k] = a.wplane[k];
+    if (threadIdx.x == 0) {
+        double sw = a.hdr->stats.sum_weight;  // nothing gridded: no normalisation
+        s_inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
+    }
+    __syncthreads();
+    const size_t half_nn = (size_t)a.n * a.n / 2;  // planes in float4 units
+    const int mh = a.m >> 1;
+    const size_t pidx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // pixel pair
+    if (pidx >= (size_t)mh * a.m) return;
+    const int pp = (int)(pidx % mh) * 2, qq = (int)(pidx / mh);  // in the image
+    const int p = pp + a.off, q = qq + a.off;                      // in the grid frame
+    PixelGeom g0 = pixel_geom(a, p, q, s_inv_sumw), g1 = pixel_geom(a, p + 1, q, s_inv_sumw);
+    float acc0 = 0.0f, acc1 = 0.0f;
+    const float4 *src = (const float4 *)(a.planes_in + ((size_t)q * a.n + p));
+    PhaseWalker ph0, ph1;
+    ph0.start(a, s_w, a.n_w, g0);
+    ph1.start(a, s_w, a.n_w, g1);
+#pragma unroll 4
+    for (int k = 0; k < a.n_w; ++k) {
+        const float4 F = src[(size_t)k * half_nn];
+        ph0.at(a, s_w, k, g0);
+        ph1.at(a, s_w, k, g1);
+        acc0 = fmaf(F.x, ph0.c, fmaf(-F.y, ph0.s, acc0));
+        acc1 = fmaf(F.z, ph1.c, fmaf(-F.w, ph1.s, acc1));
+    }
+    *(float2 *)(a.image_out + ((size_t)qq * a.m + pp)) =
+        make_float2(acc0 * g0.scale, acc1 * g1.scale);
+}
+
 __global__ void __launch_bounds__(256) wspread_kernel(WcArgs a)
 {
     extern __shared__ float4 s_w[];
@@ -202,8 +241,12 @@ extern "C" rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_d
     a.planes_in = (const float2 *)planes_dev;
     a.image_out = image_dev;
     size_t mm = (size_t)a.m * a.m;
-    wcorrect_kernel<<<(unsigned)((mm + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
-                      (cudaStream_t)stream>>>(a);
+    if ((a.off & 1) == 0 && ((uintptr_t)planes_dev & 15) == 0 && ((uintptr_t)image_dev & 7) == 0)
+        wcorrect2_kernel<<<(unsigned)((mm / 2 + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
+                           (cudaStream_t)stream>>>(a);
+    else
+        wcorrect_kernel<<<(unsigned)((mm + 255) / 256), 256, sizeof(float4) * (a.n_w + 1),
+                          (cudaStream_t)stream>>>(a);
     RICK_LAUNCH_CHECK(plan);
     return RICK_OK;
 }
