@@ -92,18 +92,28 @@ class Clocks:
                 "samples": len(use), "samples_in_window": len(inside)}
 
 
-def algorithmic_bytes(n_vis: int, n_binned: int, n: int, n_w: int) -> dict:
+def algorithmic_bytes(n_vis: int, n_binned: int, n: int, n_w: int, tile: int,
+                      tiles: int, tile_rows: int) -> dict:
+    """Bytes each stage must move at least.  tiles / tile_rows: the (plane,
+    uv-tile) and (plane, tile-row) pairs that records reach -- the only parts
+    of the planes the sparse grid and the fused transform touch."""
     planes = n_w * n * n * 8
+    cells = tiles * tile * tile * 8
     return {
         # read uvw f64x3, vis c64, weight f32; write records (value c64, offsets 2xf32,
         # cell u32) and the permutation u32
         "bin": n_vis * (24 + 8 + 4) + n_binned * (8 + 8 + 4 + 4),
-        # read each record once, write every plane cell once
-        "grid": n_binned * (8 + 8 + 4) + planes,
-        # one read and one write of the planes
-        "fft": 2 * planes,
-        # read every plane once, write the image
+        # read each record once, write the cells of the tiles records reach
+        "grid": n_binned * (8 + 8 + 4) + cells,
+        # read those cells, write and read back the transposed row transforms of
+        # the tile-rows they lie in, write the image
+        "fft_wcorrect": cells + 2 * tile_rows * tile * n * 8 + n * n * 4,
+        # the unfused stages, for comparison: the cuFFT transform (one read and
+        # one write of the planes at least) and the plane sum (read every plane,
+        # write the image); their grid step writes every plane cell
+        "cufft": 2 * planes,
         "wcorrect": planes + n * n * 4,
+        "grid_clear": n_binned * (8 + 8 + 4) + planes,
     }
 
 
@@ -236,22 +246,30 @@ def run_ours(args, wl):
         im.bin(uvw, vis, wt)
         if ev is not None:
             ev[1].record()
-        im.grid()
+        im.grid_sparse()
         if ev is not None:
             ev[2].record()
-        im.fft(+1)
+        im.fft_wcorrect(out=img)
         if ev is not None:
             ev[3].record()
+
+    def step_unfused(ev):
+        ev[0].record()
+        im.bin(uvw, vis, wt)
+        ev[1].record()
+        im.grid()
+        ev[2].record()
+        im.fft(+1)
+        ev[3].record()
         im.wcorrect(out=img)
-        if ev is not None:
-            ev[4].record()
+        ev[4].record()
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     st = im.stats()
     n_binned = st["n_binned"]
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(local)
     clocks.start()
@@ -276,8 +294,18 @@ def run_ours(args, wl):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     stage_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
-                for i, name in enumerate(["bin", "grid", "fft", "wcorrect"])}
+                for i, name in enumerate(["bin", "grid", "fft_wcorrect"])}
     value = n_vis * args.steps * world / (ms / 1e3)
+    tiles, tile_rows = im.fused_tiles()
+    # the unfused stages (grid clearing every tile, cuFFT in place, plane sum),
+    # timed after the headline steps, for comparison
+    uevs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            for _ in range(max(3, args.steps // 2))]
+    for e in uevs:
+        step_unfused(e)
+    torch.cuda.synchronize()
+    unfused_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in uevs[1:])
+                  for i, name in enumerate(["bin", "grid_clear", "cufft", "wcorrect"])}
 
     # end to end through the host-buffer calls (pinned host in, image back to
     # host): the streamed path (chunks of args.chunk visibilities, copies
@@ -339,16 +367,19 @@ def run_ours(args, wl):
     e2e_value = n_vis * args.steps * world / (e2e_ms / 1e3)
 
     peak, peak_kind = peaks()
-    alg = algorithmic_bytes(n_vis, n_binned, wl.n, wl.n_w)
-    gbps = {k: alg[k] / (stage_ms[k] * 1e-3) / 1e9 for k in alg}
-    own = ["bin", "grid", "wcorrect"]
-    dom = max(own, key=lambda k: stage_ms[k])
+    alg = algorithmic_bytes(n_vis, n_binned, wl.n, wl.n_w, wl.tile, tiles, tile_rows)
+    gbps = {k: alg[k] / (stage_ms[k] * 1e-3) / 1e9 for k in stage_ms}
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
     kernel_name = {"bin": "rick_bin (all binning kernels)", "grid": "grid_kernel",
-                   "wcorrect": "wcorrect_kernel"}[dom]
+                   "fft_wcorrect": "fft_rows_kernel + fft_cols_kernel"}[dom]
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": gbps[dom], "peak": peak,
                 "unit": "GB/s", "frac": gbps[dom] / peak,
                 "traffic": traffic_of(dom, n_vis), "algorithmic_bytes": alg[dom],
                 "peak_source": f"{peak_kind} (HBM copy bandwidth)"}
+    unfused = {"ms": unfused_ms, "ms_per_step": sum(unfused_ms.values()),
+               "gbps": {k: alg[k] / (unfused_ms[k] * 1e-3) / 1e9 for k in unfused_ms},
+               "calls": "rick_bin, rick_grid (clears record-free tiles), rick_fft_wplanes "
+                        "(cuFFT in place), rick_wcorrect_stack"}
 
     if rank != 0:
         im.close()
@@ -375,7 +406,10 @@ def run_ours(args, wl):
                 "resident_call_ms_per_step": e2e_resident_ms / args.steps},
         "roofline": roofline,
         "stages": {"ms": stage_ms, "gbps": gbps, "algorithmic_bytes": alg,
-                   "n_binned": n_binned},
+                   "n_binned": n_binned, "tiles_with_records": tiles,
+                   "tile_rows_with_records": tile_rows,
+                   "calls": "rick_bin, rick_grid_sparse, rick_fft_wcorrect (sparse)"},
+        "unfused": unfused,
         "weighting": {"scheme": "briggs, robust 0", "ms_per_image": weighting_ms / args.steps,
                       "passes": "rick_density_weights + rick_bin_values, after a binning"},
         "cpu_baseline": cpu,

@@ -318,6 +318,41 @@ rick_status rick_fft_wplanes(rick_plan *plan, void *planes_dev, int32_t directio
 rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_dev, const void *ws_dev,
                                 float *image_dev, uint32_t flags, void *stream);
 
+/* rick_grid that writes only the uv-tiles that records reach (the tiles with
+ * gridding work items in ws_dev); every other tile of planes_dev keeps what it
+ * held.  For rick_fft_wcorrect with sparse = 1 and the same ws_dev, which reads
+ * exactly those tiles: the planes then need no clearing, which on sparse uv
+ * coverage is most of the 8 n_w n^2 bytes rick_grid writes. */
+rick_status rick_grid_sparse(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream);
+
+/* Bytes of the work buffer of rick_fft_wcorrect for this plan.  Its layout,
+ * each piece starting on a 256-byte boundary: uint8 tile flags [n_w][nt][nt]
+ * (nt = n / tile; 1: the tile was read), uint8 tile-row flags [n_w][nt],
+ * uint8 plane flags [n_w], then the row transforms, complex64
+ * [n_w][image_n][n] (8 n_w image_n n bytes; image_n = n without a crop).  RICK_EINVAL if n is outside 256 ... 8192, the sizes the
+ * fused transform covers (use rick_fft_wplanes + rick_wcorrect_stack there). */
+rick_status rick_fft_wcorrect_bytes(const rick_plan *plan, size_t *work_bytes);
+
+/* The inverse FFT of every plane (§2 step 3) fused with the w-correction and
+ * plane sum (§2 step 4, Eq. 2): the same image as rick_fft_wplanes(+1)
+ * followed by rick_wcorrect_stack with the same flags, up to FP32 rounding
+ * order, without transforming the planes in place (planes_dev is only read).
+ * Two passes of 1D transforms: along u for the rows of tile-rows that hold
+ * records, stored transposed in work_dev; then along v for each image column,
+ * summing the planes into the image (the w-phase of each block of 8 planes
+ * by Horner's rule from the block's exact first-plane phase).
+ *   sparse = 1: only the tiles with gridding work items in ws_dev are read;
+ *               all other tiles are taken as zero (planes_dev from rick_grid
+ *               or rick_grid_sparse with this ws_dev).
+ *   sparse = 0: every tile is read (planes accumulated over several binnings).
+ * work_dev: device, 256-byte aligned, at least rick_fft_wcorrect_bytes; its
+ * contents are scratch.  ws_dev supplies the w range, the weight sum and (for
+ * sparse) the tiles.  RICK_EINVAL for an n outside 256 ... 8192, a short or
+ * misaligned buffer or unknown flags. */
+rick_status rick_fft_wcorrect(rick_plan *plan, const void *planes_dev, const void *ws_dev,
+                              int32_t sparse, void *work_dev, size_t work_bytes,
+                              float *image_dev, uint32_t flags, void *stream);
+
 /* Adjoint of rick_wcorrect_stack (same flags): for every plane k,
  * planes[k][q][p] = image[q][p] s(p,q) (-1)^(p+q) e^{-2 pi i w_k (n - 1)},
  * the m x m image zero-padded to the n x n grid frame (cells outside the

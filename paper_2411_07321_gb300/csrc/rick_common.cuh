@@ -80,6 +80,7 @@ struct rick_plan {
     void *fft_work;     // cuFFT work area (ours: stream-ordered allocation)
     cudaStream_t own;   // the plan's private stream for its own allocations
     float *taper_inv;  // device [n]: 1 / C(nu_p), nu_p = (p - n/2) / n
+    float2 *twid;      // device [n]: e^{2 pi i j / n} for the fused transform (or NULL)
     double beta, sigma, i0_beta;
     KernelPoly poly;   // kernel-weight polynomials (host copy, passed to kernels)
     rick_status sticky;
@@ -600,6 +601,24 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
 // Min/max keys of the finite w of visibilities [0, n) folded into hdr->wmin_key / wmax_key.
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
                         cudaStream_t st, int n_chan, const double *scale);
-// rick_grid (accumulate = 0) or rick_grid_accumulate (1).
-rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int accumulate,
+// rick_grid (RICK_GRID_OVERWRITE), rick_grid_accumulate (RICK_GRID_ACCUMULATE)
+// or rick_grid_sparse (RICK_GRID_RECORD_TILES: only the tiles that records
+// reach are written, the others keep whatever they held).
+#define RICK_GRID_OVERWRITE 0
+#define RICK_GRID_ACCUMULATE 1
+#define RICK_GRID_RECORD_TILES 2
+rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int mode,
                            void *stream);
+// The twiddle table of the fused transform (rick_fft.cu), on the plan's own
+// stream; nothing for sizes the fused transform does not cover.
+bool rick_fft_tables(rick_plan *pl);
+// Bytes of the fused transform's work buffer (0 where it does not cover n).
+size_t rick_fft_work_bytes(const rick_params *p);
+// Tiles the fused transform reads (mode 0: all; 1: this binning's; 2: add this
+// binning's to those marked), kept in the work buffer.
+rick_status rick_fft_tiles_impl(rick_plan *plan, const void *ws_dev, void *work_dev,
+                                size_t work_bytes, int mode, cudaStream_t st);
+// The fused inverse FFT + w-correction of the marked tiles.
+rick_status rick_fft_wcorrect_impl(rick_plan *plan, const void *planes_dev, const void *ws_dev,
+                                   void *work_dev, size_t work_bytes, float *image_dev,
+                                   uint32_t flags, cudaStream_t st);

@@ -1,0 +1,558 @@
+// rick_fft.cu -- the inverse 2D FFT of every w-plane (§2 step 3) fused with
+// the w-correction, the plane sum and the taper correction (§2 step 4, Eq. 2).
+// Only the uv-tiles that hold gridded records are read.
+//
+// The unnormalised inverse transform F[q][p] = sum_{j,i} g[j][i]
+// e^{+2 pi i (i p + j q) / n} of each plane runs as two passes of 1D
+// transforms:
+//  1. rows: along u, for every row v of a tile-row in which some tile holds
+//     records (a row of empty tiles transforms to zero and is skipped).  Tiles
+//     without records are read as zeros, so the grid step need not clear them.
+//     The transformed rows go out transposed, work[k][p][v], 1024/(n/16) rows
+//     per CTA (4 at n = 4096) so that each 32-byte sector of the transposed
+//     store comes from one CTA; only the image's crop columns p are kept.
+//  2. columns: along v, one transform per image column p and plane k, reading
+//     only the touched tile-rows of work[k][p].  The CTA keeps its column's
+//     pixels across the planes and sums them into the image as it goes: plane
+//     k contributes Re(F_k e^{2 pi i w_k (n - 1)}), and with equally spaced
+//     plane centres the phase of plane k is that of the block's first plane
+//     times D^(k - k0), D = e^{2 pi i dw (n - 1)}; each block of 8 planes is
+//     summed by Horner's rule (descending k) and turned by its first plane's
+//     exact phase (double-single argument, sincospif).
+//
+// Each 1D transform of N = 2^LOGN points is a Stockham autosort FFT (the
+// formulation of Govindaraju et al., SC 2008): N/16 threads with 16 points
+// each, radix-16 butterflies in registers (a radix-2, -4 or -8 stage last when
+// 16 does not divide), stages exchanged through shared memory.  The exchange
+// addresses are XOR-swizzled, a ^ ((a >> 4) & 31), which keeps every access
+// pattern of the stages free of bank conflicts.  Twiddles come from a table
+// e^{2 pi i j / n} computed in FP64 at plan creation and rounded once.
+#include "rick_common.cuh"
+#include "rick_wphase.cuh"
+
+#define RICK_FFT_LOG_MIN 8
+#define RICK_FFT_LOG_MAX 13
+
+struct FftArgs {
+    int n, n_w, nt, log2T;
+    const float2 *planes;    // [n_w][n][n]
+    float2 *work;            // [n_w][m][n]: row transforms, transposed
+    uint8_t *tflag;          // [n_w][nt][nt]: tile holds records (is read)
+    uint8_t *trow;           // [n_w][nt]: tile-row holds records
+    uint8_t *pflag;          // [n_w]: plane holds records
+    const float2 *tw;        // [n]: e^{2 pi i j / n}
+    WcArgs wc;               // image geometry, flags, taper, plane centres, weight sum
+};
+
+static __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 31); }
+
+static __device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// v e^{2 pi i e / 16}, e = 0..7 (constant after unrolling)
+static __device__ __forceinline__ float2 rot16(float2 v, int e)
+{
+    const float C1 = 0.923879532511286756f;  // cos(pi/8)
+    const float S1 = 0.382683432365089772f;  // sin(pi/8)
+    const float H = 0.707106781186547524f;   // sqrt(1/2)
+    switch (e) {
+    case 0: return v;
+    case 1: return make_float2(v.x * C1 - v.y * S1, v.x * S1 + v.y * C1);
+    case 2: return make_float2(H * (v.x - v.y), H * (v.x + v.y));
+    case 3: return make_float2(v.x * S1 - v.y * C1, v.x * C1 + v.y * S1);
+    case 4: return make_float2(-v.y, v.x);
+    case 5: return make_float2(-v.x * S1 - v.y * C1, v.x * C1 - v.y * S1);
+    case 6: return make_float2(-H * (v.x + v.y), H * (v.x - v.y));
+    default: return make_float2(-v.x * C1 - v.y * S1, v.x * S1 - v.y * C1);
+    }
+}
+
+// Bit reversal of i < R (R a power of two).
+__host__ __device__ constexpr int brev(int i, int R)
+{
+    int j = 0;
+    for (int b = 1; b < R; b <<= 1, i >>= 1) j = (j << 1) | (i & 1);
+    return j;
+}
+
+// One radix-2 level of the in-register DFT: butterflies of span LEN / 2.
+template <int R, int LEN>
+static __device__ __forceinline__ void dft_level(float2 *a)
+{
+#pragma unroll
+    for (int i = 0; i < R; i += LEN) {
+#pragma unroll
+        for (int m = 0; m < LEN / 2; ++m) {
+            const float2 u = a[i + m];
+            const float2 v = rot16(a[i + m + LEN / 2], m * (16 / LEN));
+            a[i + m] = make_float2(u.x + v.x, u.y + v.y);
+            a[i + m + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
+        }
+    }
+    if constexpr (LEN < R) dft_level<R, 2 * LEN>(a);
+}
+
+// In-register DFT of R points, A_m = sum_r a_r e^{+2 pi i r m / R}: radix-2
+// decimation in time after a bit-reversal permutation (all indices constant).
+template <int R>
+static __device__ __forceinline__ void dft_inv(float2 *a)
+{
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = brev(i, R);
+        if (j > i) {
+            const float2 t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+    }
+    if constexpr (R > 1) dft_level<R, 2>(a);
+}
+
+// One Stockham stage of radix R after sub-transforms of NS points.  x[s] holds
+// element t + P s of the current array (P = N / 16 threads per transform);
+// butterfly j = t + P b (b < 16 / R) takes elements j + r N/R, applies the
+// twiddles e^{2 pi i r (j mod NS) / (NS R)}, and its outputs m go to
+// (j - j mod NS) R + j mod NS + m NS.  After the last stage x[s] holds output
+// t + P s.  cb is the transform's offset in the exchange arrays.
+// Twiddles e^{2 pi i j / N} from two tables in shared memory: tlo[b] =
+// e^{2 pi i b / N} (b < TW_LO) and thi[a] = e^{2 pi i TW_LO a / N}; the product
+// of the two correctly rounded factors is within about 1.5 ulp.
+#define TW_LO 64
+struct Twiddles {
+    const float2 *thi, *tlo;
+    __device__ __forceinline__ float2 operator()(int j) const
+    {
+        return cmul(thi[j / TW_LO], tlo[j % TW_LO]);
+    }
+};
+
+// Fill the tables of an N-point transform from the plan's FP64-rounded table
+// (the caller synchronises before use).
+template <int N>
+static __device__ __forceinline__ void load_twiddles(float2 *s_tw, const float2 *__restrict__ tw)
+{
+    constexpr int NHI = N / TW_LO;
+    for (int i = threadIdx.x; i < TW_LO + NHI; i += blockDim.x)
+        s_tw[i] = i < TW_LO ? tw[i] : tw[(i - TW_LO) * TW_LO];
+}
+
+template <int N, int R, int NS, bool LAST>
+static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb, float *sre,
+                                                 float *sim, const Twiddles &tw)
+{
+    constexpr int P = N / 16, B = 16 / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = t + P * b, k = j & (NS - 1);
+        float2 y[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[r] = x[b + B * r];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) y[r] = cmul(y[r], tw(r * k * (N / (NS * R))));
+        }
+        dft_inv<R>(y);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) x[b + B * m] = y[m];
+        } else {
+            const int base = cb + (j - k) * R + k;
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const int i = swz(base + m * NS);
+                sre[i] = y[m].x;
+                sim[i] = y[m].y;
+            }
+        }
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const int i = swz(cb + t + P * s);
+            x[s] = make_float2(sre[i], sim[i]);
+        }
+        __syncthreads();
+    }
+}
+
+template <int N, int NS>
+static __device__ __forceinline__ void fft_stages(float2 (&x)[16], int t, int cb, float *sre,
+                                                  float *sim, const Twiddles &tw)
+{
+    constexpr int REM = N / NS;
+    constexpr int R = (REM % 16 == 0) ? 16 : REM;
+    constexpr bool LAST = (R == REM);
+    fft_stage<N, R, NS, LAST>(x, t, cb, sre, sim, tw);
+    if constexpr (!LAST) fft_stages<N, NS * R>(x, t, cb, sre, sim, tw);
+}
+
+// The unnormalised inverse DFT of N points held as x[s] = element t + P s;
+// on return x[s] = output t + P s.  Every thread of the CTA must call it.
+template <int LOGN>
+static __device__ __forceinline__ void fft_inv(float2 (&x)[16], int t, int cb, float *sre,
+                                               float *sim, const Twiddles &tw)
+{
+    fft_stages<(1 << LOGN), 1>(x, t, cb, sre, sim, tw);
+}
+
+// Tiles to read: a tile holds records iff it has gridding work items.
+// mode 0: every tile; 1: the tiles of this binning; 2: add this binning's
+// tiles to those already marked (planes gridded over several binnings).
+__global__ void __launch_bounds__(256) fft_tiles_kernel(uint8_t *tflag, const uint32_t *gbase,
+                                                        uint32_t ntiles, int mode)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint8_t has = mode == 0 || gbase[t + 1] != gbase[t];
+    tflag[t] = mode == 2 ? (uint8_t)(tflag[t] | has) : has;
+}
+
+// Tile-rows and planes with a tile to read: one block per plane.
+__global__ void __launch_bounds__(256) fft_rowflags_kernel(FftArgs a)
+{
+    const int k = blockIdx.x, nt = a.nt;
+    const uint8_t *tf = a.tflag + (size_t)k * nt * nt;
+    int any_plane = 0;
+    for (int ty = threadIdx.x; ty < nt; ty += blockDim.x) {
+        uint8_t any = 0;
+        for (int x = 0; x < nt; ++x) any |= tf[ty * nt + x];
+        a.trow[k * nt + ty] = any;
+        any_plane |= any;
+    }
+    any_plane = __syncthreads_or(any_plane);
+    if (threadIdx.x == 0) a.pflag[k] = (uint8_t)(any_plane != 0);
+}
+
+// Pass 1: ROWS = 1024 / P rows per CTA, transformed in two rounds by 512
+// threads (a thread's 16 points and twiddles then stay in registers), staged in
+// shared memory and written out transposed.  Persistent over (plane, block of
+// ROWS rows); blocks whose tile-rows hold no records are skipped.
+template <int LOGN>
+__global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
+{
+    constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
+    constexpr int ROT = ROWS >= 32 ? 1 : 32 / ROWS;
+    extern __shared__ float fsm[];
+    float *sre = fsm, *sim = fsm + 16 * 1024;
+    __shared__ uint8_t s_tf[1024];  // tile flags of the block's tile-rows
+    __shared__ float2 s_tw[TW_LO + N / TW_LO];
+    load_twiddles<N>(s_tw, a.tw);
+    const Twiddles tw{s_tw + TW_LO, s_tw};
+    const int t = threadIdx.x % P;
+    const int nt = a.nt, l2T = a.log2T, m = a.wc.m, off = a.wc.off;
+    const int nvb = N / ROWS, items = a.n_w * nvb;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int k = item / nvb, v0 = (item - k * nvb) * ROWS;
+        const int ty0 = v0 >> l2T, ty1 = (v0 + ROWS - 1) >> l2T;
+        bool any = false;
+        for (int ty = ty0; ty <= ty1; ++ty) any |= a.trow[k * nt + ty] != 0;
+        if (!any) continue;  // the same for every thread
+        __syncthreads();     // the previous block's write-out has read the staging rows
+        const int ntr = ty1 - ty0 + 1;
+        const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
+        for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
+        __syncthreads();
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            // rows of round h use their own exchange areas; the staged rows of
+            // round 0 are not touched by round 1
+            const int c = threadIdx.x / P + h * RPR, cb = c * N, v = v0 + c;
+            const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
+            const float2 *row = a.planes + ((size_t)k * N + v) * N;
+            float2 x[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int u = t + P * s;
+                x[s] = tf[u >> l2T] ? row[u] : make_float2(0.0f, 0.0f);
+            }
+            fft_inv<LOGN>(x, t, cb, sre, sim, tw);
+            // stage the row, rotated per row so that the transposed read-out is
+            // free of bank conflicts too
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int i = swz(cb + t + P * s) ^ ((c * ROT) & 31);
+                sre[i] = x[s].x;
+                sim[i] = x[s].y;
+            }
+        }
+        __syncthreads();
+        float2 *dst = a.work + (size_t)k * m * N + v0;
+        for (int i = threadIdx.x; i < ROWS * m; i += blockDim.x) {
+            const int r = i % ROWS, pc = i / ROWS;
+            const int j = swz(r * N + pc + off) ^ ((r * ROT) & 31);
+            dst[(size_t)pc * N + r] = make_float2(sre[j], sim[j]);
+        }
+    }
+}
+
+// Pass 2 and the w-correction: NT threads, COLS = NT / P image columns per
+// CTA, each column transformed for every plane.  Per pixel the CTA keeps in
+// shared memory n - 1 (double-single; plain FP32 for the FP32-phase ablation),
+// the output scale (taper, n factor, weight sum, checkerboard) and the running
+// plane sum; the Horner sum of the current block of planes and the step D stay
+// in registers.
+template <int LOGN>
+struct ColShape {
+    static constexpr int N = 1 << LOGN, P = N / 16;
+    static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
+    static constexpr size_t SMEM = 6 * sizeof(float) * NE;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 ? 2 : 1)
+    fft_cols_kernel(FftArgs a)
+{
+    using S = ColShape<LOGN>;
+    constexpr int N = S::N, P = S::P, NT = S::NT, COLS = S::COLS, NE = S::NE;
+    extern __shared__ float fsm[];
+    float *sre = fsm, *sim = fsm + NE;
+    float *g_hi = fsm + 2 * NE, *g_lo = fsm + 3 * NE, *g_sc = fsm + 4 * NE, *g_acc = fsm + 5 * NE;
+    __shared__ float2 s_tw[TW_LO + N / TW_LO];
+    load_twiddles<N>(s_tw, a.tw);
+    const Twiddles tw{s_tw + TW_LO, s_tw};
+    const WcArgs &w = a.wc;
+    const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * N;
+    const int m = w.m, off = w.off, nt = a.nt, l2T = a.log2T;
+    const int pc = blockIdx.x * COLS + c;  // image column
+    const bool live = pc < m;
+    const int p = (live ? pc : 0) + off;
+    const bool fp32ph = (w.flags & RICK_PHASE_FP32) != 0;
+    float inv_sumw;
+    {
+        const double sw = w.hdr->stats.sum_weight;  // nothing gridded: no normalisation
+        inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
+    }
+    const float4 dwp = __ldg(&w.wplane[w.n_w]);
+    float2 D[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int q = t + P * s, gi = s * NT + threadIdx.x;
+        D[s] = make_float2(1.0f, 0.0f);
+        if (live && q >= off && q < off + m) {
+            const PixelGeom g = pixel_geom(w, p, q, inv_sumw);
+            g_hi[gi] = g.nm1.hi;
+            g_lo[gi] = fp32ph ? g.nm1_f : g.nm1.lo;
+            g_sc[gi] = g.scale;
+            if (!fp32ph) {
+                const float fd = ff_frac(ff_mul(ff{dwp.x, dwp.y}, g.nm1));
+                sincospif(2.0f * fd, &D[s].y, &D[s].x);
+            }
+        } else {
+            g_hi[gi] = g_lo[gi] = g_sc[gi] = 0.0f;
+        }
+        g_acc[gi] = 0.0f;
+    }
+    __syncthreads();  // twiddle tables
+    const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
+    const float2 *col = a.work + (size_t)(live ? pc : 0) * N;
+    for (int k0 = 0; k0 < w.n_w; k0 += bs) {
+        const int k1 = min(k0 + bs, w.n_w);
+        float2 h[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) h[s] = make_float2(0.0f, 0.0f);
+        for (int k = k1 - 1; k >= k0; --k) {
+            if (!a.pflag[k]) {  // an empty plane adds nothing: h = h D
+#pragma unroll
+                for (int s = 0; s < 16; ++s) h[s] = cmul(h[s], D[s]);
+                continue;
+            }
+            const float2 *src = col + (size_t)k * m * N;
+            const uint8_t *tr = a.trow + k * nt;
+            float2 x[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int v = t + P * s;
+                x[s] = (live && tr[v >> l2T]) ? src[v] : make_float2(0.0f, 0.0f);
+            }
+            fft_inv<LOGN>(x, t, cb, sre, sim, tw);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const float2 hd = cmul(h[s], D[s]);
+                h[s] = make_float2(hd.x + x[s].x, hd.y + x[s].y);
+            }
+        }
+        // the block's sum times the exact phase of its first plane
+        const float4 wk = __ldg(&w.wplane[k0]);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const int gi = s * NT + threadIdx.x;
+            PixelGeom g;
+            g.nm1 = ff{g_hi[gi], g_lo[gi]};
+            g.nm1_f = g_lo[gi];
+            float cs, sn;
+            wphase(w, wk, g, &cs, &sn);
+            g_acc[gi] = fmaf(h[s].x, cs, fmaf(-h[s].y, sn, g_acc[gi]));
+        }
+    }
+    if (!live) return;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int q = t + P * s, gi = s * NT + threadIdx.x;
+        if (q >= off && q < off + m) w.image_out[(size_t)(q - off) * m + pc] = g_acc[gi] * g_sc[gi];
+    }
+}
+
+// ------------------------------------------------------------------------
+// Host side
+
+static bool fft_supported(const rick_params &p)
+{
+    return p.n >= (1 << RICK_FFT_LOG_MIN) && p.n <= (1 << RICK_FFT_LOG_MAX);
+}
+
+struct FftWorkLayout {
+    size_t tflag, trow, pflag, work, total;
+};
+
+static FftWorkLayout fft_work_layout(const rick_params &p)
+{
+    const size_t nt = p.n / p.tile, m = p.image_n ? p.image_n : p.n;
+    FftWorkLayout L;
+    size_t o = 0;
+    L.tflag = o; o += rick_align256((size_t)p.n_w * nt * nt);
+    L.trow = o;  o += rick_align256((size_t)p.n_w * nt);
+    L.pflag = o; o += rick_align256((size_t)p.n_w);
+    L.work = o;  o += (size_t)p.n_w * m * p.n * sizeof(float2);
+    L.total = o;
+    return L;
+}
+
+size_t rick_fft_work_bytes(const rick_params *p)
+{
+    return fft_supported(*p) ? fft_work_layout(*p).total : 0;
+}
+
+__global__ void twiddle_kernel(float2 *tw, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        double s, c;
+        sincospi(2.0 * j / n, &s, &c);
+        tw[j] = make_float2((float)c, (float)s);
+    }
+}
+
+// The plan's twiddle table (plans whose n the fused transform covers), on the
+// plan's own stream.
+bool rick_fft_tables(rick_plan *pl)
+{
+    if (!fft_supported(pl->p)) return true;
+    const int n = pl->p.n;
+    if (cudaMallocAsync((void **)&pl->twid, sizeof(float2) * n, pl->own) != cudaSuccess)
+        return false;
+    twiddle_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(pl->twid, n);
+    ++pl->launches;
+    return cudaGetLastError() == cudaSuccess;
+}
+
+template <int LOGN>
+static cudaError_t launch_fft_wc(const FftArgs &a, int num_sms, cudaStream_t st)
+{
+    using S = ColShape<LOGN>;
+    const size_t rows_smem = 2 * 16 * 1024 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<LOGN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rows_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fft_cols_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    const int items = a.n_w * (a.n / (1024 / S::P));
+    fft_rows_kernel<LOGN><<<(unsigned)min(items, num_sms), 512, rows_smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int m = a.wc.m;
+    fft_cols_kernel<LOGN><<<(unsigned)((m + S::COLS - 1) / S::COLS), S::NT, S::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+static bool fft_args_ok(const rick_plan *plan, const void *ws_dev, const void *work_dev,
+                        size_t work_bytes)
+{
+    return fft_supported(plan->p) && plan->twid && !((uintptr_t)ws_dev & 255) &&
+           !((uintptr_t)work_dev & 255) && work_bytes >= fft_work_layout(plan->p).total;
+}
+
+rick_status rick_fft_tiles_impl(rick_plan *plan, const void *ws_dev, void *work_dev,
+                                size_t work_bytes, int mode, cudaStream_t st)
+{
+    if (!fft_args_ok(plan, ws_dev, work_dev, work_bytes)) return RICK_EINVAL;
+    const rick_params &p = plan->p;
+    const FftWorkLayout L = fft_work_layout(p);
+    WsPtrs wp = rick_ws_ptrs((void *)ws_dev, rick_ws_layout(&p, plan->max_vis));
+    const uint32_t nt = p.n / p.tile, ntiles = (uint32_t)p.n_w * nt * nt;
+    fft_tiles_kernel<<<(ntiles + 255) / 256, 256, 0, st>>>((uint8_t *)work_dev + L.tflag,
+                                                           wp.gbase, ntiles, mode);
+    RICK_LAUNCH_CHECK(plan);
+    return RICK_OK;
+}
+
+rick_status rick_fft_wcorrect_impl(rick_plan *plan, const void *planes_dev, const void *ws_dev,
+                                   void *work_dev, size_t work_bytes, float *image_dev,
+                                   uint32_t flags, cudaStream_t st)
+{
+    if (!fft_args_ok(plan, ws_dev, work_dev, work_bytes) || !valid_flags(flags) ||
+        ((uintptr_t)planes_dev & 7) || ((uintptr_t)image_dev & 3))
+        return RICK_EINVAL;
+    const rick_params &p = plan->p;
+    const FftWorkLayout L = fft_work_layout(p);
+    FftArgs a;
+    a.n = p.n;
+    a.n_w = p.n_w;
+    a.nt = p.n / p.tile;
+    a.log2T = 0;
+    while ((1 << a.log2T) < p.tile) ++a.log2T;
+    a.planes = (const float2 *)planes_dev;
+    char *wb = (char *)work_dev;
+    a.tflag = (uint8_t *)(wb + L.tflag);
+    a.trow = (uint8_t *)(wb + L.trow);
+    a.pflag = (uint8_t *)(wb + L.pflag);
+    a.work = (float2 *)(wb + L.work);
+    a.tw = plan->twid;
+    a.wc = make_args(plan, ws_dev, flags);
+    a.wc.image_out = image_dev;
+    fft_rowflags_kernel<<<p.n_w, 256, 0, st>>>(a);
+    RICK_LAUNCH_CHECK(plan);
+    cudaError_t err = cudaErrorInvalidValue;
+    switch (p.n) {
+    case 256: err = launch_fft_wc<8>(a, plan->num_sms, st); break;
+    case 512: err = launch_fft_wc<9>(a, plan->num_sms, st); break;
+    case 1024: err = launch_fft_wc<10>(a, plan->num_sms, st); break;
+    case 2048: err = launch_fft_wc<11>(a, plan->num_sms, st); break;
+    case 4096: err = launch_fft_wc<12>(a, plan->num_sms, st); break;
+    case 8192: err = launch_fft_wc<13>(a, plan->num_sms, st); break;
+    }
+    plan->launches += 2;
+    RICK_CUDA_TRY(plan, err);
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_fft_wcorrect_bytes(const rick_plan *plan, size_t *work_bytes)
+{
+    if (!plan || !work_bytes) return RICK_EINVAL;
+    if (!fft_supported(plan->p)) return RICK_EINVAL;
+    *work_bytes = fft_work_layout(plan->p).total;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_fft_wcorrect(rick_plan *plan, const void *planes_dev,
+                                         const void *ws_dev, int32_t sparse, void *work_dev,
+                                         size_t work_bytes, float *image_dev, uint32_t flags,
+                                         void *stream)
+{
+    if (!plan || !planes_dev || !ws_dev || !work_dev || !image_dev || !valid_flags(flags))
+        return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (!fft_args_ok(plan, ws_dev, work_dev, work_bytes) || ((uintptr_t)planes_dev & 7) ||
+        ((uintptr_t)image_dev & 3))
+        return RICK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    rick_status s = rick_fft_tiles_impl(plan, ws_dev, work_dev, work_bytes, sparse ? 1 : 0, st);
+    if (s != RICK_OK) return s;
+    return rick_fft_wcorrect_impl(plan, planes_dev, ws_dev, work_dev, work_bytes, image_dev, flags,
+                                  st);
+}

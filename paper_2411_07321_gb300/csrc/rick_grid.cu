@@ -554,9 +554,10 @@ static cudaError_t launch_degrid(const DegridArgs &a, int num_sms, cudaStream_t 
     default: err = cudaErrorInvalidValue; \
     }
 
-rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int accumulate,
+rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int mode,
                            void *stream)
 {
+    const int accumulate = mode == RICK_GRID_ACCUMULATE;
     if (!plan || !ws_dev || !planes_dev) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (((uintptr_t)ws_dev & 255) || ((uintptr_t)planes_dev & 15)) return RICK_EINVAL;
@@ -568,7 +569,8 @@ rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int 
     a.planes = (float2 *)planes_dev;
     a.log2T = ilog2(p.tile);
     a.accumulate = accumulate;
-    a.nzero = accumulate ? 0u : (a.t.ntiles + RICK_ZERO_GROUP - 1) / RICK_ZERO_GROUP;
+    a.nzero = mode != RICK_GRID_OVERWRITE ? 0u
+                                          : (a.t.ntiles + RICK_ZERO_GROUP - 1) / RICK_ZERO_GROUP;
     cudaError_t err = cudaSuccess;
     zero_tiles_kernel<<<accumulate ? 1 : plan->num_sms * 8, 256, 0, st>>>(
         w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate);
@@ -584,13 +586,18 @@ rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int 
 
 extern "C" rick_status rick_grid(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream)
 {
-    return rick_grid_impl(plan, ws_dev, planes_dev, 0, stream);
+    return rick_grid_impl(plan, ws_dev, planes_dev, RICK_GRID_OVERWRITE, stream);
+}
+
+extern "C" rick_status rick_grid_sparse(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream)
+{
+    return rick_grid_impl(plan, ws_dev, planes_dev, RICK_GRID_RECORD_TILES, stream);
 }
 
 extern "C" rick_status rick_grid_accumulate(rick_plan *plan, void *ws_dev, void *planes_dev,
                                             void *stream)
 {
-    return rick_grid_impl(plan, ws_dev, planes_dev, 1, stream);
+    return rick_grid_impl(plan, ws_dev, planes_dev, RICK_GRID_ACCUMULATE, stream);
 }
 
 extern "C" rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,

@@ -225,6 +225,7 @@ static void plan_release(rick_plan *pl)
     if (pl->copy) cudaStreamDestroy(pl->copy);
     if (pl->own) {
         if (pl->taper_inv) cudaFreeAsync(pl->taper_inv, pl->own);
+        if (pl->twid) cudaFreeAsync(pl->twid, pl->own);
         if (pl->fft_work) cudaFreeAsync(pl->fft_work, pl->own);
         cudaStreamSynchronize(pl->own);
         cudaStreamDestroy(pl->own);
@@ -307,7 +308,7 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
         plan_release(pl);
         return RICK_ECUFFT;
     }
-    if (!kernel_tables(pl)) {
+    if (!rick_fft_tables(pl) || !kernel_tables(pl)) {
         plan_release(pl);
         return RICK_ECUDA;
     }

@@ -8,7 +8,9 @@
 // first chunk with rick_grid (every plane cell written), the later ones with
 // rick_grid_accumulate (gridding is linear in the records, so the sum over
 // chunks is the gridding of the whole set).  The plane FFT and the
-// w-correction then run once.  Gridded weight sums and drop counts are added
+// w-correction then run once: fused (rick_fft.cu), reading the tiles that
+// the records of any chunk reach, where the fused transform covers n; else
+// cuFFT in place and the plane-sum kernel.  Gridded weight sums and drop counts are added
 // up over the chunks in chunk order, so the normalisation is that of the
 // whole set.
 //
@@ -34,15 +36,16 @@
 #define RICK_STREAM_MAX_CHAN 4096
 
 struct StageLayout {
-    size_t range, total, scale, vis, weight, uvw, bytes;
+    size_t range, total, scale, vis, weight, fwork, fwork_bytes, uvw, bytes;
     size_t uvw_buf, vis_buf, weight_buf;  // bytes of one staging buffer / resident area
     int64_t chunk;
     int resident_uvw;
 };
 
 // The staging area: the range header and stats totals, two chunk buffers of
-// vis and of weight, then either two chunk buffers of uvw (given w range) or
-// two resident uvw areas (range from the data), used by alternate calls.
+// vis and of weight, the fused transform's work buffer (for the n it covers),
+// then either two chunk buffers of uvw (given w range) or two resident uvw
+// areas (range from the data), used by alternate calls.
 // The resident area size is fixed by stage_bytes (0: the size that holds
 // n_vis), so that calls with the same staging area agree on its layout.
 static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n_vis,
@@ -59,6 +62,8 @@ static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n
     S.scale = o;  o += 2 * 8 * (size_t)RICK_STREAM_MAX_CHAN;  // channel factors, per area
     S.vis = o;    o += 2 * S.vis_buf;
     S.weight = o; o += 2 * S.weight_buf;
+    S.fwork_bytes = rick_fft_work_bytes(p);
+    S.fwork = o;  o += rick_align256(S.fwork_bytes);
     S.uvw = o;
     if (!S.resident_uvw) {
         S.uvw_buf = rick_align256(24 * (size_t)S.chunk);
@@ -246,12 +251,20 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_free[b], st));
         stats_add_kernel<<<1, 1, 0, st>>>(hdr, tot, c == 0);
         RICK_LAUNCH_CHECK(plan);
-        RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev, c > 0, st));
+        RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev,
+                                c > 0 ? RICK_GRID_ACCUMULATE : RICK_GRID_OVERWRITE, st));
+        // the tiles this chunk's records reach, for the fused transform
+        if (S.fwork_bytes)
+            RICK_TRY(rick_fft_tiles_impl(plan, ws_dev, sb + S.fwork, S.fwork_bytes, c > 0 ? 2 : 1,
+                                         st));
     }
     // every binning of this call has read its resident uvw area and factors
     RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_area_free[area], st));
     stats_finish_kernel<<<1, 1, 0, st>>>(hdr, tot, stats_dev);
     RICK_LAUNCH_CHECK(plan);
+    if (S.fwork_bytes)
+        return rick_fft_wcorrect_impl(plan, planes_dev, ws_dev, sb + S.fwork, S.fwork_bytes,
+                                      image_dev, flags, st);
     RICK_TRY(rick_fft_wplanes(plan, planes_dev, 1, st));
     RICK_TRY(rick_wcorrect_stack(plan, planes_dev, ws_dev, image_dev, flags, st));
     return RICK_OK;

@@ -36,9 +36,13 @@ class Imager:
                  tile: int = 64, w_range: tuple[float, float] | None = None,
                  kb_beta: float = math.nan, gauss_sigma: float = math.nan,
                  precision: str = "fp32", max_vis: int = 1 << 20, device=None,
-                 image_n: int | None = None):
+                 image_n: int | None = None, fused: bool = True):
         """n is the grid side; the image is the central image_n x image_n crop
-        (default n: no padding), with pixel size fov / n."""
+        (default n: no padding), with pixel size fov / n.  With ``fused`` (and n
+        in 256 ... 8192) images are made by the fused sparse transform +
+        w-correction (rick_grid_sparse, rick_fft_wcorrect); otherwise, and in
+        the explicit grid / fft / wcorrect stages, by cuFFT in place and the
+        plane-sum kernel."""
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("Imager runs on a CUDA device only")
@@ -57,6 +61,8 @@ class Imager:
             self.stats_buf = torch.zeros(48, dtype=torch.uint8, device=self.device)
         self.fft_bytes = R.rick_plan_fft_bytes(self.plan)
         self.n_vis = 0
+        self.fused = bool(fused) and R.rick_fft_wcorrect_bytes(self.plan) is not None
+        self._fwork = None
 
     # ---------------------------------------------------------------- helpers
     def _stream(self) -> int:
@@ -69,8 +75,10 @@ class Imager:
             raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
     def footprint_bytes(self) -> int:
-        """Device bytes this imager holds (workspace, planes, cuFFT area)."""
-        return self.ws_bytes + self.plane_bytes + self.fft_bytes + 48
+        """Device bytes this imager holds (workspace, planes, cuFFT area, and the
+        fused transform's work buffer)."""
+        fb = R.rick_fft_wcorrect_bytes(self.plan) if self.fused else 0
+        return self.ws_bytes + self.plane_bytes + self.fft_bytes + (fb or 0) + 48
 
     # ---------------------------------------------------------------- stages
     def bin(self, uvw: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor | None = None):
@@ -148,6 +156,42 @@ class Imager:
                               out.data_ptr(), flags, self._stream())
         return out
 
+    def grid_sparse(self):
+        """Gridding that writes only the tiles records reach (for fft_wcorrect)."""
+        R.rick_grid_sparse(self.plan, self.ws.data_ptr(), self.planes.data_ptr(), self._stream())
+
+    def fft_wcorrect(self, flags: int = IMAGE_FLAGS, out: torch.Tensor | None = None,
+                     sparse: bool = True) -> torch.Tensor:
+        """The inverse FFT of the planes fused with the w-correction and plane
+        sum (rick_fft_wcorrect): the image of planes from grid() or
+        grid_sparse() (sparse: read only the tiles with records); the planes
+        are not modified."""
+        need = R.rick_fft_wcorrect_bytes(self.plan)
+        if need is None:
+            raise ValueError(f"the fused transform does not cover n = {self.n}")
+        if self._fwork is None or self._fwork.numel() < need:
+            self._fwork = None
+            self._fwork = torch.empty(need, dtype=torch.uint8, device=self.device)
+        if out is None:
+            out = torch.empty((self.m, self.m), dtype=torch.float32, device=self.device)
+        self._check(out, torch.float32, (self.m, self.m), "image")
+        R.rick_fft_wcorrect(self.plan, self.planes.data_ptr(), self.ws.data_ptr(), int(sparse),
+                            self._fwork.data_ptr(), self._fwork.numel(), out.data_ptr(), flags,
+                            self._stream())
+        return out
+
+    def fused_tiles(self) -> tuple[int, int]:
+        """(plane, uv-tile) and (plane, tile-row) pairs the last fft_wcorrect read
+        (from the flags at the head of its work buffer)."""
+        if self._fwork is None:
+            return 0, 0
+        nt = self.n // self.params.tile
+        al = lambda x: (x + 255) // 256 * 256
+        nf = self.n_w * nt * nt
+        tiles = int(self._fwork[:nf].sum())
+        rows = int(self._fwork[al(nf):al(nf) + self.n_w * nt].sum())
+        return tiles, rows
+
     def wspread(self, image: torch.Tensor, flags: int = IMAGE_FLAGS):
         self._check(image, torch.float32, (self.m, self.m), "image")
         R.rick_wspread(self.plan, image.data_ptr(), self.ws.data_ptr(), self.planes.data_ptr(),
@@ -171,6 +215,9 @@ class Imager:
         return self.image_from_binned(flags, out)
 
     def image_from_binned(self, flags: int = IMAGE_FLAGS, out=None) -> torch.Tensor:
+        if self.fused:
+            self.grid_sparse()
+            return self.fft_wcorrect(flags, out, sparse=True)
         self.grid()
         self.fft(+1)
         return self.wcorrect(flags, out)

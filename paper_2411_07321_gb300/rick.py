@@ -60,7 +60,8 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_fft_wplanes", "rick_wcorrect_stack", "rick_wspread", "rick_degrid",
            "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
-           "rick_bin_rows", "rick_image_host_rows"]
+           "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
+           "rick_fft_wcorrect"]
 
 
 def _load():
@@ -91,6 +92,9 @@ def _load():
         "rick_bin_values": [vp, vp, vp, vp, vp, vp],
         "rick_grid": [vp, vp, vp, vp],
         "rick_grid_accumulate": [vp, vp, vp, vp],
+        "rick_grid_sparse": [vp, vp, vp, vp],
+        "rick_fft_wcorrect_bytes": [vp, ctypes.POINTER(sz)],
+        "rick_fft_wcorrect": [vp, vp, vp, i32, vp, sz, vp, u32, vp],
         "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
         "rick_image_host": [vp, i64, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32, vp, vp],
         "rick_bin_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, vp],
@@ -267,6 +271,27 @@ def rick_grid(plan, ws, planes, stream) -> None:
 
 def rick_grid_accumulate(plan, ws, planes, stream) -> None:
     _check("rick_grid_accumulate", _L.rick_grid_accumulate(plan, ws, planes, stream or None))
+
+
+def rick_grid_sparse(plan, ws, planes, stream) -> None:
+    _check("rick_grid_sparse", _L.rick_grid_sparse(plan, ws, planes, stream or None))
+
+
+def rick_fft_wcorrect_bytes(plan) -> int | None:
+    """Work bytes of rick_fft_wcorrect, or None where the plan's n is outside
+    the sizes the fused transform covers."""
+    b = ctypes.c_size_t()
+    s = _L.rick_fft_wcorrect_bytes(plan, ctypes.byref(b))
+    if s == RICK_EINVAL:
+        return None
+    _check("rick_fft_wcorrect_bytes", s)
+    return b.value
+
+
+def rick_fft_wcorrect(plan, planes, ws, sparse, work, work_bytes, image, flags, stream) -> None:
+    _check("rick_fft_wcorrect", _L.rick_fft_wcorrect(plan, planes, ws, int(sparse), work,
+                                                     int(work_bytes), image, int(flags),
+                                                     stream or None))
 
 
 def rick_stream_bytes(params: rick_params, max_vis: int, n_vis: int) -> int:

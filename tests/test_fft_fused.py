@@ -1,0 +1,170 @@
+"""The fused inverse FFT + w-correction (rick_fft_wcorrect) against the cuFFT
+path (rick_fft_wplanes(+1) then rick_wcorrect_stack) on the same planes.
+
+Both compute the image of Eq. 2 from the gridded planes in FP32; they differ
+only in rounding order (two passes of radix-16 Stockham transforms and a
+Horner sum over blocks of 8 planes, against cuFFT and a phase recurrence), so
+they agree to a few FP32 ulps of the image peak.  The oracle parity of the
+fused path comes from every other image test (the Imager makes images with
+it by default); here the fused path is checked against an independent FP32
+implementation of the same arithmetic, at every n it covers (256 ... 8192),
+on dense random planes (every tile read) and on gridded sparse planes (only
+the tiles with records read, the others left as garbage), with a crop, the
+flag combinations, plane counts that are not multiples of 8, one plane, and
+an empty binning.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6  # of the image peak: a few FP32 ulps of both paths' transforms
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2411_07321_gb300 as P
+    return P
+
+
+def rel_err(a, b, cc=None):
+    """max |a - b| / max |b|; with cc, of the tapered images a cc and b cc: the
+    division by C(l) C(m) amplifies FP32 rounding of the planes (which differ
+    between two griddings in the order of their float atomics) by up to
+    max 1/(C C) near the corners, so gridded images are compared before it."""
+    a = a.double().cpu().numpy()
+    b = b.double().cpu().numpy()
+    if cc is not None:
+        a, b = a * cc, b * cc
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def taper_2d(n, kernel, support, m):
+    """C(l_p) C(m_q) / C(0)^2 over the central m x m pixels, from the oracle."""
+    op = oracle.Params(n=n, n_w=1, fov=0.03, kernel=oracle.KB if kernel == "kb" else oracle.GAUSS,
+                       support=support, tile=8)
+    off = (n - m) // 2
+    c = np.array([oracle.taper(op, (i + off - n // 2) / n) for i in range(m)])
+    c = c / oracle.taper(op, 0.0)
+    return c[:, None] * c[None, :]
+
+
+def small(n_keep):
+    d = synth.generate(synth.scaled("small", n_keep=n_keep).obs)
+    dev = torch.device("cuda:0")
+    return {k: torch.from_numpy(d[k]).to(dev) for k in ("uvw", "vis", "weight")}
+
+
+def both_paths(im, flags):
+    """Fused (sparse and dense reads) first -- it leaves the planes as they are
+    -- then the cuFFT path, which transforms them in place."""
+    a = im.fft_wcorrect(flags, sparse=True).clone()
+    b = im.fft_wcorrect(flags, sparse=False).clone()
+    im.fft(+1)
+    c = im.wcorrect(flags)
+    torch.cuda.synchronize()
+    return a, b, c
+
+
+@pytest.mark.parametrize("n,n_w,tile", [(256, 8, 32), (512, 3, 16), (1024, 13, 64),
+                                        (2048, 1, 128), (4096, 9, 64), (8192, 2, 64)])
+def test_random_planes_every_size(P, n, n_w, tile):
+    """Dense random planes: every tile is read (sparse = 0), which exercises
+    the transforms on full data at every n."""
+    dev = torch.device("cuda:0")
+    t = small(4000)
+    fov = 2.0 * math.pi / 180 * n / 256
+    im = P.Imager(n, n_w, fov, kernel="kb", support=7, tile=tile, max_vis=4000, device=dev)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    g = torch.Generator(device=dev).manual_seed(n + n_w)
+    im.planes.copy_(torch.complex(torch.randn(im.planes.shape, device=dev, generator=g),
+                                  torch.randn(im.planes.shape, device=dev, generator=g)))
+    flags = P.IMAGE_FLAGS
+    a = im.fft_wcorrect(flags, sparse=False).clone()
+    im.fft(+1)
+    c = im.wcorrect(flags)
+    err = rel_err(a, c)
+    print(f"n={n} n_w={n_w}: fused vs cuFFT {err:.2e} of peak")
+    assert err < TOL
+    im.close()
+
+
+@pytest.mark.parametrize("kernel,support,tile,n_w,image_n", [
+    ("kb", 7, 32, 8, None), ("gauss", 7, 16, 13, None), ("kb", 9, 32, 16, 128),
+    ("kb", 1, 8, 5, 200), ("kb", 4, 16, 1, None)])
+def test_gridded_planes(P, kernel, support, tile, n_w, image_n):
+    """Gridded sparse planes: the sparse read (tiles with records only) equals
+    the dense read and the cuFFT path; record-free tiles hold garbage for the
+    sparse read (rick_grid_sparse leaves them as they were)."""
+    dev = torch.device("cuda:0")
+    t = small(30001)
+    wl = synth.WORKLOADS["small"]
+    im = P.Imager(wl.n, n_w, wl.fov, kernel=kernel, support=support, tile=tile,
+                  max_vis=30001, device=dev, image_n=image_n)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    cc = taper_2d(wl.n, kernel, support, im.m)
+    for flags in (P.IMAGE_FLAGS, P.PREDICT_FLAGS, P.rick.RICK_NORMALIZE | P.rick.RICK_PHASE_FP32):
+        im.planes.fill_(float("nan"))
+        im.grid_sparse()
+        sp = im.fft_wcorrect(flags, sparse=True).clone()
+        im.grid()
+        a, b, c = both_paths(im, flags)
+        e_sparse_garbage = rel_err(sp, c, cc)
+        e_sparse, e_dense = rel_err(a, c, cc), rel_err(b, c, cc)
+        print(f"{kernel} W={support} n_w={n_w} crop={image_n} flags={flags}: sparse-garbage "
+              f"{e_sparse_garbage:.2e}, sparse {e_sparse:.2e}, dense {e_dense:.2e} (tapered); "
+              f"raw {rel_err(a, c):.2e}")
+        assert np.isfinite(sp.cpu().numpy()).all()
+        assert e_sparse_garbage < TOL and e_sparse < TOL and e_dense < TOL
+    im.close()
+
+
+def test_empty_binning_gives_zero_image(P):
+    dev = torch.device("cuda:0")
+    wl = synth.WORKLOADS["small"]
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel="kb", support=7, tile=32, max_vis=16,
+                  device=dev, w_range=(-10.0, 10.0))
+    e = torch.empty((0, 3), dtype=torch.float64, device=dev)
+    im.bin(e, torch.empty(0, dtype=torch.complex64, device=dev))
+    im.planes.fill_(float("nan"))
+    img = im.image_from_binned()
+    assert im.fused
+    assert (img.cpu().numpy() == 0).all()
+    im.close()
+
+
+def test_fused_path_is_the_default_where_covered(P):
+    dev = torch.device("cuda:0")
+    a = P.Imager(256, 4, 0.03, max_vis=16, device=dev, tile=32)
+    b = P.Imager(128, 4, 0.03, max_vis=16, device=dev, tile=32)
+    c = P.Imager(256, 4, 0.03, max_vis=16, device=dev, tile=32, fused=False)
+    assert a.fused and not b.fused and not c.fused
+    assert P.rick.rick_fft_wcorrect_bytes(b.plan) is None
+    for im in (a, b, c):
+        im.close()
+
+
+def test_rejects_bad_arguments(P):
+    dev = torch.device("cuda:0")
+    im = P.Imager(256, 4, 0.03, max_vis=16, device=dev, tile=32)
+    need = P.rick.rick_fft_wcorrect_bytes(im.plan)
+    work = torch.empty(need + 512, dtype=torch.uint8, device=dev)
+    img = torch.empty((256, 256), dtype=torch.float32, device=dev)
+    R = P.rick
+    s = torch.cuda.current_stream().cuda_stream
+    for args in ((work.data_ptr(), need - 1, 0),        # short buffer
+                 (work.data_ptr() + 128, need, 0),      # misaligned buffer
+                 (work.data_ptr(), need, 1 << 10)):     # unknown flag
+        with pytest.raises(R.RickError) as e:
+            R.rick_fft_wcorrect(im.plan, im.planes.data_ptr(), im.ws.data_ptr(), 1, args[0],
+                                args[1], img.data_ptr(), args[2], s)
+        assert e.value.status == R.RICK_EINVAL
+    im.close()
