@@ -80,7 +80,7 @@ struct rick_plan {
     void *fft_work;     // cuFFT work area (ours: stream-ordered allocation)
     cudaStream_t own;   // the plan's private stream for its own allocations
     float *taper_inv;  // device [n]: 1 / C(nu_p), nu_p = (p - n/2) / n
-    float2 *twid;      // device [n]: e^{2 pi i j / n} for the fused transform (or NULL)
+    float2 *twid;      // device: stage twiddle tables of the fused transform (or NULL)
     double beta, sigma, i0_beta;
     KernelPoly poly;   // kernel-weight polynomials (host copy, passed to kernels)
     rick_status sticky;
@@ -609,7 +609,7 @@ void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsH
 #define RICK_GRID_RECORD_TILES 2
 rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int mode,
                            void *stream);
-// The twiddle table of the fused transform (rick_fft.cu), on the plan's own
+// The twiddle tables of the fused transform (rick_fft.cu), on the plan's own
 // stream; nothing for sizes the fused transform does not cover.
 bool rick_fft_tables(rick_plan *pl);
 // Bytes of the fused transform's work buffer (0 where it does not cover n).

@@ -23,10 +23,11 @@
 // Each 1D transform of N = 2^LOGN points is a Stockham autosort FFT (the
 // formulation of Govindaraju et al., SC 2008): N/16 threads with 16 points
 // each, radix-16 butterflies in registers (a radix-2, -4 or -8 stage last when
-// 16 does not divide), stages exchanged through shared memory.  The exchange
-// addresses are XOR-swizzled, a ^ ((a >> 4) & 31), which keeps every access
-// pattern of the stages free of bank conflicts.  Twiddles come from a table
-// e^{2 pi i j / n} computed in FP64 at plan creation and rounded once.
+// 16 does not divide; the butterflies' adds two-wide), stages exchanged
+// through shared memory arrays padded by one word in 32.  Twiddles come from
+// per-stage tables computed in FP64 at plan creation and rounded once, laid
+// out so that a warp reads consecutive entries (they stay in L1; the plane
+// data is read around it).
 #include "rick_common.cuh"
 #include "rick_wphase.cuh"
 
@@ -46,27 +47,49 @@ struct FftArgs {
 
 static __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 31); }
 
+// Exchange arrays: one word of padding per 32 (a + a/32) keeps the stages'
+// access patterns free of bank conflicts (one pattern is 2-way) and leaves
+// every address a per-thread base plus a constant.
+static __device__ __forceinline__ int pad32(int a) { return a + (a >> 5); }
+
 static __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// v e^{2 pi i e / 16}, e = 0..7 (constant after unrolling)
-static __device__ __forceinline__ float2 rot16(float2 v, int e)
+// u + v and u - v, two-wide (packed) FP32
+static __device__ __forceinline__ void bfly(float2 &u, float2 &v)
+{
+    const float2 s = __fadd2_rn(u, v);
+    v = __ffma2_rn(v, make_float2(-1.0f, -1.0f), u);
+    u = s;
+}
+
+// u + v e^{2 pi i e / 16} and u - v e^{2 pi i e / 16}, e = 0..7 (constant
+// after unrolling)
+static __device__ __forceinline__ void bfly16(float2 &u, float2 &v, int e)
 {
     const float C1 = 0.923879532511286756f;  // cos(pi/8)
     const float S1 = 0.382683432365089772f;  // sin(pi/8)
     const float H = 0.707106781186547524f;   // sqrt(1/2)
+    float2 r;
     switch (e) {
-    case 0: return v;
-    case 1: return make_float2(v.x * C1 - v.y * S1, v.x * S1 + v.y * C1);
-    case 2: return make_float2(H * (v.x - v.y), H * (v.x + v.y));
-    case 3: return make_float2(v.x * S1 - v.y * C1, v.x * C1 + v.y * S1);
-    case 4: return make_float2(-v.y, v.x);
-    case 5: return make_float2(-v.x * S1 - v.y * C1, v.x * C1 - v.y * S1);
-    case 6: return make_float2(-H * (v.x + v.y), H * (v.x - v.y));
-    default: return make_float2(-v.x * C1 - v.y * S1, v.x * S1 - v.y * C1);
+    case 0: bfly(u, v); return;
+    case 4: {  // v i: scalar adds, no lane swap
+        const float2 a = make_float2(u.x - v.y, u.y + v.x);
+        v = make_float2(u.x + v.y, u.y - v.x);
+        u = a;
+        return;
     }
+    case 1: r = make_float2(v.x * C1 - v.y * S1, v.x * S1 + v.y * C1); break;
+    case 2: r = make_float2(H * (v.x - v.y), H * (v.x + v.y)); break;
+    case 3: r = make_float2(v.x * S1 - v.y * C1, v.x * C1 + v.y * S1); break;
+    case 5: r = make_float2(-v.x * S1 - v.y * C1, v.x * C1 - v.y * S1); break;
+    case 6: r = make_float2(-H * (v.x + v.y), H * (v.x - v.y)); break;
+    default: r = make_float2(-v.x * C1 - v.y * S1, v.x * S1 - v.y * C1); break;
+    }
+    v = r;
+    bfly(u, v);
 }
 
 // Bit reversal of i < R (R a power of two).
@@ -84,12 +107,7 @@ static __device__ __forceinline__ void dft_level(float2 *a)
 #pragma unroll
     for (int i = 0; i < R; i += LEN) {
 #pragma unroll
-        for (int m = 0; m < LEN / 2; ++m) {
-            const float2 u = a[i + m];
-            const float2 v = rot16(a[i + m + LEN / 2], m * (16 / LEN));
-            a[i + m] = make_float2(u.x + v.x, u.y + v.y);
-            a[i + m + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
-        }
+        for (int m = 0; m < LEN / 2; ++m) bfly16(a[i + m], a[i + m + LEN / 2], m * (16 / LEN));
     }
     if constexpr (LEN < R) dft_level<R, 2 * LEN>(a);
 }
@@ -111,37 +129,33 @@ static __device__ __forceinline__ void dft_inv(float2 *a)
     if constexpr (R > 1) dft_level<R, 2>(a);
 }
 
+// The stages of an N-point transform: radix 16 while 16 divides what is left,
+// then one radix-2, -4 or -8 stage.  Stage i after sub-transforms of NS points
+// needs the twiddles e^{2 pi i r k / (NS R)}, r = 1..R-1, k < NS (none for the
+// first stage), tabled per stage as [r - 1][k] so that the threads of a warp
+// read consecutive entries.
+__host__ __device__ constexpr int stage_radix(int N, int NS)
+{
+    return ((N / NS) % 16 == 0) ? 16 : N / NS;
+}
+
+__host__ __device__ constexpr int twiddle_entries(int N)
+{
+    int e = 0;
+    for (int ns = 1; ns < N; ns *= stage_radix(N, ns))
+        if (ns > 1) e += (stage_radix(N, ns) - 1) * ns;
+    return e;
+}
+
 // One Stockham stage of radix R after sub-transforms of NS points.  x[s] holds
 // element t + P s of the current array (P = N / 16 threads per transform);
 // butterfly j = t + P b (b < 16 / R) takes elements j + r N/R, applies the
-// twiddles e^{2 pi i r (j mod NS) / (NS R)}, and its outputs m go to
-// (j - j mod NS) R + j mod NS + m NS.  After the last stage x[s] holds output
-// t + P s.  cb is the transform's offset in the exchange arrays.
-// Twiddles e^{2 pi i j / N} from two tables in shared memory: tlo[b] =
-// e^{2 pi i b / N} (b < TW_LO) and thi[a] = e^{2 pi i TW_LO a / N}; the product
-// of the two correctly rounded factors is within about 1.5 ulp.
-#define TW_LO 64
-struct Twiddles {
-    const float2 *thi, *tlo;
-    __device__ __forceinline__ float2 operator()(int j) const
-    {
-        return cmul(thi[j / TW_LO], tlo[j % TW_LO]);
-    }
-};
-
-// Fill the tables of an N-point transform from the plan's FP64-rounded table
-// (the caller synchronises before use).
-template <int N>
-static __device__ __forceinline__ void load_twiddles(float2 *s_tw, const float2 *__restrict__ tw)
-{
-    constexpr int NHI = N / TW_LO;
-    for (int i = threadIdx.x; i < TW_LO + NHI; i += blockDim.x)
-        s_tw[i] = i < TW_LO ? tw[i] : tw[(i - TW_LO) * TW_LO];
-}
-
-template <int N, int R, int NS, bool LAST>
+// twiddles e^{2 pi i r (j mod NS) / (NS R)} (table at OFF), and its outputs m
+// go to (j - j mod NS) R + j mod NS + m NS.  After the last stage x[s] holds
+// output t + P s.  cb is the transform's offset in the exchange arrays.
+template <int N, int R, int NS, int OFF, bool LAST>
 static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb, float *sre,
-                                                 float *sim, const Twiddles &tw)
+                                                 float *sim, const float2 *__restrict__ tw)
 {
     constexpr int P = N / 16, B = 16 / R;
 #pragma unroll
@@ -152,17 +166,17 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
         for (int r = 0; r < R; ++r) y[r] = x[b + B * r];
         if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) y[r] = cmul(y[r], tw(r * k * (N / (NS * R))));
+            for (int r = 1; r < R; ++r) y[r] = cmul(y[r], __ldg(tw + OFF + (r - 1) * NS + k));
         }
         dft_inv<R>(y);
         if constexpr (LAST) {
 #pragma unroll
             for (int m = 0; m < R; ++m) x[b + B * m] = y[m];
         } else {
-            const int base = cb + (j - k) * R + k;
+            const int base = (j - k) * R + k;
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                const int i = swz(base + m * NS);
+                const int i = cb + pad32(base + m * NS);
                 sre[i] = y[m].x;
                 sim[i] = y[m].y;
             }
@@ -172,32 +186,38 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            const int i = swz(cb + t + P * s);
+            const int i = cb + pad32(t + P * s);
             x[s] = make_float2(sre[i], sim[i]);
         }
         __syncthreads();
     }
 }
 
-template <int N, int NS>
+template <int N, int NS, int OFF>
 static __device__ __forceinline__ void fft_stages(float2 (&x)[16], int t, int cb, float *sre,
-                                                  float *sim, const Twiddles &tw)
+                                                  float *sim, const float2 *__restrict__ tw)
 {
-    constexpr int REM = N / NS;
-    constexpr int R = (REM % 16 == 0) ? 16 : REM;
-    constexpr bool LAST = (R == REM);
-    fft_stage<N, R, NS, LAST>(x, t, cb, sre, sim, tw);
-    if constexpr (!LAST) fft_stages<N, NS * R>(x, t, cb, sre, sim, tw);
+    constexpr int R = stage_radix(N, NS);
+    constexpr bool LAST = (R == N / NS);
+    fft_stage<N, R, NS, OFF, LAST>(x, t, cb, sre, sim, tw);
+    if constexpr (!LAST) fft_stages<N, NS * R, OFF + (NS > 1 ? (R - 1) * NS : 0)>(x, t, cb, sre, sim, tw);
 }
 
 // The unnormalised inverse DFT of N points held as x[s] = element t + P s;
 // on return x[s] = output t + P s.  Every thread of the CTA must call it.
+// tw: the plan's stage twiddle tables.
 template <int LOGN>
 static __device__ __forceinline__ void fft_inv(float2 (&x)[16], int t, int cb, float *sre,
-                                               float *sim, const Twiddles &tw)
+                                               float *sim, const float2 *__restrict__ tw)
 {
-    fft_stages<(1 << LOGN), 1>(x, t, cb, sre, sim, tw);
+    fft_stages<(1 << LOGN), 1, 0>(x, t, cb, sre, sim, tw);
 }
+
+// Exchange arrays of one transform: N words plus the padding.
+template <int N>
+struct XLen {
+    static constexpr int L = N + N / 32;
+};
 
 // Tiles to read: a tile holds records iff it has gridding work items.
 // mode 0: every tile; 1: the tiles of this binning; 2: add this binning's
@@ -236,12 +256,10 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
 {
     constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
     constexpr int ROT = ROWS >= 32 ? 1 : 32 / ROWS;
+    constexpr int L = XLen<N>::L;
     extern __shared__ float fsm[];
-    float *sre = fsm, *sim = fsm + 16 * 1024;
+    float *sre = fsm, *sim = fsm + ROWS * L;  // exchange arrays; staging at row stride N
     __shared__ uint8_t s_tf[1024];  // tile flags of the block's tile-rows
-    __shared__ float2 s_tw[TW_LO + N / TW_LO];
-    load_twiddles<N>(s_tw, a.tw);
-    const Twiddles tw{s_tw + TW_LO, s_tw};
     const int t = threadIdx.x % P;
     const int nt = a.nt, l2T = a.log2T, m = a.wc.m, off = a.wc.off;
     const int nvb = N / ROWS, items = a.n_w * nvb;
@@ -260,21 +278,22 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         for (int h = 0; h < 2; ++h) {
             // rows of round h use their own exchange areas; the staged rows of
             // round 0 are not touched by round 1
-            const int c = threadIdx.x / P + h * RPR, cb = c * N, v = v0 + c;
+            const int c = threadIdx.x / P + h * RPR, v = v0 + c;
             const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
             const float2 *row = a.planes + ((size_t)k * N + v) * N;
             float2 x[16];
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const int u = t + P * s;
-                x[s] = tf[u >> l2T] ? row[u] : make_float2(0.0f, 0.0f);
+                x[s] = tf[u >> l2T] ? __ldcg(row + u) : make_float2(0.0f, 0.0f);
             }
-            fft_inv<LOGN>(x, t, cb, sre, sim, tw);
-            // stage the row, rotated per row so that the transposed read-out is
-            // free of bank conflicts too
+            fft_inv<LOGN>(x, t, c * L, sre, sim, a.tw);
+            // stage the row (row stride N: the staged rows of round 0 lie below
+            // the exchange arrays of round 1), XOR-swizzled and rotated per row
+            // so that the transposed read-out is free of bank conflicts too
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
-                const int i = swz(cb + t + P * s) ^ ((c * ROT) & 31);
+                const int i = swz(c * N + t + P * s) ^ ((c * ROT) & 31);
                 sre[i] = x[s].x;
                 sim[i] = x[s].y;
             }
@@ -294,12 +313,14 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
 // shared memory n - 1 (double-single; plain FP32 for the FP32-phase ablation),
 // the output scale (taper, n factor, weight sum, checkerboard) and the running
 // plane sum; the Horner sum of the current block of planes and the step D stay
-// in registers.
+// in registers.  The plane data is read around L1 (it streams), so the
+// twiddle tables stay there.
 template <int LOGN>
 struct ColShape {
     static constexpr int N = 1 << LOGN, P = N / 16;
     static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
-    static constexpr size_t SMEM = 6 * sizeof(float) * NE;
+    static constexpr int XE = COLS * XLen<N>::L;  // words of one exchange array
+    static constexpr size_t SMEM = sizeof(float) * (2 * XE + 4 * NE);
 };
 
 template <int LOGN>
@@ -308,14 +329,12 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
 {
     using S = ColShape<LOGN>;
     constexpr int N = S::N, P = S::P, NT = S::NT, COLS = S::COLS, NE = S::NE;
+    constexpr int XE = S::XE;
     extern __shared__ float fsm[];
-    float *sre = fsm, *sim = fsm + NE;
-    float *g_hi = fsm + 2 * NE, *g_lo = fsm + 3 * NE, *g_sc = fsm + 4 * NE, *g_acc = fsm + 5 * NE;
-    __shared__ float2 s_tw[TW_LO + N / TW_LO];
-    load_twiddles<N>(s_tw, a.tw);
-    const Twiddles tw{s_tw + TW_LO, s_tw};
+    float *sre = fsm, *sim = fsm + XE;
+    float *g_hi = fsm + 2 * XE, *g_lo = g_hi + NE, *g_sc = g_lo + NE, *g_acc = g_sc + NE;
     const WcArgs &w = a.wc;
-    const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * N;
+    const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * XLen<N>::L;
     const int m = w.m, off = w.off, nt = a.nt, l2T = a.log2T;
     const int pc = blockIdx.x * COLS + c;  // image column
     const bool live = pc < m;
@@ -346,7 +365,6 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
         }
         g_acc[gi] = 0.0f;
     }
-    __syncthreads();  // twiddle tables
     const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
     const float2 *col = a.work + (size_t)(live ? pc : 0) * N;
     for (int k0 = 0; k0 < w.n_w; k0 += bs) {
@@ -366,9 +384,9 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const int v = t + P * s;
-                x[s] = (live && tr[v >> l2T]) ? src[v] : make_float2(0.0f, 0.0f);
+                x[s] = (live && tr[v >> l2T]) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
             }
-            fft_inv<LOGN>(x, t, cb, sre, sim, tw);
+            fft_inv<LOGN>(x, t, cb, sre, sim, a.tw);
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const float2 hd = cmul(h[s], D[s]);
@@ -426,25 +444,36 @@ size_t rick_fft_work_bytes(const rick_params *p)
     return fft_supported(*p) ? fft_work_layout(*p).total : 0;
 }
 
-__global__ void twiddle_kernel(float2 *tw, int n)
+// The stage twiddle tables of an n-point transform: entry OFF_i + (r - 1) NS + k
+// of stage i = e^{2 pi i r k / (NS R)}, in FP64, rounded once.
+__global__ void twiddle_kernel(float2 *tw, int n, int entries)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) {
-        double s, c;
-        sincospi(2.0 * j / n, &s, &c);
-        tw[j] = make_float2((float)c, (float)s);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= entries) return;
+    int off = 0;
+    for (int ns = 1; ns < n; ns *= stage_radix(n, ns)) {
+        if (ns == 1) continue;
+        const int R = stage_radix(n, ns), cnt = (R - 1) * ns;
+        if (e < off + cnt) {
+            const int r = (e - off) / ns + 1, k = (e - off) % ns;
+            double s, c;
+            sincospi(2.0 * r * k / ((double)ns * R), &s, &c);
+            tw[e] = make_float2((float)c, (float)s);
+            return;
+        }
+        off += cnt;
     }
 }
 
-// The plan's twiddle table (plans whose n the fused transform covers), on the
+// The plan's twiddle tables (plans whose n the fused transform covers), on the
 // plan's own stream.
 bool rick_fft_tables(rick_plan *pl)
 {
     if (!fft_supported(pl->p)) return true;
-    const int n = pl->p.n;
-    if (cudaMallocAsync((void **)&pl->twid, sizeof(float2) * n, pl->own) != cudaSuccess)
+    const int n = pl->p.n, entries = twiddle_entries(n);
+    if (cudaMallocAsync((void **)&pl->twid, sizeof(float2) * entries, pl->own) != cudaSuccess)
         return false;
-    twiddle_kernel<<<(n + 255) / 256, 256, 0, pl->own>>>(pl->twid, n);
+    twiddle_kernel<<<(entries + 255) / 256, 256, 0, pl->own>>>(pl->twid, n, entries);
     ++pl->launches;
     return cudaGetLastError() == cudaSuccess;
 }
@@ -453,7 +482,7 @@ template <int LOGN>
 static cudaError_t launch_fft_wc(const FftArgs &a, int num_sms, cudaStream_t st)
 {
     using S = ColShape<LOGN>;
-    const size_t rows_smem = 2 * 16 * 1024 * sizeof(float);
+    const size_t rows_smem = 2 * sizeof(float) * (1024 / S::P) * XLen<(1 << LOGN)>::L;
     cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<LOGN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rows_smem);

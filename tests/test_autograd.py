@@ -95,7 +95,13 @@ def test_chi2_gradient_matches_finite_differences(P):
     # D^H of a visibility vector = Re(grid -> inverse FFT -> w-correct) with unit weights
     dh = oracle.image(op, d["uvw"], res, None, flags=oracle.N_DIVIDE)[0]
     exact = -2.0 * dh
-    assert np.abs(g - exact).max() <= 1e-4 * np.abs(exact).max()
+    # the gradient ends with the division by C(l) C(m), which amplifies the
+    # FP32 rounding of the transform (and its run-to-run variation with the
+    # order of the grid kernel's float atomics) by up to max 1/(C C) near the
+    # corners: compare before that division, as the image tests do
+    cc = taper_2d(op)
+    assert np.abs((g - exact) * cc).max() <= 1e-5 * np.abs(exact * cc).max()
+    assert np.abs(g - exact).max() <= 1e-3 * np.abs(exact).max()
 
     # central finite differences of the FP64 oracle at a few pixels
     for p in list(idx[:3]) + [op.n * op.n // 2 + 3]:
