@@ -41,6 +41,8 @@ struct FftArgs {
     uint8_t *tflag;          // [n_w][nt][nt]: tile holds records (is read)
     uint8_t *trow;           // [n_w][nt]: tile-row holds records
     uint8_t *pflag;          // [n_w]: plane holds records
+    unsigned long long *pmask;  // [n_w]: bit ty = tile-row ty holds records (nt <= 64)
+    unsigned long long *tmask;  // [n_w][nt]: bit tx = tile tx of the tile-row holds records (nt <= 64)
     const float2 *tw;        // [n]: e^{2 pi i j / n}
     WcArgs wc;               // image geometry, flags, taper, plane centres, weight sum
 };
@@ -236,15 +238,27 @@ __global__ void __launch_bounds__(256) fft_rowflags_kernel(FftArgs a)
 {
     const int k = blockIdx.x, nt = a.nt;
     const uint8_t *tf = a.tflag + (size_t)k * nt * nt;
+    __shared__ unsigned long long s_mask;
+    if (threadIdx.x == 0) s_mask = 0;
+    __syncthreads();
     int any_plane = 0;
     for (int ty = threadIdx.x; ty < nt; ty += blockDim.x) {
         uint8_t any = 0;
-        for (int x = 0; x < nt; ++x) any |= tf[ty * nt + x];
+        unsigned long long tm = 0;
+        for (int x = 0; x < nt; ++x) {
+            any |= tf[ty * nt + x];
+            if (x < 64 && tf[ty * nt + x]) tm |= 1ull << x;
+        }
         a.trow[k * nt + ty] = any;
+        a.tmask[k * nt + ty] = tm;
         any_plane |= any;
+        if (any && ty < 64) atomicOr(&s_mask, 1ull << ty);
     }
     any_plane = __syncthreads_or(any_plane);
-    if (threadIdx.x == 0) a.pflag[k] = (uint8_t)(any_plane != 0);
+    if (threadIdx.x == 0) {
+        a.pflag[k] = (uint8_t)(any_plane != 0);
+        a.pmask[k] = s_mask;
+    }
 }
 
 // Pass 1: ROWS = 1024 / P rows per CTA, transformed in two rounds by 512
@@ -271,21 +285,32 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         if (!any) continue;  // the same for every thread
         __syncthreads();     // the previous block's write-out has read the staging rows
         const int ntr = ty1 - ty0 + 1;
-        const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
-        for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
+        if (nt > 64) {
+            const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
+            for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
+        }
         __syncthreads();
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             // rows of round h use their own exchange areas; the staged rows of
             // round 0 are not touched by round 1
             const int c = threadIdx.x / P + h * RPR, v = v0 + c;
-            const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
             const float2 *row = a.planes + ((size_t)k * N + v) * N;
             float2 x[16];
+            if (nt <= 64) {  // the row's tiles as one bit mask
+                const unsigned long long msk = a.tmask[k * nt + (v >> l2T)];
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                const int u = t + P * s;
-                x[s] = tf[u >> l2T] ? __ldcg(row + u) : make_float2(0.0f, 0.0f);
+                for (int s = 0; s < 16; ++s) {
+                    const int u = t + P * s;
+                    x[s] = ((msk >> (u >> l2T)) & 1ull) ? __ldcg(row + u) : make_float2(0.0f, 0.0f);
+                }
+            } else {
+                const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int u = t + P * s;
+                    x[s] = tf[u >> l2T] ? __ldcg(row + u) : make_float2(0.0f, 0.0f);
+                }
             }
             fft_inv<LOGN>(x, t, c * L, sre, sim, a.tw);
             // stage the row (row stride N: the staged rows of round 0 lie below
@@ -299,6 +324,8 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
             }
         }
         __syncthreads();
+        // lanes take consecutive rows of consecutive columns, so that each warp
+        // store fills whole 32-byte sectors (ROWS x 8 bytes of a column)
         float2 *dst = a.work + (size_t)k * m * N + v0;
         for (int i = threadIdx.x; i < ROWS * m; i += blockDim.x) {
             const int r = i % ROWS, pc = i / ROWS;
@@ -379,12 +406,21 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
                 continue;
             }
             const float2 *src = col + (size_t)k * m * N;
-            const uint8_t *tr = a.trow + k * nt;
             float2 x[16];
+            if (nt <= 64) {  // the plane's tile-rows as one bit mask
+                const unsigned long long msk = live ? a.pmask[k] : 0ull;
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                const int v = t + P * s;
-                x[s] = (live && tr[v >> l2T]) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
+                for (int s = 0; s < 16; ++s) {
+                    const int v = t + P * s;
+                    x[s] = ((msk >> (v >> l2T)) & 1ull) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
+                }
+            } else {
+                const uint8_t *tr = a.trow + k * nt;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int v = t + P * s;
+                    x[s] = (live && tr[v >> l2T]) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
+                }
             }
             fft_inv<LOGN>(x, t, cb, sre, sim, a.tw);
 #pragma unroll
@@ -423,7 +459,7 @@ static bool fft_supported(const rick_params &p)
 }
 
 struct FftWorkLayout {
-    size_t tflag, trow, pflag, work, total;
+    size_t tflag, trow, pflag, pmask, tmask, work, total;
 };
 
 static FftWorkLayout fft_work_layout(const rick_params &p)
@@ -434,6 +470,8 @@ static FftWorkLayout fft_work_layout(const rick_params &p)
     L.tflag = o; o += rick_align256((size_t)p.n_w * nt * nt);
     L.trow = o;  o += rick_align256((size_t)p.n_w * nt);
     L.pflag = o; o += rick_align256((size_t)p.n_w);
+    L.pmask = o; o += rick_align256(8 * (size_t)p.n_w);
+    L.tmask = o; o += rick_align256(8 * (size_t)p.n_w * nt);
     L.work = o;  o += (size_t)p.n_w * m * p.n * sizeof(float2);
     L.total = o;
     return L;
@@ -540,6 +578,8 @@ rick_status rick_fft_wcorrect_impl(rick_plan *plan, const void *planes_dev, cons
     a.tflag = (uint8_t *)(wb + L.tflag);
     a.trow = (uint8_t *)(wb + L.trow);
     a.pflag = (uint8_t *)(wb + L.pflag);
+    a.pmask = (unsigned long long *)(wb + L.pmask);
+    a.tmask = (unsigned long long *)(wb + L.tmask);
     a.work = (float2 *)(wb + L.work);
     a.tw = plan->twid;
     a.wc = make_args(plan, ws_dev, flags);

@@ -127,7 +127,7 @@ def test_null_plan_rejected(R):
 
 def test_stream_bytes(R):
     """Staging area of the streamed path: two chunk buffers of vis and weight,
-    the fused transform's work buffer (tile, tile-row and plane flags, and the
+    the fused transform's work buffer (tile, tile-row and plane flags, tile-row and tile masks, and the
     transposed row transforms, 8 n_w n^2 bytes), plus two chunk buffers of uvw
     (given w range) or two areas holding the whole set's uvw, resident while
     its w range is found and used by alternate calls (range from the data)."""
@@ -136,7 +136,7 @@ def test_stream_bytes(R):
     given = R.make_params(256, 8, 0.035, 1, 7, w_min=-10.0, w_max=10.0, tile=32)
     data = R.make_params(256, 8, 0.035, 1, 7, tile=32)
     nt = 256 // 32
-    fwork = al(8 * nt * nt) + al(8 * nt) + al(8) + 8 * 8 * 256 * 256
+    fwork = al(8 * nt * nt) + al(8 * nt) + al(8) + al(8 * 8) + al(8 * 8 * nt) + 8 * 8 * 256 * 256
     head = R.rick_stream_bytes(given, chunk, n) - 2 * (al(24 * chunk) + al(8 * chunk) +
                                                        al(4 * chunk)) - fwork
     assert 0 < head <= 4096 + 2 * 8 * 4096  # headers and two areas of channel factors
