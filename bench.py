@@ -538,6 +538,62 @@ def run_serve(args):
     }), flush=True)
 
 
+def run_grad(args):
+    """The differentiable workload: the gradient of chi^2 = sum w |V_obs - D x|^2
+    with respect to a float32 image x of 50 point sources, on 1e7 visibilities
+    (4 channels of the LOFAR-like tracks), a 2048^2 grid, 16 w-planes, KB W=7.
+    One step = forward (DegridFn: w-spread, forward cuFFT per plane, degrid) +
+    backward (GridFn of the residual: re-weight the records, sparse grid, fused
+    inverse FFT + w-correction)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2411_07321_gb300 as P
+    from paper_2411_07321_gb300.autograd import chi2
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.WORKLOADS["diff"]
+    d = synth.generate(wl.obs)
+    n_vis = len(d["vis"])
+    t = {k: torch.from_numpy(d[k]).to(dev) for k in ("uvw", "vis", "weight")}
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                  max_vis=n_vis, device=dev)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    rng = np.random.default_rng(4)
+    x = np.zeros((wl.n, wl.n), np.float32)
+    x.flat[rng.choice(wl.n * wl.n, 50, replace=False)] = \
+        np.exp(rng.uniform(np.log(0.1), np.log(10.0), 50))
+    xt = torch.from_numpy(x).to(dev).requires_grad_(True)
+
+    def step():
+        xt.grad = None
+        chi2(xt, im, t["vis"], t["weight"]).backward()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({
+        "metric": METRIC, "mode": "grad", "unit": "vis/s", "value": n_vis / (ms * 1e-3),
+        "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"diff: {n_vis} visibilities (60 stations, 4 channels), "
+                               f"{wl.n}^2 grid, {wl.n_w} w-planes, Kaiser-Bessel support "
+                               f"{wl.support}; gradient of chi^2 wrt a 50-source float32 image",
+                   "step": "chi2 forward (predict) + backward (grid of the residual)",
+                   "fused_transform": im.fused},
+    }), flush=True)
+    im.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,6 +608,8 @@ def main():
                     help="visibilities per chunk of the streamed end-to-end call")
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload instead (its own JSON line)")
+    ap.add_argument("--grad", action="store_true",
+                    help="time the chi^2 gradient on the differentiable workload (own JSON line)")
     ap.add_argument("--serve-jobs", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--n-vis", type=int, default=None,
@@ -565,6 +623,8 @@ def main():
         synth.scaled(args.workload, n_keep=args.n_vis)
     if args.serve:
         run_serve(args)
+    elif args.grad:
+        run_grad(args)
     elif args.impl == "reference":
         run_reference(args, wl)
     else:
