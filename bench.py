@@ -567,9 +567,16 @@ def run_grad(args):
         np.exp(rng.uniform(np.log(0.1), np.log(10.0), 50))
     xt = torch.from_numpy(x).to(dev).requires_grad_(True)
 
-    def step():
+    def step(ev=None):
         xt.grad = None
-        chi2(xt, im, t["vis"], t["weight"]).backward()
+        if ev is not None:
+            ev[0].record()
+        loss = chi2(xt, im, t["vis"], t["weight"])
+        if ev is not None:
+            ev[1].record()
+        loss.backward()
+        if ev is not None:
+            ev[2].record()
 
     for _ in range(args.warmup):
         step()
@@ -581,9 +588,16 @@ def run_grad(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for ev in evs:
+        step(ev)
+    torch.cuda.synchronize()
+    fwd = statistics.mean(ev[0].elapsed_time(ev[1]) for ev in evs)
+    bwd = statistics.mean(ev[1].elapsed_time(ev[2]) for ev in evs)
     print(json.dumps({
         "metric": METRIC, "mode": "grad", "unit": "vis/s", "value": n_vis / (ms * 1e-3),
         "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
+        "ms_forward": fwd, "ms_backward": bwd,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"diff: {n_vis} visibilities (60 stations, 4 channels), "
                                f"{wl.n}^2 grid, {wl.n_w} w-planes, Kaiser-Bessel support "
