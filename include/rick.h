@@ -354,6 +354,22 @@ rick_status rick_fft_wcorrect(rick_plan *plan, const void *planes_dev, const voi
                               int32_t sparse, void *work_dev, size_t work_bytes,
                               float *image_dev, uint32_t flags, void *stream);
 
+/* The adjoint of rick_fft_wcorrect for degridding: w-spreading (the transpose
+ * of the w-correction, Eq. 2) fused with the forward FFT of every plane, the
+ * adjoint of §2 steps 3-4.  planes[k] = forward 2D DFT (e^{-2 pi i}) of
+ * image[q][p] s(p,q) (-1)^(p+q) e^{-2 pi i w_k (n - 1)} (zero outside the crop),
+ * the same as rick_wspread followed by rick_fft_wplanes(-1) with the same flags,
+ * up to FP32 rounding order -- but written only for the uv-tiles with gridding
+ * work items in ws_dev, the only cells rick_degrid reads for that binning; the
+ * other tiles of planes_dev keep what they held.  Two passes of 1D transforms
+ * (along q per image column, then along p per row of the tile-rows with
+ * records).  work_dev as for rick_fft_wcorrect (the two calls may share it; its
+ * contents are scratch).  RICK_EINVAL for an n outside 256 ... 8192, a short or
+ * misaligned buffer or unknown flags. */
+rick_status rick_wspread_fft(rick_plan *plan, const float *image_dev, const void *ws_dev,
+                             void *work_dev, size_t work_bytes, void *planes_dev, uint32_t flags,
+                             void *stream);
+
 /* Adjoint of rick_wcorrect_stack (same flags): for every plane k,
  * planes[k][q][p] = image[q][p] s(p,q) (-1)^(p+q) e^{-2 pi i w_k (n - 1)},
  * the m x m image zero-padded to the n x n grid frame (cells outside the

@@ -37,6 +37,7 @@
 struct FftArgs {
     int n, n_w, nt, log2T;
     const float2 *planes;    // [n_w][n][n]
+    float2 *planes_out;      // [n_w][n][n]: the adjoint's output (tiles with records)
     float2 *work;            // [n_w][m][n]: row transforms, transposed
     uint8_t *tflag;          // [n_w][nt][nt]: tile holds records (is read)
     uint8_t *trow;           // [n_w][nt]: tile-row holds records
@@ -451,6 +452,187 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
 }
 
 // ------------------------------------------------------------------------
+// The adjoint: w-spreading (the transpose of the w-correction) fused with the
+// forward FFT of every plane, for the tiles that records reach (the only cells
+// degridding reads).  Plane k of the adjoint is the forward 2D DFT of
+// G_k[q][p] = image[q][p] s(p, q) e^{-2 pi i w_k (n - 1)} (s with the
+// checkerboard sign; zero outside the crop).  A forward DFT is the conjugate of
+// the inverse DFT of the conjugate, so both passes reuse the inverse
+// transforms:
+//  A. per image column p and plane k: z_k[p][v] = sum_q conj(G_k[q][p])
+//     e^{+2 pi i v q / n}, conj(G) = image s e^{+2 pi i w_k (n - 1)} (the phase
+//     walked by the step D with exact anchors every 8 planes, as in the plane-sum
+//     kernels), stored transposed for the tile-rows with records;
+//  B. per row v of those tile-rows: planes[k][v][u] = conj(sum_p z_k[p][v]
+//     e^{+2 pi i u p / n}) for the tiles with records.
+
+template <int LOGN>
+struct AdjColShape {
+    static constexpr int N = 1 << LOGN, P = N / 16;
+    static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
+    static constexpr int XE = COLS * XLen<N>::L;
+    static constexpr size_t SMEM = sizeof(float) * (2 * XE + 3 * NE);
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <= 256 ? 2 : 1)
+    fft_cols_adj_kernel(FftArgs a)
+{
+    using S = AdjColShape<LOGN>;
+    constexpr int N = S::N, P = S::P, NT = S::NT, COLS = S::COLS, NE = S::NE, XE = S::XE;
+    extern __shared__ float fsm[];
+    float *sre = fsm, *sim = fsm + XE;
+    float *g_hi = fsm + 2 * XE, *g_lo = g_hi + NE, *g_a = g_lo + NE;
+    const WcArgs &w = a.wc;
+    const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * XLen<N>::L;
+    const int m = w.m, off = w.off, nt = a.nt, l2T = a.log2T;
+    const int pc = blockIdx.x * COLS + c;  // image column
+    const bool live = pc < m;
+    const int p = (live ? pc : 0) + off;
+    const bool fp32ph = (w.flags & RICK_PHASE_FP32) != 0;
+    float inv_sumw;
+    {
+        const double sw = w.hdr->stats.sum_weight;  // nothing gridded: no normalisation
+        inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
+    }
+    const float4 dwp = __ldg(&w.wplane[w.n_w]);
+    float2 D[16], ph[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int q = t + P * s, gi = s * NT + threadIdx.x;
+        D[s] = make_float2(1.0f, 0.0f);
+        ph[s] = make_float2(1.0f, 0.0f);
+        if (live && q >= off && q < off + m) {
+            const PixelGeom g = pixel_geom(w, p, q, inv_sumw);
+            g_hi[gi] = g.nm1.hi;
+            g_lo[gi] = fp32ph ? g.nm1_f : g.nm1.lo;
+            g_a[gi] = w.image_in[(size_t)(q - off) * m + pc] * g.scale;
+            if (!fp32ph) {
+                const float fd = ff_frac(ff_mul(ff{dwp.x, dwp.y}, g.nm1));
+                sincospif(2.0f * fd, &D[s].y, &D[s].x);
+            }
+        } else {
+            g_hi[gi] = g_lo[gi] = g_a[gi] = 0.0f;
+        }
+    }
+    const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
+    float2 *dst = a.work + (size_t)(live ? pc : 0) * N;
+    for (int k = 0; k < w.n_w; ++k) {
+        if (k % bs == 0) {  // exact phase of the anchor plane
+            const float4 wk = __ldg(&w.wplane[k]);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int gi = s * NT + threadIdx.x;
+                PixelGeom g;
+                g.nm1 = ff{g_hi[gi], g_lo[gi]};
+                g.nm1_f = g_lo[gi];
+                wphase(w, wk, g, &ph[s].x, &ph[s].y);
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) ph[s] = cmul(ph[s], D[s]);
+        }
+        if (!a.pflag[k]) continue;  // degridding reads nothing of this plane
+        float2 x[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const float av = g_a[s * NT + threadIdx.x];
+            x[s] = make_float2(av * ph[s].x, av * ph[s].y);
+        }
+        fft_inv<LOGN>(x, t, cb, sre, sim, a.tw);
+        if (!live) continue;
+        float2 *col = dst + (size_t)k * m * N;
+        if (nt <= 64) {
+            const unsigned long long msk = a.pmask[k];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int v = t + P * s;
+                if ((msk >> (v >> l2T)) & 1ull) __stcg(col + v, x[s]);
+            }
+        } else {
+            const uint8_t *tr = a.trow + k * nt;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int v = t + P * s;
+                if (tr[v >> l2T]) __stcg(col + v, x[s]);
+            }
+        }
+    }
+}
+
+// Pass B: ROWS = 1024 / P rows per CTA gathered from the transposed pass-A
+// output (lanes take consecutive rows of consecutive columns: whole 32-byte
+// sectors), staged in shared memory, transformed in two rounds by 512 threads
+// (exchange arrays after the staged rows), conjugated and written to the
+// tiles with records.  Persistent over (plane, block of ROWS rows).
+template <int LOGN>
+__global__ void __launch_bounds__(512, 1) fft_rows_adj_kernel(FftArgs a)
+{
+    constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
+    constexpr int ROT = ROWS >= 32 ? 1 : 32 / ROWS;
+    constexpr int L = XLen<N>::L, SW = ROWS * N + RPR * L;  // words of one array
+    extern __shared__ float fsm[];
+    float *gre = fsm, *gim = fsm + SW;                   // staged rows (row stride N)
+    float *xre = gre + ROWS * N, *xim = gim + ROWS * N;  // exchange arrays
+    __shared__ uint8_t s_tf[1024];
+    const int t = threadIdx.x % P;
+    const int nt = a.nt, l2T = a.log2T, m = a.wc.m, off = a.wc.off;
+    const int nvb = N / ROWS, items = a.n_w * nvb;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int k = item / nvb, v0 = (item - k * nvb) * ROWS;
+        const int ty0 = v0 >> l2T, ty1 = (v0 + ROWS - 1) >> l2T;
+        bool any = false;
+        for (int ty = ty0; ty <= ty1; ++ty) any |= a.trow[k * nt + ty] != 0;
+        if (!any) continue;  // the same for every thread
+        __syncthreads();     // the previous block is done with the staged rows
+        const int ntr = ty1 - ty0 + 1;
+        if (nt > 64) {
+            const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
+            for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
+        }
+        // gather: rows v0 .. v0 + ROWS - 1 of the crop columns (pass A wrote only
+        // the tile-rows with records); zeros elsewhere
+        const float2 *src = a.work + (size_t)k * m * N + v0;
+        for (int i = threadIdx.x; i < ROWS * N; i += blockDim.x) {
+            const int r = i % ROWS, p = i / ROWS, pc = p - off;
+            const float2 z = (pc >= 0 && pc < m && a.trow[k * nt + ((v0 + r) >> l2T)])
+                                 ? __ldcg(src + (size_t)pc * N + r) : make_float2(0.0f, 0.0f);
+            const int j = swz(r * N + p) ^ ((r * ROT) & 31);
+            gre[j] = z.x;
+            gim[j] = z.y;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int c = threadIdx.x / P + h * RPR, v = v0 + c;
+            float2 x[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int j = swz(c * N + t + P * s) ^ ((c * ROT) & 31);
+                x[s] = make_float2(gre[j], gim[j]);
+            }
+            fft_inv<LOGN>(x, t, (threadIdx.x / P) * L, xre, xim, a.tw);
+            float2 *row = a.planes_out + ((size_t)k * N + v) * N;
+            if (nt <= 64) {
+                const unsigned long long msk = a.tmask[k * nt + (v >> l2T)];
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int u = t + P * s;
+                    if ((msk >> (u >> l2T)) & 1ull) row[u] = make_float2(x[s].x, -x[s].y);
+                }
+            } else {
+                const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int u = t + P * s;
+                    if (tf[u >> l2T]) row[u] = make_float2(x[s].x, -x[s].y);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
 // Host side
 
 static bool fft_supported(const rick_params &p)
@@ -544,6 +726,31 @@ static bool fft_args_ok(const rick_plan *plan, const void *ws_dev, const void *w
            !((uintptr_t)work_dev & 255) && work_bytes >= fft_work_layout(plan->p).total;
 }
 
+// Kernel arguments of the fused transforms (the planes and image set by the caller).
+static FftArgs fft_args(rick_plan *plan, const void *ws_dev, void *work_dev, uint32_t flags)
+{
+    const rick_params &p = plan->p;
+    const FftWorkLayout L = fft_work_layout(p);
+    FftArgs a;
+    a.n = p.n;
+    a.n_w = p.n_w;
+    a.nt = p.n / p.tile;
+    a.log2T = 0;
+    while ((1 << a.log2T) < p.tile) ++a.log2T;
+    a.planes = NULL;
+    a.planes_out = NULL;
+    char *wb = (char *)work_dev;
+    a.tflag = (uint8_t *)(wb + L.tflag);
+    a.trow = (uint8_t *)(wb + L.trow);
+    a.pflag = (uint8_t *)(wb + L.pflag);
+    a.pmask = (unsigned long long *)(wb + L.pmask);
+    a.tmask = (unsigned long long *)(wb + L.tmask);
+    a.work = (float2 *)(wb + L.work);
+    a.tw = plan->twid;
+    a.wc = make_args(plan, ws_dev, flags);
+    return a;
+}
+
 rick_status rick_fft_tiles_impl(rick_plan *plan, const void *ws_dev, void *work_dev,
                                 size_t work_bytes, int mode, cudaStream_t st)
 {
@@ -566,23 +773,8 @@ rick_status rick_fft_wcorrect_impl(rick_plan *plan, const void *planes_dev, cons
         ((uintptr_t)planes_dev & 7) || ((uintptr_t)image_dev & 3))
         return RICK_EINVAL;
     const rick_params &p = plan->p;
-    const FftWorkLayout L = fft_work_layout(p);
-    FftArgs a;
-    a.n = p.n;
-    a.n_w = p.n_w;
-    a.nt = p.n / p.tile;
-    a.log2T = 0;
-    while ((1 << a.log2T) < p.tile) ++a.log2T;
+    FftArgs a = fft_args(plan, ws_dev, work_dev, flags);
     a.planes = (const float2 *)planes_dev;
-    char *wb = (char *)work_dev;
-    a.tflag = (uint8_t *)(wb + L.tflag);
-    a.trow = (uint8_t *)(wb + L.trow);
-    a.pflag = (uint8_t *)(wb + L.pflag);
-    a.pmask = (unsigned long long *)(wb + L.pmask);
-    a.tmask = (unsigned long long *)(wb + L.tmask);
-    a.work = (float2 *)(wb + L.work);
-    a.tw = plan->twid;
-    a.wc = make_args(plan, ws_dev, flags);
     a.wc.image_out = image_dev;
     fft_rowflags_kernel<<<p.n_w, 256, 0, st>>>(a);
     RICK_LAUNCH_CHECK(plan);
@@ -594,6 +786,61 @@ rick_status rick_fft_wcorrect_impl(rick_plan *plan, const void *planes_dev, cons
     case 2048: err = launch_fft_wc<11>(a, plan->num_sms, st); break;
     case 4096: err = launch_fft_wc<12>(a, plan->num_sms, st); break;
     case 8192: err = launch_fft_wc<13>(a, plan->num_sms, st); break;
+    }
+    plan->launches += 2;
+    RICK_CUDA_TRY(plan, err);
+    return RICK_OK;
+}
+
+template <int LOGN>
+static cudaError_t launch_wspread_fft(const FftArgs &a, int num_sms, cudaStream_t st)
+{
+    using S = AdjColShape<LOGN>;
+    constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
+    const size_t rows_smem = 2 * sizeof(float) * (ROWS * N + RPR * XLen<N>::L);
+    cudaError_t e = cudaFuncSetAttribute(fft_cols_adj_kernel<LOGN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fft_rows_adj_kernel<LOGN>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);
+    if (e != cudaSuccess) return e;
+    const int m = a.wc.m;
+    fft_cols_adj_kernel<LOGN><<<(unsigned)((m + S::COLS - 1) / S::COLS), S::NT, S::SMEM, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int items = a.n_w * (N / ROWS);
+    fft_rows_adj_kernel<LOGN><<<(unsigned)min(items, num_sms), 512, rows_smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+extern "C" rick_status rick_wspread_fft(rick_plan *plan, const float *image_dev,
+                                        const void *ws_dev, void *work_dev, size_t work_bytes,
+                                        void *planes_dev, uint32_t flags, void *stream)
+{
+    if (!plan || !image_dev || !ws_dev || !work_dev || !planes_dev || !valid_flags(flags))
+        return RICK_EINVAL;
+    if (plan->sticky != RICK_OK) return plan->sticky;
+    if (!fft_args_ok(plan, ws_dev, work_dev, work_bytes) || ((uintptr_t)planes_dev & 7) ||
+        ((uintptr_t)image_dev & 3))
+        return RICK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    rick_status s = rick_fft_tiles_impl(plan, ws_dev, work_dev, work_bytes, 1, st);
+    if (s != RICK_OK) return s;
+    const rick_params &p = plan->p;
+    FftArgs a = fft_args(plan, ws_dev, work_dev, flags);
+    a.wc.image_in = image_dev;
+    a.planes_out = (float2 *)planes_dev;
+    fft_rowflags_kernel<<<p.n_w, 256, 0, st>>>(a);
+    RICK_LAUNCH_CHECK(plan);
+    cudaError_t err = cudaErrorInvalidValue;
+    switch (p.n) {
+    case 256: err = launch_wspread_fft<8>(a, plan->num_sms, st); break;
+    case 512: err = launch_wspread_fft<9>(a, plan->num_sms, st); break;
+    case 1024: err = launch_wspread_fft<10>(a, plan->num_sms, st); break;
+    case 2048: err = launch_wspread_fft<11>(a, plan->num_sms, st); break;
+    case 4096: err = launch_wspread_fft<12>(a, plan->num_sms, st); break;
+    case 8192: err = launch_wspread_fft<13>(a, plan->num_sms, st); break;
     }
     plan->launches += 2;
     RICK_CUDA_TRY(plan, err);

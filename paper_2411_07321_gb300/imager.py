@@ -166,12 +166,7 @@ class Imager:
         sum (rick_fft_wcorrect): the image of planes from grid() or
         grid_sparse() (sparse: read only the tiles with records); the planes
         are not modified."""
-        need = R.rick_fft_wcorrect_bytes(self.plan)
-        if need is None:
-            raise ValueError(f"the fused transform does not cover n = {self.n}")
-        if self._fwork is None or self._fwork.numel() < need:
-            self._fwork = None
-            self._fwork = torch.empty(need, dtype=torch.uint8, device=self.device)
+        self._fused_work()
         if out is None:
             out = torch.empty((self.m, self.m), dtype=torch.float32, device=self.device)
         self._check(out, torch.float32, (self.m, self.m), "image")
@@ -179,6 +174,24 @@ class Imager:
                             self._fwork.data_ptr(), self._fwork.numel(), out.data_ptr(), flags,
                             self._stream())
         return out
+
+    def _fused_work(self) -> torch.Tensor:
+        need = R.rick_fft_wcorrect_bytes(self.plan)
+        if need is None:
+            raise ValueError(f"the fused transform does not cover n = {self.n}")
+        if self._fwork is None or self._fwork.numel() < need:
+            self._fwork = None
+            self._fwork = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._fwork
+
+    def wspread_fft(self, image: torch.Tensor, flags: int = IMAGE_FLAGS):
+        """w-spreading fused with the forward FFT of the planes (rick_wspread_fft):
+        the adjoint's planes, written for the tiles the last binning's records
+        reach (what degrid reads)."""
+        self._check(image, torch.float32, (self.m, self.m), "image")
+        w = self._fused_work()
+        R.rick_wspread_fft(self.plan, image.data_ptr(), self.ws.data_ptr(), w.data_ptr(),
+                           w.numel(), self.planes.data_ptr(), flags, self._stream())
 
     def fused_tiles(self) -> tuple[int, int]:
         """(plane, uv-tile) and (plane, tile-row) pairs the last fft_wcorrect read
@@ -223,10 +236,15 @@ class Imager:
         return self.wcorrect(flags, out)
 
     def adjoint(self, image: torch.Tensor, weight=None, flags: int = IMAGE_FLAGS,
-                out=None) -> torch.Tensor:
-        """Transpose of image_from_binned: w-spread -> forward FFT -> degrid."""
-        self.wspread(image, flags)
-        self.fft(-1)
+                out=None, fused: bool | None = None) -> torch.Tensor:
+        """Transpose of image_from_binned: w-spread -> forward FFT -> degrid (the
+        first two fused where the imager uses the fused transform, unless
+        ``fused`` is False)."""
+        if self.fused if fused is None else fused:
+            self.wspread_fft(image, flags)
+        else:
+            self.wspread(image, flags)
+            self.fft(-1)
         return self.degrid(weight, out)
 
     def predict(self, image: torch.Tensor, out=None) -> torch.Tensor:

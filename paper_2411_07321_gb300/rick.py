@@ -61,7 +61,7 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
            "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
-           "rick_fft_wcorrect"]
+           "rick_fft_wcorrect", "rick_wspread_fft"]
 
 
 def _load():
@@ -95,6 +95,7 @@ def _load():
         "rick_grid_sparse": [vp, vp, vp, vp],
         "rick_fft_wcorrect_bytes": [vp, ctypes.POINTER(sz)],
         "rick_fft_wcorrect": [vp, vp, vp, i32, vp, sz, vp, u32, vp],
+        "rick_wspread_fft": [vp, vp, vp, vp, sz, vp, u32, vp],
         "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
         "rick_image_host": [vp, i64, vp, vp, vp, vp, sz, vp, sz, vp, vp, u32, vp, vp],
         "rick_bin_channels": [vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, vp],
@@ -292,6 +293,11 @@ def rick_fft_wcorrect(plan, planes, ws, sparse, work, work_bytes, image, flags, 
     _check("rick_fft_wcorrect", _L.rick_fft_wcorrect(plan, planes, ws, int(sparse), work,
                                                      int(work_bytes), image, int(flags),
                                                      stream or None))
+
+
+def rick_wspread_fft(plan, image, ws, work, work_bytes, planes, flags, stream) -> None:
+    _check("rick_wspread_fft", _L.rick_wspread_fft(plan, image, ws, work, int(work_bytes), planes,
+                                                   int(flags), stream or None))
 
 
 def rick_stream_bytes(params: rick_params, max_vis: int, n_vis: int) -> int:

@@ -168,3 +168,58 @@ def test_rejects_bad_arguments(P):
                                 args[1], img.data_ptr(), args[2], s)
         assert e.value.status == R.RICK_EINVAL
     im.close()
+
+
+@pytest.mark.parametrize("kernel,support,tile,n_w,image_n,n", [
+    ("kb", 7, 32, 8, None, 256), ("gauss", 7, 16, 13, None, 256), ("kb", 9, 32, 16, 128, 256),
+    ("kb", 1, 8, 5, 200, 256), ("kb", 7, 16, 4, None, 512), ("kb", 7, 8, 3, None, 1024)])
+def test_adjoint_matches_cufft_adjoint(P, kernel, support, tile, n_w, image_n, n):
+    """The fused adjoint (rick_wspread_fft, then degrid) equals w-spread + cuFFT
+    forward + degrid on the same binning, with the planes' record-free tiles
+    left as garbage for the fused one; tile 8 at n = 1024 takes the per-tile
+    flags instead of the bit masks (n / tile > 64)."""
+    dev = torch.device("cuda:0")
+    t = small(30001)
+    wl = synth.WORKLOADS["small"]
+    fov = wl.fov * n / 256
+    im = P.Imager(n, n_w, fov, kernel=kernel, support=support, tile=tile, max_vis=30001,
+                  device=dev, image_n=image_n)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    cc = taper_2d(n, kernel, support, im.m)
+    rng = np.random.default_rng(n + n_w)
+    y = torch.from_numpy((rng.normal(size=(im.m, im.m)) * cc).astype(np.float32)).to(dev)
+    for flags in (P.IMAGE_FLAGS, P.PREDICT_FLAGS, P.rick.RICK_NORMALIZE | P.rick.RICK_PHASE_FP32):
+        im.planes.fill_(float("nan"))
+        vf = im.adjoint(y, t["weight"], flags, fused=True).clone()
+        vc = im.adjoint(y, t["weight"], flags, fused=False)
+        torch.cuda.synchronize()
+        a, b = vf.cpu().numpy(), vc.cpu().numpy()
+        err = np.abs(a - b).max() / np.abs(b).max()
+        print(f"{kernel} W={support} T={tile} n={n} n_w={n_w} crop={image_n} flags={flags}: "
+              f"fused adjoint vs cuFFT adjoint {err:.2e} of max |V|")
+        assert np.isfinite(a).all()
+        assert err < 1e-5
+    im.close()
+
+
+def test_adjoint_dot_product_identity(P):
+    """<A x, y> = Re <x, A^H y> with both A (image_from_binned) and A^H (adjoint)
+    on the fused transforms, in FP32 (1e-5 of the sum of |terms|)."""
+    dev = torch.device("cuda:0")
+    t = small(20000)
+    wl = synth.WORKLOADS["small"]
+    im = P.Imager(wl.n, 8, wl.fov, kernel="kb", support=7, tile=32, max_vis=20000, device=dev)
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    rng = np.random.default_rng(11)
+    x = torch.from_numpy((rng.normal(size=20000) + 1j * rng.normal(size=20000))
+                         .astype(np.complex64)).to(dev)
+    y = torch.from_numpy(rng.normal(size=(wl.n, wl.n)).astype(np.float32)).to(dev)
+    im.bin_values(x, t["weight"])
+    ax = im.image_from_binned().double()
+    aty = im.adjoint(y, t["weight"]).to(torch.complex128)
+    lhs = float((ax * y.double()).sum())
+    rhs = float((x.to(torch.complex128).conj() * aty).sum().real)
+    scale = float((ax.abs() * y.double().abs()).sum())
+    print(f"<Ax,y> {lhs:.9e}  Re<x,A^H y> {rhs:.9e}  rel {abs(lhs - rhs) / scale:.2e}")
+    assert abs(lhs - rhs) <= 1e-5 * scale
+    im.close()
