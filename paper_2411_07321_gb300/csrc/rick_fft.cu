@@ -28,6 +28,10 @@
 // per-stage tables computed in FP64 at plan creation and rounded once, laid
 // out so that a warp reads consecutive entries (they stay in L1; the plane
 // data is read around it).
+//
+// The adjoint (w-spreading + forward FFT, for degridding) runs the same two
+// passes in the opposite order on the same inverse transforms, by conjugation;
+// it writes only the tiles that degridding reads (see the section below).
 #include "rick_common.cuh"
 #include "rick_wphase.cuh"
 
@@ -44,10 +48,13 @@ struct FftArgs {
     uint8_t *pflag;          // [n_w]: plane holds records
     unsigned long long *pmask;  // [n_w]: bit ty = tile-row ty holds records (nt <= 64)
     unsigned long long *tmask;  // [n_w][nt]: bit tx = tile tx of the tile-row holds records (nt <= 64)
-    const float2 *tw;        // [n]: e^{2 pi i j / n}
+    const float2 *tw;        // the plan's stage twiddle tables (twiddle_kernel)
     WcArgs wc;               // image geometry, flags, taper, plane centres, weight sum
 };
 
+// Staged rows (written out or gathered transposed): an XOR swizzle of the low
+// five bits, which with a per-row rotation keeps both the row-wise and the
+// column-wise accesses free of bank conflicts.
 static __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 31); }
 
 // Exchange arrays: one word of padding per 32 (a + a/32) keeps the stages'
