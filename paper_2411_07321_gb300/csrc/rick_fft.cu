@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) fft_rowflags_kernel(FftArgs a)
     }
 }
 
-// Pass 1: ROWS = 1024 / P rows per CTA, transformed in two rounds by 512
+// Pass 1: ROWS = 1024 / P rows per CTA, transformed in two batches by 512
 // threads (a thread's 16 points and twiddles then stay in registers), staged in
 // shared memory and written out transposed.  Persistent over (plane, block of
 // ROWS rows); blocks whose tile-rows hold no records are skipped.
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         __syncthreads();
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-            // rows of round h use their own exchange areas; the staged rows of
-            // round 0 are not touched by round 1
+            // the rows of batch h use their own exchange areas; the staged rows
+            // of batch 0 are not touched by batch 1
             const int c = threadIdx.x / P + h * RPR, v = v0 + c;
             const float2 *row = a.planes + ((size_t)k * N + v) * N;
             float2 x[16];
@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
                 }
             }
             fft_inv<LOGN>(x, t, c * L, sre, sim, a.tw);
-            // stage the row (row stride N: the staged rows of round 0 lie below
-            // the exchange arrays of round 1), XOR-swizzled and rotated per row
+            // stage the row (row stride N: the staged rows of batch 0 lie below
+            // the exchange arrays of batch 1), XOR-swizzled and rotated per row
             // so that the transposed read-out is free of bank conflicts too
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
 
 // Pass B: ROWS = 1024 / P rows per CTA gathered from the transposed pass-A
 // output (lanes take consecutive rows of consecutive columns: whole 32-byte
-// sectors), staged in shared memory, transformed in two rounds by 512 threads
+// sectors), staged in shared memory, transformed in two batches by 512 threads
 // (exchange arrays after the staged rows), conjugated and written to the
 // tiles with records.  Persistent over (plane, block of ROWS rows).
 template <int LOGN>
