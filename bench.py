@@ -142,6 +142,23 @@ def traffic_of(stage: str, n_vis: int):
     return None
 
 
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The largest of the ranks' times in ms (the whole job ends with its slowest
+    replica); ``ms`` itself without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, steps: int, world: int, ms: float) -> float:
+    """Units per second of the whole job: every replica processes units_per_rank
+    units per step, and the job takes the slowest replica's ms for all steps."""
+    return units_per_rank * steps * world / (ms / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -288,14 +305,10 @@ def run_ours(args, wl):
         dist.barrier()
     clk = clocks.stop(h0, h1)
     launches = im.launches() - l0
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
     stage_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
                 for i, name in enumerate(["bin", "grid", "fft_wcorrect"])}
-    value = n_vis * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(n_vis, args.steps, world, ms)
     tiles, tile_rows = im.fused_tiles()
     # the unfused stages (grid clearing every tile, cuFFT in place, plane sum),
     # timed after the headline steps, for comparison
@@ -327,11 +340,8 @@ def run_ours(args, wl):
             call()
         e1.record()
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1)
+        t = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         if dist:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
             dist.barrier()
         return t
 
@@ -364,7 +374,7 @@ def run_ours(args, wl):
         call = (f"Imager.image_streamed (rick_image_host), chunks of {min(args.chunk, n_vis)} "
                 f"visibilities, w range from the data")
     ims.close()
-    e2e_value = n_vis * args.steps * world / (e2e_ms / 1e3)
+    e2e_value = whole_job_rate(n_vis, args.steps, world, e2e_ms)
 
     peak, peak_kind = peaks()
     alg = algorithmic_bytes(n_vis, n_binned, wl.n, wl.n_w, wl.tile, tiles, tile_rows)
@@ -399,7 +409,7 @@ def run_ours(args, wl):
                 "d2h_bytes_per_step": wl.n * wl.n * 4, "ms_per_step": e2e_ms / args.steps,
                 "call": call,
                 "per_visibility_uvw": {
-                    "value": n_vis * args.steps * world / (e2e_vis_ms / 1e3),
+                    "value": whole_job_rate(n_vis, args.steps, world, e2e_vis_ms),
                     "ms_per_step": e2e_vis_ms / args.steps,
                     "h2d_bytes_per_step": n_vis * (24 + 8 + 4),
                     "call": "Imager.image_streamed (rick_image_host), uvw per visibility"},
