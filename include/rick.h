@@ -325,6 +325,13 @@ rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_dev, const v
  * coverage is most of the 8 n_w n^2 bytes rick_grid writes. */
 rick_status rick_grid_sparse(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream);
 
+/* Bytes of the fused transform's work buffer (rick_fft_wcorrect,
+ * rick_wspread_fft) for plans of these parameters, without a plan: 0 where n is
+ * outside 256 ... 8192.  Host-only; enqueues nothing.  RICK_EINVAL for invalid
+ * parameters.  For sizing device memory before plans exist (the serving
+ * admission). */
+rick_status rick_fused_work_bytes(const rick_params *params, size_t *work_bytes);
+
 /* Bytes of the work buffer of rick_fft_wcorrect for this plan.  Its layout,
  * each piece starting on a 256-byte boundary: uint8 tile flags [n_w][nt][nt]
  * (nt = n / tile; 1: the tile was read), uint8 tile-row flags [n_w][nt],

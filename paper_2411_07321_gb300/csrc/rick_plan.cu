@@ -397,6 +397,15 @@ extern "C" rick_status rick_workspace_bytes(const rick_params *params, int64_t n
     return RICK_OK;
 }
 
+extern "C" rick_status rick_fused_work_bytes(const rick_params *params, size_t *work_bytes)
+{
+    if (!work_bytes) return RICK_EINVAL;
+    rick_status st = check_params(params);
+    if (st != RICK_OK) return st;
+    *work_bytes = rick_fft_work_bytes(params);
+    return RICK_OK;
+}
+
 extern "C" rick_status rick_plan_fft_bytes(const rick_plan *plan, size_t *fft_bytes)
 {
     if (!plan || !fft_bytes) return RICK_EINVAL;

@@ -61,7 +61,7 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
            "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
-           "rick_fft_wcorrect", "rick_wspread_fft"]
+           "rick_fft_wcorrect", "rick_wspread_fft", "rick_fused_work_bytes"]
 
 
 def _load():
@@ -94,6 +94,7 @@ def _load():
         "rick_grid_accumulate": [vp, vp, vp, vp],
         "rick_grid_sparse": [vp, vp, vp, vp],
         "rick_fft_wcorrect_bytes": [vp, ctypes.POINTER(sz)],
+        "rick_fused_work_bytes": [P, ctypes.POINTER(sz)],
         "rick_fft_wcorrect": [vp, vp, vp, i32, vp, sz, vp, u32, vp],
         "rick_wspread_fft": [vp, vp, vp, vp, sz, vp, u32, vp],
         "rick_stream_bytes": [P, i64, i64, ctypes.POINTER(sz)],
@@ -286,6 +287,15 @@ def rick_fft_wcorrect_bytes(plan) -> int | None:
     if s == RICK_EINVAL:
         return None
     _check("rick_fft_wcorrect_bytes", s)
+    return b.value
+
+
+def rick_fused_work_bytes(params: rick_params) -> int:
+    """Work bytes of the fused transform for plans of these parameters (0 where
+    it does not cover n); host-only."""
+    b = ctypes.c_size_t()
+    _check("rick_fused_work_bytes", _L.rick_fused_work_bytes(ctypes.byref(params),
+                                                             ctypes.byref(b)))
     return b.value
 
 

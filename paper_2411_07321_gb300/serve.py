@@ -161,8 +161,9 @@ def slot_footprint(job: ImagingJob) -> int:
     cap = capacity_class(job.n_vis)
     ws, planes = R.rick_workspace_bytes(p, cap)
     # planes + workspace + cuFFT area (bounded by the planes' size for in-place
-    # C2C) + image + resident input buffers (uvw, vis, weight)
-    return ws + 2 * planes + job.n * job.n * 4 + cap * (24 + 8 + 4)
+    # C2C) + the fused transform's work buffer + image + resident input buffers
+    # (uvw, vis, weight)
+    return ws + 2 * planes + R.rick_fused_work_bytes(p) + job.n * job.n * 4 + cap * (24 + 8 + 4)
 
 
 class _Slot:

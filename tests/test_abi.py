@@ -150,3 +150,21 @@ def test_stream_bytes(R):
     assert R.rick_stream_bytes(given, chunk, 10 * n) == R.rick_stream_bytes(given, chunk, n)
     with pytest.raises(R.RickError):
         R.rick_stream_bytes(given, -1, n)
+
+
+def test_fused_work_bytes(R):
+    """The fused transform's work buffer without a plan: flags and bit masks, then
+    the transposed row transforms (8 n_w image_n n bytes); the same bytes the
+    streamed call stages; none where the fused transform does not cover n."""
+    al = lambda x: (x + 255) // 256 * 256
+    for n, n_w, tile, image_n in ((256, 8, 32, 0), (4096, 16, 64, 0), (8192, 3, 8, 4096)):
+        p = R.make_params(n, n_w, 0.03, 1, 7, tile=tile, image_n=image_n)
+        nt, m = n // tile, image_n or n
+        want = al(n_w * nt * nt) + al(n_w * nt) + al(n_w) + al(8 * n_w) + al(8 * n_w * nt) + \
+            8 * n_w * m * n
+        assert R.rick_fused_work_bytes(p) == want
+    assert R.rick_fused_work_bytes(R.make_params(128, 4, 0.03, 1, 7, tile=32)) == 0
+    assert R.rick_fused_work_bytes(R.make_params(16384, 4, 0.03, 1, 7, tile=64)) == 0
+    with pytest.raises(R.RickError) as e:
+        R.rick_fused_work_bytes(R.make_params(100, 4, 0.03, 1, 7, tile=32))
+    assert e.value.status == R.RICK_EINVAL
