@@ -337,8 +337,9 @@ rick_status rick_fused_work_bytes(const rick_params *params, size_t *work_bytes)
  * (nt = n / tile; 1: the tile was read), uint8 tile-row flags [n_w][nt],
  * uint8 plane flags [n_w], uint64 tile-row bit masks [n_w] and tile bit
  * masks [n_w][nt] (for nt <= 64), then the row transforms, complex64
- * [n_w][image_n][n] (8 n_w image_n n bytes; image_n = n without a crop).  RICK_EINVAL if n is outside 256 ... 8192, the sizes the
- * fused transform covers (use rick_fft_wplanes + rick_wcorrect_stack there). */
+ * [n_w][image_n][n] (8 n_w image_n n bytes; image_n = n without a crop).
+ * RICK_EINVAL if n is outside 256 ... 8192, the sizes the fused transform
+ * covers (use rick_fft_wplanes + rick_wcorrect_stack there). */
 rick_status rick_fft_wcorrect_bytes(const rick_plan *plan, size_t *work_bytes);
 
 /* The inverse FFT of every plane (§2 step 3) fused with the w-correction and
@@ -354,8 +355,8 @@ rick_status rick_fft_wcorrect_bytes(const rick_plan *plan, size_t *work_bytes);
  *               or rick_grid_sparse with this ws_dev).
  *   sparse = 0: every tile is read (planes accumulated over several binnings).
  * work_dev: device, 256-byte aligned, at least rick_fft_wcorrect_bytes; its
- * contents are scratch.  ws_dev supplies the w range, the weight sum and (for
- * sparse) the tiles.  RICK_EINVAL for an n outside 256 ... 8192, a short or
+ * contents are scratch, and calls that share it must not overlap on the device.
+ * ws_dev supplies the w range, the weight sum and (for sparse) the tiles.  RICK_EINVAL for an n outside 256 ... 8192, a short or
  * misaligned buffer or unknown flags. */
 rick_status rick_fft_wcorrect(rick_plan *plan, const void *planes_dev, const void *ws_dev,
                               int32_t sparse, void *work_dev, size_t work_bytes,
