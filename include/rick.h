@@ -255,11 +255,14 @@ rick_status rick_bin_layout(const rick_plan *plan, rick_bin_view *out);
  * the buffers it owns, a real-time loop may forbid allocator calls (they can
  * block and synchronise the device), or memory may be carved up in advance
  * from a fixed budget.  This entry point computes exactly what rick_bin
- * computes -- into the same workspace layout, which the later calls read --
- * but keeps its temporaries (per-visibility keys, cells and offsets, the
- * ranks, histogram, scan temporaries, weight-sum partials) in a fixed array compiled
- * into the library (about 13 MB, held on every GPU that loads the library until
- * the process exits) instead of in ws_dev's scratch regions.  It calls no
+ * computes and writes the same workspace regions that later calls read --
+ * the header and stats, the per-visibility keys and corner cells (read by
+ * rick_degrid and rick_density_weights), the records, the permutation, the
+ * bin offsets and the work lists -- but keeps its temporaries (the
+ * per-visibility ranks and fractional offsets, the histogram, the scan
+ * temporaries and the weight-sum partials) in a fixed array compiled into the
+ * library (about 11.6 MB, held on every GPU that loads the library until the
+ * process exits) instead of in ws_dev's scratch regions.  It calls no
  * cudaMalloc, cudaFree or allocating library routine.
  * The paper has no counterpart; this is an interface convenience.
  *   Limits: n_vis <= 262144 and 4 n_w (n/T)^2 <= 131072 bins, else

@@ -770,17 +770,18 @@ extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const f
 
 // ------------------------------------------------------------------------
 // rick_bin_noalloc: the binning above for callers that must not allocate
-// device memory.  Its temporaries -- per-visibility keys, cells and
-// fractional offsets, the histogram / cursor array, the scan temporaries and
-// the weight-sum partials -- live in this file-scope array instead of the
-// caller's workspace.  The array is part of the library image: every GPU that
-// loads librick.so holds it (about 13 MB) until the process exits.
+// device memory.  Its temporaries -- the per-visibility ranks and fractional
+// offsets, the histogram / cursor array, the scan temporaries and the
+// weight-sum partials -- live in this file-scope array instead of the
+// caller's workspace.  The per-visibility keys and corner cells stay in the
+// caller's workspace, where rick_bin writes them: degridding and the density
+// weights read them after the binning.  The array is part of the library
+// image: every GPU that loads librick.so holds it (about 11.6 MB) until the
+// process exits.
 
 #define NOALLOC_MAX_VIS (1 << 18)
 #define NOALLOC_MAX_BINS (1 << 17)
-#define NOALLOC_KEY (0)
-#define NOALLOC_CELL (NOALLOC_KEY + 4 * NOALLOC_MAX_VIS)
-#define NOALLOC_FRAC (NOALLOC_CELL + 4 * NOALLOC_MAX_VIS)
+#define NOALLOC_FRAC (0)
 #define NOALLOC_RANK (NOALLOC_FRAC + 8 * NOALLOC_MAX_VIS)
 #define NOALLOC_HIST (NOALLOC_RANK + 4 * NOALLOC_MAX_VIS)
 #define NOALLOC_SUBOFF (NOALLOC_HIST + 4 * (RICK_BIN_SUBS * NOALLOC_MAX_BINS + 256))
@@ -835,10 +836,9 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     }
     const int64_t nkb = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) /
                         (RICK_KEY_THREADS * RICK_KEY_ITEMS);
-    // outputs in the caller's workspace, temporaries in the fixed array
+    // outputs (records, offsets, work lists, and the keys and corner cells that
+    // later calls read) in the caller's workspace, temporaries in the fixed array
     WsPtrs w = rick_ws_ptrs(ws_dev, L);
-    w.key = (uint32_t *)(scratch + NOALLOC_KEY);
-    w.cell = (uint32_t *)(scratch + NOALLOC_CELL);
     w.rank = (uint32_t *)(scratch + NOALLOC_RANK);
     w.frac = (float2 *)(scratch + NOALLOC_FRAC);
     w.hist = (uint32_t *)(scratch + NOALLOC_HIST);

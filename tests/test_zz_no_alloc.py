@@ -90,3 +90,48 @@ def test_noalloc_rejects_sizes_beyond_its_array(P):
                            big.ws_bytes, None, torch.cuda.current_stream().cuda_stream)
     assert e.value.status == R.RICK_ERANGE
     big.close()
+
+
+def test_noalloc_binning_feeds_degrid_and_density_weights(P):
+    """Degridding and the density weights read the keys and corner cells a
+    binning leaves in the workspace.  A workspace that only ever saw
+    rick_bin_noalloc (filled with 0xFF first, so nothing from another binning
+    can stand in) must give them what rick_bin gives, including the dropped
+    visibilities (some placed off the grid)."""
+    R = P.rick
+    dev = torch.device("cuda:0")
+    wl = synth.WORKLOADS["small"]
+    d = synth.generate(synth.scaled("small", n_keep=30000).obs)
+    uvw = d["uvw"].copy()
+    uvw[::97, 0] = 1.0e6  # far outside the grid: dropped
+    t = {"uvw": torch.from_numpy(uvw).to(dev), "vis": torch.from_numpy(d["vis"]).to(dev),
+         "weight": torch.from_numpy(d["weight"]).to(dev)}
+    n = uvw.shape[0]
+    out = {}
+    rng = np.random.default_rng(3)
+    planes = (rng.normal(size=(wl.n_w, wl.n, wl.n)) +
+              1j * rng.normal(size=(wl.n_w, wl.n, wl.n))).astype(np.complex64)
+    for noalloc in (False, True):
+        im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                      max_vis=n, device=dev)
+        im.ws.fill_(0xFF)
+        fn = R.rick_bin_noalloc if noalloc else R.rick_bin
+        fn(im.plan, n, t["uvw"].data_ptr(), t["vis"].data_ptr(), t["weight"].data_ptr(),
+           im.ws.data_ptr(), im.ws_bytes, im.stats_buf.data_ptr(),
+           torch.cuda.current_stream().cuda_stream)
+        im.n_vis = n
+        im.planes.copy_(torch.from_numpy(planes).to(dev))
+        out[noalloc] = dict(stats=im.stats(), degrid=im.degrid(t["weight"]).cpu().numpy(),
+                            uniform=im.density_weights("uniform", 0.0, t["weight"]).cpu().numpy(),
+                            briggs=im.density_weights("briggs", 0.5, t["weight"]).cpu().numpy())
+        torch.cuda.synchronize()
+        im.close()
+    ref, got = out[False], out[True]
+    assert ref["stats"]["n_dropped_uv"] > 0
+    assert got["stats"] == ref["stats"]
+    # each model value comes from one record, whose content is the same
+    assert np.array_equal(got["degrid"], ref["degrid"])
+    assert np.all(got["degrid"][::97] == 0)
+    for k in ("uniform", "briggs"):  # densities summed with float atomics (any order)
+        assert np.all(got[k][::97] == 0)
+        assert np.allclose(got[k], ref[k], rtol=1e-6, atol=0), k
