@@ -3,23 +3,29 @@
 
 One step = one pass of the whole hot path over one batch of visibilities:
 bin -> grid -> per-plane inverse FFT -> w-correct + stack + taper (the stages of
-§2 of De Rubeis et al.), on the LOFAR-like workload: 5e7 synthetic
-visibilities, 4096^2 grid, 16 w-planes, Kaiser-Bessel support 7.
+§2 of De Rubeis et al.), by default on the large workload: 2e8 synthetic
+LOFAR-like visibilities (60 stations, 64 channels), 8192^2 grid, 32 w-planes,
+Kaiser-Bessel support 9.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 Prints one JSON line.  ``value`` is visibilities/s with the inputs already
 resident in HBM; ``e2e`` is the same metric through the streamed host-buffer
 API call (pinned host inputs streamed to the GPU in chunks, copies overlapping
-binning and gridding, and the image copied back, all inside the timed region).  The inputs (1.8 GB) are larger than L2, so no L2 flush is needed
-between steps.  ``--impl reference`` times the FP64 oracle on the host cores
-instead (on a bounded sample of the same workload).
+binning and gridding, and the image copied back to pinned host memory, all
+inside the timed region).  The inputs (7.2 GB) are larger than L2, so no L2
+flush is needed between steps.  Extra keys: the LOFAR-like workload's step
+(5e7 visibilities, 4096^2 x 16 planes, KB W=7), a reduced serving trace
+(served vs plain), the chi^2 gradient step, and the FP64 oracle on the host
+cores.  ``--impl reference`` times the FP64 oracle alone, on per-plane slabs
+of the same workload.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -117,6 +123,56 @@ def algorithmic_bytes(n_vis: int, n_binned: int, n: int, n_w: int, tile: int,
     }
 
 
+def probe_rates(P) -> dict:
+    """Per-SM throughput of the units that bound the tile kernels, measured on
+    this GPU by the library's probe (operations per SM clock)."""
+    R = P.rick
+    kinds = {"smem_rmw_f32": R.RICK_PROBE_SMEM_RMW, "smem_atomic_f32": R.RICK_PROBE_SMEM_ATOMIC_F32,
+             "smem_atomic_u32": R.RICK_PROBE_SMEM_ATOMIC_U32,
+             "smem_atomic_u64": R.RICK_PROBE_SMEM_ATOMIC_U64, "ffma": R.RICK_PROBE_FFMA,
+             "ffma2": R.RICK_PROBE_FFMA2}
+    return {k: R.rick_probe_throughput(v) for k, v in kinds.items()}
+
+
+def stage_rooflines(wl, m: dict, rates: dict, sms: int, sm_mhz: float, hbm_peak: float) -> dict:
+    """Each stage against the unit that bounds it:
+    - bin: HBM (algorithmic bytes / measured copy bandwidth);
+    - grid: shared memory -- Eq. 3 accumulates 2 W^2 FP32 values per visibility;
+      the peak is the measured plain read-modify-write rate of shared memory
+      (the faster of the two ways to add into it); HBM bytes alongside;
+    - fft_wcorrect: FP32 arithmetic -- 5 N log2 N flops per N-point complex
+      transform (the usual count), one per row of the tile-rows with records
+      plus one per image column and plane with records, against the measured
+      paired-FMA rate (2 flops per FMA)."""
+    clk = sm_mhz * 1e6
+    out = {}
+    ms = m["stage_ms"]
+    alg = m["alg"]
+    hb = {k: alg[k] / (ms[k] * 1e-3) / 1e9 for k in ms}
+    out["bin"] = {"bound": "hbm", "achieved": hb["bin"], "peak": hbm_peak, "unit": "GB/s",
+                  "frac": hb["bin"] / hbm_peak, "work": alg["bin"]}
+    smem_ops = 2 * wl.support ** 2 * m["n_binned"]
+    smem_peak = rates["smem_rmw_f32"] * sms * clk
+    g = smem_ops / (ms["grid"] * 1e-3)
+    out["grid"] = {"bound": "smem", "achieved": g / 1e9, "peak": smem_peak / 1e9,
+                   "unit": "G FP32 shared read-modify-writes/s", "frac": g / smem_peak,
+                   "work": smem_ops, "hbm_frac": hb["grid"] / hbm_peak,
+                   "peak_note": f"{rates['smem_rmw_f32']:.2f} RMW/clk/SM measured x {sms} SMs x "
+                                f"{sm_mhz:.0f} MHz"}
+    n = wl.n
+    m_img = n
+    transforms = m["tile_rows"] * wl.tile + m_img * m["planes_read"]
+    flops = 5.0 * n * math.log2(n) * transforms
+    fpeak = 2.0 * rates["ffma2"] * sms * clk
+    f = flops / (ms["fft_wcorrect"] * 1e-3)
+    out["fft_wcorrect"] = {"bound": "alu", "achieved": f / 1e12, "peak": fpeak / 1e12,
+                           "unit": "TFLOP/s (FP32)", "frac": f / fpeak, "work": flops,
+                           "hbm_frac": hb["fft_wcorrect"] / hbm_peak,
+                           "peak_note": f"{rates['ffma2']:.1f} FP32 FMA/clk/SM measured (paired "
+                                        f"FMAs) x 2 flops x {sms} SMs x {sm_mhz:.0f} MHz"}
+    return out
+
+
 def traffic_of(stage: str, n_vis: int):
     """DRAM bytes per launch of a stage's kernels from the committed ncu summary
     (a "traffic <stage> <bytes> bytes n_vis <n> sources <file>=<sha256[:16]> ..."
@@ -166,54 +222,120 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_baseline(wl, data, n_sample: int) -> dict:
-    """The FP64 oracle as it stands, on the first n_sample visibilities of the
-    workload, full grid and plane count."""
+def oracle_params(wl, n_w=None):
+    import oracle
+    return oracle.Params(n=wl.n, n_w=wl.n_w if n_w is None else n_w, fov=wl.fov,
+                         kernel=oracle.KB if wl.kernel == "kb" else oracle.GAUSS,
+                         support=wl.support, tile=wl.tile)
+
+
+def oracle_slabs(wl, data):
+    """The workload cut along w for timing the oracle in bounded pieces: the
+    oracle's own plane of every kept visibility (wl.n_w planes over the whole w
+    range), and per plane the indices of its visibilities, in input order.
+    Returns the planes in an interleaved order (outer and inner planes mixed)
+    and the slabs."""
     import numpy as np
 
     import oracle
+    g = oracle.coords(oracle_params(wl), data["uvw"])
+    kept = np.flatnonzero(g["status"] == 0)
+    pl = g["plane"][kept]
+    order = np.argsort(pl, kind="stable")
+    counts = np.bincount(pl, minlength=wl.n_w)
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    slabs = [kept[order[starts[k]:starts[k + 1]]] for k in range(wl.n_w)]
+    step = 7 if wl.n_w % 7 else 5
+    return [(k * step) % wl.n_w for k in range(wl.n_w)], slabs
 
-    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov,
-                       kernel=oracle.KB if wl.kernel == "kb" else oracle.GAUSS,
-                       support=wl.support, tile=wl.tile)
-    s = slice(0, n_sample)
-    t0 = time.perf_counter()
-    oracle.image(op, data["uvw"][s], data["vis"][s], data["weight"][s].astype(np.float64))
-    dt = time.perf_counter() - t0
-    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"first {n_sample} of {len(data['vis'])} visibilities of the workload, "
-                      f"full {wl.n}^2 x {wl.n_w}-plane grid (FFT and w-correction at full size); "
-                      f"{dt:.1f} s"}
+
+def slab_arrays(data, idx):
+    """One slab's inputs in the dtypes the oracle computes in (FP64, complex128),
+    so that its call converts nothing."""
+    import numpy as np
+    return (np.ascontiguousarray(data["uvw"][idx]), data["vis"][idx].astype(np.complex128),
+            data["weight"][idx].astype(np.float64))
+
+
+def oracle_slab(wl, arrays):
+    """The oracle's image of one slab: its visibilities gridded on the full
+    n x n grid as one w-plane, the FFT of that plane, its w-correction and the
+    taper division -- 1/n_w of the whole job's planes with their visibilities."""
+    import oracle
+    uvw, vis, wt = arrays
+    oracle.image(oracle_params(wl, n_w=1), uvw, vis, wt)
+
+
+def cpu_baseline(wl, data, budget_s: float = 20.0) -> dict:
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the
+    workload: whole w-plane slabs (each slab's visibilities gridded on the full
+    grid, one FFT, the w-correction), until about budget_s seconds have been
+    spent; plus the split of one slab into gridding, FFT and the rest."""
+    import numpy as np
+
+    import oracle
+    order, slabs = oracle_slabs(wl, data)
+    oracle_slab(wl, slab_arrays(data, slabs[order[0]][:1000]))  # the taper table (kept)
+    done_vis, spent, planes = 0, 0.0, 0
+    split = None
+    for k in order:
+        arr = slab_arrays(data, slabs[k])
+        t0 = time.perf_counter()
+        oracle_slab(wl, arr)
+        dt = time.perf_counter() - t0
+        if split is None:
+            t1 = time.perf_counter()
+            oracle.grid(oracle_params(wl, n_w=1), *arr)
+            t_grid = time.perf_counter() - t1
+            t1 = time.perf_counter()
+            oracle.fft2d(np.zeros((wl.n, wl.n), np.complex128), +1)
+            t_fft = time.perf_counter() - t1
+            split = {"plane": int(k), "n_vis": int(len(slabs[k])), "total_s": dt,
+                     "grid_s": t_grid, "fft_s": t_fft,
+                     "wcorrect_taper_s": max(dt - t_grid - t_fft, 0.0),
+                     "grid_includes": "coordinates, plane and kernel weights of every visibility"}
+        done_vis += len(slabs[k])
+        spent += dt
+        planes += 1
+        if spent >= budget_s:
+            break
+    n_kept = sum(len(x) for x in slabs)
+    return {"value": done_vis / spent, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{planes} of the {wl.n_w} w-plane slabs of the workload ({done_vis} of its "
+                      f"{n_kept} kept visibilities), each imaged by the oracle as one plane on "
+                      f"the full {wl.n}^2 grid (gridding, FFT, w-correction, taper); {spent:.1f} s",
+            "whole_job_estimate_s": n_kept / (done_vis / spent),
+            "split_one_slab": split}
 
 
 def run_reference(args, wl):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
     import synth
 
-    n_sample = args.ref_sample
-    data = synth.generate(synth.scaled(args.workload, n_keep=n_sample).obs)
-    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov,
-                       kernel=oracle.KB if wl.kernel == "kb" else oracle.GAUSS,
-                       support=wl.support, tile=wl.tile)
-    wt = data["weight"].astype(np.float64)
-    for _ in range(args.warmup):
-        oracle.image(op, data["uvw"], data["vis"], wt)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.image(op, data["uvw"], data["vis"], wt)
-    dt = time.perf_counter() - t0
-    value = n_sample * args.steps / dt
+    data = synth.generate(wl.obs)
+    order, slabs = oracle_slabs(wl, data)
+    oracle_slab(wl, slab_arrays(data, slabs[order[0]][:1000]))  # the taper table (kept)
+    plan = [order[s % len(order)] for s in range(args.warmup + args.steps)]
+    for k in plan[:args.warmup]:
+        oracle_slab(wl, slab_arrays(data, slabs[k]))
+    spent, vis = 0.0, 0
+    for k in plan[args.warmup:]:
+        arr = slab_arrays(data, slabs[k])
+        t0 = time.perf_counter()
+        oracle_slab(wl, arr)
+        spent += time.perf_counter() - t0
+        vis += len(slabs[k])
+    value = vis / spent
     cores = oracle.max_threads()
-    sample = (f"each step: the first {n_sample} of {wl.obs.n_keep} visibilities of the workload "
-              f"on the full {wl.n}^2 x {wl.n_w}-plane grid")
+    sample = (f"each step: one of the {wl.n_w} w-plane slabs of the workload (its visibilities "
+              f"gridded by the oracle as one plane on the full {wl.n}^2 grid, one FFT, the "
+              f"w-correction and taper), the planes in turn; {vis} visibilities in the timed steps")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": spent / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(wl),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -232,27 +354,16 @@ def config_of(wl) -> dict:
             "l2": "inputs (uvw+vis+weight) larger than L2; no flush"}
 
 
-def run_ours(args, wl):
-    import numpy as np
+def device_step(P, wl, data, dev, steps, warmup, dist=None, local=0, sample_clocks=False):
+    """Time `steps` steps (bin, sparse grid, fused FFT + w-correct) of a workload
+    with its inputs resident in HBM: CUDA events on the current stream, the
+    whole region and each stage.  Returns the measurements and the imager
+    (still open) with the device inputs."""
     import torch
-
-    import synth
-    import paper_2411_07321_gb300 as P
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    data = synth.generate(wl.obs, rows=True)
     n_vis = len(data["vis"])
-    uvw_h = torch.from_numpy(data["uvw"]).pin_memory()
-    vis_h = torch.from_numpy(data["vis"]).pin_memory()
-    wt_h = torch.from_numpy(data["weight"]).pin_memory()
-    uvw, vis, wt = uvw_h.to(dev), vis_h.to(dev), wt_h.to(dev)
+    uvw = torch.from_numpy(data["uvw"]).to(dev)
+    vis = torch.from_numpy(data["vis"]).to(dev)
+    wt = torch.from_numpy(data["weight"]).to(dev)
     im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
                   max_vis=n_vis, device=dev)
     img = torch.empty((wl.n, wl.n), dtype=torch.float32, device=dev)
@@ -270,135 +381,208 @@ def run_ours(args, wl):
         if ev is not None:
             ev[3].record()
 
-    def step_unfused(ev):
-        ev[0].record()
-        im.bin(uvw, vis, wt)
-        ev[1].record()
-        im.grid()
-        ev[2].record()
-        im.fft(+1)
-        ev[3].record()
-        im.wcorrect(out=img)
-        ev[4].record()
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    st = im.stats()
-    n_binned = st["n_binned"]
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    n_binned = im.stats()["n_binned"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(local)
-    clocks.start()
+    clocks = Clocks(local) if sample_clocks else None
+    if clocks:
+        clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = im.launches()
     h0 = time.time()
     t_start.record()
-    for k in range(args.steps):
+    for k in range(steps):
         step(evs[k])
     t_end.record()
     torch.cuda.synchronize()
     h1 = time.time()
     if dist:
         dist.barrier()
-    clk = clocks.stop(h0, h1)
-    launches = im.launches() - l0
-    ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
-    stage_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
-                for i, name in enumerate(["bin", "grid", "fft_wcorrect"])}
+    out = {"clocks": clocks.stop(h0, h1) if clocks else None,
+           "launches": im.launches() - l0,
+           "ms": max_over_ranks(t_start.elapsed_time(t_end), dist, dev),
+           "stage_ms": {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
+                        for i, name in enumerate(["bin", "grid", "fft_wcorrect"])},
+           "n_vis": n_vis, "n_binned": n_binned}
+    out["tiles"], out["tile_rows"], out["planes_read"] = im.fused_tiles(planes=True)
+    alg = algorithmic_bytes(n_vis, n_binned, wl.n, wl.n_w, wl.tile, out["tiles"], out["tile_rows"])
+    out["alg"] = alg
+    out["gbps"] = {k: alg[k] / (out["stage_ms"][k] * 1e-3) / 1e9 for k in out["stage_ms"]}
+    return out, im, (uvw, vis, wt, img)
+
+
+def timed_calls(call, steps, warmup, dist=None, dev=None, finish=None):
+    """ms of `steps` calls of `call` on the current stream (CUDA events), after
+    `warmup` untimed calls; `finish` (enqueue-only) runs before the end event,
+    e.g. to join copies that the calls left on another stream."""
+    import torch
+    for _ in range(max(1, warmup)):
+        call()
+    if finish:
+        finish()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        call()
+    if finish:
+        finish()
+    e1.record()
+    torch.cuda.synchronize()
+    t = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    if dist:
+        dist.barrier()
+    return t
+
+
+def run_ours(args, wl):
+    import torch
+
+    import synth
+    import paper_2411_07321_gb300 as P
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    data = synth.generate(wl.obs, rows=True)
+    n_vis = len(data["vis"])
+    m, im, (uvw, vis, wt, img) = device_step(P, wl, data, dev, args.steps, args.warmup, dist,
+                                              local, sample_clocks=True)
+    ms = m["ms"]
     value = whole_job_rate(n_vis, args.steps, world, ms)
-    tiles, tile_rows = im.fused_tiles()
+
     # the unfused stages (grid clearing every tile, cuFFT in place, plane sum),
     # timed after the headline steps, for comparison
     uevs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
             for _ in range(max(3, args.steps // 2))]
     for e in uevs:
-        step_unfused(e)
+        e[0].record()
+        im.bin(uvw, vis, wt)
+        e[1].record()
+        im.grid()
+        e[2].record()
+        im.fft(+1)
+        e[3].record()
+        im.wcorrect(out=img)
+        e[4].record()
     torch.cuda.synchronize()
     unfused_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in uevs[1:])
                   for i, name in enumerate(["bin", "grid_clear", "cufft", "wcorrect"])}
 
-    # end to end through the host-buffer calls (pinned host in, image back to
-    # host): the streamed path (chunks of args.chunk visibilities, copies
-    # overlapping binning and gridding) is the headline; the resident path
-    # (all inputs copied, then imaged) is kept for comparison
-    out_h = torch.empty((wl.n, wl.n), dtype=torch.float32).pin_memory()
-    ims = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
-                   max_vis=min(args.chunk, n_vis), device=dev)
+    # the w-phase ablation: the fused transform with the phase argument in
+    # plain FP32 instead of double-single arithmetic, on the same binning
+    im.bin(uvw, vis, wt)
+    im.grid_sparse()
+    fp32_phase_ms = timed_calls(
+        lambda: im.fft_wcorrect(flags=P.imager.IMAGE_FLAGS | P.rick.RICK_PHASE_FP32, out=img),
+        args.steps, args.warmup, dist, dev) / args.steps
+    ds_phase_ms = timed_calls(lambda: im.fft_wcorrect(out=img), args.steps, args.warmup,
+                              dist, dev) / args.steps
 
-    def timed(call):
-        for _ in range(max(1, args.warmup)):
-            call()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            call()
-        e1.record()
-        torch.cuda.synchronize()
-        t = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        if dist:
-            dist.barrier()
-        return t
-
-    # Briggs-robust weighting: the extra passes per image, after a
-    # binning of the same visibilities -- density weights, then re-weighting
-    # the records
+    # Briggs-robust weighting: the extra passes per image, after a binning of
+    # the same visibilities -- density weights, then re-weighting the records
     im.bin(uvw, vis, wt)
 
     def reweight():
         w2 = im.density_weights("briggs", 0.0, wt)
         im.bin_values(vis, w2)
 
-    weighting_ms = timed(reweight)
-    e2e_vis_ms = timed(lambda: ims.image_streamed(uvw_h, vis_h, wt_h, out_h))
-    e2e_resident_ms = timed(lambda: im.image_from_host(uvw_h, vis_h, wt_h, out_h))
+    weighting_ms = timed_calls(reweight, args.steps, args.warmup, dist, dev)
+
+    # end to end through the host-buffer calls (pinned host in, image back to
+    # pinned host memory, every copy inside the timed region): the streamed
+    # path (chunks of args.chunk visibilities, copies overlapping binning and
+    # gridding) is the headline; the resident path (all inputs copied, then
+    # imaged) is kept for comparison
+    uvw_h = torch.from_numpy(data["uvw"]).pin_memory()
+    vis_h = torch.from_numpy(data["vis"]).pin_memory()
+    wt_h = torch.from_numpy(data["weight"]).pin_memory()
+    out_h = torch.empty((wl.n, wl.n), dtype=torch.float32).pin_memory()
+    ims = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                   max_vis=min(args.chunk, n_vis), device=dev)
+    e2e_vis_ms = timed_calls(lambda: ims.image_streamed(uvw_h, vis_h, wt_h, out_h), args.steps,
+                             args.warmup, dist, dev, finish=ims.join_out)
+    e2e_resident_ms = timed_calls(lambda: im.image_from_host(uvw_h, vis_h, wt_h, out_h),
+                                  args.steps, args.warmup, dist, dev)
     # the same visibilities as rows of n_chan channels (a measurement set's
     # layout): uvw once per row and a factor per channel
     n_chan = wl.obs.n_chan
-    rows_ok = n_vis % n_chan == 0
-    if rows_ok:
+    if n_vis % n_chan == 0:
         rows_h = torch.from_numpy(data["uvw_rows"]).pin_memory()
         scale_h = torch.from_numpy(data["chan_scale"]).pin_memory()
-        e2e_ms = timed(lambda: ims.image_streamed(rows_h, vis_h, wt_h, out_h, chan_scale=scale_h))
+        e2e_ms = timed_calls(
+            lambda: ims.image_streamed(rows_h, vis_h, wt_h, out_h, chan_scale=scale_h),
+            args.steps, args.warmup, dist, dev, finish=ims.join_out)
         h2d = rows_h.numel() * 8 + scale_h.numel() * 8 + n_vis * (8 + 4)
         call = (f"Imager.image_streamed with chan_scale (rick_image_host_rows, one "
-                f"correlation): rows of {n_chan} channels with uvw once per row, chunks of {min(args.chunk, n_vis)} "
-                f"visibilities, w range from the data")
+                f"correlation): rows of {n_chan} channels with uvw once per row, chunks of "
+                f"{min(args.chunk, n_vis)} visibilities, w range from the data; the image "
+                f"copied back to pinned host memory inside the timed region")
     else:
         e2e_ms, h2d = e2e_vis_ms, n_vis * (24 + 8 + 4)
         call = (f"Imager.image_streamed (rick_image_host), chunks of {min(args.chunk, n_vis)} "
                 f"visibilities, w range from the data")
     ims.close()
+    im.close()
+    del uvw, vis, wt, img, ims, im
+    torch.cuda.empty_cache()
     e2e_value = whole_job_rate(n_vis, args.steps, world, e2e_ms)
 
+    stage_ms, alg, gbps = m["stage_ms"], m["alg"], m["gbps"]
     peak, peak_kind = peaks()
-    alg = algorithmic_bytes(n_vis, n_binned, wl.n, wl.n_w, wl.tile, tiles, tile_rows)
-    gbps = {k: alg[k] / (stage_ms[k] * 1e-3) / 1e9 for k in stage_ms}
+    rates = probe_rates(P)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (m["clocks"] or {}).get("sm_mhz") or (m["clocks"] or {}).get("sm_max_mhz") or 2070.0
+    roofs = stage_rooflines(wl, m, rates, sms, sm_mhz, peak)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     kernel_name = {"bin": "rick_bin (all binning kernels)", "grid": "grid_kernel",
                    "fft_wcorrect": "fft_rows_kernel + fft_cols_kernel"}[dom]
-    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": gbps[dom], "peak": peak,
-                "unit": "GB/s", "frac": gbps[dom] / peak,
+    roofline = {**roofs[dom], "kernel": kernel_name, "stage": dom,
                 "traffic": traffic_of(dom, n_vis), "algorithmic_bytes": alg[dom],
-                "peak_source": f"{peak_kind} (HBM copy bandwidth)"}
+                "peak_source": ("measured HBM copy bandwidth" if roofs[dom]["bound"] == "hbm"
+                                else "measured by rick_probe_throughput on this GPU") +
+                               f" ({peak_kind} MEASURED_PEAKS.json for HBM)"}
     unfused = {"ms": unfused_ms, "ms_per_step": sum(unfused_ms.values()),
                "gbps": {k: alg[k] / (unfused_ms[k] * 1e-3) / 1e9 for k in unfused_ms},
                "calls": "rick_bin, rick_grid (clears record-free tiles), rick_fft_wplanes "
                         "(cuFFT in place), rick_wcorrect_stack"}
 
+    extras = {}
+    if world == 1 and args.n_vis is None and not args.no_extras and args.workload != "lofar":
+        # the LOFAR-like workload's step (device-resident inputs)
+        lw = synth.WORKLOADS["lofar"]
+        ld = synth.generate(lw.obs)
+        lm, lim, _ = device_step(P, lw, ld, dev, args.steps, args.warmup)
+        lim.close()
+        del lim, _
+        torch.cuda.empty_cache()
+        extras["lofar"] = {
+            "workload": config_of(lw)["workload"], "value": len(ld["vis"]) / (lm["ms"] / args.steps * 1e-3),
+            "unit": UNIT, "ms_per_step": lm["ms"] / args.steps, "stage_ms": lm["stage_ms"],
+            "gbps": lm["gbps"], "launches": lm["launches"]}
+        del ld
+        extras["serving"] = serve_measure(args.extra_serve_jobs, args.serve_slots)
+        extras["grad"] = grad_measure(args.steps, args.warmup)
+
     if rank != 0:
-        im.close()
         if dist:
             dist.destroy_process_group()
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.n_vis is None:
-        cpu = cpu_baseline(wl, data, args.cpu_sample)
+        cpu = cpu_baseline(wl, data, args.cpu_budget)
     line = {
         **({"profiling_subset": True} if args.n_vis is not None else {}),
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -415,25 +599,31 @@ def run_ours(args, wl):
                     "call": "Imager.image_streamed (rick_image_host), uvw per visibility"},
                 "resident_call_ms_per_step": e2e_resident_ms / args.steps},
         "roofline": roofline,
-        "stages": {"ms": stage_ms, "gbps": gbps, "algorithmic_bytes": alg,
-                   "n_binned": n_binned, "tiles_with_records": tiles,
-                   "tile_rows_with_records": tile_rows,
+        "stages": {"ms": stage_ms, "gbps": gbps, "algorithmic_bytes": alg, "roofline": roofs,
+                   "probe_ops_per_clock_per_sm": rates, "planes_read": m["planes_read"],
+                   "n_binned": m["n_binned"], "tiles_with_records": m["tiles"],
+                   "tile_rows_with_records": m["tile_rows"],
                    "calls": "rick_bin, rick_grid_sparse, rick_fft_wcorrect (sparse)"},
         "unfused": unfused,
+        "phase_ablation": {"fft_wcorrect_ms": {"double_single": ds_phase_ms,
+                                               "fp32": fp32_phase_ms},
+                           "what": "rick_fft_wcorrect with the w-phase argument in "
+                                   "double-single arithmetic (default) and with "
+                                   "RICK_PHASE_FP32, same binning and planes"},
         "weighting": {"scheme": "briggs, robust 0", "ms_per_image": weighting_ms / args.steps,
                       "passes": "rick_density_weights + rick_bin_values, after a binning"},
+        **extras,
         "cpu_baseline": cpu,
-        "clocks": clk,
-        "gpu_launches": launches,
+        "clocks": m["clocks"],
+        "gpu_launches": m["launches"],
     }
     print(json.dumps(line), flush=True)
-    im.close()
     if dist:
         dist.destroy_process_group()
 
 
-def run_serve(args):
-    """The serving workload: 256 imaging requests with Poisson arrivals,
+def serve_measure(n_jobs: int, slots: int) -> dict:
+    """The serving workload: n_jobs imaging requests with Poisson arrivals,
     log-uniform 1e4..1e7 visibilities (prefixes of the LOFAR-like tracks), grids
     512^2..4096^2, 4..16 w-planes, Gaussian or Kaiser-Bessel W=7.  The plain
     per-request path (fresh plan and buffers per request) is run first,
@@ -449,7 +639,6 @@ def run_serve(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    n_jobs = args.serve_jobs
     d = synth.generate(synth.scaled("lofar", n_keep=10_000_000).obs)
     host = {k: torch.from_numpy(d[k]).pin_memory() for k in ("uvw", "vis", "weight")}
     rng = np.random.default_rng(5)
@@ -496,7 +685,7 @@ def run_serve(args):
     plain_wall = done - t_base
 
     # served path on the same trace
-    with S.Server(dev, max_running=args.serve_slots) as srv:
+    with S.Server(dev, max_running=slots) as srv:
         # saturated throughput: every request queued at once (also warms the slots)
         t0 = time.perf_counter()
         sat = [srv.submit(job(sp)) for sp in specs]
@@ -534,21 +723,26 @@ def run_serve(args):
                 "p50_ms": 1e3 * S.percentile(lat, 50), "p99_ms": 1e3 * S.percentile(lat, 99),
                 "mean_ms": 1e3 * float(np.mean(lat)), "wall_s": wall}
 
-    print(json.dumps({
-        "metric": METRIC, "mode": "serve", "unit": "jobs/s", "n_gpus": 1, "n_jobs": n_jobs,
-        "value": n_jobs / served_wall, "higher_is_better": True, "data": "synthetic",
-        "config": {"workload": "256 requests, Poisson arrivals at 0.8 / mean plain service "
-                               "time; n_vis log-uniform 1e4..1e7 (LOFAR-like tracks); grids "
-                               "512..4096; 4..16 w-planes; Gaussian or KB W=7",
-                   "arrival_rate_hz": rate, "slots": args.serve_slots},
+    return {
+        "n_jobs": n_jobs, "unit": "jobs/s", "value": n_jobs / served_wall,
+        "config": {"workload": f"{n_jobs} requests, Poisson arrivals at 0.8 / mean plain "
+                               "service time; n_vis log-uniform 1e4..1e7 (LOFAR-like tracks); "
+                               "grids 512..4096; 4..16 w-planes; Gaussian or KB W=7",
+                   "arrival_rate_hz": rate, "slots": slots},
         "served": summary(lat_served, served_wall), "plain": summary(lat_plain, plain_wall),
         "saturated_jobs_per_s": {"served": served_saturated, "plain": plain_saturated},
         "plain_mean_service_ms": 1e3 * mean_service, "served_peak_hbm_bytes": peak_used,
         "max_rel_diff_served_vs_plain_inner": err, "server_counters": counters,
-    }), flush=True)
+    }
 
 
-def run_grad(args):
+def run_serve(args):
+    r = serve_measure(args.serve_jobs, args.serve_slots)
+    print(json.dumps({"metric": METRIC, "mode": "serve", "n_gpus": 1, "higher_is_better": True,
+                      "data": "synthetic", **r}), flush=True)
+
+
+def grad_measure(steps: int, warmup: int) -> dict:
     """The differentiable workload: the gradient of chi^2 = sum w |V_obs - D x|^2
     with respect to a float32 image x of 50 point sources, on 1e7 visibilities
     (4 channels of the LOFAR-like tracks), a 2048^2 grid, 16 w-planes, KB W=7.
@@ -588,34 +782,40 @@ def run_grad(args):
         if ev is not None:
             ev[2].record()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ms = e0.elapsed_time(e1) / steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
     for ev in evs:
         step(ev)
     torch.cuda.synchronize()
     fwd = statistics.mean(ev[0].elapsed_time(ev[1]) for ev in evs)
     bwd = statistics.mean(ev[1].elapsed_time(ev[2]) for ev in evs)
-    print(json.dumps({
-        "metric": METRIC, "mode": "grad", "unit": "vis/s", "value": n_vis / (ms * 1e-3),
-        "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
+    out = {
+        "unit": "vis/s", "value": n_vis / (ms * 1e-3),
+        "ms_per_step": ms, "steps": steps, "warmup": warmup,
         "ms_forward": fwd, "ms_backward": bwd,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"diff: {n_vis} visibilities (60 stations, 4 channels), "
                                f"{wl.n}^2 grid, {wl.n_w} w-planes, Kaiser-Bessel support "
                                f"{wl.support}; gradient of chi^2 wrt a 50-source float32 image",
                    "step": "chi2 forward (predict) + backward (grid of the residual)",
                    "fused_transform": im.fused},
-    }), flush=True)
+    }
     im.close()
+    return out
+
+
+def run_grad(args):
+    r = grad_measure(args.steps, args.warmup)
+    print(json.dumps({"metric": METRIC, "mode": "grad", "n_gpus": 1, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic", **r}), flush=True)
 
 
 def main():
@@ -624,10 +824,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="lofar")
-    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
-    ap.add_argument("--ref-sample", type=int, default=500_000)
+    ap.add_argument("--workload", default="large")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle work in cpu_baseline (whole w-plane slabs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra keys (LOFAR-like step, serving trace, gradient)")
+    ap.add_argument("--extra-serve-jobs", type=int, default=64,
+                    help="requests of the serving trace in the default line")
     ap.add_argument("--chunk", type=int, default=1 << 24,
                     help="visibilities per chunk of the streamed end-to-end call")
     ap.add_argument("--serve", action="store_true",
@@ -638,13 +842,18 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--n-vis", type=int, default=None,
                     help="profiling aid: image only the first N visibilities (not a bench line)")
+    ap.add_argument("--n-w", type=int, default=None,
+                    help="profiling aid: this many w-planes (not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: --warmup must be at least 3")
     import synth
 
-    wl = synth.WORKLOADS[args.workload] if args.n_vis is None else \
-        synth.scaled(args.workload, n_keep=args.n_vis)
+    wl = synth.WORKLOADS[args.workload]
+    if args.n_vis is not None or args.n_w is not None:
+        wl = synth.scaled(args.workload, n_keep=args.n_vis,
+                          **({"n_w": args.n_w} if args.n_w is not None else {}))
+        args.n_vis = wl.obs.n_keep
     if args.serve:
         run_serve(args)
     elif args.grad:

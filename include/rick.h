@@ -60,6 +60,17 @@ typedef int32_t rick_status;
 #define RICK_N_DIVIDE 4u  /* divide by n (the 1/n of Eq. 1, for prediction)             */
 #define RICK_PHASE_FP32 8u /* ablation: w-phase argument in plain FP32 instead of       */
                            /* double-single (~48-bit) arithmetic                         */
+#define RICK_IMAG_PART 16u /* write Im of the plane sum instead of Re (imaging calls    */
+                           /* only): a check that Hermitian data give a real image      */
+
+/* Options of a plan (rick_params.options, bit-or): */
+#define RICK_OPT_HERMITIAN_MIRROR 1 /* grid every visibility twice: V at (u, v, w) and    */
+                                    /* conj(V) at (-u, -v, -w), the sky being real (§2:  */
+                                    /* the image is the real part); with the w range     */
+                                    /* from the data it is then -max|w| ... max|w|       */
+#define RICK_OPT_DETERMINISTIC 2    /* bitwise repeatable binning and gridding: records  */
+                                    /* of a bin in input order, tile sums in 64-bit      */
+                                    /* fixed point (no floating-point atomics)           */
 
 /* Imaging-weight schemes of rick_density_weights. */
 #define RICK_WEIGHT_UNIFORM 1 /* w / D                                           */
@@ -84,7 +95,7 @@ typedef struct rick_params {
                         /*   pixel p' of the image is pixel p' + (n - m)/2 of the grid   */
                         /*   frame, so the pixel size stays fov/n and the phase centre   */
                         /*   is pixel m/2.  Even, 16 <= m <= n; 0 means m = n (no crop)  */
-    int32_t reserved;   /* must be 0                                                     */
+    int32_t options;    /* bit-or of RICK_OPT_* (0: none)                                */
 } rick_params;
 
 /* Geometry and counts of the last rick_bin, written to device memory. */
@@ -484,6 +495,24 @@ rick_status rick_image_host_rows(rick_plan *plan, int64_t n_rows, int32_t n_chan
                                  size_t ws_bytes, void *stage_dev, size_t stage_bytes,
                                  void *planes_dev, float *image_dev, uint32_t flags,
                                  rick_bin_stats *stats_dev, void *stream);
+
+/* Measured per-SM throughput of this GPU (the current device), for stating the
+ * gridding and transform kernels against the on-chip units that bound them
+ * (the shared-memory read-modify-writes of Eq. 3's accumulation, the FP32
+ * arithmetic of the transforms).  The paper has no counterpart; this is a
+ * measurement aid.  One CTA of 1024 threads per SM repeats the operation on
+ * eight private words (or registers) per thread, conflict-free, timed with the
+ * SM's cycle counter; *ops_per_clock_per_sm is the median over the SMs, in
+ * operations per SM clock (FP32 FMAs for the two FMA kinds).  Synchronous: it
+ * allocates a few KB with cudaMalloc and synchronises the device.
+ * Errors: RICK_EINVAL (unknown kind, NULL output), RICK_ENOMEM, RICK_ECUDA. */
+#define RICK_PROBE_SMEM_RMW 0        /* plain FP32 load-add-store of shared memory   */
+#define RICK_PROBE_SMEM_ATOMIC_F32 1 /* FP32 atomic add to shared memory             */
+#define RICK_PROBE_SMEM_ATOMIC_U32 2 /* 32-bit integer atomic add to shared memory   */
+#define RICK_PROBE_SMEM_ATOMIC_U64 3 /* 64-bit integer atomic add to shared memory   */
+#define RICK_PROBE_FFMA 4            /* FP32 fused multiply-add, one per instruction */
+#define RICK_PROBE_FFMA2 5           /* FP32 fused multiply-add, two per instruction */
+rick_status rick_probe_throughput(int32_t kind, double *ops_per_clock_per_sm);
 
 #ifdef __cplusplus
 }

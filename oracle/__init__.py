@@ -113,6 +113,7 @@ def lib():
         L.or_kernel.argtypes = [P, ctypes.c_double]
         L.or_taper.restype = ctypes.c_double
         L.or_taper.argtypes = [P, ctypes.c_double]
+        L.or_taper_row.argtypes = [P, _D]
         L.or_fft1d.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
         L.or_fft2d.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
         L.or_wrange.argtypes = [ctypes.c_int64, _D, _D, _D]
@@ -181,6 +182,13 @@ def kernel(p: Params, d: float) -> float:
 
 def taper(p: Params, nu: float) -> float:
     return lib().or_taper(ctypes.byref(p.c()), float(nu))
+
+
+def taper_row(p: Params) -> np.ndarray:
+    """C((i - n/2) / n) for i = 0 .. n-1 (the taper along one grid axis)."""
+    out = np.empty(p.n, np.float64)
+    lib().or_taper_row(ctypes.byref(p.c()), out.ctypes.data_as(_D))
+    return out
 
 
 def fft1d(a, sign: int) -> np.ndarray:

@@ -88,11 +88,14 @@ static cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32
 
 // range_src (optional): a header whose w-range keys stand in for a given
 // range (the exact range of a larger set, found by an earlier pass).
+// n_vis: records (inputs, or twice the inputs with the Hermitian mirror).
 __global__ void bin_init_kernel(WsHeader *hdr, uint64_t n_vis, uint32_t chunk_cap, int given,
                                 uint64_t wmin_key, uint64_t wmax_key, uint32_t n_key_blocks,
-                                const WsHeader *range_src)
+                                const WsHeader *range_src, uint64_t n_src, int mirror)
 {
     hdr->n_vis = n_vis;
+    hdr->n_src = n_src;
+    hdr->mirror = (uint32_t)mirror;
     hdr->fault = 0;
     hdr->drop_uv = 0;
     hdr->drop_w = 0;
@@ -128,8 +131,9 @@ __device__ __forceinline__ void wrange_fold(double w, uint64_t &lo, uint64_t &hi
 // factor is positive and finite, rounding is monotone in the factor, so a
 // row's extremes are its products with the smallest and the largest factor
 // (unless one of those overflows, when every channel is folded).
+// With mirror, the mirrored visibilities' -w are folded in too.
 __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n_chan,
-                              const double *scale)
+                              const double *scale, int mirror)
 {
     __shared__ double s_min[32], s_max[32];
     __shared__ int s_ok[32];
@@ -137,8 +141,11 @@ __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (n_chan <= 0) {
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x)
-            wrange_fold(uvw[3 * i + 2], lo, hi);
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double w = uvw[3 * i + 2];
+            wrange_fold(w, lo, hi);
+            if (mirror) wrange_fold(-w, lo, hi);
+        }
     } else {
         // smallest and largest factor, and whether all are positive and finite
         double fmin = INFINITY, fmax = 0.0;
@@ -193,7 +200,7 @@ __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
                         cudaStream_t st, int n_chan, const double *scale)
 {
-    wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr, n_chan, scale);
+    wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr, n_chan, scale, 0);
 }
 
 // ------------------------------------------------------------------------
@@ -237,6 +244,7 @@ struct KeyArgs {
     int n_chan;               // > 0: uvw holds rows of n_chan visibilities, scaled per channel
     int n_corr;               // correlations per visibility (weights [n_vis][n_corr])
     const double *chan_scale;
+    int64_t n_src;            // inputs; records i >= n_src mirror input i - n_src (n_vis = 2 n_src)
     WsPtrs ws;
 };
 
@@ -297,7 +305,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
     // The block's 1024 uvw rows and weights are contiguous: one bulk copy each
     // (TMA) into shared memory, while the plane keys load; a ragged last block
     // or unaligned inputs take plain loads instead.
-    const bool bulk = a.bulk && nitems == NI;
+    const bool bulk = a.bulk && nitems == NI && blk0 + NI <= a.n_src;
     if (bulk && threadIdx.x == 0) {
         rick_mbar_init(&s_bar, 1);
         rick_mbar_expect_tx(&s_bar, 24 * NI + (a.weight ? 4 * NI : 0));
@@ -321,11 +329,14 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
             if (a.weight && a.n_corr == 1) s_wt[i] = a.weight[blk0 + i];
         }
     } else if (!bulk) {
+        // records past the inputs mirror input i - n_src: -uvw (its weight)
         for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
-            s_uvw[3 * i] = a.uvw[3 * (blk0 + i)];
-            s_uvw[3 * i + 1] = a.uvw[3 * (blk0 + i) + 1];
-            s_uvw[3 * i + 2] = a.uvw[3 * (blk0 + i) + 2];
-            if (a.weight) s_wt[i] = a.weight[blk0 + i];
+            const int64_t r = blk0 + i, src = r < a.n_src ? r : r - a.n_src;
+            const double sg = r < a.n_src ? 1.0 : -1.0;
+            s_uvw[3 * i] = sg * a.uvw[3 * src];
+            s_uvw[3 * i + 1] = sg * a.uvw[3 * src + 1];
+            s_uvw[3 * i + 2] = sg * a.uvw[3 * src + 2];
+            if (a.weight) s_wt[i] = a.weight[src];
         }
     }
     __syncthreads();
@@ -473,10 +484,11 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
 //
 // With CORR, each visibility has n_corr correlations (vis and weight
 // [n_vis][n_corr]) and its record carries their weighted sum, sum_c w_c V_c.
+// Records i >= n_src (the Hermitian mirror) carry conj(V) of input i - n_src.
 template <bool CORR>
 __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const float2 *vis,
                                                           const float *weight, WsPtrs ws,
-                                                          int n_corr)
+                                                          int n_corr, int64_t n_src)
 {
     constexpr int U = RICK_SCATTER_U;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * U;
@@ -503,8 +515,11 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
                     v[u] = acc;
                     wt[u] = 1.0f;
                 } else {
-                    v[u] = vis[idx[u]];
-                    wt[u] = weight ? weight[idx[u]] : 1.0f;
+                    const bool mir = idx[u] >= n_src;
+                    const int64_t src = mir ? idx[u] - n_src : idx[u];
+                    v[u] = vis[src];
+                    if (mir) v[u].y = -v[u].y;
+                    wt[u] = weight ? weight[src] : 1.0f;
                 }
                 fr[u] = ws.frac[idx[u]];
                 cl[u] = ws.cell[idx[u]];
@@ -537,22 +552,33 @@ __global__ void bin_offsets_kernel(const uint32_t *suboff, uint32_t *offsets, in
 // Re-pack record values for new visibilities through an existing permutation,
 // and sum the new weights: double-single per thread and warp, FP64 per block,
 // block partials in wpart (summed in a fixed order by values_finalize_kernel).
+// det: also the blocks' sums of |Re| + |Im| of the new values (the bound of the
+// deterministic mode's fixed-point scale).
 __global__ void __launch_bounds__(256) bin_values_kernel(const float2 *vis, const float *weight,
-                                                         WsPtrs ws)
+                                                         WsPtrs ws, int det)
 {
     __shared__ double s_part[8];
+    __shared__ float s_bound[8];
+    float bound = 0.0f;
     const WsHeader *hdr = ws.hdr;
     const int64_t nb = hdr->stats.n_binned;
     ff acc = {0.0f, 0.0f};
+    const int64_t n_src = (int64_t)hdr->n_src;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t i = ws.perm[r];
-        const float2 v = vis[i];
+        const int64_t i0 = ws.perm[r];
+        const bool mir = i0 >= n_src;  // the Hermitian mirror: conj V of input i0 - n_src
+        const int64_t i = mir ? i0 - n_src : i0;
+        float2 v = vis[i];
+        if (mir) v.y = -v.y;
         const float wt = weight ? weight[i] : 1.0f;
         float2 *val = (float2 *)&ws.rec[r];  // the value half of the record
         *val = make_float2(v.x * wt, v.y * wt);
+        bound += fabsf(v.x * wt) + fabsf(v.y * wt);
         acc = ff_add(acc, ff{wt, 0.0f});
     }
+    for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(FULL, bound, o);
+    if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = bound;
     for (int o = 16; o > 0; o >>= 1) {
         const ff other = {__shfl_xor_sync(FULL, acc.hi, o), __shfl_xor_sync(FULL, acc.lo, o)};
         acc = ff_add(acc, other);
@@ -560,9 +586,13 @@ __global__ void __launch_bounds__(256) bin_values_kernel(const float2 *vis, cons
     if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = (double)acc.hi + (double)acc.lo;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_part[k];
+        double t = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            t += s_part[k];
+            b += s_bound[k];
+        }
         ws.wpart[blockIdx.x] = t;
+        if (det) ws.vpart[blockIdx.x] = b;
     }
 }
 
@@ -580,6 +610,211 @@ __global__ void __launch_bounds__(1024) values_finalize_kernel(const double *wpa
     }
     if (threadIdx.x == 0)
         hdr->stats.sum_weight = unit_weights ? (double)hdr->stats.n_binned : s[0];
+}
+
+// ------------------------------------------------------------------------
+// Deterministic mode (RICK_OPT_DETERMINISTIC): the ranks the key pass takes
+// from atomics order a bin's records by arrival, which differs from run to
+// run.  Instead, (key, input index) pairs are sorted by a stable LSD radix
+// sort -- RICK_DET_DIGIT-bit digits, least significant first, over blocks of
+// RICK_DET_BLOCK records -- so that the records of each bin are in input
+// order, and then gathered.  A dropped record's all-ones key sorts after every
+// bin in every pass.
+
+// Per block, the count of each digit: cnt[digit * nblk + block] (digit-major,
+// so that one exclusive scan gives every (digit, block) its first position).
+__global__ void __launch_bounds__(256) det_hist_kernel(const uint32_t *key, int64_t n, int shift,
+                                                       uint32_t *cnt, uint32_t nblk)
+{
+    __shared__ uint32_t h[1 << RICK_DET_DIGIT];
+    for (int d = threadIdx.x; d < (1 << RICK_DET_DIGIT); d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * RICK_DET_BLOCK;
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < RICK_DET_BLOCK; j += blockDim.x) {
+        const int64_t i = b0 + j;
+        const uint32_t d = i < n ? (key[i] >> shift) & ((1u << RICK_DET_DIGIT) - 1) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (d != 0xFFFFFFFFu && (peers & ((1u << lane) - 1u)) == 0u)  // one add per digit
+            atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < (1 << RICK_DET_DIGIT); d += blockDim.x)
+        cnt[(size_t)d * nblk + blockIdx.x] = h[d];
+}
+
+// One stable pass: the block's records in rounds of 256 consecutive ones; a
+// record's place is its (digit, block) start, plus the records of its digit in
+// the block's earlier rounds, in earlier warps of its round and in earlier
+// lanes of its warp.  idx_in NULL: the identity (the first pass).
+__global__ void __launch_bounds__(256) det_scatter_kernel(const uint32_t *key_in,
+                                                          const uint32_t *idx_in, int64_t n,
+                                                          int shift, const uint32_t *start,
+                                                          uint32_t nblk, uint32_t *key_out,
+                                                          uint32_t *idx_out)
+{
+    constexpr int ND = 1 << RICK_DET_DIGIT;
+    __shared__ uint32_t run[ND];     // next place of each digit
+    __shared__ uint32_t wc[8][ND];   // this round: records of each digit per warp
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int d = t; d < ND; d += 256) {
+        run[d] = start[(size_t)d * nblk + blockIdx.x];
+        for (int w = 0; w < 8; ++w) wc[w][d] = 0;
+    }
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * RICK_DET_BLOCK;
+    for (int r = 0; r < RICK_DET_BLOCK / 256; ++r) {
+        const int64_t i = b0 + r * 256 + t;
+        const bool live = i < n;
+        uint32_t k = 0, idx = 0, d = 0xFFFFFFFFu;
+        if (live) {
+            k = key_in[i];
+            idx = idx_in ? idx_in[i] : (uint32_t)i;
+            d = (k >> shift) & (ND - 1);
+        }
+        const unsigned peers = __match_any_sync(FULL, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (live && rank == 0) wc[wid][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (live) {
+            uint32_t pos = run[d] + (uint32_t)rank;
+            for (int w = 0; w < wid; ++w) pos += wc[w][d];
+            key_out[pos] = k;
+            idx_out[pos] = idx;
+        }
+        __syncthreads();
+        for (int dd = t; dd < ND; dd += 256) {
+            uint32_t tot = 0;
+            for (int w = 0; w < 8; ++w) {
+                tot += wc[w][dd];
+                wc[w][dd] = 0;
+            }
+            run[dd] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// The records in sorted order: record r is input sidx[r] (records past n_src
+// mirror input i - n_src; with CORR the weighted sum of the correlations).
+// Each block also sums |Re| + |Im| of its record values (a fixed order: the
+// grid-stride split and the reductions depend only on the sizes), the bound
+// from which the fixed-point scale of the tile sums is chosen.
+template <bool CORR>
+__global__ void __launch_bounds__(256) det_records_kernel(const uint32_t *sidx, const float2 *vis,
+                                                          const float *weight, WsPtrs ws,
+                                                          int n_corr, int64_t n_src)
+{
+    __shared__ float s_part[8];
+    const int64_t nb = ws.hdr->stats.n_binned;
+    float bound = 0.0f;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = sidx[r];
+        float2 v;
+        if (CORR) {
+            v = make_float2(0.0f, 0.0f);
+            for (int c = 0; c < n_corr; ++c) {
+                const float2 vc = vis[(int64_t)i * n_corr + c];
+                const float wc = weight ? weight[(int64_t)i * n_corr + c] : 1.0f;
+                v.x = __fmaf_rn(vc.x, wc, v.x);
+                v.y = __fmaf_rn(vc.y, wc, v.y);
+            }
+        } else {
+            const bool mir = (int64_t)i >= n_src;
+            const int64_t src = mir ? (int64_t)i - n_src : (int64_t)i;
+            v = vis[src];
+            if (mir) v.y = -v.y;
+            const float wt = weight ? weight[src] : 1.0f;
+            v = make_float2(v.x * wt, v.y * wt);
+        }
+        const float2 fr = ws.frac[i];
+        ws.perm[r] = i;
+        ws.rec[r] = make_float4(v.x, v.y, fr.x, fr.y);
+        ws.rcell[r] = ws.cell[i];
+        bound += fabsf(v.x) + fabsf(v.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(FULL, bound, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = bound;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_part[k];
+        ws.vpart[blockIdx.x] = t;
+    }
+}
+
+// The fixed-point scale: 2^k with the sum of all |values| (each kernel weight
+// is at most about 1, so every tile sum is bounded by it) below 2^60, so that
+// 64-bit sums cannot overflow.
+__global__ void det_scale_kernel(WsHeader *hdr, const double *vpart, int nparts)
+{
+    double b = 0.0;
+    for (int i = 0; i < nparts; ++i) b += vpart[i];
+    int e = 0;
+    frexp(b * 1.01 + 1e-30, &e);  // b * 1.01 < 2^e
+    int k = 60 - e;
+    k = k > 100 ? 100 : (k < -100 ? -100 : k);
+    hdr->fx_scale = ldexpf(1.0f, k);
+    hdr->fx_inv = ldexpf(1.0f, -k);
+}
+
+// Slots of the tiles gridded by several work items (deterministic mode): a
+// flag per tile, then its exclusive scan is the tile's slot.
+__global__ void det_mc_flags_kernel(const uint32_t *gbase, uint32_t *slot, uint32_t ntiles)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) slot[t] = gbase[t + 1] - gbase[t] > 1 ? 1u : 0u;
+    if (t == ntiles) slot[t] = 0u;
+}
+
+__global__ void det_mc_count_kernel(WsHeader *hdr, const uint32_t *slot, uint32_t ntiles)
+{
+    hdr->mc_count = slot[ntiles];
+}
+
+// Enqueue the deterministic ordering and the records.  Keys of n records are
+// in w.key (input order); nbins bins.
+static rick_status det_sort_records(rick_plan *plan, WsPtrs w, const WsLayout &L, int64_t n,
+                                    const void *vis, const float *weight, int n_corr,
+                                    int64_t n_src, cudaStream_t st)
+{
+    const uint32_t nblk = (uint32_t)((n + RICK_DET_BLOCK - 1) / RICK_DET_BLOCK);
+    int passes = 1;
+    while (passes * RICK_DET_DIGIT < 32 && ((int64_t)1 << (passes * RICK_DET_DIGIT)) <= L.nbins)
+        ++passes;
+    // ping-pong between two (key, index) buffers; the input-order keys in
+    // w.key stay (degridding and the density weights read them)
+    const uint32_t *kin = w.key, *iin = NULL;
+    uint32_t *kbuf[2] = {w.dkey, w.dkey2}, *ibuf[2] = {w.didx, w.rank};
+    if (n > 0) {
+        for (int ps = 0; ps < passes; ++ps) {
+            const int shift = ps * RICK_DET_DIGIT;
+            det_hist_kernel<<<nblk, 256, 0, st>>>(kin, n, shift, w.dcnt, nblk);
+            RICK_LAUNCH_CHECK(plan);
+            RICK_CUDA_TRY(plan, scan_u32(w.dcnt, w.dcnt, (int64_t)nblk << RICK_DET_DIGIT, w.scan,
+                                         st, &plan->launches));
+            uint32_t *ko = kbuf[ps & 1], *io = ibuf[ps & 1];
+            det_scatter_kernel<<<nblk, 256, 0, st>>>(kin, iin, n, shift, w.dcnt, nblk, ko, io);
+            RICK_LAUNCH_CHECK(plan);
+            kin = ko;
+            iin = io;
+        }
+    }
+    int blocks = plan->num_sms * 8;
+    if (blocks > (int)L.ndetblocks + 1) blocks = (int)L.ndetblocks + 1;
+    if (n > 0) {
+        if (n_corr > 1)
+            det_records_kernel<true><<<blocks, 256, 0, st>>>(iin, (const float2 *)vis, weight, w,
+                                                             n_corr, n);
+        else
+            det_records_kernel<false><<<blocks, 256, 0, st>>>(iin, (const float2 *)vis, weight,
+                                                              w, 1, n_src);
+        RICK_LAUNCH_CHECK(plan);
+    }
+    det_scale_kernel<<<1, 1, 0, st>>>(w.hdr, w.vpart, n > 0 ? blocks : 0);
+    RICK_LAUNCH_CHECK(plan);
+    return RICK_OK;
 }
 
 // ------------------------------------------------------------------------
@@ -629,23 +864,38 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     if (n_chan < 0 || (n_chan > 0 && n_vis > 0 && !chan_scale)) return RICK_EINVAL;
     if (n_vis > plan->max_vis) return RICK_ERANGE;
     const rick_params &p = plan->p;
+    // the Hermitian mirror: input-order records, then the mirrored ones (per-
+    // visibility input only: not with channels, correlations or streaming)
+    const int mirror = (p.options & RICK_OPT_HERMITIAN_MIRROR) != 0;
+    if (mirror && (n_chan > 0 || n_corr != 1 || range_src)) return RICK_EINVAL;
+    const int64_t n_src = n_vis;
+    n_vis = rick_n_records(&p, n_src);  // records from here on
     WsLayout L = rick_ws_layout(&p, plan->max_vis);
     if (ws_bytes < L.total) return RICK_ERANGE;
     const int64_t nkb = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) /
                         (RICK_KEY_THREADS * RICK_KEY_ITEMS);
     WsPtrs w = rick_ws_ptrs(ws_dev, L);
     cudaStream_t st = (cudaStream_t)stream;
+    const bool det = (p.options & RICK_OPT_DETERMINISTIC) != 0;
     uint32_t cap = rick_chunk_cap(n_vis, plan->num_sms);
+    if (det) {
+        // enough records per work item that the tiles with several items fit
+        // the workspace's slots (a record is visited by at most four tiles)
+        const int64_t slots = rick_det_slots(&p, rick_n_records(&p, plan->max_vis));
+        int64_t c = (4 * n_vis + slots - 1) / slots;
+        c = (c + 255) & ~(int64_t)255;
+        if (c > cap) cap = (uint32_t)c;
+    }
     int given = !isnan(p.w_min) || range_src != NULL;
 
     bin_init_kernel<<<1, 1, 0, st>>>(w.hdr, (uint64_t)n_vis, cap, given,
                                      isnan(p.w_min) ? 0 : rick_dkey(p.w_min),
                                      isnan(p.w_min) ? 0 : rick_dkey(p.w_max), (uint32_t)nkb,
-                                     range_src);
+                                     range_src, (uint64_t)n_src, mirror);
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
         int blocks = plan->num_sms * 4;
-        wrange_kernel<<<blocks, 256, 0, st>>>(uvw, n_vis, w.hdr, n_chan, chan_scale);
+        wrange_kernel<<<blocks, 256, 0, st>>>(uvw, n_src, w.hdr, n_chan, chan_scale, mirror);
         RICK_LAUNCH_CHECK(plan);
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
@@ -671,6 +921,7 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
         ka.n_chan = n_chan;
         ka.n_corr = n_corr;
         ka.chan_scale = chan_scale;
+        ka.n_src = mirror ? n_src : n_vis;
         ka.bulk = n_chan == 0 && n_corr == 1 && ((uintptr_t)uvw & 15) == 0 &&
                   ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
@@ -687,15 +938,19 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     bin_offsets_kernel<<<(unsigned)((L.nbins + 256) / 256), 256, 0, st>>>(w.suboff, w.offsets,
                                                                           L.nbins);
     RICK_LAUNCH_CHECK(plan);
-    if (n_vis > 0) {
+    if (det) {
+        rick_status ds = det_sort_records(plan, w, L, n_vis, vis, weight, n_corr,
+                                          mirror ? n_src : n_vis, st);
+        if (ds != RICK_OK) return ds;
+    } else if (n_vis > 0) {
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
         if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
         if (n_corr == 1)
-            bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
-                                                                        weight, w, 1);
+            bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
+                n_vis, (const float2 *)vis, weight, w, 1, mirror ? n_src : n_vis);
         else
-            bin_scatter_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
-                                                                       weight, w, n_corr);
+            bin_scatter_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
+                n_vis, (const float2 *)vis, weight, w, n_corr, n_vis);
         RICK_LAUNCH_CHECK(plan);
     }
     uint32_t nt = (uint32_t)L.ntiles;
@@ -704,6 +959,14 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     RICK_LAUNCH_CHECK(plan);
     RICK_CUDA_TRY(plan, scan_u32(w.gbase, w.gbase, L.ntiles + 1, w.scan, st, &plan->launches));
     RICK_CUDA_TRY(plan, scan_u32(w.dbase, w.dbase, L.ntiles + 1, w.scan, st, &plan->launches));
+    if (det) {  // slots of the tiles with several grid work items
+        det_mc_flags_kernel<<<(nt + 256) / 256, 256, 0, st>>>(w.gbase, w.mcslot, nt);
+        RICK_LAUNCH_CHECK(plan);
+        RICK_CUDA_TRY(plan, scan_u32(w.mcslot, w.mcslot, L.ntiles + 1, w.scan, st,
+                                     &plan->launches));
+        det_mc_count_kernel<<<1, 1, 0, st>>>(w.hdr, w.mcslot, nt);
+        RICK_LAUNCH_CHECK(plan);
+    }
     if (stats_dev)
         RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
                                             cudaMemcpyDeviceToDevice, st));
@@ -756,12 +1019,19 @@ extern "C" rick_status rick_bin_values(rick_plan *plan, const void *vis, const f
     const WsLayout L = rick_ws_layout(&plan->p, plan->max_vis);
     WsPtrs w = rick_ws_ptrs(ws_dev, L);
     // one weight partial per block: the workspace holds nkeyblocks + 1 of them
+    // (and ndetblocks + 1 bound partials in deterministic mode)
+    const int det = (plan->p.options & RICK_OPT_DETERMINISTIC) != 0;
     int blocks = plan->num_sms * 8;
     if (blocks > (int)L.nkeyblocks + 1) blocks = (int)L.nkeyblocks + 1;
-    bin_values_kernel<<<blocks, 256, 0, st>>>((const float2 *)vis, weight, w);
+    if (det && blocks > (int)L.ndetblocks + 1) blocks = (int)L.ndetblocks + 1;
+    bin_values_kernel<<<blocks, 256, 0, st>>>((const float2 *)vis, weight, w, det);
     RICK_LAUNCH_CHECK(plan);
     values_finalize_kernel<<<1, 1024, 0, st>>>(w.wpart, blocks, weight == NULL, w.hdr);
     RICK_LAUNCH_CHECK(plan);
+    if (det) {  // the fixed-point scale for the new values
+        det_scale_kernel<<<1, 1, 0, st>>>(w.hdr, w.vpart, blocks);
+        RICK_LAUNCH_CHECK(plan);
+    }
     if (stats_dev)
         RICK_CUDA_TRY(plan, cudaMemcpyAsync(stats_dev, &w.hdr->stats, sizeof(rick_bin_stats),
                                             cudaMemcpyDeviceToDevice, st));
@@ -824,6 +1094,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         return RICK_EINVAL;
     if (n_vis > plan->max_vis) return RICK_ERANGE;
     const rick_params &p = plan->p;
+    if (p.options != 0) return RICK_EINVAL;  // plain binning only
     WsLayout L = rick_ws_layout(&p, plan->max_vis);
     if (ws_bytes < L.total) return RICK_ERANGE;
     // the fixed scratch bounds the problem size
@@ -852,10 +1123,10 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     // the same stages as rick_bin, in the same order
     bin_init_kernel<<<1, 1, 0, st>>>(w.hdr, (uint64_t)n_vis, cap, given,
                                      given ? rick_dkey(p.w_min) : 0, given ? rick_dkey(p.w_max) : 0,
-                                     (uint32_t)nkb, NULL);
+                                     (uint32_t)nkb, NULL, (uint64_t)n_vis, 0);
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
-        wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr, 0, NULL);
+        wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr, 0, NULL, 0);
         RICK_LAUNCH_CHECK(plan);
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
@@ -881,6 +1152,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         ka.n_chan = 0;
         ka.n_corr = 1;
         ka.chan_scale = NULL;
+        ka.n_src = n_vis;
         ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
         RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,
@@ -900,7 +1172,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
         if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
         bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
-                                                                    weight, w, 1);
+                                                                    weight, w, 1, n_vis);
         RICK_LAUNCH_CHECK(plan);
     }
     uint32_t nt = (uint32_t)L.ntiles;

@@ -112,12 +112,17 @@ struct WsHeader {
     uint32_t grid_next, degrid_next;    // work counters of the persistent tile kernels
     uint32_t zero_next;                 // counter of the grid kernel's tile-clearing items
     uint32_t fault;                     // a bounded device-side wait ran out (never expected)
+    uint32_t mirror;                    // records i >= n_src mirror input i - n_src
+    unsigned long long n_src;           // input visibilities of the last rick_bin
+    // deterministic mode: tile sums in fixed point, value = integer * fx_inv
+    float fx_scale, fx_inv;             // 2^k and 2^-k
+    uint32_t mc_count;                  // tiles gridded by several work items
 };
 
 struct WsLayout {
     size_t header, key, rank, cell, frac, perm, rec, rcell, hist, suboff, offsets, gbase, dbase, scan,
-        wpart, bkey, wplane, total;
-    int64_t n_vis, nbins, ntiles, nscan, nkeyblocks;
+        wpart, bkey, wplane, dkey, didx, dkey2, dcnt, vpart, mcslot, mcacc, total;
+    int64_t n_vis, nbins, ntiles, nscan, nkeyblocks, ndetblocks;
 };
 
 // Key pass blocks: 1024 visibilities, staged in 28 KB of shared memory, so that
@@ -131,6 +136,15 @@ struct WsLayout {
 // input's rank within its (bin, sub-counter) range.
 #define RICK_BIN_SUBS 8
 
+// Deterministic mode (RICK_OPT_DETERMINISTIC).  The records of each bin are
+// put in input order by a stable radix sort of (key, input index) in passes of
+// RICK_DET_DIGIT bits over blocks of RICK_DET_BLOCK records.  Tiles gridded by
+// several work items add 64-bit fixed-point sums into one of at most
+// RICK_DET_MAX_MC workspace slots of T x T (re, im) int64 pairs; the records
+// per work item are raised so that no more tiles than that need a slot.
+#define RICK_DET_DIGIT 8
+#define RICK_DET_BLOCK 2048
+#define RICK_DET_MAX_MC 16384
 RICK_HD size_t rick_align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Temporary elements of the recursive exclusive scan of `n` elements.
@@ -144,15 +158,40 @@ static inline int64_t rick_scan_tmp(int64_t n)
     return t + 1;
 }
 
-static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
+// Records of a binning of n_vis visibilities: two per visibility with the
+// Hermitian mirror (V at uvw and conj V at -uvw), else one.
+RICK_HD int64_t rick_n_records(const rick_params *p, int64_t n_vis)
+{
+    return (p->options & RICK_OPT_HERMITIAN_MIRROR) ? 2 * n_vis : n_vis;
+}
+
+// Multi-work-item tiles of a deterministic binning of n_rec records need a
+// slot each; at most RICK_DET_MAX_MC of them.
+static inline int64_t rick_det_slots(const rick_params *p, int64_t n_rec)
+{
+    if (!(p->options & RICK_OPT_DETERMINISTIC)) return 0;
+    // a tile with several work items holds more than 1024 record visits, and
+    // a record is visited by at most four tiles
+    const int64_t b = 4 * n_rec / 1024 + 1;
+    return b < RICK_DET_MAX_MC ? b : RICK_DET_MAX_MC;
+}
+
+static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis_in)
 {
     WsLayout L;
     int64_t nt = p->n / p->tile;
+    const int64_t n_vis = rick_n_records(p, n_vis_in);
+    const bool det = (p->options & RICK_OPT_DETERMINISTIC) != 0;
     L.n_vis = n_vis;
     L.ntiles = (int64_t)p->n_w * nt * nt;
     L.nbins = 4 * L.ntiles;
     L.nkeyblocks = (n_vis + RICK_KEY_THREADS * RICK_KEY_ITEMS - 1) / (RICK_KEY_THREADS * RICK_KEY_ITEMS);
+    L.ndetblocks = det ? (n_vis + RICK_DET_BLOCK - 1) / RICK_DET_BLOCK : 0;
     L.nscan = rick_scan_tmp(RICK_BIN_SUBS * L.nbins + 1);
+    if (det) {
+        const int64_t d = rick_scan_tmp((1 << RICK_DET_DIGIT) * L.ndetblocks + 1);
+        if (d > L.nscan) L.nscan = d;
+    }
     int64_t nv = n_vis > 0 ? n_vis : 1;
     size_t o = 0;
     L.header = o; o += rick_align256(sizeof(WsHeader));
@@ -173,6 +212,17 @@ static inline WsLayout rick_ws_layout(const rick_params *p, int64_t n_vis)
     L.wpart = o;  o += rick_align256(8 * (size_t)(L.nkeyblocks + 1));
     L.bkey = o;   o += rick_align256(8 * (size_t)(p->n_w + 1));
     L.wplane = o; o += rick_align256(16 * (size_t)(p->n_w + 1));
+    // deterministic mode only (empty otherwise): the radix sort's second
+    // (key, index) buffer and digit counts, the value-bound partials of the
+    // fixed-point scale, the slot of each multi-work-item tile and the slots
+    const size_t dn = det ? (size_t)nv : 0;
+    L.dkey = o;   o += rick_align256(4 * dn);
+    L.didx = o;   o += rick_align256(4 * dn);
+    L.dkey2 = o;  o += rick_align256(4 * dn);
+    L.dcnt = o;   o += rick_align256(det ? 4 * (size_t)((1 << RICK_DET_DIGIT) * L.ndetblocks + 1) : 0);
+    L.vpart = o;  o += rick_align256(det ? 8 * (size_t)(L.ndetblocks + 1) : 0);
+    L.mcslot = o; o += rick_align256(det ? 4 * (size_t)(L.ntiles + 1) : 0);
+    L.mcacc = o;  o += rick_align256(16 * (size_t)rick_det_slots(p, n_vis) * p->tile * p->tile);
     L.total = o;
     return L;
 }
@@ -186,6 +236,9 @@ struct WsPtrs {
     double *wpart;
     unsigned long long *bkey;
     float4 *wplane;  // per plane: (w_k hi, w_k lo, w_k as float, 0)
+    uint32_t *dkey, *didx, *dkey2, *dcnt, *mcslot;  // deterministic mode
+    double *vpart;
+    unsigned long long *mcacc;
 };
 
 static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
@@ -209,6 +262,13 @@ static inline WsPtrs rick_ws_ptrs(void *ws, const WsLayout &L)
     w.wpart = (double *)(b + L.wpart);
     w.bkey = (unsigned long long *)(b + L.bkey);
     w.wplane = (float4 *)(b + L.wplane);
+    w.dkey = (uint32_t *)(b + L.dkey);
+    w.didx = (uint32_t *)(b + L.didx);
+    w.dkey2 = (uint32_t *)(b + L.dkey2);
+    w.dcnt = (uint32_t *)(b + L.dcnt);
+    w.vpart = (double *)(b + L.vpart);
+    w.mcslot = (uint32_t *)(b + L.mcslot);
+    w.mcacc = (unsigned long long *)(b + L.mcacc);
     return w;
 }
 

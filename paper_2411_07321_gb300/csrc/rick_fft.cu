@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
     const bool live = pc < m;
     const int p = (live ? pc : 0) + off;
     const bool fp32ph = (w.flags & RICK_PHASE_FP32) != 0;
+    const bool imag = (w.flags & RICK_IMAG_PART) != 0;  // Im of the plane sum instead of Re
     float inv_sumw;
     {
         const double sw = w.hdr->stats.sum_weight;  // nothing gridded: no normalisation
@@ -447,7 +448,8 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
             g.nm1_f = g_lo[gi];
             float cs, sn;
             wphase(w, wk, g, &cs, &sn);
-            g_acc[gi] = fmaf(h[s].x, cs, fmaf(-h[s].y, sn, g_acc[gi]));
+            g_acc[gi] = imag ? fmaf(h[s].x, sn, fmaf(h[s].y, cs, g_acc[gi]))
+                             : fmaf(h[s].x, cs, fmaf(-h[s].y, sn, g_acc[gi]));
         }
     }
     if (!live) return;
@@ -825,7 +827,7 @@ extern "C" rick_status rick_wspread_fft(rick_plan *plan, const float *image_dev,
                                         const void *ws_dev, void *work_dev, size_t work_bytes,
                                         void *planes_dev, uint32_t flags, void *stream)
 {
-    if (!plan || !image_dev || !ws_dev || !work_dev || !planes_dev || !valid_flags(flags))
+    if (!plan || !image_dev || !ws_dev || !work_dev || !planes_dev || !valid_flags(flags, true))
         return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (!fft_args_ok(plan, ws_dev, work_dev, work_bytes) || ((uintptr_t)planes_dev & 7) ||

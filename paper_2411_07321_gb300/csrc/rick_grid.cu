@@ -24,7 +24,16 @@ struct GridArgs {
     int log2T;
     int accumulate;  // add into the planes instead of overwriting them
     uint32_t nzero;  // tile-clearing items (RICK_ZERO_GROUP tiles each); 0 when accumulating
+    const uint32_t *mcslot;     // deterministic mode: slot of each multi-item tile
+    unsigned long long *mcacc;  // deterministic mode: the slots' int64 (re, im) sums
 };
+
+// Accumulation modes of the grid kernel: FP32 shared-memory sums, FP32 rounds
+// folded by compensated summation, or 64-bit fixed point (deterministic: the
+// sums do not depend on the order of the atomics).
+#define GM_PLAIN 0
+#define GM_COMP 1
+#define GM_DET 2
 
 // Tiles per clearing item of the grid kernel.
 #define RICK_ZERO_GROUP 8
@@ -107,11 +116,33 @@ __device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T,
     }
 }
 
-// n records of one segment of the tile's record list, starting at record r0.
+// The same into the 64-bit fixed-point tile: each row sum scaled by 2^k and
+// rounded to an integer, then added with integer atomics (exact, so the tile
+// does not depend on the order in which the groups flush).
 template <int W>
+__device__ __forceinline__ void group_flush_det(unsigned long long *acc64, float fx, int T, int TP,
+                                                int lx, int row, bool live, const float *ar,
+                                                const float *ai)
+{
+    if (!live || (unsigned)row >= (unsigned)T) return;
+#pragma unroll
+    for (int jx = 0; jx < W; ++jx) {
+        int col = lx + jx;
+        if ((unsigned)col < (unsigned)T) {
+            int i = 2 * (row * TP + col);
+            atomicAdd(&acc64[i], (unsigned long long)__float2ll_rn(ar[jx] * fx));
+            atomicAdd(&acc64[i + 1], (unsigned long long)__float2ll_rn(ai[jx] * fx));
+        }
+    }
+}
+
+// n records of one segment of the tile's record list, starting at record r0.
+// DET: the flushes go to the 64-bit fixed-point tile acc64 (scale fx).
+template <int W, bool DET>
 __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n, int x0,
                                             int y0, float *acc_re, float *acc_im, int T, int TP,
-                                            const float2 *coef2)
+                                            const float2 *coef2, unsigned long long *acc64,
+                                            float fx)
 {
     constexpr int G = StreamShape<W>::G;
     const int lane = threadIdx.x & 31, grp = lane / G;
@@ -132,8 +163,12 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         const float4 nq = rec[i + 1];
         const uint32_t ncell = rcell[i + 1];
         if (cell != cur) {
-            group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
-                           (int)(cur >> 16) - y0 + j, live, ar, ai);
+            if (DET)
+                group_flush_det<W>(acc64, fx, T, TP, (int)(cur & 0xFFFFu) - x0,
+                                   (int)(cur >> 16) - y0 + j, live, ar, ai);
+            else
+                group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
+                               (int)(cur >> 16) - y0 + j, live, ar, ai);
 #pragma unroll
             for (int jx = 0; jx < W; ++jx) ar[jx] = ai[jx] = 0.0f;
             cur = cell;
@@ -173,14 +208,19 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         q = nq;
         cell = ncell;
     }
-    group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0 + j,
-                   live, ar, ai);
+    if (DET)
+        group_flush_det<W>(acc64, fx, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0 + j,
+                           live, ar, ai);
+    else
+        group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
+                       (int)(cur >> 16) - y0 + j, live, ar, ai);
 }
 
-template <int W, bool COMP>
+template <int W, int MODE>
 __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_t t, float *sm,
                                           const float2 *coef2)
 {
+    constexpr bool COMP = MODE == GM_COMP, DET = MODE == GM_DET;
     const TileArgs &ta = a.t;
     const uint32_t chunk = b - ta.base[t], nch = ta.base[t + 1] - ta.base[t];
     const int T = 1 << a.log2T, TP = T + 1, TT = T * TP, nt = ta.nt;
@@ -222,9 +262,16 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     // different rows, which then fall in different banks
     float *acc_re = sm, *acc_im = sm + TT;
     float *sum_re = sm + 2 * TT, *sum_im = sm + 3 * TT, *cmp_re = sm + 4 * TT, *cmp_im = sm + 5 * TT;
+    unsigned long long *acc64 = (unsigned long long *)sm;  // DET: (re, im) pairs
+    const float fx = DET ? ta.hdr->fx_scale : 0.0f;
     for (int i = threadIdx.x; i < TT; i += blockDim.x) {
-        acc_re[i] = 0.0f;
-        acc_im[i] = 0.0f;
+        if (DET) {
+            acc64[2 * i] = 0ull;
+            acc64[2 * i + 1] = 0ull;
+        } else {
+            acc_re[i] = 0.0f;
+            acc_im[i] = 0.0f;
+        }
         if (COMP) sum_re[i] = sum_im[i] = cmp_re[i] = cmp_im[i] = 0.0f;
     }
     __syncthreads();
@@ -253,8 +300,8 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
                 const uint32_t per = (a1 - a0 + nstreams - 1) / nstreams;
                 const uint32_t v0 = min(a0 + stream * per, a1), v1 = min(v0 + per, a1);
                 if (streaming && v0 < v1)
-                    grid_stream<W>(ta, s_rs[g] + (v0 - base), v1 - v0, x0, y0, acc_re, acc_im, T,
-                                   TP, coef2);
+                    grid_stream<W, DET>(ta, s_rs[g] + (v0 - base), v1 - v0, x0, y0, acc_re, acc_im,
+                                        T, TP, coef2, acc64, fx);
             }
             base += lg;
         }
@@ -274,11 +321,24 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
     // flush: (-1)^(i+j) folded in; plain stores unless the tile has several chunks
     const int n = ta.n;
     float2 *plane = a.planes + (size_t)k * n * n;
+    if (DET && nch > 1) {  // several work items: exact integer sums in the tile's slot
+        unsigned long long *slot = a.mcacc + (size_t)a.mcslot[t] * 2 * T * T;
+        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+            const int ip = (i >> a.log2T) * TP + (i & (T - 1));
+            const unsigned long long re = acc64[2 * ip], im = acc64[2 * ip + 1];
+            if (re) atomicAdd(&slot[2 * i], re);
+            if (im) atomicAdd(&slot[2 * i + 1], im);
+        }
+        return;
+    }
+    const float fxi = DET ? ta.hdr->fx_inv : 0.0f;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         int row = i >> a.log2T, col = i & (T - 1), ip = row * TP + col;
         int gi = x0 + col, gj = y0 + row;
-        float re = COMP ? sum_re[ip] + cmp_re[ip] : acc_re[ip];
-        float im = COMP ? sum_im[ip] + cmp_im[ip] : acc_im[ip];
+        float re = DET ? __ll2float_rn((long long)acc64[2 * ip]) * fxi
+                 : COMP ? sum_re[ip] + cmp_re[ip] : acc_re[ip];
+        float im = DET ? __ll2float_rn((long long)acc64[2 * ip + 1]) * fxi
+                 : COMP ? sum_im[ip] + cmp_im[ip] : acc_im[ip];
         if ((gi + gj) & 1) {
             re = -re;
             im = -im;
@@ -321,8 +381,8 @@ __device__ __forceinline__ void zero_group(const GridArgs &a, uint32_t z)
 // gridding of the others.  Four CTAs per SM for W <= 8 (64 registers a
 // thread): the record loop is latency-bound, and the extra warps hide more of
 // it than the few spilled registers cost.
-template <int W, bool COMP>
-__global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(GridArgs a)
+template <int W, int MODE>
+__global__ void __launch_bounds__(256, (W <= 8 && MODE == GM_PLAIN) ? 4 : 3) grid_kernel(GridArgs a)
 {
     extern __shared__ float sm[];
     __shared__ uint32_t s_b, s_tile, s_z;
@@ -344,7 +404,7 @@ __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(Gr
         __syncthreads();  // everyone has the item before thread 0 takes the next
         if (b >= total && z >= a.nzero) break;
         if (b < total) {
-            grid_item<W, COMP>(a, b, t, sm, coef2);
+            grid_item<W, MODE>(a, b, t, sm, coef2);
             __syncthreads();  // the accumulator is reused by the next item
         }
         if (z < a.nzero) zero_group(a, z);
@@ -356,19 +416,32 @@ __global__ void __launch_bounds__(256, (W <= 8 && !COMP) ? 4 : 3) grid_kernel(Gr
 // Grid-stride, one warp per tile, 16-byte stores.  Tiles without records are
 // cleared by the grid kernel itself; when gridding adds into existing planes
 // nothing is cleared.
+// Deterministic mode (mcacc != NULL): the int64 slots of those tiles are
+// zeroed instead, accumulating or not (the slots are added into the planes
+// after gridding).
 __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, uint32_t ntiles,
                                                          int nt, int log2T, int n, float2 *planes,
-                                                         WsHeader *hdr, int accumulate)
+                                                         WsHeader *hdr, int accumulate,
+                                                         const uint32_t *mcslot,
+                                                         unsigned long long *mcacc)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr->grid_next = 0;
         hdr->zero_next = 0;
     }
-    if (accumulate) return;
     int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const int T = 1 << log2T, half = T >> 1;  // float4 = two cells
+    if (mcacc) {
+        for (uint32_t t = warp; t < ntiles; t += nwarps) {
+            if (base[t + 1] - base[t] <= 1) continue;
+            ulonglong2 *slot = (ulonglong2 *)(mcacc + (size_t)mcslot[t] * 2 * T * T);
+            for (int i = lane; i < T * T; i += 32) slot[i] = make_ulonglong2(0ull, 0ull);
+        }
+        return;
+    }
+    if (accumulate) return;
     for (uint32_t t = warp; t < ntiles; t += nwarps) {
         if (base[t + 1] - base[t] <= 1) continue;
         uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
@@ -381,9 +454,50 @@ __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, u
     }
 }
 
+// Deterministic mode: the tiles gridded by several work items, from their
+// int64 slots into the planes (written, or added with accumulate), the
+// checkerboard (-1)^(i+j) folded in.  One warp per tile.
+__global__ void __launch_bounds__(256) det_mc_convert_kernel(const uint32_t *base, uint32_t ntiles,
+                                                             int nt, int log2T, int n,
+                                                             float2 *planes, const WsHeader *hdr,
+                                                             int accumulate,
+                                                             const uint32_t *mcslot,
+                                                             const unsigned long long *mcacc)
+{
+    const int lane = threadIdx.x & 31, T = 1 << log2T;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const float inv = hdr->fx_inv;
+    for (uint32_t t = warp; t < ntiles; t += nwarps) {
+        if (base[t + 1] - base[t] <= 1) continue;
+        const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
+        const unsigned long long *slot = mcacc + (size_t)mcslot[t] * 2 * T * T;
+        float2 *plane = planes + (size_t)k * n * n;
+        for (int i = lane; i < T * T; i += 32) {
+            const int row = i >> log2T, col = i & (T - 1);
+            const int gi = (int)(tx << log2T) + col, gj = (int)(ty << log2T) + row;
+            float re = __ll2float_rn((long long)slot[2 * i]) * inv;
+            float im = __ll2float_rn((long long)slot[2 * i + 1]) * inv;
+            if ((gi + gj) & 1) {
+                re = -re;
+                im = -im;
+            }
+            float2 *dst = plane + (size_t)gj * n + gi;
+            if (accumulate) {
+                const float2 o = *dst;
+                re += o.x;
+                im += o.y;
+            }
+            *dst = make_float2(re, im);
+        }
+    }
+}
+
+// n_src: with the Hermitian mirror the inputs (records from n_src on mirror
+// input i - n_src), else 0.
 template <int W>
 __device__ __forceinline__ void degrid_item(const DegridArgs &a, uint32_t b, uint32_t t,
-                                            float2 *stage)
+                                            float2 *stage, uint32_t n_src)
 {
     const TileArgs &ta = a.t;
     const uint32_t chunk = b - ta.base[t];
@@ -431,9 +545,19 @@ __device__ __forceinline__ void degrid_item(const DegridArgs &a, uint32_t b, uin
             sr = fmaf(gy[jy], rr, sr);
             si = fmaf(gy[jy], ri, si);
         }
-        uint32_t m = ta.perm[r];
-        float wt = a.weight ? a.weight[m] : 1.0f;
-        a.vis_out[m] = make_float2(sr * wt, si * wt);
+        const uint32_t m = ta.perm[r];
+        if (n_src == 0) {
+            const float wt = a.weight ? a.weight[m] : 1.0f;
+            a.vis_out[m] = make_float2(sr * wt, si * wt);
+        } else {
+            // the Hermitian mirror: input m' gets its record's value plus the
+            // conjugate of its mirrored record's (two adds onto zero, so the
+            // result does not depend on their order)
+            const bool mir = m >= n_src;
+            const uint32_t src = mir ? m - n_src : m;
+            const float wt = a.weight ? a.weight[src] : 1.0f;
+            atomicAdd(&a.vis_out[src], make_float2(sr * wt, mir ? -si * wt : si * wt));
+        }
     }
 }
 
@@ -443,6 +567,7 @@ __global__ void __launch_bounds__(256) degrid_kernel(DegridArgs a)
     extern __shared__ float2 stage[];
     __shared__ uint32_t s_b, s_tile;
     const uint32_t total = a.t.base[a.t.ntiles];
+    const uint32_t n_src = a.t.hdr->mirror ? (uint32_t)a.t.hdr->n_src : 0u;
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t b = atomicAdd(&a.t.hdr->degrid_next, 1u);
@@ -452,19 +577,21 @@ __global__ void __launch_bounds__(256) degrid_kernel(DegridArgs a)
         __syncthreads();
         const uint32_t b = s_b, t = s_tile;
         if (b >= total) break;
-        degrid_item<W>(a, b, t, stage);
+        degrid_item<W>(a, b, t, stage, n_src);
         __syncthreads();
     }
 }
 
-// Dropped visibilities (key == all ones) get a zero model value.
+// Dropped visibilities (key == all ones) get a zero model value.  With the
+// Hermitian mirror every output is zeroed: both records of an input add into it.
 __global__ void degrid_zero_dropped_kernel(WsHeader *hdr, const uint32_t *key, float2 *vis_out)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->degrid_next = 0;
-    int64_t n = (int64_t)hdr->n_vis;
+    const bool all = hdr->mirror != 0;
+    int64_t n = (int64_t)(all ? hdr->n_src : hdr->n_vis);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (key[i] == 0xFFFFFFFFu) vis_out[i] = make_float2(0.f, 0.f);
+        if (all || key[i] == 0xFFFFFFFFu) vis_out[i] = make_float2(0.f, 0.f);
 }
 
 // ------------------------------------------------------------------------
@@ -507,20 +634,24 @@ static unsigned persistent_blocks(K kernel, size_t smem, int num_sms)
     return (unsigned)(per_sm * num_sms);
 }
 
-template <int W, bool COMP>
+template <int W, int MODE>
 static cudaError_t launch_grid_t(const GridArgs &a, int num_sms, cudaStream_t st)
 {
-    size_t smem = (COMP ? 6 : 2) * (size_t)a.t.T * (a.t.T + 1) * sizeof(float);
-    cudaFuncSetAttribute(grid_kernel<W, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // float words: two T (T + 1) arrays; compensated six; 64-bit sums four
+    const int words = MODE == GM_COMP ? 6 : MODE == GM_DET ? 4 : 2;
+    size_t smem = words * (size_t)a.t.T * (a.t.T + 1) * sizeof(float);
+    cudaFuncSetAttribute(grid_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    grid_kernel<W, COMP><<<persistent_blocks(grid_kernel<W, COMP>, smem, num_sms), 256, smem, st>>>(a);
+    grid_kernel<W, MODE><<<persistent_blocks(grid_kernel<W, MODE>, smem, num_sms), 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int W>
-static cudaError_t launch_grid(const GridArgs &a, bool comp, int num_sms, cudaStream_t st)
+static cudaError_t launch_grid(const GridArgs &a, int mode, int num_sms, cudaStream_t st)
 {
-    return comp ? launch_grid_t<W, true>(a, num_sms, st) : launch_grid_t<W, false>(a, num_sms, st);
+    return mode == GM_COMP ? launch_grid_t<W, GM_COMP>(a, num_sms, st)
+         : mode == GM_DET  ? launch_grid_t<W, GM_DET>(a, num_sms, st)
+                           : launch_grid_t<W, GM_PLAIN>(a, num_sms, st);
 }
 
 template <int W>
@@ -572,15 +703,25 @@ rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int 
     a.nzero = mode != RICK_GRID_OVERWRITE ? 0u
                                           : (a.t.ntiles + RICK_ZERO_GROUP - 1) / RICK_ZERO_GROUP;
     cudaError_t err = cudaSuccess;
-    zero_tiles_kernel<<<accumulate ? 1 : plan->num_sms * 8, 256, 0, st>>>(
-        w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate);
+    const bool det = (p.options & RICK_OPT_DETERMINISTIC) != 0;
+    a.mcslot = det ? w.mcslot : NULL;
+    a.mcacc = det ? w.mcacc : NULL;
+    zero_tiles_kernel<<<(accumulate && !det) ? 1 : plan->num_sms * 8, 256, 0, st>>>(
+        w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate, a.mcslot,
+        a.mcacc);
     RICK_LAUNCH_CHECK(plan);
-    bool comp = p.precision == RICK_PREC_FP32_COMPENSATED;
-#define CALL_GRID(WW) err = launch_grid<WW>(a, comp, plan->num_sms, st)
+    const int gmode = det ? GM_DET : p.precision == RICK_PREC_FP32_COMPENSATED ? GM_COMP : GM_PLAIN;
+#define CALL_GRID(WW) err = launch_grid<WW>(a, gmode, plan->num_sms, st)
     RICK_W_SWITCH(p.support, CALL_GRID);
 #undef CALL_GRID
     ++plan->launches;
     RICK_CUDA_TRY(plan, err);
+    if (det) {
+        det_mc_convert_kernel<<<plan->num_sms * 8, 256, 0, st>>>(
+            w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate, a.mcslot,
+            a.mcacc);
+        RICK_LAUNCH_CHECK(plan);
+    }
     return RICK_OK;
 }
 

@@ -37,7 +37,12 @@ static rick_status check_params(const rick_params *p)
     if (!is_pow2(p->n) || p->n < 16 || p->n > 32768) return RICK_EINVAL;
     if (p->n_w < 1 || p->n_w > 1024) return RICK_EINVAL;
     if (!(p->fov > 0.0) || !isfinite(p->fov)) return RICK_EINVAL;
-    if (p->reserved != 0) return RICK_EINVAL;
+    if (p->options & ~(RICK_OPT_HERMITIAN_MIRROR | RICK_OPT_DETERMINISTIC)) return RICK_EINVAL;
+    // the deterministic tile holds 64-bit sums (2 T (T + 1) 8 bytes of shared
+    // memory) and has its own exact accumulation in place of the compensated one
+    if ((p->options & RICK_OPT_DETERMINISTIC) &&
+        (p->tile > 64 || p->precision != RICK_PREC_FP32))
+        return RICK_EINVAL;
     if (p->image_n != 0 && (p->image_n < 16 || p->image_n > p->n || (p->image_n & 1)))
         return RICK_EINVAL;
     // the image (the kept crop of a padded grid) must stay inside the unit
@@ -271,7 +276,7 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
     if (!out) return RICK_EINVAL;
     rick_status st = check_params(params);
     if (st != RICK_OK) return st;
-    if (max_vis < 0 || max_vis >= (1ll << 31)) return RICK_EINVAL;
+    if (max_vis < 0 || rick_n_records(params, max_vis) >= (1ll << 31)) return RICK_EINVAL;
     rick_plan *pl = (rick_plan *)calloc(1, sizeof(rick_plan));
     if (!pl) return RICK_ENOMEM;
     pl->p = *params;

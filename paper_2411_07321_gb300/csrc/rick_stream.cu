@@ -148,6 +148,7 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (n_chan < 0 || n_chan > RICK_STREAM_MAX_CHAN) return n_chan < 0 ? RICK_EINVAL : RICK_ERANGE;
+    if (plan->p.options & RICK_OPT_HERMITIAN_MIRROR) return RICK_EINVAL;  // resident binning only
     if (n_corr < 1 || n_corr > RICK_MAX_CORR || (n_corr > 1 && n_chan < 1)) return RICK_EINVAL;
     if (n_units > 0 && (!uvw_host || !vis_host || (n_chan > 0 && !scale_host)))
         return RICK_EINVAL;

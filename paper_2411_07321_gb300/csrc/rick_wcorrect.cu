@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
     if (oidx >= (size_t)a.m * a.m) return;
     const int p = (int)(oidx % a.m) + a.off, q = (int)(oidx / a.m) + a.off;
     PixelGeom g = pixel_geom(a, p, q, s_inv_sumw);
+    const bool imag = (a.flags & RICK_IMAG_PART) != 0;  // Im of the sum instead of Re
     float acc = 0.0f;
     const float2 *src = a.planes_in + ((size_t)q * a.n + p);
     PhaseWalker ph;
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(256) wcorrect_kernel(WcArgs a)
     for (int k = 0; k < a.n_w; ++k) {
         float2 F = src[(size_t)k * nn];
         ph.at(a, s_w, k, g);
-        acc = fmaf(F.x, ph.c, fmaf(-F.y, ph.s, acc));
+        acc = imag ? fmaf(F.x, ph.s, fmaf(F.y, ph.c, acc)) : fmaf(F.x, ph.c, fmaf(-F.y, ph.s, acc));
     }
     a.image_out[oidx] = acc * g.scale;
 }
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(256) wcorrect2_kernel(WcArgs a)
     const int pp = (int)(pidx % mh) * 2, qq = (int)(pidx / mh);  // in the image
     const int p = pp + a.off, q = qq + a.off;                      // in the grid frame
     PixelGeom g0 = pixel_geom(a, p, q, s_inv_sumw), g1 = pixel_geom(a, p + 1, q, s_inv_sumw);
+    const bool imag = (a.flags & RICK_IMAG_PART) != 0;  // Im of the sum instead of Re
     float acc0 = 0.0f, acc1 = 0.0f;
     const float4 *src = (const float4 *)(a.planes_in + ((size_t)q * a.n + p));
     PhaseWalker ph0, ph1;
@@ -78,8 +80,13 @@ __global__ void __launch_bounds__(256) wcorrect2_kernel(WcArgs a)
         const float4 F = src[(size_t)k * half_nn];
         ph0.at(a, s_w, k, g0);
         ph1.at(a, s_w, k, g1);
-        acc0 = fmaf(F.x, ph0.c, fmaf(-F.y, ph0.s, acc0));
-        acc1 = fmaf(F.z, ph1.c, fmaf(-F.w, ph1.s, acc1));
+        if (imag) {
+            acc0 = fmaf(F.x, ph0.s, fmaf(F.y, ph0.c, acc0));
+            acc1 = fmaf(F.z, ph1.s, fmaf(F.w, ph1.c, acc1));
+        } else {
+            acc0 = fmaf(F.x, ph0.c, fmaf(-F.y, ph0.s, acc0));
+            acc1 = fmaf(F.z, ph1.c, fmaf(-F.w, ph1.s, acc1));
+        }
     }
     *(float2 *)(a.image_out + ((size_t)qq * a.m + pp)) =
         make_float2(acc0 * g0.scale, acc1 * g1.scale);
@@ -141,7 +148,8 @@ extern "C" rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_d
 extern "C" rick_status rick_wspread(rick_plan *plan, const float *image_dev, const void *ws_dev,
                                     void *planes_dev, uint32_t flags, void *stream)
 {
-    if (!plan || !planes_dev || !ws_dev || !image_dev || !valid_flags(flags)) return RICK_EINVAL;
+    if (!plan || !planes_dev || !ws_dev || !image_dev || !valid_flags(flags, true))
+        return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
     if (((uintptr_t)ws_dev & 255) || ((uintptr_t)planes_dev & 7) || ((uintptr_t)image_dev & 3))
         return RICK_EINVAL;

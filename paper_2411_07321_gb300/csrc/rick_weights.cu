@@ -143,6 +143,7 @@ extern "C" rick_status rick_density_weights(rick_plan *plan, int64_t n_vis,
         return RICK_EINVAL;
     if (n_vis > plan->max_vis) return RICK_ERANGE;
     const rick_params &p = plan->p;
+    if (p.options & RICK_OPT_HERMITIAN_MIRROR) return RICK_EINVAL;  // per-input records only
     const DensityLayout D = density_layout(&p);
     if (scratch_bytes < D.total) return RICK_ERANGE;
     const WsPtrs w = rick_ws_ptrs(ws_dev, rick_ws_layout(&p, plan->max_vis));

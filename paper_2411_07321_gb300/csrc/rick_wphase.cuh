@@ -121,9 +121,12 @@ static WcArgs make_args(rick_plan *plan, const void *ws_dev, uint32_t flags)
     return a;
 }
 
-static bool valid_flags(uint32_t f)
+// Flags of an imaging call (w-correction, plane sum) or, with adjoint, of a
+// w-spreading call, which has no imaginary part to select.
+static bool valid_flags(uint32_t f, bool adjoint = false)
 {
-    return (f & ~(RICK_N_CORRECT | RICK_NORMALIZE | RICK_N_DIVIDE | RICK_PHASE_FP32)) == 0 &&
-           !((f & RICK_N_CORRECT) && (f & RICK_N_DIVIDE));
+    const uint32_t known = RICK_N_CORRECT | RICK_NORMALIZE | RICK_N_DIVIDE | RICK_PHASE_FP32 |
+                           (adjoint ? 0u : RICK_IMAG_PART);
+    return (f & ~known) == 0 && !((f & RICK_N_CORRECT) && (f & RICK_N_DIVIDE));
 }
 

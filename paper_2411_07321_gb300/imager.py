@@ -36,20 +36,25 @@ class Imager:
                  tile: int = 64, w_range: tuple[float, float] | None = None,
                  kb_beta: float = math.nan, gauss_sigma: float = math.nan,
                  precision: str = "fp32", max_vis: int = 1 << 20, device=None,
-                 image_n: int | None = None, fused: bool = True):
+                 image_n: int | None = None, fused: bool = True,
+                 hermitian_mirror: bool = False, deterministic: bool = False):
         """n is the grid side; the image is the central image_n x image_n crop
         (default n: no padding), with pixel size fov / n.  With ``fused`` (and n
         in 256 ... 8192) images are made by the fused sparse transform +
         w-correction (rick_grid_sparse, rick_fft_wcorrect); otherwise, and in
         the explicit grid / fft / wcorrect stages, by cuFFT in place and the
-        plane-sum kernel."""
+        plane-sum kernel.  ``hermitian_mirror`` grids every visibility also as
+        conj(V) at -uvw (RICK_OPT_HERMITIAN_MIRROR); ``deterministic`` makes
+        binning and gridding bitwise repeatable (RICK_OPT_DETERMINISTIC)."""
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("Imager runs on a CUDA device only")
         wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)
         self.params = R.make_params(n, n_w, fov, KERNELS[kernel], support, wmin, wmax, kb_beta,
                                     gauss_sigma, tile, PRECISIONS[precision],
-                                    0 if image_n is None else image_n)
+                                    0 if image_n is None else image_n,
+                                    (R.RICK_OPT_HERMITIAN_MIRROR if hermitian_mirror else 0) |
+                                    (R.RICK_OPT_DETERMINISTIC if deterministic else 0))
         self.n, self.n_w, self.max_vis = int(n), int(n_w), int(max_vis)
         self.m = int(image_n) if image_n else self.n
         with torch.cuda.device(self.device):
@@ -193,17 +198,22 @@ class Imager:
         R.rick_wspread_fft(self.plan, image.data_ptr(), self.ws.data_ptr(), w.data_ptr(),
                            w.numel(), self.planes.data_ptr(), flags, self._stream())
 
-    def fused_tiles(self) -> tuple[int, int]:
+    def fused_tiles(self, planes: bool = False):
         """(plane, uv-tile) and (plane, tile-row) pairs the last fft_wcorrect read
-        (from the flags at the head of its work buffer)."""
+        (from the flags at the head of its work buffer); with ``planes`` also the
+        number of planes it transformed."""
         if self._fwork is None:
-            return 0, 0
+            return (0, 0, 0) if planes else (0, 0)
         nt = self.n // self.params.tile
         al = lambda x: (x + 255) // 256 * 256
         nf = self.n_w * nt * nt
         tiles = int(self._fwork[:nf].sum())
-        rows = int(self._fwork[al(nf):al(nf) + self.n_w * nt].sum())
-        return tiles, rows
+        o = al(nf)
+        rows = int(self._fwork[o:o + self.n_w * nt].sum())
+        if not planes:
+            return tiles, rows
+        o += al(self.n_w * nt)
+        return tiles, rows, int(self._fwork[o:o + self.n_w].sum())
 
     def wspread(self, image: torch.Tensor, flags: int = IMAGE_FLAGS):
         self._check(image, torch.float32, (self.m, self.m), "image")
@@ -357,6 +367,15 @@ class Imager:
         else:
             self._out_done[i] = None
         return img
+
+    def join_out(self):
+        """Make the current stream wait for this imager's pending copies into
+        ``out_host`` (enqueue only): work or events recorded on the stream
+        afterwards follow those copies."""
+        cur = torch.cuda.current_stream(self.device)
+        for ev in getattr(self, "_out_done", None) or ():
+            if ev is not None:
+                cur.wait_event(ev)
 
     def wait_out(self):
         """Wait until the copies into ``out_host`` of ``image_streamed`` are done."""

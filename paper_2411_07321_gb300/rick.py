@@ -20,9 +20,12 @@ LIB_PATH = os.path.join(_HERE, "librick.so")
 RICK_OK, RICK_EINVAL, RICK_ENOMEM, RICK_ECUDA, RICK_ECUFFT, RICK_ERANGE = 0, -1, -2, -3, -4, -5
 RICK_KERNEL_GAUSS, RICK_KERNEL_KB = 0, 1
 RICK_PREC_FP32, RICK_PREC_FP32_COMPENSATED = 0, 1
-RICK_N_CORRECT, RICK_NORMALIZE, RICK_N_DIVIDE, RICK_PHASE_FP32 = 1, 2, 4, 8
+RICK_N_CORRECT, RICK_NORMALIZE, RICK_N_DIVIDE, RICK_PHASE_FP32, RICK_IMAG_PART = 1, 2, 4, 8, 16
+RICK_OPT_HERMITIAN_MIRROR, RICK_OPT_DETERMINISTIC = 1, 2
 RICK_WEIGHT_UNIFORM, RICK_WEIGHT_BRIGGS = 1, 2
 RICK_MAX_CORR = 4
+(RICK_PROBE_SMEM_RMW, RICK_PROBE_SMEM_ATOMIC_F32, RICK_PROBE_SMEM_ATOMIC_U32,
+ RICK_PROBE_SMEM_ATOMIC_U64, RICK_PROBE_FFMA, RICK_PROBE_FFMA2) = range(6)
 
 
 class RickError(RuntimeError):
@@ -37,7 +40,7 @@ class rick_params(ctypes.Structure):
                 ("kernel", ctypes.c_int32), ("support", ctypes.c_int32),
                 ("kb_beta", ctypes.c_double), ("gauss_sigma", ctypes.c_double),
                 ("tile", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("image_n", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("image_n", ctypes.c_int32), ("options", ctypes.c_int32)]
 
 
 class rick_bin_stats(ctypes.Structure):
@@ -61,7 +64,8 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_stream_bytes", "rick_image_host", "rick_bin_channels",
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
            "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
-           "rick_fft_wcorrect", "rick_wspread_fft", "rick_fused_work_bytes"]
+           "rick_fft_wcorrect", "rick_wspread_fft", "rick_fused_work_bytes",
+           "rick_probe_throughput"]
 
 
 def _load():
@@ -111,6 +115,7 @@ def _load():
         "rick_wcorrect_stack": [vp, vp, vp, vp, u32, vp],
         "rick_wspread": [vp, vp, vp, vp, u32, vp],
         "rick_degrid": [vp, vp, vp, vp, vp, vp],
+        "rick_probe_throughput": [i32, ctypes.POINTER(ctypes.c_double)],
     }.items():
         f = getattr(L, name)
         f.restype = i32
@@ -132,10 +137,10 @@ def _check(fn: str, s: int) -> None:
 
 def make_params(n, n_w, fov, kernel=RICK_KERNEL_KB, support=7, w_min=math.nan, w_max=math.nan,
                 kb_beta=math.nan, gauss_sigma=math.nan, tile=64,
-                precision=RICK_PREC_FP32, image_n=0) -> rick_params:
+                precision=RICK_PREC_FP32, image_n=0, options=0) -> rick_params:
     return rick_params(int(n), int(n_w), float(fov), float(w_min), float(w_max), int(kernel),
                        int(support), float(kb_beta), float(gauss_sigma), int(tile),
-                       int(precision), int(image_n), 0)
+                       int(precision), int(image_n), int(options))
 
 
 def rick_plan_create(params: rick_params, max_vis: int) -> int:
@@ -190,6 +195,13 @@ def rick_plan_fft_bytes(plan: int) -> int:
     b = ctypes.c_size_t()
     _check("rick_plan_fft_bytes", _L.rick_plan_fft_bytes(plan, ctypes.byref(b)))
     return b.value
+
+
+def rick_probe_throughput(kind: int) -> float:
+    """Operations per SM clock of one unit of the current device (RICK_PROBE_*)."""
+    v = ctypes.c_double()
+    _check("rick_probe_throughput", _L.rick_probe_throughput(int(kind), ctypes.byref(v)))
+    return v.value
 
 
 def rick_bin_layout(plan: int) -> rick_bin_view:

@@ -86,11 +86,12 @@ def test_invalid_params_rejected_on_host(R, bad):
 
 
 def test_crop_params(R):
-    """A crop relaxes the unit-circle bound to the kept field; reserved must be 0."""
+    """A crop relaxes the unit-circle bound to the kept field; unknown option bits
+    are refused."""
     kw = dict(n=256, n_w=8, fov=2.0, kernel=1, support=7, tile=32)
     R.rick_workspace_bytes(R.make_params(**kw, image_n=128), 1000)  # 2 * 0.5 / sqrt 2 < 1
     p = R.make_params(**dict(kw, fov=0.03))
-    p.reserved = 1
+    p.options = 4
     with pytest.raises(R.RickError):
         R.rick_workspace_bytes(p, 1000)
 

@@ -66,6 +66,19 @@ def build_case(P, name, dev):
     return im, op, d, t
 
 
+# The raw whole-image error (no taper weighting) of each case, bounded.  The
+# division by C(l) C(m) multiplies the FP32 transform's rounding near the image
+# corners by up to max 1/(C C) (about 3e3 for KB W=7 at these sizes, 3e4 for
+# W=9, unbounded for a truncated Gaussian whose C crosses zero), so the raw
+# error meets the 1e-5 bar only where that amplification is small (W=1, even
+# W=4); elsewhere the bound is twice the measured value, to catch a
+# regression.  Padding the grid (test_padding) brings the raw error of the kept
+# field under 1e-5 for every kernel.
+RAW_BOUND = {"gauss7_t32": 1e-1, "kb7_t16": 5e-5, "kb9_t32_ragged": 5e-4, "w1_t8": 1e-5,
+             "even_w4_t16": 1e-5, "nw1": 2e-5, "given_range": 5e-5, "compensated": 7e-5,
+             "gauss_small_fov_drops": 1.2e-1}
+
+
 def taper_2d(op):
     """C(l_p) C(m_q) / C(0)^2 from the oracle (1 for W == 1)."""
     c = np.array([oracle.taper(op, (i - op.n // 2) / op.n) for i in range(op.n)])
@@ -155,6 +168,7 @@ def test_stages_match_oracle(P, name):
     print(f"{name}: image error vs FP64 oracle: full {e['full']:.2e}, tapered "
           f"{e['tapered']:.2e}, inner {e['inner']:.2e} (of peak)")
     assert e["tapered"] <= TOL and e["inner"] <= TOL, e
+    assert e["full"] <= RAW_BOUND[name], e
     im.close()
 
 

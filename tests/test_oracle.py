@@ -195,12 +195,19 @@ def test_bin_is_stable_counting_sort_with_edge_classes():
     counts = np.bincount(key[kept], minlength=oracle.nbins(p))
     assert np.array_equal(off, np.concatenate([[0], np.cumsum(counts)]))
     nt = n // T
-    for i in kept[:500]:
+    # the edge class from the footprint itself: enumerate its W x W cells and
+    # collect the tiles they fall in, relative to the corner's tile
+    by_tiles = {frozenset({(0, 0)}): 0, frozenset({(0, 0), (1, 0)}): 1,
+                frozenset({(0, 0), (1, 0), (0, 1), (1, 1)}): 2, frozenset({(0, 0), (0, 1)}): 3}
+    classes = set()
+    for i in kept:
         ax, ay, k = b["ax"][i], b["ay"][i], b["plane"][i]
-        east = (ax % T) + W - 1 >= T
-        south = (ay % T) + W - 1 >= T
-        cls = {(0, 0): 0, (1, 0): 1, (1, 1): 2, (0, 1): 3}[(int(east), int(south))]
+        tiles = frozenset(((ax + jx) // T - ax // T, (ay + jy) // T - ay // T)
+                          for jx in range(W) for jy in range(W))
+        cls = by_tiles[tiles]  # a footprint never reaches west, north or two tiles away
+        classes.add(cls)
         assert key[i] == ((k * nt + ay // T) * nt + ax // T) * 4 + cls
+    assert classes == {0, 1, 2, 3}  # every class occurs
 
 
 # ---------------------------------------------------------------- the image vs Eq. 1's DFT
