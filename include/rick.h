@@ -164,6 +164,18 @@ rick_status rick_plan_set_image_n(rick_plan *plan, int32_t image_n);
  * not positive. */
 double rick_kb_beta(int32_t support, double alpha);
 
+/* Poll limit of the binning's bounded device-side wait (the key pass waits on
+ * an mbarrier for the bulk copies of its inputs into shared memory).  Past the
+ * limit a block gives up: it leaves its inputs out, lets its copies land (a
+ * second wait, always with the default limit) and returns, and the binning
+ * reports n_binned = -1 (and must not be used).  The default,
+ * RICK_WAIT_POLLS_DEFAULT, is far more than a copy ever needs; polls = 0 gives
+ * up without polling, which makes the give-up path run, for testing it.  The
+ * paper has no counterpart.  Host-only; affects calls enqueued afterwards.
+ * RICK_EINVAL for a NULL plan. */
+#define RICK_WAIT_POLLS_DEFAULT (1u << 24)
+rick_status rick_plan_set_wait_limit(rick_plan *plan, uint32_t polls);
+
 /* Number of library kernels this plan has enqueued since it was created
  * (cuFFT's kernels are not included), for launch accounting. */
 rick_status rick_plan_launch_count(const rick_plan *plan, uint64_t *count);

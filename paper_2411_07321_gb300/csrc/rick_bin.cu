@@ -245,6 +245,7 @@ struct KeyArgs {
     int n_corr;               // correlations per visibility (weights [n_vis][n_corr])
     const double *chan_scale;
     int64_t n_src;            // inputs; records i >= n_src mirror input i - n_src (n_vis = 2 n_src)
+    uint32_t wait_polls;      // limit of the wait for the block's bulk copies
     WsPtrs ws;
 };
 
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
         }
     }
     __syncthreads();
-    const bool landed = !bulk || rick_mbar_wait(&s_bar, 0, 1u << 24);
+    const bool landed = !bulk || rick_mbar_wait(&s_bar, 0, a.wait_polls);
     if (!__syncthreads_and(landed)) {
         // the copy did not complete in time (never expected): leave this block's
         // inputs out of the binning, flag the fault (reported as n_binned < 0),
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(RICK_KEY_THREADS) bin_key_kernel(KeyArgs a)
             a.ws.wpart[blockIdx.x] = 0.0;
         }
         for (int i = threadIdx.x; i < nitems; i += blockDim.x) a.ws.key[blk0 + i] = 0xFFFFFFFFu;
-        rick_mbar_wait(&s_bar, 0, 1u << 24);
+        rick_mbar_wait(&s_bar, 0, RICK_WAIT_POLLS);  // drain: the copies land before the block ends
         return;
     }
     const bool degenerate = rick_dbits(hdr->dw) == 0;
@@ -922,6 +923,7 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
         ka.n_corr = n_corr;
         ka.chan_scale = chan_scale;
         ka.n_src = mirror ? n_src : n_vis;
+        ka.wait_polls = plan->wait_polls;
         ka.bulk = n_chan == 0 && n_corr == 1 && ((uintptr_t)uvw & 15) == 0 &&
                   ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
@@ -1153,6 +1155,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
         ka.n_corr = 1;
         ka.chan_scale = NULL;
         ka.n_src = n_vis;
+        ka.wait_polls = plan->wait_polls;
         ka.bulk = ((uintptr_t)uvw & 15) == 0 && ((uintptr_t)weight & 15) == 0;
         const size_t smem = key_pass_smem(p.n_w);
         RICK_CUDA_TRY(plan, cudaFuncSetAttribute(bin_key_kernel,

@@ -85,6 +85,7 @@ struct rick_plan {
     KernelPoly poly;   // kernel-weight polynomials (host copy, passed to kernels)
     rick_status sticky;
     unsigned long long launches;  // library kernels enqueued so far (cuFFT's not included)
+    uint32_t wait_polls;          // poll limit of the key pass's bounded wait for its copies
     // streaming from host memory (created on first use): the copy stream and
     // its events -- start of a call, chunk copied into staging buffer b,
     // staging buffer b free again, uvw chunk resident, resident uvw area a
@@ -135,6 +136,9 @@ struct WsLayout {
 // instead of one.  The value a counter held before an input's atomic is the
 // input's rank within its (bin, sub-counter) range.
 #define RICK_BIN_SUBS 8
+// Polls of a bounded device-side wait before it gives up (and the drain wait
+// of a block that gave up: its copies must land before its shared memory goes).
+#define RICK_WAIT_POLLS RICK_WAIT_POLLS_DEFAULT
 
 // Deterministic mode (RICK_OPT_DETERMINISTIC).  The records of each bin are
 // put in input order by a stable radix sort of (key, input index) in passes of

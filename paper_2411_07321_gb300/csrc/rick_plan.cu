@@ -281,6 +281,7 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
     if (!pl) return RICK_ENOMEM;
     pl->p = *params;
     pl->max_vis = max_vis;
+    pl->wait_polls = RICK_WAIT_POLLS;
     if (cudaGetDevice(&pl->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device) !=
             cudaSuccess ||
@@ -380,6 +381,13 @@ extern "C" rick_status rick_plan_set_image_n(rick_plan *plan, int32_t image_n)
     rick_status st = check_params(&q);
     if (st != RICK_OK) return st;
     plan->p = q;
+    return RICK_OK;
+}
+
+extern "C" rick_status rick_plan_set_wait_limit(rick_plan *plan, uint32_t polls)
+{
+    if (!plan) return RICK_EINVAL;
+    plan->wait_polls = polls;
     return RICK_OK;
 }
 

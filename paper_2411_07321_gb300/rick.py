@@ -22,6 +22,7 @@ RICK_KERNEL_GAUSS, RICK_KERNEL_KB = 0, 1
 RICK_PREC_FP32, RICK_PREC_FP32_COMPENSATED = 0, 1
 RICK_N_CORRECT, RICK_NORMALIZE, RICK_N_DIVIDE, RICK_PHASE_FP32, RICK_IMAG_PART = 1, 2, 4, 8, 16
 RICK_OPT_HERMITIAN_MIRROR, RICK_OPT_DETERMINISTIC = 1, 2
+RICK_WAIT_POLLS_DEFAULT = 1 << 24
 RICK_WEIGHT_UNIFORM, RICK_WEIGHT_BRIGGS = 1, 2
 RICK_MAX_CORR = 4
 (RICK_PROBE_SMEM_RMW, RICK_PROBE_SMEM_ATOMIC_F32, RICK_PROBE_SMEM_ATOMIC_U32,
@@ -65,7 +66,7 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
            "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
            "rick_fft_wcorrect", "rick_wspread_fft", "rick_fused_work_bytes",
-           "rick_probe_throughput"]
+           "rick_probe_throughput", "rick_plan_set_wait_limit"]
 
 
 def _load():
@@ -116,6 +117,7 @@ def _load():
         "rick_wspread": [vp, vp, vp, vp, u32, vp],
         "rick_degrid": [vp, vp, vp, vp, vp, vp],
         "rick_probe_throughput": [i32, ctypes.POINTER(ctypes.c_double)],
+        "rick_plan_set_wait_limit": [vp, ctypes.c_uint32],
     }.items():
         f = getattr(L, name)
         f.restype = i32
@@ -195,6 +197,10 @@ def rick_plan_fft_bytes(plan: int) -> int:
     b = ctypes.c_size_t()
     _check("rick_plan_fft_bytes", _L.rick_plan_fft_bytes(plan, ctypes.byref(b)))
     return b.value
+
+
+def rick_plan_set_wait_limit(plan: int, polls: int) -> None:
+    _check("rick_plan_set_wait_limit", _L.rick_plan_set_wait_limit(plan, int(polls)))
 
 
 def rick_probe_throughput(kind: int) -> float:

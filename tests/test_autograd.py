@@ -116,3 +116,58 @@ def test_chi2_gradient_matches_finite_differences(P):
         assert abs(fd - exact.flat[p]) <= 1e-6 * abs(exact.flat[p]) + 1e-13 * abs(cp) / h
         assert g.flat[p] == pytest.approx(fd, rel=1e-3, abs=1e-4 * np.abs(exact).max())
     im.close()
+
+
+@pytest.mark.slow
+def test_chi2_gradient_at_full_size(P):
+    """The differentiable configuration at its full size: 1e7 visibilities (4
+    channels of the LOFAR-like tracks), a 2048^2 grid with 16 w-planes, KB W=7,
+    the gradient of chi^2 with respect to a 50-source float32 image -- against
+    the oracle's exact gradient -2 Re D^H w (V_obs - D x) and central finite
+    differences of the oracle's chi^2 at sampled pixels."""
+    from paper_2411_07321_gb300.autograd import chi2
+
+    wl = synth.WORKLOADS["diff"]
+    d = synth.generate(wl.obs)
+    dev = torch.device("cuda:0")
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel=wl.kernel, support=wl.support, tile=wl.tile,
+                  max_vis=len(d["vis"]), device=dev)
+    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov, kernel=oracle.KB, support=wl.support,
+                       tile=wl.tile)
+    t = {k: torch.from_numpy(d[k]).to(dev) for k in ("uvw", "vis", "weight")}
+    im.bin(t["uvw"], t["vis"], t["weight"])
+    torch.cuda.synchronize()
+    st = im.stats()
+    rng = np.random.default_rng(4)
+    x = np.zeros((wl.n, wl.n))
+    idx = rng.choice(wl.n * wl.n, 50, replace=False)
+    x.flat[idx] = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 50))
+    x32 = x.astype(np.float32)
+    keep = oracle.coords(op, d["uvw"])["status"] == 0
+    w = d["weight"].astype(np.float64)
+    vobs = d["vis"].astype(np.complex128)
+    xt = torch.from_numpy(x32).to(dev).requires_grad_(True)
+    wt = t["weight"] * torch.from_numpy(keep.astype(np.float32)).to(dev)
+    chi2(xt, im, t["vis"], wt).backward()
+    g = xt.grad.double().cpu().numpy()
+    im.close()
+
+    _, pred = _oracle_chi2(op, d, x32.astype(np.float64), st, vobs, w)
+    res = np.where(keep, w * (vobs - pred), 0)
+    exact = -2.0 * oracle.image(op, d["uvw"], res, None, flags=oracle.N_DIVIDE)[0]
+    c = oracle.taper_row(op)
+    c = c / c[wl.n // 2]
+    cc = np.outer(c, c)
+    e_tap = np.abs((g - exact) * cc).max() / np.abs(exact * cc).max()
+    e_raw = np.abs(g - exact).max() / np.abs(exact).max()
+    print(f"full-size chi^2 gradient vs oracle: tapered {e_tap:.2e}, raw {e_raw:.2e}")
+    assert e_tap <= 1e-5 and e_raw <= 1e-3
+    for p in list(idx[:2]) + [wl.n * wl.n // 2 + 3]:
+        h = 1e-3 * max(abs(x.flat[p]), 1.0)
+        xp, xm = x32.astype(np.float64).copy(), x32.astype(np.float64).copy()
+        xp.flat[p] += h
+        xm.flat[p] -= h
+        cp, cm = _oracle_chi2(op, d, xp, st, vobs, w)[0], _oracle_chi2(op, d, xm, st, vobs, w)[0]
+        fd = (cp - cm) / (2 * h)
+        assert abs(fd - exact.flat[p]) <= 1e-6 * abs(exact.flat[p]) + 1e-13 * abs(cp) / h
+        assert g.flat[p] == pytest.approx(fd, rel=1e-3, abs=1e-4 * np.abs(exact).max())
