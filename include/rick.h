@@ -156,6 +156,17 @@ rick_status rick_plan_set_kernel(rick_plan *plan, int32_t kernel, int32_t suppor
  * (the plan is then unchanged). */
 rick_status rick_plan_set_image_n(rick_plan *plan, int32_t image_n);
 
+/* Change a plan's number of w-planes to n_w, at most the number it was
+ * created with, without rebuilding it: lets a resident plan (and buffers sized
+ * for its created count: rick_workspace_bytes, the planes, the fused work
+ * buffer) serve jobs with fewer planes.  The later calls lay out the
+ * workspace, planes and work buffer for n_w.  rick_fft_wplanes needs the
+ * created count (its batched cuFFT plan transforms that many planes) and
+ * returns RICK_EINVAL otherwise; the fused transform covers the rest.
+ * Host-only, like rick_plan_set_geometry.  RICK_EINVAL if n_w is out of range
+ * (the plan is then unchanged). */
+rick_status rick_plan_set_planes(rick_plan *plan, int32_t n_w);
+
 /* Kaiser-Bessel shape for a grid oversampling alpha = n / image_n (Beatty,
  * Nishimura & Pauly 2005): beta = pi sqrt((W/alpha)^2 (alpha - 1/2)^2 - 0.8),
  * which puts the first zero of the kernel's transform just beyond the first
@@ -328,7 +339,8 @@ rick_status rick_grid_accumulate(rick_plan *plan, void *ws_dev, void *planes_dev
 
 /* Per-plane 2D FFT (§2 step 3, §3.1): cuFFT complex64, unnormalised, in place,
  * batched over the n_w planes.  direction +1: inverse (e^{+2 pi i}), used for
- * imaging; -1: forward, used by degridding. */
+ * imaging; -1: forward, used by degridding.  RICK_EINVAL for a plan whose
+ * plane count rick_plan_set_planes changed. */
 rick_status rick_fft_wplanes(rick_plan *plan, void *planes_dev, int32_t direction, void *stream);
 
 /* w-correction and plane sum (§2 step 4, Eq. 2):

@@ -131,9 +131,10 @@ __device__ __forceinline__ void wrange_fold(double w, uint64_t &lo, uint64_t &hi
 // factor is positive and finite, rounding is monotone in the factor, so a
 // row's extremes are its products with the smallest and the largest factor
 // (unless one of those overflows, when every channel is folded).
-// With mirror, the mirrored visibilities' -w are folded in too.
+// MIRROR: the mirrored visibilities' -w are folded in too.
+template <bool MIRROR>
 __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n_chan,
-                              const double *scale, int mirror)
+                              const double *scale)
 {
     __shared__ double s_min[32], s_max[32];
     __shared__ int s_ok[32];
@@ -144,7 +145,7 @@ __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n
              i += (int64_t)gridDim.x * blockDim.x) {
             const double w = uvw[3 * i + 2];
             wrange_fold(w, lo, hi);
-            if (mirror) wrange_fold(-w, lo, hi);
+            if (MIRROR) wrange_fold(-w, lo, hi);
         }
     } else {
         // smallest and largest factor, and whether all are positive and finite
@@ -200,7 +201,7 @@ __global__ void wrange_kernel(const double *uvw, int64_t n, WsHeader *hdr, int n
 void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsHeader *hdr,
                         cudaStream_t st, int n_chan, const double *scale)
 {
-    wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr, n_chan, scale, 0);
+    wrange_kernel<false><<<plan->num_sms * 4, 256, 0, st>>>(uvw, n, hdr, n_chan, scale);
 }
 
 // ------------------------------------------------------------------------
@@ -485,8 +486,9 @@ __global__ void __launch_bounds__(1024) bin_finalize_kernel(WsHeader *hdr, const
 //
 // With CORR, each visibility has n_corr correlations (vis and weight
 // [n_vis][n_corr]) and its record carries their weighted sum, sum_c w_c V_c.
-// Records i >= n_src (the Hermitian mirror) carry conj(V) of input i - n_src.
-template <bool CORR>
+// MIRROR: records i >= n_src (the Hermitian mirror) carry conj(V) of input
+// i - n_src.
+template <bool CORR, bool MIRROR>
 __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const float2 *vis,
                                                           const float *weight, WsPtrs ws,
                                                           int n_corr, int64_t n_src)
@@ -515,12 +517,15 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int64_t n_vis, const f
                     }
                     v[u] = acc;
                     wt[u] = 1.0f;
-                } else {
+                } else if (MIRROR) {
                     const bool mir = idx[u] >= n_src;
                     const int64_t src = mir ? idx[u] - n_src : idx[u];
                     v[u] = vis[src];
                     if (mir) v[u].y = -v[u].y;
                     wt[u] = weight ? weight[src] : 1.0f;
+                } else {
+                    v[u] = vis[idx[u]];
+                    wt[u] = weight ? weight[idx[u]] : 1.0f;
                 }
                 fr[u] = ws.frac[idx[u]];
                 cl[u] = ws.cell[idx[u]];
@@ -896,7 +901,10 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
         int blocks = plan->num_sms * 4;
-        wrange_kernel<<<blocks, 256, 0, st>>>(uvw, n_src, w.hdr, n_chan, chan_scale, mirror);
+        if (mirror)
+            wrange_kernel<true><<<blocks, 256, 0, st>>>(uvw, n_src, w.hdr, n_chan, chan_scale);
+        else
+            wrange_kernel<false><<<blocks, 256, 0, st>>>(uvw, n_src, w.hdr, n_chan, chan_scale);
         RICK_LAUNCH_CHECK(plan);
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
@@ -947,12 +955,15 @@ rick_status rick_bin_impl(rick_plan *plan, int64_t n_vis, const double *uvw, con
     } else if (n_vis > 0) {
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
         if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
-        if (n_corr == 1)
-            bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
-                n_vis, (const float2 *)vis, weight, w, 1, mirror ? n_src : n_vis);
-        else
-            bin_scatter_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
+        if (n_corr > 1)
+            bin_scatter_kernel<true, false><<<(unsigned)blocks, 256, 0, st>>>(
                 n_vis, (const float2 *)vis, weight, w, n_corr, n_vis);
+        else if (mirror)
+            bin_scatter_kernel<false, true><<<(unsigned)blocks, 256, 0, st>>>(
+                n_vis, (const float2 *)vis, weight, w, 1, n_src);
+        else
+            bin_scatter_kernel<false, false><<<(unsigned)blocks, 256, 0, st>>>(
+                n_vis, (const float2 *)vis, weight, w, 1, n_vis);
         RICK_LAUNCH_CHECK(plan);
     }
     uint32_t nt = (uint32_t)L.ntiles;
@@ -1128,7 +1139,7 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
                                      (uint32_t)nkb, NULL, (uint64_t)n_vis, 0);
     RICK_LAUNCH_CHECK(plan);
     if (!given && n_vis > 0) {
-        wrange_kernel<<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr, 0, NULL, 0);
+        wrange_kernel<false><<<plan->num_sms * 4, 256, 0, st>>>(uvw, n_vis, w.hdr, 0, NULL);
         RICK_LAUNCH_CHECK(plan);
     }
     bin_setup_kernel<<<1, 1, 0, st>>>(w.hdr, w.bkey, w.wplane, p.n_w);
@@ -1174,8 +1185,8 @@ extern "C" rick_status rick_bin_noalloc(rick_plan *plan, int64_t n_vis, const do
     if (n_vis > 0) {
         int64_t blocks = (n_vis + 256 * RICK_SCATTER_U - 1) / (256 * RICK_SCATTER_U);
         if (blocks > (int64_t)plan->num_sms * 64) blocks = (int64_t)plan->num_sms * 64;
-        bin_scatter_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(n_vis, (const float2 *)vis,
-                                                                    weight, w, 1, n_vis);
+        bin_scatter_kernel<false, false><<<(unsigned)blocks, 256, 0, st>>>(
+            n_vis, (const float2 *)vis, weight, w, 1, n_vis);
         RICK_LAUNCH_CHECK(plan);
     }
     uint32_t nt = (uint32_t)L.ntiles;

@@ -86,6 +86,7 @@ struct rick_plan {
     rick_status sticky;
     unsigned long long launches;  // library kernels enqueued so far (cuFFT's not included)
     uint32_t wait_polls;          // poll limit of the key pass's bounded wait for its copies
+    int32_t n_w_created;          // planes the plan was created for (its cuFFT batch)
     // streaming from host memory (created on first use): the copy stream and
     // its events -- start of a call, chunk copied into staging buffer b,
     // staging buffer b free again, uvw chunk resident, resident uvw area a

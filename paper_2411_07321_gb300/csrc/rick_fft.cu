@@ -48,8 +48,7 @@ struct FftArgs {
     uint8_t *pflag;          // [n_w]: plane holds records
     unsigned long long *pmask;  // [n_w]: bit ty = tile-row ty holds records (nt <= 64)
     unsigned long long *tmask;  // [n_w][nt]: bit tx = tile tx of the tile-row holds records (nt <= 64)
-    const float2 *tw;        // the plan's stage twiddle tables (twiddle_kernel), 16 points a thread
-    const float2 *tw8;       // the same for 8 points a thread
+    const float2 *tw;        // the plan's stage twiddle tables (twiddle_kernel)
     WcArgs wc;               // image geometry, flags, taper, plane centres, weight sum
 };
 
@@ -140,35 +139,35 @@ static __device__ __forceinline__ void dft_inv(float2 *a)
     if constexpr (R > 1) dft_level<R, 2>(a);
 }
 
-// The stages of an N-point transform held PT points per thread (16 or 8):
-// radix PT while PT divides what is left, then one smaller stage.  Stage i
-// after sub-transforms of NS points needs the twiddles e^{2 pi i r k / (NS R)},
-// r = 1..R-1, k < NS (none for the first stage), tabled per stage as
-// [r - 1][k] so that the threads of a warp read consecutive entries.
-__host__ __device__ constexpr int stage_radix(int N, int NS, int PT = 16)
+// The stages of an N-point transform: radix 16 while 16 divides what is left,
+// then one radix-2, -4 or -8 stage.  Stage i after sub-transforms of NS points
+// needs the twiddles e^{2 pi i r k / (NS R)}, r = 1..R-1, k < NS (none for the
+// first stage), tabled per stage as [r - 1][k] so that the threads of a warp
+// read consecutive entries.
+__host__ __device__ constexpr int stage_radix(int N, int NS)
 {
-    return ((N / NS) % PT == 0) ? PT : N / NS;
+    return ((N / NS) % 16 == 0) ? 16 : N / NS;
 }
 
-__host__ __device__ constexpr int twiddle_entries(int N, int PT = 16)
+__host__ __device__ constexpr int twiddle_entries(int N)
 {
     int e = 0;
-    for (int ns = 1; ns < N; ns *= stage_radix(N, ns, PT))
-        if (ns > 1) e += (stage_radix(N, ns, PT) - 1) * ns;
+    for (int ns = 1; ns < N; ns *= stage_radix(N, ns))
+        if (ns > 1) e += (stage_radix(N, ns) - 1) * ns;
     return e;
 }
 
 // One Stockham stage of radix R after sub-transforms of NS points.  x[s] holds
-// element t + P s of the current array (P = N / PT threads per transform);
-// butterfly j = t + P b (b < PT / R) takes elements j + r N/R, applies the
+// element t + P s of the current array (P = N / 16 threads per transform);
+// butterfly j = t + P b (b < 16 / R) takes elements j + r N/R, applies the
 // twiddles e^{2 pi i r (j mod NS) / (NS R)} (table at OFF), and its outputs m
 // go to (j - j mod NS) R + j mod NS + m NS.  After the last stage x[s] holds
 // output t + P s.  cb is the transform's offset in the exchange arrays.
-template <int N, int PT, int R, int NS, int OFF, bool LAST>
-static __device__ __forceinline__ void fft_stage(float2 (&x)[PT], int t, int cb, float *sre,
+template <int N, int R, int NS, int OFF, bool LAST>
+static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb, float *sre,
                                                  float *sim, const float2 *__restrict__ tw)
 {
-    constexpr int P = N / PT, B = PT / R;
+    constexpr int P = N / 16, B = 16 / R;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = t + P * b, k = j & (NS - 1);
@@ -196,7 +195,7 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[PT], int t, int cb,
     if constexpr (!LAST) {
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < PT; ++s) {
+        for (int s = 0; s < 16; ++s) {
             const int i = cb + pad32(t + P * s);
             x[s] = make_float2(sre[i], sim[i]);
         }
@@ -204,25 +203,24 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[PT], int t, int cb,
     }
 }
 
-template <int N, int PT, int NS, int OFF>
-static __device__ __forceinline__ void fft_stages(float2 (&x)[PT], int t, int cb, float *sre,
+template <int N, int NS, int OFF>
+static __device__ __forceinline__ void fft_stages(float2 (&x)[16], int t, int cb, float *sre,
                                                   float *sim, const float2 *__restrict__ tw)
 {
-    constexpr int R = stage_radix(N, NS, PT);
+    constexpr int R = stage_radix(N, NS);
     constexpr bool LAST = (R == N / NS);
-    fft_stage<N, PT, R, NS, OFF, LAST>(x, t, cb, sre, sim, tw);
-    if constexpr (!LAST)
-        fft_stages<N, PT, NS * R, OFF + (NS > 1 ? (R - 1) * NS : 0)>(x, t, cb, sre, sim, tw);
+    fft_stage<N, R, NS, OFF, LAST>(x, t, cb, sre, sim, tw);
+    if constexpr (!LAST) fft_stages<N, NS * R, OFF + (NS > 1 ? (R - 1) * NS : 0)>(x, t, cb, sre, sim, tw);
 }
 
-// The unnormalised inverse DFT of N points held as x[s] = element t + P s
-// (P = N / PT); on return x[s] = output t + P s.  Every thread of the CTA must
-// call it.  tw: the plan's stage twiddle tables for PT points per thread.
-template <int LOGN, int PT = 16>
-static __device__ __forceinline__ void fft_inv(float2 (&x)[PT], int t, int cb, float *sre,
+// The unnormalised inverse DFT of N points held as x[s] = element t + P s;
+// on return x[s] = output t + P s.  Every thread of the CTA must call it.
+// tw: the plan's stage twiddle tables.
+template <int LOGN>
+static __device__ __forceinline__ void fft_inv(float2 (&x)[16], int t, int cb, float *sre,
                                                float *sim, const float2 *__restrict__ tw)
 {
-    fft_stages<(1 << LOGN), PT, 1, 0>(x, t, cb, sre, sim, tw);
+    fft_stages<(1 << LOGN), 1, 0>(x, t, cb, sre, sim, tw);
 }
 
 // Exchange arrays of one transform: N words plus the padding.
@@ -462,128 +460,6 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
     }
 }
 
-// Pass 2 for the large transforms, 8 points per thread: one CTA of NT = N / 8
-// threads per image column, twice the warps of the 16-point form at the same
-// registers per SM (the 16-point column kernel's 128 registers a thread leave
-// room for 16 warps per SM at n = 8192, too few to hide the latency of the
-// exchanges and the twiddle and plane loads).  Per pixel the CTA keeps in
-// shared memory the step D = e^{2 pi i dw (n - 1)} and n - 1 (double-single);
-// the Horner sums of the current block of planes and the running image sums
-// stay in registers; the output scale is formed again at the end.
-#ifndef RICK_COLS_PT8_MIN_LOG
-#define RICK_COLS_PT8_MIN_LOG 12
-#endif
-template <int LOGN>
-struct Col8Shape {
-    static constexpr int N = 1 << LOGN, PT = 8, NT = N / PT;
-    static constexpr int XL = XLen<N>::L;  // words of one exchange array
-    // exchange arrays, D (float2), n - 1 hi and lo
-    static constexpr size_t SMEM = sizeof(float) * (2 * (size_t)XL + 4 * (size_t)N);
-};
-
-template <int LOGN>
-__global__ void __launch_bounds__(Col8Shape<LOGN>::NT, Col8Shape<LOGN>::NT <= 512 ? 2 : 1)
-    fft_cols8_kernel(FftArgs a)
-{
-    using S = Col8Shape<LOGN>;
-    constexpr int N = S::N, PT = 8, P = S::NT, XL = S::XL;
-    extern __shared__ float fsm[];
-    float *sre = fsm, *sim = fsm + XL;
-    float2 *sD = (float2 *)(fsm + 2 * XL);
-    float *g_hi = fsm + 2 * XL + 2 * N, *g_lo = g_hi + N;
-    const WcArgs &w = a.wc;
-    const int t = threadIdx.x;
-    const int m = w.m, off = w.off, nt = a.nt, l2T = a.log2T;
-    const int pc = blockIdx.x;  // image column
-    const int p = pc + off;
-    const bool fp32ph = (w.flags & RICK_PHASE_FP32) != 0;
-    const bool imag = (w.flags & RICK_IMAG_PART) != 0;  // Im of the plane sum instead of Re
-    float inv_sumw;
-    {
-        const double sw = w.hdr->stats.sum_weight;  // nothing gridded: no normalisation
-        inv_sumw = sw != 0.0 ? (float)(1.0 / sw) : 1.0f;
-    }
-    const float4 dwp = __ldg(&w.wplane[w.n_w]);
-    // every pixel q = t + P s is this thread's alone: no barrier before its use
-#pragma unroll
-    for (int s = 0; s < PT; ++s) {
-        const int q = t + P * s;
-        float2 D = make_float2(1.0f, 0.0f);
-        if (q >= off && q < off + m) {
-            const PixelGeom g = pixel_geom(w, p, q, inv_sumw);
-            g_hi[q] = g.nm1.hi;
-            g_lo[q] = fp32ph ? g.nm1_f : g.nm1.lo;
-            if (!fp32ph) {
-                const float fd = ff_frac(ff_mul(ff{dwp.x, dwp.y}, g.nm1));
-                sincospif(2.0f * fd, &D.y, &D.x);
-            }
-        } else {
-            g_hi[q] = g_lo[q] = 0.0f;
-        }
-        sD[q] = D;
-    }
-    float acc[PT];
-#pragma unroll
-    for (int s = 0; s < PT; ++s) acc[s] = 0.0f;
-    const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
-    const float2 *col = a.work + (size_t)pc * N;
-    for (int k0 = 0; k0 < w.n_w; k0 += bs) {
-        const int k1 = min(k0 + bs, w.n_w);
-        float2 h[PT];
-#pragma unroll
-        for (int s = 0; s < PT; ++s) h[s] = make_float2(0.0f, 0.0f);
-        for (int k = k1 - 1; k >= k0; --k) {
-            if (!a.pflag[k]) {  // an empty plane adds nothing: h = h D
-#pragma unroll
-                for (int s = 0; s < PT; ++s) h[s] = cmul(h[s], sD[t + P * s]);
-                continue;
-            }
-            const float2 *src = col + (size_t)k * m * N;
-            float2 x[PT];
-            if (nt <= 64) {  // the plane's tile-rows as one bit mask
-                const unsigned long long msk = a.pmask[k];
-#pragma unroll
-                for (int s = 0; s < PT; ++s) {
-                    const int v = t + P * s;
-                    x[s] = ((msk >> (v >> l2T)) & 1ull) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
-                }
-            } else {
-                const uint8_t *tr = a.trow + k * nt;
-#pragma unroll
-                for (int s = 0; s < PT; ++s) {
-                    const int v = t + P * s;
-                    x[s] = tr[v >> l2T] ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
-                }
-            }
-            fft_inv<LOGN, 8>(x, t, 0, sre, sim, a.tw8);
-#pragma unroll
-            for (int s = 0; s < PT; ++s) {
-                const float2 hd = cmul(h[s], sD[t + P * s]);
-                h[s] = make_float2(hd.x + x[s].x, hd.y + x[s].y);
-            }
-        }
-        // the block's sum times the exact phase of its first plane
-        const float4 wk = __ldg(&w.wplane[k0]);
-#pragma unroll
-        for (int s = 0; s < PT; ++s) {
-            const int q = t + P * s;
-            PixelGeom g;
-            g.nm1 = ff{g_hi[q], g_lo[q]};
-            g.nm1_f = g_lo[q];
-            float cs, sn;
-            wphase(w, wk, g, &cs, &sn);
-            acc[s] = imag ? fmaf(h[s].x, sn, fmaf(h[s].y, cs, acc[s]))
-                          : fmaf(h[s].x, cs, fmaf(-h[s].y, sn, acc[s]));
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < PT; ++s) {
-        const int q = t + P * s;
-        if (q >= off && q < off + m)
-            w.image_out[(size_t)(q - off) * m + pc] = acc[s] * pixel_geom(w, p, q, inv_sumw).scale;
-    }
-}
-
 // ------------------------------------------------------------------------
 // The adjoint: w-spreading (the transpose of the w-correction) fused with the
 // forward FFT of every plane, for the tiles that records reach (the only cells
@@ -797,17 +673,16 @@ size_t rick_fft_work_bytes(const rick_params *p)
     return fft_supported(*p) ? fft_work_layout(*p).total : 0;
 }
 
-// The stage twiddle tables of an n-point transform of pt points per thread:
-// entry OFF_i + (r - 1) NS + k of stage i = e^{2 pi i r k / (NS R)}, in FP64,
-// rounded once.
-__global__ void twiddle_kernel(float2 *tw, int n, int entries, int pt)
+// The stage twiddle tables of an n-point transform: entry OFF_i + (r - 1) NS + k
+// of stage i = e^{2 pi i r k / (NS R)}, in FP64, rounded once.
+__global__ void twiddle_kernel(float2 *tw, int n, int entries)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= entries) return;
     int off = 0;
-    for (int ns = 1; ns < n; ns *= stage_radix(n, ns, pt)) {
+    for (int ns = 1; ns < n; ns *= stage_radix(n, ns)) {
         if (ns == 1) continue;
-        const int R = stage_radix(n, ns, pt), cnt = (R - 1) * ns;
+        const int R = stage_radix(n, ns), cnt = (R - 1) * ns;
         if (e < off + cnt) {
             const int r = (e - off) / ns + 1, k = (e - off) % ns;
             double s, c;
@@ -824,13 +699,11 @@ __global__ void twiddle_kernel(float2 *tw, int n, int entries, int pt)
 bool rick_fft_tables(rick_plan *pl)
 {
     if (!fft_supported(pl->p)) return true;
-    // the tables for 16 points a thread, then those for 8
-    const int n = pl->p.n, e16 = twiddle_entries(n, 16), e8 = twiddle_entries(n, 8);
-    if (cudaMallocAsync((void **)&pl->twid, sizeof(float2) * (e16 + e8), pl->own) != cudaSuccess)
+    const int n = pl->p.n, entries = twiddle_entries(n);
+    if (cudaMallocAsync((void **)&pl->twid, sizeof(float2) * entries, pl->own) != cudaSuccess)
         return false;
-    twiddle_kernel<<<(e16 + 255) / 256, 256, 0, pl->own>>>(pl->twid, n, e16, 16);
-    twiddle_kernel<<<(e8 + 255) / 256, 256, 0, pl->own>>>(pl->twid + e16, n, e8, 8);
-    pl->launches += 2;
+    twiddle_kernel<<<(entries + 255) / 256, 256, 0, pl->own>>>(pl->twid, n, entries);
+    ++pl->launches;
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -851,14 +724,6 @@ static cudaError_t launch_fft_wc(const FftArgs &a, int num_sms, cudaStream_t st)
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int m = a.wc.m;
-    if (LOGN >= RICK_COLS_PT8_MIN_LOG) {
-        using S8 = Col8Shape<LOGN>;
-        e = cudaFuncSetAttribute(fft_cols8_kernel<LOGN>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S8::SMEM);
-        if (e != cudaSuccess) return e;
-        fft_cols8_kernel<LOGN><<<(unsigned)m, S8::NT, S8::SMEM, st>>>(a);
-        return cudaGetLastError();
-    }
     fft_cols_kernel<LOGN><<<(unsigned)((m + S::COLS - 1) / S::COLS), S::NT, S::SMEM, st>>>(a);
     return cudaGetLastError();
 }
@@ -891,7 +756,6 @@ static FftArgs fft_args(rick_plan *plan, const void *ws_dev, void *work_dev, uin
     a.tmask = (unsigned long long *)(wb + L.tmask);
     a.work = (float2 *)(wb + L.work);
     a.tw = plan->twid;
-    a.tw8 = plan->twid + twiddle_entries(p.n, 16);
     a.wc = make_args(plan, ws_dev, flags);
     return a;
 }

@@ -138,9 +138,6 @@ __device__ __forceinline__ void group_flush_det(unsigned long long *acc64, float
 
 // n records of one segment of the tile's record list, starting at record r0.
 // DET: the flushes go to the 64-bit fixed-point tile acc64 (scale fx).
-// Every lane of the warp calls it (n = 0 for lanes without a stream); the warp
-// walks as many steps as its longest stream, the others idle through the
-// rest, so that the column-weight shuffles take the whole warp at every step.
 template <int W, bool DET>
 __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n, int x0,
                                             int y0, float *acc_re, float *acc_im, int T, int TP,
@@ -150,30 +147,22 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
     constexpr int G = StreamShape<W>::G;
     const int lane = threadIdx.x & 31, grp = lane / G;
     const int j = lane - grp * G;  // this lane's row / kernel segment
-    const bool live = j < W && n > 0;
-    const uint32_t steps = __reduce_max_sync(0xffffffffu, n);
-    if (steps == 0) return;
+    const bool live = j < W;
+    const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    if (n == 0) return;
     float ar[W], ai[W];
 #pragma unroll
     for (int jx = 0; jx < W; ++jx) ar[jx] = ai[jx] = 0.0f;
     const float4 *rec = ta.rec + r0;
     const uint32_t *rcell = ta.rcell + r0;
-    // r0 lies in [0, n_binned], and the record arrays end with one record of
-    // padding: the first record (and each next one below, up to r0 + n) can be
-    // read whether or not the stream is empty
     uint32_t cur = rcell[0];
     float4 q = rec[0];
     uint32_t cell = cur;
-    for (uint32_t i = 0; i < steps; ++i) {
-        const bool act = i < n;
-        // prefetch the next record
-        float4 nq = q;
-        uint32_t ncell = cell;
-        if (act) {
-            nq = rec[i + 1];
-            ncell = rcell[i + 1];
-        }
-        if (act && cell != cur) {
+    for (uint32_t i = 0; i < n; ++i) {
+        // prefetch the next record (the record arrays end with one of padding)
+        const float4 nq = rec[i + 1];
+        const uint32_t ncell = rcell[i + 1];
+        if (cell != cur) {
             if (DET)
                 group_flush_det<W>(acc64, fx, T, TP, (int)(cur & 0xFFFFu) - x0,
                                    (int)(cur >> 16) - y0 + j, live, ar, ai);
@@ -201,22 +190,20 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
             // power-of-two groups: the lane inside the group is an immediate
             // (width form); groups of W lanes: the absolute lane
             wv[jx] = W == 1 ? gx
-                   : (G & (G - 1)) == 0 ? __shfl_sync(0xffffffffu, gx, jx, G)
-                                        : __shfl_sync(0xffffffffu, gx, grp * G + jx);
+                   : (G & (G - 1)) == 0 ? __shfl_sync(gmask, gx, jx, G)
+                                        : __shfl_sync(gmask, gx, grp * G + jx);
         }
-        if (act) {
 #pragma unroll
-            for (int jx = 0; jx + 1 < W; jx += 2) {
-                const float2 w2 = make_float2(wv[jx], wv[jx + 1]);
-                const float2 a2 = __ffma2_rn(vr2, w2, make_float2(ar[jx], ar[jx + 1]));
-                const float2 b2 = __ffma2_rn(vi2, w2, make_float2(ai[jx], ai[jx + 1]));
-                ar[jx] = a2.x; ar[jx + 1] = a2.y;
-                ai[jx] = b2.x; ai[jx + 1] = b2.y;
-            }
-            if (W & 1) {
-                ar[W - 1] = __fmaf_rn(vv.x, wv[W - 1], ar[W - 1]);
-                ai[W - 1] = __fmaf_rn(vv.y, wv[W - 1], ai[W - 1]);
-            }
+        for (int jx = 0; jx + 1 < W; jx += 2) {
+            const float2 w2 = make_float2(wv[jx], wv[jx + 1]);
+            const float2 a2 = __ffma2_rn(vr2, w2, make_float2(ar[jx], ar[jx + 1]));
+            const float2 b2 = __ffma2_rn(vi2, w2, make_float2(ai[jx], ai[jx + 1]));
+            ar[jx] = a2.x; ar[jx + 1] = a2.y;
+            ai[jx] = b2.x; ai[jx + 1] = b2.y;
+        }
+        if (W & 1) {
+            ar[W - 1] = __fmaf_rn(vv.x, wv[W - 1], ar[W - 1]);
+            ai[W - 1] = __fmaf_rn(vv.y, wv[W - 1], ai[W - 1]);
         }
         q = nq;
         cell = ncell;
@@ -312,9 +299,9 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
             if (a0 < a1) {
                 const uint32_t per = (a1 - a0 + nstreams - 1) / nstreams;
                 const uint32_t v0 = min(a0 + stream * per, a1), v1 = min(v0 + per, a1);
-                // every lane takes part (lanes without a stream with n = 0)
-                grid_stream<W, DET>(ta, s_rs[g] + (v0 - base), streaming ? v1 - v0 : 0u, x0, y0,
-                                    acc_re, acc_im, T, TP, coef2, acc64, fx);
+                if (streaming && v0 < v1)
+                    grid_stream<W, DET>(ta, s_rs[g] + (v0 - base), v1 - v0, x0, y0, acc_re, acc_im,
+                                        T, TP, coef2, acc64, fx);
             }
             base += lg;
         }

@@ -282,6 +282,7 @@ extern "C" rick_status rick_plan_create(const rick_params *params, int64_t max_v
     pl->p = *params;
     pl->max_vis = max_vis;
     pl->wait_polls = RICK_WAIT_POLLS;
+    pl->n_w_created = params->n_w;
     if (cudaGetDevice(&pl->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device) !=
             cudaSuccess ||
@@ -384,6 +385,17 @@ extern "C" rick_status rick_plan_set_image_n(rick_plan *plan, int32_t image_n)
     return RICK_OK;
 }
 
+extern "C" rick_status rick_plan_set_planes(rick_plan *plan, int32_t n_w)
+{
+    if (!plan || n_w < 1 || n_w > plan->n_w_created) return RICK_EINVAL;
+    rick_params q = plan->p;
+    q.n_w = n_w;
+    rick_status st = check_params(&q);
+    if (st != RICK_OK) return st;
+    plan->p = q;
+    return RICK_OK;
+}
+
 extern "C" rick_status rick_plan_set_wait_limit(rick_plan *plan, uint32_t polls)
 {
     if (!plan) return RICK_EINVAL;
@@ -431,7 +443,8 @@ extern "C" rick_status rick_fft_wplanes(rick_plan *plan, void *planes, int32_t d
 {
     if (!plan || !planes || (direction != 1 && direction != -1)) return RICK_EINVAL;
     if (plan->sticky != RICK_OK) return plan->sticky;
-    if (((uintptr_t)planes & 7) != 0) return RICK_EINVAL;
+    // the batched cuFFT plan transforms the plane count it was made for
+    if (((uintptr_t)planes & 7) != 0 || plan->p.n_w != plan->n_w_created) return RICK_EINVAL;
     if (cufftSetStream(plan->fft, (cudaStream_t)stream) != CUFFT_SUCCESS ||
         cufftExecC2C(plan->fft, (cufftComplex *)planes, (cufftComplex *)planes,
                      direction > 0 ? CUFFT_INVERSE : CUFFT_FORWARD) != CUFFT_SUCCESS) {

@@ -61,8 +61,9 @@ class Imager:
             self.plan = R.rick_plan_create(self.params, self.max_vis)
             self.ws_bytes, self.plane_bytes = R.rick_workspace_bytes(self.params, self.max_vis)
             self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
-            self.planes = torch.empty((self.n_w, self.n, self.n), dtype=torch.complex64,
-                                      device=self.device)
+            self._planes_all = torch.empty((self.n_w, self.n, self.n), dtype=torch.complex64,
+                                           device=self.device)
+            self.planes = self._planes_all
             self.stats_buf = torch.zeros(48, dtype=torch.uint8, device=self.device)
         self.fft_bytes = R.rick_plan_fft_bytes(self.plan)
         self.n_vis = 0
@@ -387,6 +388,14 @@ class Imager:
         wmin, wmax = (math.nan, math.nan) if w_range is None else map(float, w_range)
         R.rick_plan_set_geometry(self.plan, fov, wmin, wmax)
         self.params.fov, self.params.w_min, self.params.w_max = float(fov), wmin, wmax
+
+    def set_planes(self, n_w: int):
+        """Re-target the resident plan to n_w w-planes, at most the count it was
+        created with (rick_plan_set_planes): the buffers stay, the planes are
+        their first n_w."""
+        R.rick_plan_set_planes(self.plan, n_w)
+        self.params.n_w = self.n_w = int(n_w)
+        self.planes = self._planes_all[:self.n_w]
 
     def set_image_n(self, image_n: int | None):
         """Re-target the resident plan to another crop of its grid (None: no crop)."""

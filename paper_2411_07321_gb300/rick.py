@@ -66,7 +66,7 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
            "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
            "rick_fft_wcorrect", "rick_wspread_fft", "rick_fused_work_bytes",
-           "rick_probe_throughput", "rick_plan_set_wait_limit"]
+           "rick_probe_throughput", "rick_plan_set_wait_limit", "rick_plan_set_planes"]
 
 
 def _load():
@@ -118,6 +118,7 @@ def _load():
         "rick_degrid": [vp, vp, vp, vp, vp, vp],
         "rick_probe_throughput": [i32, ctypes.POINTER(ctypes.c_double)],
         "rick_plan_set_wait_limit": [vp, ctypes.c_uint32],
+        "rick_plan_set_planes": [vp, i32],
     }.items():
         f = getattr(L, name)
         f.restype = i32
@@ -197,6 +198,10 @@ def rick_plan_fft_bytes(plan: int) -> int:
     b = ctypes.c_size_t()
     _check("rick_plan_fft_bytes", _L.rick_plan_fft_bytes(plan, ctypes.byref(b)))
     return b.value
+
+
+def rick_plan_set_planes(plan: int, n_w: int) -> None:
+    _check("rick_plan_set_planes", _L.rick_plan_set_planes(plan, int(n_w)))
 
 
 def rick_plan_set_wait_limit(plan: int, polls: int) -> None:

@@ -14,10 +14,11 @@ slot's stream, and completes the request when the stream's event fires.  Work of
 requests admitted while others run overlaps on the device.
 
 Admission is by HBM footprint: a request needs a slot with the same grid size,
-plane count, tile and precision, and a visibility capacity at least its own;
-the slot's plan is re-targeted to the request's field of view, w range, image
-crop and gridding kernel (rick_plan_set_geometry, rick_plan_set_image_n,
-rick_plan_set_kernel), so the cuFFT plan and the buffers are reused.  If no idle slot fits, a new one is created
+tile and precision, and visibility and plane capacities at least its own; the
+slot's plan is re-targeted to the request's plane count, field of view, w
+range, image crop and gridding kernel (rick_plan_set_planes,
+rick_plan_set_geometry, rick_plan_set_image_n, rick_plan_set_kernel), so the
+plan and the buffers are reused.  If no idle slot fits, a new one is created
 when budget - used >= its footprint, after evicting idle slots
 least-recently-used first.  A request larger than the whole budget is rejected
 with an error, and only that request fails.
@@ -39,7 +40,8 @@ import numpy as np
 
 from .imager import IMAGE_FLAGS, Imager
 
-MIN_CAPACITY = 1 << 14
+MIN_CAPACITY = 1 << 20  # smaller requests share slots of this capacity
+MIN_PLANES = 16         # plane capacity of a slot (more if a request needs more)
 
 
 def capacity_class(n_vis: int) -> int:
@@ -48,6 +50,16 @@ def capacity_class(n_vis: int) -> int:
     while c < n_vis:
         c <<= 1
     return c
+
+
+def plane_class(n_w: int) -> int:
+    """Plane capacity of the slot serving n_w planes."""
+    return max(int(n_w), MIN_PLANES)
+
+
+def capacities(job) -> tuple:
+    """(visibilities, planes) a slot must hold for the job."""
+    return capacity_class(job.n_vis), plane_class(job.n_w)
 
 
 @dataclass
@@ -80,8 +92,8 @@ class ImagingJob:
         return int(self.image_n) if self.image_n else self.n
 
     def key(self):
-        """What a slot must share with the request (its capacity may be larger)."""
-        return (self.n, self.n_w, self.tile, self.precision)
+        """What a slot must share with the request (its capacities may be larger)."""
+        return (self.n, self.tile, self.precision)
 
 
 @dataclass
@@ -109,15 +121,22 @@ class Admission:
     def used(self) -> int:
         return sum(s["bytes"] for s in self.slots.values())
 
-    def plan(self, key, bytes_needed: int, cap: int = 0):
+    def plan(self, key, bytes_needed: int, cap=0):
         """('reuse', id) | ('new', [ids to evict]) | None (wait).  An idle slot
-        of the same key with capacity >= cap is reused (the smallest such, then
-        the least recently used).  Raises AdmissionError if bytes_needed
-        exceeds the whole budget."""
+        of the same key with capacity >= cap (a number, or a tuple compared
+        element by element) is reused (the smallest such, then the least
+        recently used).  Raises AdmissionError if bytes_needed exceeds the
+        whole budget."""
         if bytes_needed > self.budget:
             raise AdmissionError(f"request needs {bytes_needed} B, budget is {self.budget} B")
+
+        def holds(c):
+            if isinstance(cap, tuple):
+                return all(a >= b for a, b in zip(c, cap))
+            return c >= cap
+
         idle_same = [i for i, s in self.slots.items()
-                     if s["key"] == key and not s["busy"] and s["cap"] >= cap]
+                     if s["key"] == key and not s["busy"] and holds(s["cap"])]
         if idle_same:
             return ("reuse", min(idle_same, key=lambda i: (self.slots[i]["cap"],
                                                           self.slots[i]["last"])))
@@ -134,9 +153,10 @@ class Admission:
         fits = free >= bytes_needed and (self.max_slots is None or count < self.max_slots)
         return ("new", evict) if fits else None
 
-    def add(self, key, nbytes: int, now: float, cap: int = 0) -> int:
+    def add(self, key, nbytes: int, now: float, cap=0) -> int:
         i = next(self._ids)
-        self.slots[i] = dict(key=key, bytes=int(nbytes), busy=True, last=now, cap=int(cap))
+        self.slots[i] = dict(key=key, bytes=int(nbytes), busy=True, last=now,
+                             cap=cap if isinstance(cap, tuple) else int(cap))
         assert self.used() <= self.budget
         return i
 
@@ -156,9 +176,9 @@ def slot_footprint(job: ImagingJob) -> int:
     """Device bytes of a slot for job's key (without creating it)."""
     from . import rick as R
     from .imager import KERNELS, PRECISIONS
-    p = R.make_params(job.n, job.n_w, job.fov, KERNELS[job.kernel], job.support, tile=job.tile,
+    cap, planes_cap = capacities(job)
+    p = R.make_params(job.n, planes_cap, job.fov, KERNELS[job.kernel], job.support, tile=job.tile,
                       precision=PRECISIONS[job.precision], image_n=job.image_n or 0)
-    cap = capacity_class(job.n_vis)
     ws, planes = R.rick_workspace_bytes(p, cap)
     # planes + workspace + cuFFT area (bounded by the planes' size for in-place
     # C2C) + the fused transform's work buffer + image + resident input buffers
@@ -170,10 +190,10 @@ class _Slot:
     def __init__(self, job: ImagingJob, device, out_host):
         import torch
         self.key = job.key()
-        self.imager = Imager(job.n, job.n_w, job.fov, kernel=job.kernel, support=job.support,
-                             tile=job.tile, precision=job.precision,
-                             max_vis=capacity_class(job.n_vis), device=device,
-                             image_n=job.image_n)
+        cap, planes_cap = capacities(job)
+        self.imager = Imager(job.n, planes_cap, job.fov, kernel=job.kernel, support=job.support,
+                             tile=job.tile, precision=job.precision, max_vis=cap,
+                             device=device, image_n=job.image_n)
         self.kernel = (job.kernel, job.support)
         self.stream = torch.cuda.Stream(device=device)
         self.out = out_host  # pinned image buffer, from the server's pool
@@ -270,7 +290,7 @@ class Server:
             job, fut = self._pending.popleft()
             try:
                 need = slot_footprint(job)
-                decision = self.admission.plan(job.key(), need, capacity_class(job.n_vis))
+                decision = self.admission.plan(job.key(), need, capacities(job))
             except Exception as e:  # invalid request or larger than the budget
                 fut.set_exception(e)
                 progressed = True
@@ -289,7 +309,7 @@ class Server:
                     for sid in decision[1]:
                         self._evict(sid)
                     slot = _Slot(job, self.device, self._pinned.get(job.side))
-                    sid = self.admission.add(job.key(), need, now, capacity_class(job.n_vis))
+                    sid = self.admission.add(job.key(), need, now, capacities(job))
                     self._slots[sid] = slot
                     self.peak_used = max(self.peak_used, self.admission.used())
                     self.counters["new_slots"] += 1
@@ -326,6 +346,8 @@ class Server:
             slot.kernel = (job.kernel, job.support)
         if slot.imager.m != job.side:
             slot.imager.set_image_n(job.image_n)
+        if slot.imager.n_w != job.n_w:
+            slot.imager.set_planes(job.n_w)
         with torch.cuda.stream(slot.stream):
             slot.imager.set_geometry(job.fov, job.w_range)
             slot.imager.image_from_host(job.uvw, job.vis, job.weight, slot.out, job.flags)

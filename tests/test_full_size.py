@@ -12,7 +12,7 @@ w-planes, Kaiser-Bessel W=7, uv-tile 64.
   oracle's image of the whole set, 1e-5 of peak on the tapered image and on
   the inner region (as in test_gpu_parity); the raw whole image, whose corner
   pixels carry the FP32 transform's rounding times 1/(C C) (about 3e3 for KB
-  W=7), within twice its measured error (9.2e-6 resident, 1.3e-5 streamed).
+  W=7), within about three times its typical measured error.
 - Precision: the same image with compensated FP32 gridding
   (RICK_PREC_FP32_COMPENSATED) against the same oracle image.
 
@@ -30,8 +30,11 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL = 1e-5
-RAW_RESIDENT = 2e-5   # twice the measured raw error of the device-resident image
-RAW_STREAMED = 3e-5   # the same for the streamed calls (another summation order)
+# The raw error varies from run to run with the order of the float atomics
+# (measured 0.8-1.1e-5 resident, 1.3-2.6e-5 streamed): bounded at about three
+# times its typical value, to catch a regression.
+RAW_RESIDENT = 3e-5
+RAW_STREAMED = 6e-5
 
 
 @pytest.fixture(scope="module")

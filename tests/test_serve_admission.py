@@ -26,10 +26,24 @@ def S():
 
 
 def test_capacity_classes(S):
-    assert S.capacity_class(1) == 1 << 14
-    assert S.capacity_class(1 << 14) == 1 << 14
-    assert S.capacity_class((1 << 14) + 1) == 1 << 15
+    m = S.MIN_CAPACITY
+    assert S.capacity_class(1) == m
+    assert S.capacity_class(m) == m
+    assert S.capacity_class(m + 1) == 2 * m
     assert S.capacity_class(10_000_000) == 1 << 24
+    assert S.plane_class(4) == S.plane_class(S.MIN_PLANES) == S.MIN_PLANES
+    assert S.plane_class(40) == 40
+
+
+def test_tuple_capacities_compare_element_by_element(S):
+    a = S.Admission(1000)
+    k = ("A",)
+    i = a.add(k, 300, now=0.0, cap=(1 << 20, 16))
+    a.release(i, now=1.0)
+    assert a.plan(k, 300, (1 << 20, 8)) == ("reuse", i)
+    assert a.plan(k, 300, (1 << 19, 16)) == ("reuse", i)
+    assert a.plan(k, 300, (1 << 21, 8)) == ("new", [])  # too few visibilities
+    assert a.plan(k, 300, (1 << 20, 17)) == ("new", [])  # too few planes
 
 
 def test_reuse_idle_slot_of_same_key(S):
@@ -126,14 +140,15 @@ def test_reuse_prefers_the_smallest_idle_slot_with_enough_capacity(S):
     assert a.plan(k, 100, cap=1 << 15) == ("reuse", big)   # the next larger one
 
 
-def test_job_key_leaves_out_kernel_and_capacity(S):
+def test_job_key_leaves_out_kernel_planes_and_capacity(S):
     import numpy as np
     uvw = np.zeros((10, 3))
     a = S.ImagingJob(uvw, None, None, n=512, n_w=8, fov=0.01, kernel="kb", support=7)
-    b = S.ImagingJob(np.zeros((100_000, 3)), None, None, n=512, n_w=8, fov=0.02,
+    b = S.ImagingJob(np.zeros((100_000, 3)), None, None, n=512, n_w=12, fov=0.02,
                      kernel="gauss", support=5)
     assert a.key() == b.key()
-    c = S.ImagingJob(uvw, None, None, n=512, n_w=9, fov=0.01)
+    assert S.capacities(a) == (S.MIN_CAPACITY, S.MIN_PLANES)
+    c = S.ImagingJob(uvw, None, None, n=1024, n_w=8, fov=0.01)
     assert a.key() != c.key()
     d = S.ImagingJob(uvw, None, None, n=512, n_w=8, fov=0.01, image_n=300)
     assert d.key() == a.key() and (d.side, a.side) == (300, 512)
