@@ -273,3 +273,30 @@ def test_probe_throughput(P):
         assert 0.5 < v <= 4 * 32 * (2 if k.endswith("FFMA2") else 1) * 1.05, (k, v)
     with pytest.raises(R.RickError):
         R.rick_probe_throughput(99)
+
+
+def test_set_planes_retargets_a_plan(P):
+    """A plan made for 16 planes and re-targeted to 8 (rick_plan_set_planes)
+    images like a plan made for 8; its cuFFT stage, batched for 16, refuses."""
+    R = P.rick
+    dev = torch.device("cuda:0")
+    wl = synth.WORKLOADS["small"]
+    d = small(30000, 11)
+    t = to_dev(d, dev)
+    kw = params(wl, n_w=8, kernel="kb", support=7)
+    fresh = P.Imager(**kw, max_vis=30000, device=dev)
+    ref = fresh.image(t["uvw"], t["vis"], t["weight"]).cpu().numpy()
+    big = P.Imager(**dict(kw, n_w=16), max_vis=65536, device=dev)
+    big.image(t["uvw"], t["vis"], t["weight"])
+    torch.cuda.synchronize()
+    big.set_planes(8)
+    got = big.image(t["uvw"], t["vis"], t["weight"]).cpu().numpy()
+    op = oracle_params(kw)
+    cc = cc_of(op)
+    assert np.abs((got - ref) * cc).max() <= 1e-6 * np.abs(ref * cc).max()
+    with pytest.raises(R.RickError):
+        big.fft(+1)
+    with pytest.raises(R.RickError):
+        big.set_planes(17)
+    fresh.close()
+    big.close()
