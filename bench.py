@@ -130,7 +130,7 @@ def probe_rates(P) -> dict:
     kinds = {"smem_rmw_f32": R.RICK_PROBE_SMEM_RMW, "smem_atomic_f32": R.RICK_PROBE_SMEM_ATOMIC_F32,
              "smem_atomic_u32": R.RICK_PROBE_SMEM_ATOMIC_U32,
              "smem_atomic_u64": R.RICK_PROBE_SMEM_ATOMIC_U64, "ffma": R.RICK_PROBE_FFMA,
-             "ffma2": R.RICK_PROBE_FFMA2}
+             "ffma2": R.RICK_PROBE_FFMA2, "shfl": R.RICK_PROBE_SHFL, "f2i": R.RICK_PROBE_F2I}
     return {k: R.rick_probe_throughput(v) for k, v in kinds.items()}
 
 

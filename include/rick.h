@@ -536,6 +536,8 @@ rick_status rick_image_host_rows(rick_plan *plan, int64_t n_rows, int32_t n_chan
 #define RICK_PROBE_SMEM_ATOMIC_U64 3 /* 64-bit integer atomic add to shared memory   */
 #define RICK_PROBE_FFMA 4            /* FP32 fused multiply-add, one per instruction */
 #define RICK_PROBE_FFMA2 5           /* FP32 fused multiply-add, two per instruction */
+#define RICK_PROBE_SHFL 6            /* 32-bit warp shuffle (per lane)               */
+#define RICK_PROBE_F2I 7             /* FP32 to int32 conversion, round to nearest    */
 rick_status rick_probe_throughput(int32_t kind, double *ops_per_clock_per_sm);
 
 #ifdef __cplusplus

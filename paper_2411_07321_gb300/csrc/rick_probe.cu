@@ -72,6 +72,29 @@ __global__ void __launch_bounds__(PROBE_THREADS, 1)
         }
 #pragma unroll
         for (int j = 0; j < PROBE_WORDS; ++j) acc += r[j].x + r[j].y;
+    } else if (KIND == RICK_PROBE_SHFL) {
+        float r[PROBE_WORDS];
+#pragma unroll
+        for (int j = 0; j < PROBE_WORDS; ++j) r[j] = v + j;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < PROBE_WORDS; ++j)
+                r[j] = __shfl_sync(0xffffffffu, r[j], (threadIdx.x + j + 1) & 31);
+        }
+#pragma unroll
+        for (int j = 0; j < PROBE_WORDS; ++j) acc += r[j];
+    } else if (KIND == RICK_PROBE_F2I) {
+        // float to integer, round to nearest (cvt.rni.s32.f32), chained through
+        // an integer add so that every conversion is live
+        int r[PROBE_WORDS];
+#pragma unroll
+        for (int j = 0; j < PROBE_WORDS; ++j) r[j] = t + j;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < PROBE_WORDS; ++j) r[j] = __float2int_rn(__int_as_float(r[j] | 0x3f800000));
+        }
+#pragma unroll
+        for (int j = 0; j < PROBE_WORDS; ++j) acc += (float)r[j];
     }
     __syncthreads();
     const unsigned long long c1 = clock64();
@@ -93,7 +116,7 @@ static cudaError_t probe_launch(int blocks, int iters, unsigned long long *cyc, 
 
 extern "C" rick_status rick_probe_throughput(int32_t kind, double *ops_per_clock_per_sm)
 {
-    if (!ops_per_clock_per_sm || kind < RICK_PROBE_SMEM_RMW || kind > RICK_PROBE_FFMA2)
+    if (!ops_per_clock_per_sm || kind < RICK_PROBE_SMEM_RMW || kind > RICK_PROBE_F2I)
         return RICK_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -108,6 +131,7 @@ extern "C" rick_status rick_probe_throughput(int32_t kind, double *ops_per_clock
         return RICK_ENOMEM;
     }
     const int iters = (kind == RICK_PROBE_FFMA || kind == RICK_PROBE_FFMA2) ? 16384 : 2048;
+    // (each conversion above also pays an OR: the figure bounds F2I from below)
     rick_status st = RICK_OK;
     std::vector<unsigned long long> h((size_t)sms);
     for (int rep = 0; rep < 2 && st == RICK_OK; ++rep) {  // the first run warms up
@@ -119,6 +143,8 @@ extern "C" rick_status rick_probe_throughput(int32_t kind, double *ops_per_clock
         case RICK_PROBE_SMEM_ATOMIC_U64: e = probe_launch<RICK_PROBE_SMEM_ATOMIC_U64>(sms, iters, cyc, sink); break;
         case RICK_PROBE_FFMA: e = probe_launch<RICK_PROBE_FFMA>(sms, iters, cyc, sink); break;
         case RICK_PROBE_FFMA2: e = probe_launch<RICK_PROBE_FFMA2>(sms, iters, cyc, sink); break;
+        case RICK_PROBE_SHFL: e = probe_launch<RICK_PROBE_SHFL>(sms, iters, cyc, sink); break;
+        case RICK_PROBE_F2I: e = probe_launch<RICK_PROBE_F2I>(sms, iters, cyc, sink); break;
         }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e == cudaSuccess)

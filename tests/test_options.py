@@ -267,7 +267,8 @@ def test_probe_throughput(P):
     R = P.rick
     rates = {k: R.rick_probe_throughput(getattr(R, k)) for k in
              ("RICK_PROBE_SMEM_RMW", "RICK_PROBE_SMEM_ATOMIC_F32", "RICK_PROBE_SMEM_ATOMIC_U32",
-              "RICK_PROBE_SMEM_ATOMIC_U64", "RICK_PROBE_FFMA", "RICK_PROBE_FFMA2")}
+              "RICK_PROBE_SMEM_ATOMIC_U64", "RICK_PROBE_FFMA", "RICK_PROBE_FFMA2",
+              "RICK_PROBE_SHFL", "RICK_PROBE_F2I")}
     print("probe (operations per SM clock):", {k: round(v, 2) for k, v in rates.items()})
     for k, v in rates.items():
         assert 0.5 < v <= 4 * 32 * (2 if k.endswith("FFMA2") else 1) * 1.05, (k, v)
