@@ -52,15 +52,19 @@ struct FftArgs {
     WcArgs wc;               // image geometry, flags, taper, plane centres, weight sum
 };
 
+// Shared arrays hold complex points as float2, one 8-byte access each: a warp's
+// access is two half-warps of 16 points, conflict-free when the 16 fall in
+// distinct 8-byte bank pairs (index mod 16).
+//
 // Staged rows (written out or gathered transposed): an XOR swizzle of the low
-// five bits, which with a per-row rotation keeps both the row-wise and the
+// four bits, which with a per-row rotation keeps both the row-wise and the
 // column-wise accesses free of bank conflicts.
-static __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 31); }
+static __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
 
-// Exchange arrays: one word of padding per 32 (a + a/32) keeps the stages'
-// access patterns free of bank conflicts (one pattern is 2-way) and leaves
-// every address a per-thread base plus a constant.
-static __device__ __forceinline__ int pad32(int a) { return a + (a >> 5); }
+// Exchange arrays: one point of padding per 16 (a + a/16) keeps the stages'
+// access patterns free of bank conflicts and leaves every address a
+// per-thread base plus a constant.
+static __device__ __forceinline__ int pad16(int a) { return a + (a >> 4); }
 
 static __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -164,8 +168,8 @@ __host__ __device__ constexpr int twiddle_entries(int N)
 // go to (j - j mod NS) R + j mod NS + m NS.  After the last stage x[s] holds
 // output t + P s.  cb is the transform's offset in the exchange arrays.
 template <int N, int R, int NS, int OFF, bool LAST>
-static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb, float *sre,
-                                                 float *sim, const float2 *__restrict__ tw)
+static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb, float2 *sx,
+                                                 const float2 *__restrict__ tw)
 {
     constexpr int P = N / 16, B = 16 / R;
 #pragma unroll
@@ -186,9 +190,7 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
             const int base = (j - k) * R + k;
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                const int i = cb + pad32(base + m * NS);
-                sre[i] = y[m].x;
-                sim[i] = y[m].y;
+                sx[cb + pad16(base + m * NS)] = y[m];
             }
         }
     }
@@ -196,37 +198,36 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            const int i = cb + pad32(t + P * s);
-            x[s] = make_float2(sre[i], sim[i]);
+            x[s] = sx[cb + pad16(t + P * s)];
         }
         __syncthreads();
     }
 }
 
 template <int N, int NS, int OFF>
-static __device__ __forceinline__ void fft_stages(float2 (&x)[16], int t, int cb, float *sre,
-                                                  float *sim, const float2 *__restrict__ tw)
+static __device__ __forceinline__ void fft_stages(float2 (&x)[16], int t, int cb, float2 *sx,
+                                                  const float2 *__restrict__ tw)
 {
     constexpr int R = stage_radix(N, NS);
     constexpr bool LAST = (R == N / NS);
-    fft_stage<N, R, NS, OFF, LAST>(x, t, cb, sre, sim, tw);
-    if constexpr (!LAST) fft_stages<N, NS * R, OFF + (NS > 1 ? (R - 1) * NS : 0)>(x, t, cb, sre, sim, tw);
+    fft_stage<N, R, NS, OFF, LAST>(x, t, cb, sx, tw);
+    if constexpr (!LAST) fft_stages<N, NS * R, OFF + (NS > 1 ? (R - 1) * NS : 0)>(x, t, cb, sx, tw);
 }
 
 // The unnormalised inverse DFT of N points held as x[s] = element t + P s;
 // on return x[s] = output t + P s.  Every thread of the CTA must call it.
 // tw: the plan's stage twiddle tables.
 template <int LOGN>
-static __device__ __forceinline__ void fft_inv(float2 (&x)[16], int t, int cb, float *sre,
-                                               float *sim, const float2 *__restrict__ tw)
+static __device__ __forceinline__ void fft_inv(float2 (&x)[16], int t, int cb, float2 *sx,
+                                               const float2 *__restrict__ tw)
 {
-    fft_stages<(1 << LOGN), 1, 0>(x, t, cb, sre, sim, tw);
+    fft_stages<(1 << LOGN), 1, 0>(x, t, cb, sx, tw);
 }
 
-// Exchange arrays of one transform: N words plus the padding.
+// Exchange array of one transform: N points plus the padding.
 template <int N>
 struct XLen {
-    static constexpr int L = N + N / 32;
+    static constexpr int L = N + N / 16;
 };
 
 // Tiles to read: a tile holds records iff it has gridding work items.
@@ -277,10 +278,9 @@ template <int LOGN>
 __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
 {
     constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
-    constexpr int ROT = ROWS >= 32 ? 1 : 32 / ROWS;
+    constexpr int ROT = ROWS >= 16 ? 1 : 16 / ROWS;
     constexpr int L = XLen<N>::L;
-    extern __shared__ float fsm[];
-    float *sre = fsm, *sim = fsm + ROWS * L;  // exchange arrays; staging at row stride N
+    extern __shared__ float2 sx[];  // exchange arrays (row stride L); staging at row stride N
     __shared__ uint8_t s_tf[1024];  // tile flags of the block's tile-rows
     const int t = threadIdx.x % P;
     const int nt = a.nt, l2T = a.log2T, m = a.wc.m, off = a.wc.off;
@@ -320,16 +320,12 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
                     x[s] = tf[u >> l2T] ? __ldcg(row + u) : make_float2(0.0f, 0.0f);
                 }
             }
-            fft_inv<LOGN>(x, t, c * L, sre, sim, a.tw);
+            fft_inv<LOGN>(x, t, c * L, sx, a.tw);
             // stage the row (row stride N: the staged rows of batch 0 lie below
             // the exchange arrays of batch 1), XOR-swizzled and rotated per row
             // so that the transposed read-out is free of bank conflicts too
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                const int i = swz(c * N + t + P * s) ^ ((c * ROT) & 31);
-                sre[i] = x[s].x;
-                sim[i] = x[s].y;
-            }
+            for (int s = 0; s < 16; ++s) sx[swz(c * N + t + P * s) ^ ((c * ROT) & 15)] = x[s];
         }
         __syncthreads();
         // lanes take consecutive rows of consecutive columns, so that each warp
@@ -337,8 +333,7 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         float2 *dst = a.work + (size_t)k * m * N + v0;
         for (int i = threadIdx.x; i < ROWS * m; i += blockDim.x) {
             const int r = i % ROWS, pc = i / ROWS;
-            const int j = swz(r * N + pc + off) ^ ((r * ROT) & 31);
-            dst[(size_t)pc * N + r] = make_float2(sre[j], sim[j]);
+            dst[(size_t)pc * N + r] = sx[swz(r * N + pc + off) ^ ((r * ROT) & 15)];
         }
     }
 }
@@ -354,8 +349,8 @@ template <int LOGN>
 struct ColShape {
     static constexpr int N = 1 << LOGN, P = N / 16;
     static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
-    static constexpr int XE = COLS * XLen<N>::L;  // words of one exchange array
-    static constexpr size_t SMEM = sizeof(float) * (2 * XE + 4 * NE);
+    static constexpr int XE = COLS * XLen<N>::L;  // points of the exchange arrays
+    static constexpr size_t SMEM = sizeof(float2) * XE + sizeof(float) * 4 * NE;
 };
 
 template <int LOGN>
@@ -366,7 +361,7 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
     constexpr int N = S::N, P = S::P, NT = S::NT, COLS = S::COLS, NE = S::NE;
     constexpr int XE = S::XE;
     extern __shared__ float fsm[];
-    float *sre = fsm, *sim = fsm + XE;
+    float2 *sx = (float2 *)fsm;
     float *g_hi = fsm + 2 * XE, *g_lo = g_hi + NE, *g_sc = g_lo + NE, *g_acc = g_sc + NE;
     const WcArgs &w = a.wc;
     const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * XLen<N>::L;
@@ -431,7 +426,7 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
                     x[s] = (live && tr[v >> l2T]) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
                 }
             }
-            fft_inv<LOGN>(x, t, cb, sre, sim, a.tw);
+            fft_inv<LOGN>(x, t, cb, sx, a.tw);
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const float2 hd = cmul(h[s], D[s]);
@@ -479,8 +474,8 @@ template <int LOGN>
 struct AdjColShape {
     static constexpr int N = 1 << LOGN, P = N / 16;
     static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
-    static constexpr int XE = COLS * XLen<N>::L;
-    static constexpr size_t SMEM = sizeof(float) * (2 * XE + 3 * NE);
+    static constexpr int XE = COLS * XLen<N>::L;  // points of the exchange arrays
+    static constexpr size_t SMEM = sizeof(float2) * XE + sizeof(float) * 3 * NE;
 };
 
 template <int LOGN>
@@ -490,7 +485,7 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
     using S = AdjColShape<LOGN>;
     constexpr int N = S::N, P = S::P, NT = S::NT, COLS = S::COLS, NE = S::NE, XE = S::XE;
     extern __shared__ float fsm[];
-    float *sre = fsm, *sim = fsm + XE;
+    float2 *sx = (float2 *)fsm;
     float *g_hi = fsm + 2 * XE, *g_lo = g_hi + NE, *g_a = g_lo + NE;
     const WcArgs &w = a.wc;
     const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * XLen<N>::L;
@@ -548,7 +543,7 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
             const float av = g_a[s * NT + threadIdx.x];
             x[s] = make_float2(av * ph[s].x, av * ph[s].y);
         }
-        fft_inv<LOGN>(x, t, cb, sre, sim, a.tw);
+        fft_inv<LOGN>(x, t, cb, sx, a.tw);
         if (!live) continue;
         float2 *col = dst + (size_t)k * m * N;
         if (nt <= 64) {
@@ -578,11 +573,10 @@ template <int LOGN>
 __global__ void __launch_bounds__(512, 1) fft_rows_adj_kernel(FftArgs a)
 {
     constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
-    constexpr int ROT = ROWS >= 32 ? 1 : 32 / ROWS;
-    constexpr int L = XLen<N>::L, SW = ROWS * N + RPR * L;  // words of one array
-    extern __shared__ float fsm[];
-    float *gre = fsm, *gim = fsm + SW;                   // staged rows (row stride N)
-    float *xre = gre + ROWS * N, *xim = gim + ROWS * N;  // exchange arrays
+    constexpr int ROT = ROWS >= 16 ? 1 : 16 / ROWS;
+    constexpr int L = XLen<N>::L;
+    extern __shared__ float2 gx[];   // staged rows (row stride N)
+    float2 *xx = gx + ROWS * N;      // exchange arrays (row stride L)
     __shared__ uint8_t s_tf[1024];
     const int t = threadIdx.x % P;
     const int nt = a.nt, l2T = a.log2T, m = a.wc.m, off = a.wc.off;
@@ -606,9 +600,7 @@ __global__ void __launch_bounds__(512, 1) fft_rows_adj_kernel(FftArgs a)
             const int r = i % ROWS, p = i / ROWS, pc = p - off;
             const float2 z = (pc >= 0 && pc < m && a.trow[k * nt + ((v0 + r) >> l2T)])
                                  ? __ldcg(src + (size_t)pc * N + r) : make_float2(0.0f, 0.0f);
-            const int j = swz(r * N + p) ^ ((r * ROT) & 31);
-            gre[j] = z.x;
-            gim[j] = z.y;
+            gx[swz(r * N + p) ^ ((r * ROT) & 15)] = z;
         }
         __syncthreads();
 #pragma unroll 1
@@ -617,10 +609,9 @@ __global__ void __launch_bounds__(512, 1) fft_rows_adj_kernel(FftArgs a)
             float2 x[16];
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
-                const int j = swz(c * N + t + P * s) ^ ((c * ROT) & 31);
-                x[s] = make_float2(gre[j], gim[j]);
+                x[s] = gx[swz(c * N + t + P * s) ^ ((c * ROT) & 15)];
             }
-            fft_inv<LOGN>(x, t, (threadIdx.x / P) * L, xre, xim, a.tw);
+            fft_inv<LOGN>(x, t, (threadIdx.x / P) * L, xx, a.tw);
             float2 *row = a.planes_out + ((size_t)k * N + v) * N;
             if (nt <= 64) {
                 const unsigned long long msk = a.tmask[k * nt + (v >> l2T)];
@@ -711,7 +702,7 @@ template <int LOGN>
 static cudaError_t launch_fft_wc(const FftArgs &a, int num_sms, cudaStream_t st)
 {
     using S = ColShape<LOGN>;
-    const size_t rows_smem = 2 * sizeof(float) * (1024 / S::P) * XLen<(1 << LOGN)>::L;
+    const size_t rows_smem = sizeof(float2) * (1024 / S::P) * XLen<(1 << LOGN)>::L;
     cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<LOGN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rows_smem);
@@ -806,7 +797,7 @@ static cudaError_t launch_wspread_fft(const FftArgs &a, int num_sms, cudaStream_
 {
     using S = AdjColShape<LOGN>;
     constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
-    const size_t rows_smem = 2 * sizeof(float) * (ROWS * N + RPR * XLen<N>::L);
+    const size_t rows_smem = sizeof(float2) * (ROWS * N + RPR * XLen<N>::L);
     cudaError_t e = cudaFuncSetAttribute(fft_cols_adj_kernel<LOGN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::SMEM);
