@@ -373,8 +373,8 @@ rick_status rick_fused_work_bytes(const rick_params *params, size_t *work_bytes)
 /* Bytes of the work buffer of rick_fft_wcorrect for this plan.  Its layout,
  * each piece starting on a 256-byte boundary: uint8 tile flags [n_w][nt][nt]
  * (nt = n / tile; 1: the tile was read), uint8 tile-row flags [n_w][nt],
- * uint8 plane flags [n_w], uint64 tile-row bit masks [n_w] and tile bit
- * masks [n_w][nt] (for nt <= 64), then the row transforms, complex64
+ * uint8 plane flags [n_w], 128-bit tile-row bit masks [n_w] and tile bit
+ * masks [n_w][nt] (two uint64 each, for nt <= 128), then the row transforms, complex64
  * [n_w][image_n][n] (8 n_w image_n n bytes; image_n = n without a crop).
  * RICK_EINVAL if n is outside 256 ... 8192, the sizes the fused transform
  * covers (use rick_fft_wplanes + rick_wcorrect_stack there). */

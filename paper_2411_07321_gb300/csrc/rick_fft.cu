@@ -46,8 +46,8 @@ struct FftArgs {
     uint8_t *tflag;          // [n_w][nt][nt]: tile holds records (is read)
     uint8_t *trow;           // [n_w][nt]: tile-row holds records
     uint8_t *pflag;          // [n_w]: plane holds records
-    unsigned long long *pmask;  // [n_w]: bit ty = tile-row ty holds records (nt <= 64)
-    unsigned long long *tmask;  // [n_w][nt]: bit tx = tile tx of the tile-row holds records (nt <= 64)
+    ulonglong2 *pmask;       // [n_w]: bit ty = tile-row ty holds records (nt <= 128)
+    ulonglong2 *tmask;       // [n_w][nt]: bit tx = tile tx of the tile-row holds records (nt <= 128)
     const float2 *tw;        // the plan's stage twiddle tables (twiddle_kernel)
     WcArgs wc;               // image geometry, flags, taper, plane centres, weight sum
 };
@@ -224,6 +224,29 @@ static __device__ __forceinline__ void fft_inv(float2 (&x)[16], int t, int cb, f
     fft_stages<(1 << LOGN), 1, 0>(x, t, cb, sx, tw);
 }
 
+// Tile masks of up to 128 tiles (x: bits 0..63, y: bits 64..127), for grids of
+// at most RICK_FFT_MASK_TILES tiles a side; larger grids read byte flags.
+#define RICK_FFT_MASK_TILES 128
+
+static __device__ __forceinline__ bool mask_bit(const ulonglong2 &msk, int b)
+{
+    return ((b < 64 ? msk.x : msk.y) >> (b & 63)) & 1ull;
+}
+
+// x[s] = src[t + P s] where the tile of t + P s is set in msk, else 0 (WIDE:
+// up to 128 tiles; else up to 64, one word and no selection).
+template <int P, bool WIDE>
+static __device__ __forceinline__ void load_masked(float2 (&x)[16], const float2 *src,
+                                                   const ulonglong2 &msk, int t, int l2T)
+{
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int u = t + P * s;
+        const bool on = WIDE ? mask_bit(msk, u >> l2T) : ((msk.x >> (u >> l2T)) & 1ull);
+        x[s] = on ? __ldcg(src + u) : make_float2(0.0f, 0.0f);
+    }
+}
+
 // Exchange array of one transform: N points plus the padding.
 template <int N>
 struct XLen {
@@ -247,26 +270,27 @@ __global__ void __launch_bounds__(256) fft_rowflags_kernel(FftArgs a)
 {
     const int k = blockIdx.x, nt = a.nt;
     const uint8_t *tf = a.tflag + (size_t)k * nt * nt;
-    __shared__ unsigned long long s_mask;
-    if (threadIdx.x == 0) s_mask = 0;
+    __shared__ unsigned long long s_mask[2];
+    if (threadIdx.x < 2) s_mask[threadIdx.x] = 0;
     __syncthreads();
     int any_plane = 0;
     for (int ty = threadIdx.x; ty < nt; ty += blockDim.x) {
         uint8_t any = 0;
-        unsigned long long tm = 0;
+        unsigned long long tm[2] = {0, 0};
         for (int x = 0; x < nt; ++x) {
-            any |= tf[ty * nt + x];
-            if (x < 64 && tf[ty * nt + x]) tm |= 1ull << x;
+            const uint8_t f = tf[ty * nt + x];
+            any |= f;
+            if (x < RICK_FFT_MASK_TILES && f) tm[x >> 6] |= 1ull << (x & 63);
         }
         a.trow[k * nt + ty] = any;
-        a.tmask[k * nt + ty] = tm;
+        a.tmask[k * nt + ty] = make_ulonglong2(tm[0], tm[1]);
         any_plane |= any;
-        if (any && ty < 64) atomicOr(&s_mask, 1ull << ty);
+        if (any && ty < RICK_FFT_MASK_TILES) atomicOr(&s_mask[ty >> 6], 1ull << (ty & 63));
     }
     any_plane = __syncthreads_or(any_plane);
     if (threadIdx.x == 0) {
         a.pflag[k] = (uint8_t)(any_plane != 0);
-        a.pmask[k] = s_mask;
+        a.pmask[k] = make_ulonglong2(s_mask[0], s_mask[1]);
     }
 }
 
@@ -293,7 +317,7 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         if (!any) continue;  // the same for every thread
         __syncthreads();     // the previous block's write-out has read the staging rows
         const int ntr = ty1 - ty0 + 1;
-        if (nt > 64) {
+        if (nt > RICK_FFT_MASK_TILES) {
             const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
             for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
         }
@@ -305,13 +329,10 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
             const int c = threadIdx.x / P + h * RPR, v = v0 + c;
             const float2 *row = a.planes + ((size_t)k * N + v) * N;
             float2 x[16];
-            if (nt <= 64) {  // the row's tiles as one bit mask
-                const unsigned long long msk = a.tmask[k * nt + (v >> l2T)];
-#pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int u = t + P * s;
-                    x[s] = ((msk >> (u >> l2T)) & 1ull) ? __ldcg(row + u) : make_float2(0.0f, 0.0f);
-                }
+            if (nt <= 64) {  // the row's tiles as a bit mask
+                load_masked<P, false>(x, row, a.tmask[k * nt + (v >> l2T)], t, l2T);
+            } else if (nt <= RICK_FFT_MASK_TILES) {
+                load_masked<P, true>(x, row, a.tmask[k * nt + (v >> l2T)], t, l2T);
             } else {
                 const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
 #pragma unroll
@@ -411,13 +432,10 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
             }
             const float2 *src = col + (size_t)k * m * N;
             float2 x[16];
-            if (nt <= 64) {  // the plane's tile-rows as one bit mask
-                const unsigned long long msk = live ? a.pmask[k] : 0ull;
-#pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int v = t + P * s;
-                    x[s] = ((msk >> (v >> l2T)) & 1ull) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
-                }
+            if (nt <= RICK_FFT_MASK_TILES) {  // the plane's tile-rows as a bit mask
+                const ulonglong2 msk = live ? a.pmask[k] : make_ulonglong2(0ull, 0ull);
+                if (nt <= 64) load_masked<P, false>(x, src, msk, t, l2T);
+                else load_masked<P, true>(x, src, msk, t, l2T);
             } else {
                 const uint8_t *tr = a.trow + k * nt;
 #pragma unroll
@@ -546,12 +564,12 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
         fft_inv<LOGN>(x, t, cb, sx, a.tw);
         if (!live) continue;
         float2 *col = dst + (size_t)k * m * N;
-        if (nt <= 64) {
-            const unsigned long long msk = a.pmask[k];
+        if (nt <= RICK_FFT_MASK_TILES) {
+            const ulonglong2 msk = a.pmask[k];
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const int v = t + P * s;
-                if ((msk >> (v >> l2T)) & 1ull) __stcg(col + v, x[s]);
+                if (mask_bit(msk, v >> l2T)) __stcg(col + v, x[s]);
             }
         } else {
             const uint8_t *tr = a.trow + k * nt;
@@ -589,7 +607,7 @@ __global__ void __launch_bounds__(512, 1) fft_rows_adj_kernel(FftArgs a)
         if (!any) continue;  // the same for every thread
         __syncthreads();     // the previous block is done with the staged rows
         const int ntr = ty1 - ty0 + 1;
-        if (nt > 64) {
+        if (nt > RICK_FFT_MASK_TILES) {
             const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
             for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
         }
@@ -613,12 +631,12 @@ __global__ void __launch_bounds__(512, 1) fft_rows_adj_kernel(FftArgs a)
             }
             fft_inv<LOGN>(x, t, (threadIdx.x / P) * L, xx, a.tw);
             float2 *row = a.planes_out + ((size_t)k * N + v) * N;
-            if (nt <= 64) {
-                const unsigned long long msk = a.tmask[k * nt + (v >> l2T)];
+            if (nt <= RICK_FFT_MASK_TILES) {
+                const ulonglong2 msk = a.tmask[k * nt + (v >> l2T)];
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     const int u = t + P * s;
-                    if ((msk >> (u >> l2T)) & 1ull) row[u] = make_float2(x[s].x, -x[s].y);
+                    if (mask_bit(msk, u >> l2T)) row[u] = make_float2(x[s].x, -x[s].y);
                 }
             } else {
                 const uint8_t *tf = s_tf + ((v >> l2T) - ty0) * nt;
@@ -652,8 +670,8 @@ static FftWorkLayout fft_work_layout(const rick_params &p)
     L.tflag = o; o += rick_align256((size_t)p.n_w * nt * nt);
     L.trow = o;  o += rick_align256((size_t)p.n_w * nt);
     L.pflag = o; o += rick_align256((size_t)p.n_w);
-    L.pmask = o; o += rick_align256(8 * (size_t)p.n_w);
-    L.tmask = o; o += rick_align256(8 * (size_t)p.n_w * nt);
+    L.pmask = o; o += rick_align256(sizeof(ulonglong2) * (size_t)p.n_w);
+    L.tmask = o; o += rick_align256(sizeof(ulonglong2) * (size_t)p.n_w * nt);
     L.work = o;  o += (size_t)p.n_w * m * p.n * sizeof(float2);
     L.total = o;
     return L;
@@ -743,8 +761,8 @@ static FftArgs fft_args(rick_plan *plan, const void *ws_dev, void *work_dev, uin
     a.tflag = (uint8_t *)(wb + L.tflag);
     a.trow = (uint8_t *)(wb + L.trow);
     a.pflag = (uint8_t *)(wb + L.pflag);
-    a.pmask = (unsigned long long *)(wb + L.pmask);
-    a.tmask = (unsigned long long *)(wb + L.tmask);
+    a.pmask = (ulonglong2 *)(wb + L.pmask);
+    a.tmask = (ulonglong2 *)(wb + L.tmask);
     a.work = (float2 *)(wb + L.work);
     a.tw = plan->twid;
     a.wc = make_args(plan, ws_dev, flags);

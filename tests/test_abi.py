@@ -128,7 +128,7 @@ def test_null_plan_rejected(R):
 
 def test_stream_bytes(R):
     """Staging area of the streamed path: two chunk buffers of vis and weight,
-    the fused transform's work buffer (tile, tile-row and plane flags, tile-row and tile masks, and the
+    the fused transform's work buffer (tile, tile-row and plane flags, 128-bit tile-row and tile masks, and the
     transposed row transforms, 8 n_w n^2 bytes), plus two chunk buffers of uvw
     (given w range) or two areas holding the whole set's uvw, resident while
     its w range is found and used by alternate calls (range from the data)."""
@@ -137,7 +137,7 @@ def test_stream_bytes(R):
     given = R.make_params(256, 8, 0.035, 1, 7, w_min=-10.0, w_max=10.0, tile=32)
     data = R.make_params(256, 8, 0.035, 1, 7, tile=32)
     nt = 256 // 32
-    fwork = al(8 * nt * nt) + al(8 * nt) + al(8) + al(8 * 8) + al(8 * 8 * nt) + 8 * 8 * 256 * 256
+    fwork = al(8 * nt * nt) + al(8 * nt) + al(8) + al(16 * 8) + al(16 * 8 * nt) + 8 * 8 * 256 * 256
     head = R.rick_stream_bytes(given, chunk, n) - 2 * (al(24 * chunk) + al(8 * chunk) +
                                                        al(4 * chunk)) - fwork
     assert 0 < head <= 4096 + 2 * 8 * 4096  # headers and two areas of channel factors
@@ -154,14 +154,14 @@ def test_stream_bytes(R):
 
 
 def test_fused_work_bytes(R):
-    """The fused transform's work buffer without a plan: flags and bit masks, then
+    """The fused transform's work buffer without a plan: flags and 128-bit masks, then
     the transposed row transforms (8 n_w image_n n bytes); the same bytes the
     streamed call stages; none where the fused transform does not cover n."""
     al = lambda x: (x + 255) // 256 * 256
     for n, n_w, tile, image_n in ((256, 8, 32, 0), (4096, 16, 64, 0), (8192, 3, 8, 4096)):
         p = R.make_params(n, n_w, 0.03, 1, 7, tile=tile, image_n=image_n)
         nt, m = n // tile, image_n or n
-        want = al(n_w * nt * nt) + al(n_w * nt) + al(n_w) + al(8 * n_w) + al(8 * n_w * nt) + \
+        want = al(n_w * nt * nt) + al(n_w * nt) + al(n_w) + al(16 * n_w) + al(16 * n_w * nt) + \
             8 * n_w * m * n
         assert R.rick_fused_work_bytes(p) == want
     assert R.rick_fused_work_bytes(R.make_params(128, 4, 0.03, 1, 7, tile=32)) == 0
