@@ -247,6 +247,29 @@ static __device__ __forceinline__ void load_masked(float2 (&x)[16], const float2
     }
 }
 
+// Selector of the 16 points t + P s (s < 16) of the threads of class c = t / T
+// when P is a multiple of the tile side T: the points lie in tile-rows (or
+// tiles) c + s S, S = P / T; bit s is set where that one holds records.
+static __device__ __forceinline__ uint32_t class_sel(const ulonglong2 &msk, int c, int S)
+{
+    uint32_t sel = 0;
+    for (int s = 0; s < 16; ++s) sel |= (uint32_t)mask_bit(msk, c + s * S) << s;
+    return sel;
+}
+
+// x[s] = src[t + P s] where bit s of sel is set, else 0.
+template <int P>
+static __device__ __forceinline__ void load_sel(float2 (&x)[16], const float2 *src, uint32_t sel,
+                                                int t)
+{
+#pragma unroll
+    for (int s = 0; s < 16; ++s)
+        x[s] = ((sel >> s) & 1u) ? __ldcg(src + t + P * s) : make_float2(0.0f, 0.0f);
+}
+
+// Classes of threads whose selectors are tabled per CTA (P / T for T >= 16).
+#define RICK_FFT_SEL_CLASSES 32
+
 // Exchange array of one transform: N points plus the padding.
 template <int N>
 struct XLen {
@@ -306,8 +329,14 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
     constexpr int L = XLen<N>::L;
     extern __shared__ float2 sx[];  // exchange arrays (row stride L); staging at row stride N
     __shared__ uint8_t s_tf[1024];  // tile flags of the block's tile-rows
+    __shared__ uint16_t s_rsel[8][RICK_FFT_SEL_CLASSES];  // selectors per tile-row and class
     const int t = threadIdx.x % P;
     const int nt = a.nt, l2T = a.log2T, m = a.wc.m, off = a.wc.off;
+    // selectors from the tile masks when P is a multiple of the tile side
+    // and the masks take two words (one word is tested as cheaply in place)
+    const int ncls = P >> l2T;
+    const bool tabled = nt > 64 && nt <= RICK_FFT_MASK_TILES && ncls >= 1 &&
+                        ncls <= RICK_FFT_SEL_CLASSES && ROWS <= 8 << l2T;
     const int nvb = N / ROWS, items = a.n_w * nvb;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int k = item / nvb, v0 = (item - k * nvb) * ROWS;
@@ -320,6 +349,9 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         if (nt > RICK_FFT_MASK_TILES) {
             const uint8_t *tfg = a.tflag + ((size_t)k * nt + ty0) * nt;
             for (int i = threadIdx.x; i < ntr * nt; i += blockDim.x) s_tf[i] = tfg[i];
+        } else if (tabled && threadIdx.x < ntr * ncls) {
+            const int r = threadIdx.x / ncls, c = threadIdx.x - r * ncls;
+            s_rsel[r][c] = (uint16_t)class_sel(a.tmask[k * nt + ty0 + r], c, ncls);
         }
         __syncthreads();
 #pragma unroll 1
@@ -329,7 +361,9 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
             const int c = threadIdx.x / P + h * RPR, v = v0 + c;
             const float2 *row = a.planes + ((size_t)k * N + v) * N;
             float2 x[16];
-            if (nt <= 64) {  // the row's tiles as a bit mask
+            if (tabled) {
+                load_sel<P>(x, row, s_rsel[(v >> l2T) - ty0][t >> l2T], t);
+            } else if (nt <= 64) {  // the row's tiles as a bit mask
                 load_masked<P, false>(x, row, a.tmask[k * nt + (v >> l2T)], t, l2T);
             } else if (nt <= RICK_FFT_MASK_TILES) {
                 load_masked<P, true>(x, row, a.tmask[k * nt + (v >> l2T)], t, l2T);
@@ -419,8 +453,22 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
     }
     const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
     const float2 *col = a.work + (size_t)(live ? pc : 0) * N;
+    // selectors of the block's planes per thread class (P a multiple of the
+    // tile side), tabled at the start of each block of planes
+    __shared__ uint16_t s_sel[RICK_PHASE_ANCHOR][RICK_FFT_SEL_CLASSES];
+    const int ncls = P >> l2T;
+    const bool tabled = nt <= RICK_FFT_MASK_TILES && ncls >= 1 && ncls <= RICK_FFT_SEL_CLASSES;
     for (int k0 = 0; k0 < w.n_w; k0 += bs) {
         const int k1 = min(k0 + bs, w.n_w);
+        if (tabled) {
+            // the previous block's reads of the table precede the barriers of
+            // its transforms
+            for (int i = threadIdx.x; i < (k1 - k0) * ncls; i += NT) {
+                const int r = i / ncls, c = i - r * ncls;
+                s_sel[r][c] = (uint16_t)class_sel(a.pmask[k0 + r], c, ncls);
+            }
+            __syncthreads();
+        }
         float2 h[16];
 #pragma unroll
         for (int s = 0; s < 16; ++s) h[s] = make_float2(0.0f, 0.0f);
@@ -432,7 +480,9 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
             }
             const float2 *src = col + (size_t)k * m * N;
             float2 x[16];
-            if (nt <= RICK_FFT_MASK_TILES) {  // the plane's tile-rows as a bit mask
+            if (tabled) {
+                load_sel<P>(x, src, live ? (uint32_t)s_sel[k - k0][t >> l2T] : 0u, t);
+            } else if (nt <= RICK_FFT_MASK_TILES) {  // the plane's tile-rows as a bit mask
                 const ulonglong2 msk = live ? a.pmask[k] : make_ulonglong2(0ull, 0ull);
                 if (nt <= 64) load_masked<P, false>(x, src, msk, t, l2T);
                 else load_masked<P, true>(x, src, msk, t, l2T);

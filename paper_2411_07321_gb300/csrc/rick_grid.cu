@@ -100,18 +100,21 @@ struct StreamShape {
     static constexpr int LIVE = NG * G;  // lanes of a warp that carry a stream
 };
 
+// The lane's row sums into the tile accumulator: fb is the index of the row's
+// first cell, bit jx of fv says whether column jx lies inside the tile (fv = 0
+// when the row is outside it or the lane carries no row).  Both are set once
+// per footprint corner, so the loop over records carries two registers for
+// the flush instead of the corner's geometry.
 template <int W>
-__device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int T, int TP, int lx,
-                                            int row, bool live, const float *ar, const float *ai)
+__device__ __forceinline__ void group_flush(float *acc_re, float *acc_im, int fb, uint32_t fv,
+                                            const float *ar, const float *ai)
 {
-    if (!live || (unsigned)row >= (unsigned)T) return;
+    if (!fv) return;
 #pragma unroll
     for (int jx = 0; jx < W; ++jx) {
-        int col = lx + jx;
-        if ((unsigned)col < (unsigned)T) {
-            int i = row * TP + col;
-            atomicAdd(&acc_re[i], ar[jx]);
-            atomicAdd(&acc_im[i], ai[jx]);
+        if ((fv >> jx) & 1u) {
+            atomicAdd(&acc_re[fb + jx], ar[jx]);
+            atomicAdd(&acc_im[fb + jx], ai[jx]);
         }
     }
 }
@@ -158,6 +161,18 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
     uint32_t cur = rcell[0];
     float4 q = rec[0];
     uint32_t cell = cur;
+    // the flush target of corner cur (group_flush)
+    int fb;
+    uint32_t fv;
+    auto target = [&](uint32_t c) {
+        const int lx = (int)(c & 0xFFFFu) - x0, row = (int)(c >> 16) - y0 + j;
+        fb = row * TP + lx;
+        uint32_t m = 0;
+#pragma unroll
+        for (int jx = 0; jx < W; ++jx) m |= ((unsigned)(lx + jx) < (unsigned)T ? 1u : 0u) << jx;
+        fv = (live && (unsigned)row < (unsigned)T) ? m : 0u;
+    };
+    target(cur);
     for (uint32_t i = 0; i < n; ++i) {
         // prefetch the next record (the record arrays end with one of padding)
         const float4 nq = rec[i + 1];
@@ -167,11 +182,11 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
                 group_flush_det<W>(acc64, fx, T, TP, (int)(cur & 0xFFFFu) - x0,
                                    (int)(cur >> 16) - y0 + j, live, ar, ai);
             else
-                group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
-                               (int)(cur >> 16) - y0 + j, live, ar, ai);
+                group_flush<W>(acc_re, acc_im, fb, fv, ar, ai);
 #pragma unroll
             for (int jx = 0; jx < W; ++jx) ar[jx] = ai[jx] = 0.0f;
             cur = cell;
+            target(cur);
         }
         float gx = 1.0f, gy = 1.0f;
         if (W > 1) {
@@ -212,8 +227,7 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         group_flush_det<W>(acc64, fx, T, TP, (int)(cur & 0xFFFFu) - x0, (int)(cur >> 16) - y0 + j,
                            live, ar, ai);
     else
-        group_flush<W>(acc_re, acc_im, T, TP, (int)(cur & 0xFFFFu) - x0,
-                       (int)(cur >> 16) - y0 + j, live, ar, ai);
+        group_flush<W>(acc_re, acc_im, fb, fv, ar, ai);
 }
 
 template <int W, int MODE>
