@@ -172,6 +172,7 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
                                                  const float2 *__restrict__ tw)
 {
     constexpr int P = N / 16, B = 16 / R;
+    static_assert(P % 16 == 0 && (NS > 1 || R == 16), "exchange addressing assumes these");
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = t + P * b, k = j & (NS - 1);
@@ -187,18 +188,22 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
 #pragma unroll
             for (int m = 0; m < R; ++m) x[b + B * m] = y[m];
         } else {
+            // outputs base + m NS: with NS >= 16 the padding of output m is that
+            // of base plus m NS / 16; with NS = 1, base = R j and the R outputs
+            // share the padding j R / 16 (R <= 16)
             const int base = (j - k) * R + k;
+            float2 *dst = sx + cb + (NS >= 16 ? pad16(base) : base + (base >> 4));
 #pragma unroll
-            for (int m = 0; m < R; ++m) {
-                sx[cb + pad16(base + m * NS)] = y[m];
-            }
+            for (int m = 0; m < R; ++m) dst[m * (NS >= 16 ? NS + NS / 16 : 1)] = y[m];
         }
     }
     if constexpr (!LAST) {
         __syncthreads();
+        // elements t + P s, P a multiple of 16: padding t / 16 + s P / 16
+        const float2 *src = sx + cb + pad16(t);
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            x[s] = sx[cb + pad16(t + P * s)];
+            x[s] = src[s * (P + P / 16)];
         }
         __syncthreads();
     }

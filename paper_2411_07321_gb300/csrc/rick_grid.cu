@@ -142,7 +142,8 @@ __device__ __forceinline__ void group_flush_det(unsigned long long *acc64, float
 // n records of one segment of the tile's record list, starting at record r0.
 // DET: the flushes go to the 64-bit fixed-point tile acc64 (scale fx).
 template <int W, bool DET>
-__device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n, int x0,
+__device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uint32_t n,
+                                            uint32_t ntrip, int x0,
                                             int y0, float *acc_re, float *acc_im, int T, int TP,
                                             const float2 *coef2, unsigned long long *acc64,
                                             float fx)
@@ -150,9 +151,9 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
     constexpr int G = StreamShape<W>::G;
     const int lane = threadIdx.x & 31, grp = lane / G;
     const int j = lane - grp * G;  // this lane's row / kernel segment
-    const bool live = j < W;
-    const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-    if (n == 0) return;
+    const bool live = lane < StreamShape<W>::LIVE && j < W && n > 0;
+    if (ntrip == 0) return;
+    const uint32_t last = n > 0 ? n - 1 : 0;
     float ar[W], ai[W];
 #pragma unroll
     for (int jx = 0; jx < W; ++jx) ar[jx] = ai[jx] = 0.0f;
@@ -173,10 +174,11 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         fv = (live && (unsigned)row < (unsigned)T) ? m : 0u;
     };
     target(cur);
-    for (uint32_t i = 0; i < n; ++i) {
-        // prefetch the next record (the record arrays end with one of padding)
-        const float4 nq = rec[i + 1];
-        const uint32_t ncell = rcell[i + 1];
+    for (uint32_t i = 0; i < ntrip; ++i) {
+        // prefetch the next record; past the stream's end the last one again
+        const uint32_t ln = min(i + 1, last);
+        const float4 nq = rec[ln];
+        const uint32_t ncell = rcell[ln];
         if (cell != cur) {
             if (DET)
                 group_flush_det<W>(acc64, fx, T, TP, (int)(cur & 0xFFFFu) - x0,
@@ -197,7 +199,8 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
             gx = g2.x;
             gy = g2.y;
         }
-        const float2 vv = __fmul2_rn(make_float2(q.x, q.y), make_float2(gy, gy));
+        const float gz = i < n ? gy : 0.0f;
+        const float2 vv = __fmul2_rn(make_float2(q.x, q.y), make_float2(gz, gz));
         const float2 vr2 = make_float2(vv.x, vv.x), vi2 = make_float2(vv.y, vv.y);
         float wv[W];
 #pragma unroll
@@ -205,8 +208,8 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
             // power-of-two groups: the lane inside the group is an immediate
             // (width form); groups of W lanes: the absolute lane
             wv[jx] = W == 1 ? gx
-                   : (G & (G - 1)) == 0 ? __shfl_sync(gmask, gx, jx, G)
-                                        : __shfl_sync(gmask, gx, grp * G + jx);
+                   : (G & (G - 1)) == 0 ? __shfl_sync(0xffffffffu, gx, jx, G)
+                                        : __shfl_sync(0xffffffffu, gx, grp * G + jx);
         }
 #pragma unroll
         for (int jx = 0; jx + 1 < W; jx += 2) {
@@ -313,8 +316,9 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
             if (a0 < a1) {
                 const uint32_t per = (a1 - a0 + nstreams - 1) / nstreams;
                 const uint32_t v0 = min(a0 + stream * per, a1), v1 = min(v0 + per, a1);
-                if (streaming && v0 < v1)
-                    grid_stream<W, DET>(ta, s_rs[g] + (v0 - base), v1 - v0, x0, y0, acc_re, acc_im,
+                const uint32_t nv = streaming ? v1 - v0 : 0u;
+                grid_stream<W, DET>(ta, s_rs[g] + ((nv ? v0 : a0) - base), nv, per, x0, y0,
+                                    acc_re, acc_im,
                                         T, TP, coef2, acc64, fx);
             }
             base += lg;
