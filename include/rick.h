@@ -375,7 +375,8 @@ rick_status rick_fused_work_bytes(const rick_params *params, size_t *work_bytes)
  * (nt = n / tile; 1: the tile was read), uint8 tile-row flags [n_w][nt],
  * uint8 plane flags [n_w], 128-bit tile-row bit masks [n_w] and tile bit
  * masks [n_w][nt] (two uint64 each, for nt <= 128), then the row transforms, complex64
- * [n_w][image_n][n] (8 n_w image_n n bytes; image_n = n without a crop).
+ * [n_w][image_n][n] (8 n_w image_n n bytes; image_n = n without a crop; at
+ * n = 8192 the columns are stored in interleaved pairs, [n_w][image_n/2][n][2]).
  * RICK_EINVAL if n is outside 256 ... 8192, the sizes the fused transform
  * covers (use rick_fft_wplanes + rick_wcorrect_stack there). */
 rick_status rick_fft_wcorrect_bytes(const rick_plan *plan, size_t *work_bytes);

@@ -10,7 +10,9 @@
 //     without records are read as zeros, so the grid step need not clear them.
 //     The transformed rows go out transposed, work[k][p][v], 1024/(n/16) rows
 //     per CTA (4 at n = 4096) so that each 32-byte sector of the transposed
-//     store comes from one CTA; only the image's crop columns p are kept.
+//     store comes from one CTA; at n = 8192 (two rows per CTA) columns are
+//     stored in interleaved pairs, work[k][p/2][v][p%2], for the same reason.
+//     Only the image's crop columns p are kept.
 //  2. columns: along v, one transform per image column p and plane k, reading
 //     only the touched tile-rows of work[k][p].  The CTA keeps its column's
 //     pixels across the planes and sums them into the image as it goes: plane
@@ -95,11 +97,17 @@ static __device__ __forceinline__ void bfly16(float2 &u, float2 &v, int e)
         u = a;
         return;
     }
+    case 2:    // v e^{i pi/4} = sqrt(1/2) (x - y, x + y): the scale rides on the packed FMAs
+    case 6: {  // v e^{3 i pi/4} = sqrt(1/2) (-(x + y), x - y)
+        const float2 d = e == 2 ? make_float2(v.x - v.y, v.x + v.y)
+                                : make_float2(-v.x - v.y, v.x - v.y);
+        v = __ffma2_rn(d, make_float2(-H, -H), u);
+        u = __ffma2_rn(d, make_float2(H, H), u);
+        return;
+    }
     case 1: r = make_float2(v.x * C1 - v.y * S1, v.x * S1 + v.y * C1); break;
-    case 2: r = make_float2(H * (v.x - v.y), H * (v.x + v.y)); break;
     case 3: r = make_float2(v.x * S1 - v.y * C1, v.x * C1 + v.y * S1); break;
     case 5: r = make_float2(-v.x * S1 - v.y * C1, v.x * C1 - v.y * S1); break;
-    case 6: r = make_float2(-H * (v.x + v.y), H * (v.x - v.y)); break;
     default: r = make_float2(-v.x * C1 - v.y * S1, v.x * S1 - v.y * C1); break;
     }
     v = r;
@@ -238,9 +246,9 @@ static __device__ __forceinline__ bool mask_bit(const ulonglong2 &msk, int b)
     return ((b < 64 ? msk.x : msk.y) >> (b & 63)) & 1ull;
 }
 
-// x[s] = src[t + P s] where the tile of t + P s is set in msk, else 0 (WIDE:
-// up to 128 tiles; else up to 64, one word and no selection).
-template <int P, bool WIDE>
+// x[s] = src[VS (t + P s)] where the tile of t + P s is set in msk, else 0
+// (WIDE: up to 128 tiles; else up to 64, one word and no selection).
+template <int P, bool WIDE, int VS = 1>
 static __device__ __forceinline__ void load_masked(float2 (&x)[16], const float2 *src,
                                                    const ulonglong2 &msk, int t, int l2T)
 {
@@ -248,7 +256,7 @@ static __device__ __forceinline__ void load_masked(float2 (&x)[16], const float2
     for (int s = 0; s < 16; ++s) {
         const int u = t + P * s;
         const bool on = WIDE ? mask_bit(msk, u >> l2T) : ((msk.x >> (u >> l2T)) & 1ull);
-        x[s] = on ? __ldcg(src + u) : make_float2(0.0f, 0.0f);
+        x[s] = on ? __ldcg(src + VS * u) : make_float2(0.0f, 0.0f);
     }
 }
 
@@ -262,18 +270,30 @@ static __device__ __forceinline__ uint32_t class_sel(const ulonglong2 &msk, int 
     return sel;
 }
 
-// x[s] = src[t + P s] where bit s of sel is set, else 0.
-template <int P>
+// x[s] = src[VS (t + P s)] where bit s of sel is set, else 0.
+template <int P, int VS = 1>
 static __device__ __forceinline__ void load_sel(float2 (&x)[16], const float2 *src, uint32_t sel,
                                                 int t)
 {
 #pragma unroll
     for (int s = 0; s < 16; ++s)
-        x[s] = ((sel >> s) & 1u) ? __ldcg(src + t + P * s) : make_float2(0.0f, 0.0f);
+        x[s] = ((sel >> s) & 1u) ? __ldcg(src + VS * (t + P * s)) : make_float2(0.0f, 0.0f);
 }
 
 // Classes of threads whose selectors are tabled per CTA (P / T for T >= 16).
 #define RICK_FFT_SEL_CLASSES 32
+
+// Layout of the row transforms in the work buffer, per plane k (plane stride
+// m n; the image side m is even): transposed, column p's n values contiguous
+// ([p][v]); or, where a row-pass block holds only two rows (n = 8192), in
+// interleaved column pairs ([p/2][v][p%2]), so that the block's write-out fills
+// whole 32-byte sectors (two rows of two columns) and the column pass reads
+// every second point.
+template <int N>
+struct WorkPairs {
+    static constexpr bool ON = 1024 / (N / 16) < 4;
+    static constexpr int VS = ON ? 2 : 1;  // element stride of a column
+};
 
 // Exchange array of one transform: N points plus the padding.
 template <int N>
@@ -390,10 +410,23 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
         __syncthreads();
         // lanes take consecutive rows of consecutive columns, so that each warp
         // store fills whole 32-byte sectors (ROWS x 8 bytes of a column)
-        float2 *dst = a.work + (size_t)k * m * N + v0;
-        for (int i = threadIdx.x; i < ROWS * m; i += blockDim.x) {
-            const int r = i % ROWS, pc = i / ROWS;
-            dst[(size_t)pc * N + r] = sx[swz(r * N + pc + off) ^ ((r * ROT) & 15)];
+        if constexpr (WorkPairs<N>::ON) {
+            // column pairs: lanes take the two rows of two columns (a 32-byte
+            // sector) in order
+            float2 *dst = a.work + (size_t)k * m * N + 2 * v0;
+            for (int i = threadIdx.x; i < ROWS * m; i += blockDim.x) {
+                const int e = i % (2 * ROWS), cp = i / (2 * ROWS);
+                const int r = e >> 1, pc = 2 * cp + (e & 1);
+                dst[(size_t)cp * 2 * N + e] = sx[swz(r * N + pc + off) ^ ((r * ROT) & 15)];
+            }
+        } else {
+            // lanes take consecutive rows of consecutive columns, so that each
+            // warp store fills whole 32-byte sectors (ROWS x 8 bytes of a column)
+            float2 *dst = a.work + (size_t)k * m * N + v0;
+            for (int i = threadIdx.x; i < ROWS * m; i += blockDim.x) {
+                const int r = i % ROWS, pc = i / ROWS;
+                dst[(size_t)pc * N + r] = sx[swz(r * N + pc + off) ^ ((r * ROT) & 15)];
+            }
         }
     }
 }
@@ -457,7 +490,9 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
         g_acc[gi] = 0.0f;
     }
     const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
-    const float2 *col = a.work + (size_t)(live ? pc : 0) * N;
+    constexpr int VS = WorkPairs<N>::VS;
+    const int pl = live ? pc : 0;
+    const float2 *col = a.work + (VS == 2 ? (size_t)(pl >> 1) * 2 * N + (pl & 1) : (size_t)pl * N);
     // selectors of the block's planes per thread class (P a multiple of the
     // tile side), tabled at the start of each block of planes
     __shared__ uint16_t s_sel[RICK_PHASE_ANCHOR][RICK_FFT_SEL_CLASSES];
@@ -486,17 +521,17 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
             const float2 *src = col + (size_t)k * m * N;
             float2 x[16];
             if (tabled) {
-                load_sel<P>(x, src, live ? (uint32_t)s_sel[k - k0][t >> l2T] : 0u, t);
+                load_sel<P, VS>(x, src, live ? (uint32_t)s_sel[k - k0][t >> l2T] : 0u, t);
             } else if (nt <= RICK_FFT_MASK_TILES) {  // the plane's tile-rows as a bit mask
                 const ulonglong2 msk = live ? a.pmask[k] : make_ulonglong2(0ull, 0ull);
-                if (nt <= 64) load_masked<P, false>(x, src, msk, t, l2T);
-                else load_masked<P, true>(x, src, msk, t, l2T);
+                if (nt <= 64) load_masked<P, false, VS>(x, src, msk, t, l2T);
+                else load_masked<P, true, VS>(x, src, msk, t, l2T);
             } else {
                 const uint8_t *tr = a.trow + k * nt;
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     const int v = t + P * s;
-                    x[s] = (live && tr[v >> l2T]) ? __ldcg(src + v) : make_float2(0.0f, 0.0f);
+                    x[s] = (live && tr[v >> l2T]) ? __ldcg(src + VS * v) : make_float2(0.0f, 0.0f);
                 }
             }
             fft_inv<LOGN>(x, t, cb, sx, a.tw);

@@ -158,7 +158,8 @@ def test_fused_work_bytes(R):
     the transposed row transforms (8 n_w image_n n bytes); the same bytes the
     streamed call stages; none where the fused transform does not cover n."""
     al = lambda x: (x + 255) // 256 * 256
-    for n, n_w, tile, image_n in ((256, 8, 32, 0), (4096, 16, 64, 0), (8192, 3, 8, 4096)):
+    for n, n_w, tile, image_n in ((256, 8, 32, 0), (4096, 16, 64, 0), (8192, 3, 8, 4096),
+                                  (8192, 2, 64, 4094)):
         p = R.make_params(n, n_w, 0.03, 1, 7, tile=tile, image_n=image_n)
         nt, m = n // tile, image_n or n
         want = al(n_w * nt * nt) + al(n_w * nt) + al(n_w) + al(16 * n_w) + al(16 * n_w * nt) + \

@@ -74,7 +74,13 @@ def build_case(P, name, dev):
 # W=4); elsewhere the bound is twice the measured value, to catch a
 # regression.  Padding the grid (test_padding) brings the raw error of the kept
 # field under 1e-5 for every kernel.
-RAW_BOUND = {"gauss7_t32": 1e-1, "kb7_t16": 5e-5, "kb9_t32_ragged": 5e-4, "w1_t8": 1e-5,
+# The whole (raw) image divides by C(l)C(m), which near the corners amplifies
+# the FP32 rounding of the planes; that rounding depends on the summation order
+# of the records inside a bin, which is free outside the deterministic mode, so
+# the raw error varies from run to run (kb9_t32_ragged: 1.9e-4 .. 5.2e-4 over
+# five runs, tapered 2.9e-7 .. 3.6e-7).  Each bound is about three times the
+# largest value seen.
+RAW_BOUND = {"gauss7_t32": 1e-1, "kb7_t16": 5e-5, "kb9_t32_ragged": 1.5e-3, "w1_t8": 1e-5,
              "even_w4_t16": 1e-5, "nw1": 2e-5, "given_range": 5e-5, "compensated": 7e-5,
              "gauss_small_fov_drops": 1.2e-1}
 
