@@ -433,17 +433,21 @@ __global__ void __launch_bounds__(512, 1) fft_rows_kernel(FftArgs a)
 
 // Pass 2 and the w-correction: NT threads, COLS = NT / P image columns per
 // CTA, each column transformed for every plane.  Per pixel the CTA keeps in
-// shared memory n - 1 (double-single; plain FP32 for the FP32-phase ablation),
-// the output scale (taper, n factor, weight sum, checkerboard) and the running
-// plane sum; the Horner sum of the current block of planes and the step D stay
-// in registers.  The plane data is read around L1 (it streams), so the
-// twiddle tables stay there.
+// shared memory n - 1 (double-single with the low word in 16 bits; plain FP32
+// for the FP32-phase ablation) and the running plane sum; the output scale
+// (taper, n factor, weight sum, checkerboard) is formed at the end, and the
+// Horner sum of the current block of planes and the step D stay in registers.
+// The plane data is read around L1 (it streams), so the twiddle tables stay
+// there: the shared arrays are kept small enough (148 KB per SM at n = 8192,
+// and for the two CTAs per SM below) that the SM's unified L1 / shared memory
+// leaves 92 KB of L1, which holds the largest transform's 65 KB of tables.
 template <int LOGN>
 struct ColShape {
     static constexpr int N = 1 << LOGN, P = N / 16;
     static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
     static constexpr int XE = COLS * XLen<N>::L;  // points of the exchange arrays
-    static constexpr size_t SMEM = sizeof(float2) * XE + sizeof(float) * 4 * NE;
+    static constexpr size_t SMEM = sizeof(float2) * XE + sizeof(float) * 2 * NE +
+                                   sizeof(__half) * NE;
 };
 
 template <int LOGN>
@@ -455,7 +459,8 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
     constexpr int XE = S::XE;
     extern __shared__ float fsm[];
     float2 *sx = (float2 *)fsm;
-    float *g_hi = fsm + 2 * XE, *g_lo = g_hi + NE, *g_sc = g_lo + NE, *g_acc = g_sc + NE;
+    float *g_hi = fsm + 2 * XE, *g_acc = g_hi + NE;
+    __half *g_lo = (__half *)(g_acc + NE);
     const WcArgs &w = a.wc;
     const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * XLen<N>::L;
     const int m = w.m, off = w.off, nt = a.nt, l2T = a.log2T;
@@ -477,15 +482,15 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
         D[s] = make_float2(1.0f, 0.0f);
         if (live && q >= off && q < off + m) {
             const PixelGeom g = pixel_geom(w, p, q, inv_sumw);
-            g_hi[gi] = g.nm1.hi;
-            g_lo[gi] = fp32ph ? g.nm1_f : g.nm1.lo;
-            g_sc[gi] = g.scale;
+            g_hi[gi] = fp32ph ? g.nm1_f : g.nm1.hi;
+            g_lo[gi] = fp32ph ? __float2half_rn(0.0f) : nm1_lo_encode(g.nm1);
             if (!fp32ph) {
                 const float fd = ff_frac(ff_mul(ff{dwp.x, dwp.y}, g.nm1));
                 sincospif(2.0f * fd, &D[s].y, &D[s].x);
             }
         } else {
-            g_hi[gi] = g_lo[gi] = g_sc[gi] = 0.0f;
+            g_hi[gi] = 0.0f;
+            g_lo[gi] = __float2half_rn(0.0f);
         }
         g_acc[gi] = 0.0f;
     }
@@ -547,8 +552,9 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
         for (int s = 0; s < 16; ++s) {
             const int gi = s * NT + threadIdx.x;
             PixelGeom g;
-            g.nm1 = ff{g_hi[gi], g_lo[gi]};
-            g.nm1_f = g_lo[gi];
+            const float hi = g_hi[gi];
+            g.nm1 = ff{hi, nm1_lo_decode(hi, g_lo[gi])};
+            g.nm1_f = hi;
             float cs, sn;
             wphase(w, wk, g, &cs, &sn);
             g_acc[gi] = imag ? fmaf(h[s].x, sn, fmaf(h[s].y, cs, g_acc[gi]))
@@ -559,7 +565,10 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, ColShape<LOGN>::NT <= 256 
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const int q = t + P * s, gi = s * NT + threadIdx.x;
-        if (q >= off && q < off + m) w.image_out[(size_t)(q - off) * m + pc] = g_acc[gi] * g_sc[gi];
+        // n = 1 + (n - 1) to FP32 rounding
+        if (q >= off && q < off + m)
+            w.image_out[(size_t)(q - off) * m + pc] =
+                g_acc[gi] * pixel_scale(w, p, q, 1.0f + g_hi[gi], inv_sumw);
     }
 }
 
@@ -583,7 +592,8 @@ struct AdjColShape {
     static constexpr int N = 1 << LOGN, P = N / 16;
     static constexpr int NT = P < 256 ? 256 : P, COLS = NT / P, NE = NT * 16;
     static constexpr int XE = COLS * XLen<N>::L;  // points of the exchange arrays
-    static constexpr size_t SMEM = sizeof(float2) * XE + sizeof(float) * 3 * NE;
+    static constexpr size_t SMEM = sizeof(float2) * XE + sizeof(float) * 2 * NE +
+                                   sizeof(__half) * NE;
 };
 
 template <int LOGN>
@@ -594,7 +604,8 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
     constexpr int N = S::N, P = S::P, NT = S::NT, COLS = S::COLS, NE = S::NE, XE = S::XE;
     extern __shared__ float fsm[];
     float2 *sx = (float2 *)fsm;
-    float *g_hi = fsm + 2 * XE, *g_lo = g_hi + NE, *g_a = g_lo + NE;
+    float *g_hi = fsm + 2 * XE, *g_a = g_hi + NE;
+    __half *g_lo = (__half *)(g_a + NE);
     const WcArgs &w = a.wc;
     const int c = threadIdx.x / P, t = threadIdx.x % P, cb = c * XLen<N>::L;
     const int m = w.m, off = w.off, nt = a.nt, l2T = a.log2T;
@@ -616,15 +627,16 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
         ph[s] = make_float2(1.0f, 0.0f);
         if (live && q >= off && q < off + m) {
             const PixelGeom g = pixel_geom(w, p, q, inv_sumw);
-            g_hi[gi] = g.nm1.hi;
-            g_lo[gi] = fp32ph ? g.nm1_f : g.nm1.lo;
+            g_hi[gi] = fp32ph ? g.nm1_f : g.nm1.hi;
+            g_lo[gi] = fp32ph ? __float2half_rn(0.0f) : nm1_lo_encode(g.nm1);
             g_a[gi] = w.image_in[(size_t)(q - off) * m + pc] * g.scale;
             if (!fp32ph) {
                 const float fd = ff_frac(ff_mul(ff{dwp.x, dwp.y}, g.nm1));
                 sincospif(2.0f * fd, &D[s].y, &D[s].x);
             }
         } else {
-            g_hi[gi] = g_lo[gi] = g_a[gi] = 0.0f;
+            g_hi[gi] = g_a[gi] = 0.0f;
+            g_lo[gi] = __float2half_rn(0.0f);
         }
     }
     const int bs = fp32ph ? 1 : RICK_PHASE_ANCHOR;
@@ -636,8 +648,9 @@ __global__ void __launch_bounds__(AdjColShape<LOGN>::NT, AdjColShape<LOGN>::NT <
             for (int s = 0; s < 16; ++s) {
                 const int gi = s * NT + threadIdx.x;
                 PixelGeom g;
-                g.nm1 = ff{g_hi[gi], g_lo[gi]};
-                g.nm1_f = g_lo[gi];
+                const float hi = g_hi[gi];
+                g.nm1 = ff{hi, nm1_lo_decode(hi, g_lo[gi])};
+                g.nm1_f = hi;
                 wphase(w, wk, g, &ph[s].x, &ph[s].y);
             }
         } else {
@@ -806,17 +819,31 @@ bool rick_fft_tables(rick_plan *pl)
     return cudaGetLastError() == cudaSuccess;
 }
 
+// Shared memory of a transform kernel and the unified L1 / shared-memory split
+// it prefers: 70 % of the SM's 228 KB for shared memory (the 164 KB
+// configuration), which holds the resident CTAs of the column passes and of the
+// imaging row pass (at most 154 KB per SM) and leaves 92 KB of L1 for the
+// twiddle tables.
+#define RICK_FFT_SMEM_CARVEOUT 70
+
+template <typename K>
+static cudaError_t fft_smem_attrs(K kernel, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                RICK_FFT_SMEM_CARVEOUT);
+}
+
 template <int LOGN>
 static cudaError_t launch_fft_wc(const FftArgs &a, int num_sms, cudaStream_t st)
 {
     using S = ColShape<LOGN>;
     const size_t rows_smem = sizeof(float2) * (1024 / S::P) * XLen<(1 << LOGN)>::L;
-    cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<LOGN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rows_smem);
+    cudaError_t e = fft_smem_attrs(fft_rows_kernel<LOGN>, rows_smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fft_cols_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)S::SMEM);
+    e = fft_smem_attrs(fft_cols_kernel<LOGN>, S::SMEM);
     if (e != cudaSuccess) return e;
     const int items = a.n_w * (a.n / (1024 / S::P));
     fft_rows_kernel<LOGN><<<(unsigned)min(items, num_sms), 512, rows_smem, st>>>(a);
@@ -906,9 +933,7 @@ static cudaError_t launch_wspread_fft(const FftArgs &a, int num_sms, cudaStream_
     using S = AdjColShape<LOGN>;
     constexpr int N = 1 << LOGN, P = N / 16, ROWS = 1024 / P, RPR = 512 / P;
     const size_t rows_smem = sizeof(float2) * (ROWS * N + RPR * XLen<N>::L);
-    cudaError_t e = cudaFuncSetAttribute(fft_cols_adj_kernel<LOGN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM);
+    cudaError_t e = fft_smem_attrs(fft_cols_adj_kernel<LOGN>, S::SMEM);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fft_rows_adj_kernel<LOGN>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);

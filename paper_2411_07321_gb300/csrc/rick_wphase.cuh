@@ -9,6 +9,8 @@
 // goes to sincospif.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "rick_common.cuh"
 
 struct WcArgs {
@@ -32,6 +34,34 @@ struct PixelGeom {
     float scale; // s(p, q) including the checkerboard sign
 };
 
+// The output scale s(p, q) of a pixel: the taper correction 1 / (C(l) C(m)),
+// the n factor (nn = n, RICK_N_CORRECT / RICK_N_DIVIDE), the weight
+// normalisation and the checkerboard sign of the centred transform.
+__device__ __forceinline__ float pixel_scale(const WcArgs &a, int p, int q, float nn,
+                                             float inv_sumw)
+{
+    float s = a.taper_inv[p] * a.taper_inv[q];
+    if (a.flags & RICK_N_CORRECT) s *= nn;
+    if (a.flags & RICK_N_DIVIDE) s /= nn;
+    if (a.flags & RICK_NORMALIZE) s *= inv_sumw;
+    return ((p + q) & 1) ? -s : s;
+}
+
+// The low word of a double-single n - 1 kept in 16 bits, for kernels that hold
+// n - 1 of many pixels in shared memory: lo / hi scaled by 2^24 (|lo| <=
+// ulp(hi) / 2 <= 2^-24 |hi|, so the ratio lies in [-1, 1]) as a half.  The
+// decoded low word carries a relative error of 2^-11, about 2^-35 of n - 1:
+// below 1e-9 cycles of w-phase for |w (n - 1)| up to 100 cycles.
+__device__ __forceinline__ __half nm1_lo_encode(ff v)
+{
+    return __float2half_rn(v.hi != 0.0f ? v.lo / v.hi * 16777216.0f : 0.0f);
+}
+
+__device__ __forceinline__ float nm1_lo_decode(float hi, __half e)
+{
+    return __half2float(e) * hi * 5.9604644775390625e-8f;  // 2^-24
+}
+
 __device__ __forceinline__ PixelGeom pixel_geom(const WcArgs &a, int p, int q, float inv_sumw)
 {
     PixelGeom g;
@@ -40,12 +70,7 @@ __device__ __forceinline__ PixelGeom pixel_geom(const WcArgs &a, int p, int q, f
     g.nm1 = ff_nm1(ff_mul_int(p - h, a.dl), ff_mul_int(q - h, a.dl), &r2);
     float l = (p - h) * a.dl_f, m = (q - h) * a.dl_f, r2f = l * l + m * m;
     g.nm1_f = -r2f / (1.0f + sqrtf(1.0f - r2f));
-    float s = a.taper_inv[p] * a.taper_inv[q];
-    float nn = sqrtf(1.0f - r2.hi);
-    if (a.flags & RICK_N_CORRECT) s *= nn;
-    if (a.flags & RICK_N_DIVIDE) s /= nn;
-    if (a.flags & RICK_NORMALIZE) s *= inv_sumw;
-    g.scale = ((p + q) & 1) ? -s : s;
+    g.scale = pixel_scale(a, p, q, sqrtf(1.0f - r2.hi), inv_sumw);
     return g;
 }
 
