@@ -738,6 +738,13 @@ def serve_measure(n_jobs: int, slots: int) -> dict:
                 res08 = res
         peak_used = srv.peak_used
         counters = dict(srv.counters)
+    # the same saturated run (a fresh server, as above) with every request on
+    # its own launches: no merged gridding of small requests
+    with S.Server(dev, max_running=slots, merge_small=False) as srv:
+        t0 = time.perf_counter()
+        for f in [srv.submit(job(sp)) for sp in specs]:
+            f.result()
+        served_unmerged = n_jobs / (time.perf_counter() - t0)
     err = 0.0  # inner region |l|, |m| < fov/4: clear of the taper's corner amplification
     for jid, img in plain_imgs.items():
         n = img.shape[0]
@@ -755,7 +762,8 @@ def serve_measure(n_jobs: int, slots: int) -> dict:
                    "slots": slots},
         "served": served["0.8"], "plain": plain["0.8"],
         "overload_1_5": {"served": served["1.5"], "plain": plain["1.5"]},
-        "saturated_jobs_per_s": {"served": served_saturated, "plain": plain_saturated},
+        "saturated_jobs_per_s": {"served": served_saturated, "plain": plain_saturated,
+                                 "served_without_merged_gridding": served_unmerged},
         "plain_mean_service_ms": 1e3 * mean_service, "served_peak_hbm_bytes": peak_used,
         "max_rel_diff_served_vs_plain_inner": err, "server_counters": counters,
     }

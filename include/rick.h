@@ -363,6 +363,24 @@ rick_status rick_wcorrect_stack(rick_plan *plan, const void *planes_dev, const v
  * coverage is most of the 8 n_w n^2 bytes rick_grid writes. */
 rick_status rick_grid_sparse(rick_plan *plan, void *ws_dev, void *planes_dev, void *stream);
 
+/* rick_grid_sparse of n_jobs imaging jobs in one launch (§2 step 2, Eq. 3, for
+ * each job): the work items (uv-tile, chunk of records) of every job's last
+ * rick_bin form one list, which one persistent grid kernel works through.  For
+ * serving many small jobs, whose own launches would each leave most of the GPU
+ * idle.  plans[j], ws_dev[j], planes_dev[j]: job j's plan, the workspace of its
+ * binning and its planes (each job its own workspace and planes).
+ * 1 <= n_jobs <= RICK_GRID_BATCH_MAX (else RICK_ERANGE).  Every plan must have
+ * the same support and tile and be on one device, with RICK_PREC_FP32 and
+ * without RICK_OPT_DETERMINISTIC (else RICK_EINVAL).  Each job's planes then
+ * hold what rick_grid_sparse would have written (the same sums, possibly added
+ * in another order).  Enqueued on stream; the caller orders it after every
+ * job's binning (and before what reads the planes).  A CUDA launch error marks
+ * every plan of the batch with RICK_ECUDA.  Uses the first job's workspace
+ * header as the batch's work counter. */
+#define RICK_GRID_BATCH_MAX 16
+rick_status rick_grid_sparse_batch(rick_plan *const *plans, void *const *ws_dev,
+                                   void *const *planes_dev, int32_t n_jobs, void *stream);
+
 /* Bytes of the fused transform's work buffer (rick_fft_wcorrect,
  * rick_wspread_fft) for plans of these parameters, without a plan: 0 where n is
  * outside 256 ... 8192.  Host-only; enqueues nothing.  RICK_EINVAL for invalid

@@ -13,6 +13,7 @@ built -- there is no fallback path.
 import importlib
 
 _LAZY = {"Imager": "imager", "IMAGE_FLAGS": "imager", "PREDICT_FLAGS": "imager",
+         "grid_sparse_batch": "imager",
          "GridFn": "autograd", "DegridFn": "autograd", "Server": "serve"}
 _SUBMODULES = ("rick", "imager", "autograd", "serve", "build")
 

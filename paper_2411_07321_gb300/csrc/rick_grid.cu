@@ -540,6 +540,17 @@ __global__ void __launch_bounds__(32 * RICK_GRID_WARPS, (W <= 8 && MODE == GM_PL
     }
 }
 
+// Several imaging jobs gridded by one launch (rick_grid_sparse_batch): the jobs'
+// work items form one list, job after job, taken from one counter (the first
+// job's).  Every job has the same support W and tile T, and plain FP32 sums.
+// RICK_GRID_BATCH_MAX (rick.h) jobs at most: the arguments travel as one
+// kernel parameter.
+
+struct GridBatchArgs {
+    int n_jobs;
+    GridArgs job[RICK_GRID_BATCH_MAX];
+};
+
 // Zero the tiles whose chunks add into them with atomics (more than one work
 // item) before the grid kernel runs, and reset the grid kernel's counters.
 // Grid-stride, one warp per tile, 16-byte stores.  Tiles without records are
@@ -580,6 +591,79 @@ __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, u
             plane[((size_t)((ty << log2T) + row) * n + (tx << log2T)) / 2 + col2] =
                 make_float4(0.f, 0.f, 0.f, 0.f);
         }
+    }
+}
+
+// The batch's multi-item tiles zeroed (one row of CTAs per job, blockIdx.y) and
+// its item counter reset.
+__global__ void __launch_bounds__(256) zero_tiles_batch_kernel(const __grid_constant__ GridBatchArgs ba)
+{
+    const GridArgs &a = ba.job[blockIdx.y];
+    const TileArgs &ta = a.t;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ta.hdr->grid_next = 0;
+    const int lane = threadIdx.x & 31, log2T = a.log2T, T = 1 << log2T, half = T >> 1;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nt = ta.nt, n = ta.n;
+    for (uint32_t t = warp; t < ta.ntiles; t += nwarps) {
+        if (ta.base[t + 1] - ta.base[t] <= 1) continue;
+        const uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
+        float4 *plane = (float4 *)(a.planes + (size_t)k * n * n);
+        for (int i = lane; i < T * half; i += 32) {
+            const int row = i / half, col2 = i - row * half;
+            plane[((size_t)((ty << log2T) + row) * n + (tx << log2T)) / 2 + col2] =
+                make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+// Persistent over the batch's work items: item b of the list belongs to the
+// job j with cum[j] <= b < cum[j + 1] (cum: running totals of the jobs' items),
+// and is that job's item b - cum[j].  A CTA reloads its lanes' kernel
+// coefficients when the job changes.
+template <int W>
+__global__ void __launch_bounds__(32 * RICK_GRID_WARPS, W <= 8 ? 4 : 3)
+    grid_batch_kernel(const __grid_constant__ GridBatchArgs ba)
+{
+    extern __shared__ float sm[];
+    __shared__ uint32_t s_cum[RICK_GRID_BATCH_MAX + 1];
+    __shared__ uint32_t s_b, s_tile, s_job;
+    if (threadIdx.x == 0) {
+        uint32_t c = 0;
+        s_cum[0] = 0;
+        for (int j = 0; j < ba.n_jobs; ++j) {
+            c += ba.job[j].t.base[ba.job[j].t.ntiles];
+            s_cum[j + 1] = c;
+        }
+    }
+    __syncthreads();
+    const uint32_t total = s_cum[ba.n_jobs];
+    const int seg = min((int)((threadIdx.x & 31) % StreamShape<W>::G), W - 1);
+    float2 coef2[RICK_POLY_N];
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t b = atomicAdd(&ba.job[0].t.hdr->grid_next, 1u);
+            int j = 0;
+            while (j + 1 < ba.n_jobs && s_cum[j + 1] <= b) ++j;
+            s_b = b;
+            s_job = (uint32_t)j;
+            s_tile = b < total ? find_tile(ba.job[j].t.base, ba.job[j].t.ntiles, b - s_cum[j]) : 0u;
+        }
+        __syncthreads();
+        const uint32_t b = s_b, t = s_tile;
+        const int j = (int)s_job;
+        __syncthreads();  // everyone has the item before thread 0 takes the next
+        if (b >= total) break;
+        const GridArgs &a = ba.job[j];
+        if (j != cur) {
+#pragma unroll
+            for (int k = 0; k < RICK_POLY_N; ++k)
+                coef2[k] = make_float2(a.t.kp.c[seg][k], a.t.kp.c[seg][k]);
+            cur = j;
+        }
+        grid_item<W, GM_PLAIN>(a, b - s_cum[j], t, sm, coef2);
+        __syncthreads();  // the accumulator is reused by the next item
     }
 }
 
@@ -869,6 +953,71 @@ extern "C" rick_status rick_grid_accumulate(rick_plan *plan, void *ws_dev, void 
                                             void *stream)
 {
     return rick_grid_impl(plan, ws_dev, planes_dev, RICK_GRID_ACCUMULATE, stream);
+}
+
+template <int W>
+static cudaError_t launch_grid_batch(const GridBatchArgs &ba, int num_sms, cudaStream_t st)
+{
+    const size_t smem = 2 * (size_t)ba.job[0].t.T * (ba.job[0].t.T + 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(grid_batch_kernel<W>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    grid_batch_kernel<W><<<persistent_blocks(grid_batch_kernel<W>, smem, num_sms),
+                           32 * RICK_GRID_WARPS, smem, st>>>(ba);
+    return cudaGetLastError();
+}
+
+extern "C" rick_status rick_grid_sparse_batch(rick_plan *const *plans, void *const *ws_dev,
+                                              void *const *planes_dev, int32_t n_jobs,
+                                              void *stream)
+{
+    if (!plans || !ws_dev || !planes_dev) return RICK_EINVAL;
+    if (n_jobs < 1 || n_jobs > RICK_GRID_BATCH_MAX) return RICK_ERANGE;
+    for (int j = 0; j < n_jobs; ++j) {
+        const rick_plan *pl = plans[j];
+        if (!pl || !ws_dev[j] || !planes_dev[j]) return RICK_EINVAL;
+        if (pl->sticky != RICK_OK) return pl->sticky;
+        if (((uintptr_t)ws_dev[j] & 255) || ((uintptr_t)planes_dev[j] & 15)) return RICK_EINVAL;
+        if (pl->p.support != plans[0]->p.support || pl->p.tile != plans[0]->p.tile ||
+            pl->device != plans[0]->device || pl->p.precision != RICK_PREC_FP32 ||
+            (pl->p.options & RICK_OPT_DETERMINISTIC))
+            return RICK_EINVAL;
+        for (int i = 0; i < j; ++i)  // each job needs its own workspace and planes
+            if (ws_dev[i] == ws_dev[j] || planes_dev[i] == planes_dev[j]) return RICK_EINVAL;
+    }
+    rick_plan *p0 = plans[0];
+    GridBatchArgs ba;
+    memset(&ba, 0, sizeof(ba));
+    ba.n_jobs = n_jobs;
+    int tiles_max = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const rick_params &p = plans[j]->p;
+        WsPtrs w = rick_ws_ptrs(ws_dev[j], rick_ws_layout(&p, plans[j]->max_vis));
+        GridArgs &a = ba.job[j];
+        a.t = make_tile_args(plans[j], w, w.gbase);
+        a.planes = (float2 *)planes_dev[j];
+        a.log2T = ilog2(p.tile);
+        a.accumulate = 0;
+        a.nzero = 0;
+        a.mcslot = NULL;
+        a.mcacc = NULL;
+        tiles_max = max(tiles_max, (int)a.t.ntiles);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned bx = (unsigned)max(1, min(p0->num_sms * 8 / n_jobs, (tiles_max + 7) / 8));
+    zero_tiles_batch_kernel<<<dim3(bx, (unsigned)n_jobs), 256, 0, st>>>(ba);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) {
+#define CALL_GRID_BATCH(WW) err = launch_grid_batch<WW>(ba, p0->num_sms, st)
+        RICK_W_SWITCH(p0->p.support, CALL_GRID_BATCH);
+#undef CALL_GRID_BATCH
+    }
+    p0->launches += 2;
+    if (err != cudaSuccess) {
+        for (int j = 0; j < n_jobs; ++j) plans[j]->sticky = RICK_ECUDA;
+        return RICK_ECUDA;
+    }
+    return RICK_OK;
 }
 
 extern "C" rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,

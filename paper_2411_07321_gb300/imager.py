@@ -268,6 +268,15 @@ class Imager:
         """The image from host buffers (pinned for asynchronous copies): the
         inputs are copied into resident device buffers, imaged, and the image is
         copied back into ``out_host``, all on the current stream."""
+        self.bin_from_host(uvw_host, vis_host, weight_host)
+        self.image_from_binned(flags, out=self._image_buffer())
+        out_host.copy_(self._out_img, non_blocking=True)
+        return out_host
+
+    def bin_from_host(self, uvw_host: torch.Tensor, vis_host: torch.Tensor,
+                      weight_host: torch.Tensor | None):
+        """The first half of image_from_host: the host inputs copied into the
+        resident device buffers and binned, on the current stream."""
         n = uvw_host.shape[0]
         if n > self.max_vis:
             raise ValueError(f"{n} visibilities exceed this imager's capacity {self.max_vis}")
@@ -275,8 +284,6 @@ class Imager:
             self._in_uvw = torch.empty((self.max_vis, 3), dtype=torch.float64, device=self.device)
             self._in_vis = torch.empty(self.max_vis, dtype=torch.complex64, device=self.device)
             self._in_wt = torch.empty(self.max_vis, dtype=torch.float32, device=self.device)
-        if getattr(self, "_out_img", None) is None or self._out_img.shape[0] != self.m:
-            self._out_img = torch.empty((self.m, self.m), dtype=torch.float32, device=self.device)
         uvw, vis = self._in_uvw[:n], self._in_vis[:n]
         uvw.copy_(uvw_host, non_blocking=True)
         vis.copy_(vis_host, non_blocking=True)
@@ -284,9 +291,20 @@ class Imager:
         if weight_host is not None:
             wt = self._in_wt[:n]
             wt.copy_(weight_host, non_blocking=True)
-        self.image(uvw, vis, wt, flags, out=self._out_img)
+        self.bin(uvw, vis, wt)
+
+    def transform_to_host(self, out_host: torch.Tensor, flags: int = IMAGE_FLAGS) -> torch.Tensor:
+        """The second half of image_from_host after gridding: the fused
+        transform of the gridded planes (rick_fft_wcorrect, sparse) and the
+        image copied into ``out_host``, on the current stream."""
+        self.fft_wcorrect(flags, self._image_buffer(), sparse=True)
         out_host.copy_(self._out_img, non_blocking=True)
         return out_host
+
+    def _image_buffer(self) -> torch.Tensor:
+        if getattr(self, "_out_img", None) is None or self._out_img.shape[0] != self.m:
+            self._out_img = torch.empty((self.m, self.m), dtype=torch.float32, device=self.device)
+        return self._out_img
 
     def image_streamed(self, uvw_host: torch.Tensor, vis_host: torch.Tensor,
                        weight_host: torch.Tensor | None, out_host: torch.Tensor | None = None,
@@ -450,3 +468,16 @@ class Imager:
             self.close()
         except Exception:
             pass
+
+
+def grid_sparse_batch(imagers) -> None:
+    """rick_grid_sparse of several imagers' last binnings in one launch
+    (rick_grid_sparse_batch), on the current stream of the first imager's
+    device.  The imagers share support and tile, use FP32 sums and are not
+    deterministic; at most RICK_GRID_BATCH_MAX of them."""
+    imagers = list(imagers)
+    if not imagers:
+        return
+    st = torch.cuda.current_stream(imagers[0].device).cuda_stream
+    R.rick_grid_sparse_batch([im.plan for im in imagers], [im.ws.data_ptr() for im in imagers],
+                             [im.planes.data_ptr() for im in imagers], st)

@@ -25,6 +25,7 @@ RICK_OPT_HERMITIAN_MIRROR, RICK_OPT_DETERMINISTIC = 1, 2
 RICK_WAIT_POLLS_DEFAULT = 1 << 24
 RICK_WEIGHT_UNIFORM, RICK_WEIGHT_BRIGGS = 1, 2
 RICK_MAX_CORR = 4
+RICK_GRID_BATCH_MAX = 16
 (RICK_PROBE_SMEM_RMW, RICK_PROBE_SMEM_ATOMIC_F32, RICK_PROBE_SMEM_ATOMIC_U32,
  RICK_PROBE_SMEM_ATOMIC_U64, RICK_PROBE_FFMA, RICK_PROBE_FFMA2, RICK_PROBE_SHFL,
  RICK_PROBE_F2I) = range(8)
@@ -67,7 +68,8 @@ EXPORTS = ["rick_status_string", "rick_plan_create", "rick_plan_destroy", "rick_
            "rick_image_host_channels", "rick_density_scratch_bytes", "rick_density_weights",
            "rick_bin_rows", "rick_image_host_rows", "rick_grid_sparse", "rick_fft_wcorrect_bytes",
            "rick_fft_wcorrect", "rick_wspread_fft", "rick_fused_work_bytes",
-           "rick_probe_throughput", "rick_plan_set_wait_limit", "rick_plan_set_planes"]
+           "rick_probe_throughput", "rick_plan_set_wait_limit", "rick_plan_set_planes",
+           "rick_grid_sparse_batch"]
 
 
 def _load():
@@ -99,6 +101,8 @@ def _load():
         "rick_grid": [vp, vp, vp, vp],
         "rick_grid_accumulate": [vp, vp, vp, vp],
         "rick_grid_sparse": [vp, vp, vp, vp],
+        "rick_grid_sparse_batch": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   i32, vp],
         "rick_fft_wcorrect_bytes": [vp, ctypes.POINTER(sz)],
         "rick_fused_work_bytes": [P, ctypes.POINTER(sz)],
         "rick_fft_wcorrect": [vp, vp, vp, i32, vp, sz, vp, u32, vp],
@@ -301,6 +305,17 @@ def rick_grid_accumulate(plan, ws, planes, stream) -> None:
 
 def rick_grid_sparse(plan, ws, planes, stream) -> None:
     _check("rick_grid_sparse", _L.rick_grid_sparse(plan, ws, planes, stream or None))
+
+
+def rick_grid_sparse_batch(plans, ws, planes, stream) -> None:
+    """One gridding launch for several jobs: plans, ws and planes are equal-length
+    sequences of plan handles and device pointers (at most RICK_GRID_BATCH_MAX)."""
+    n = len(plans)
+    if len(ws) != n or len(planes) != n:
+        raise ValueError("plans, ws and planes must have the same length")
+    arr = ctypes.c_void_p * max(n, 1)
+    _check("rick_grid_sparse_batch",
+           _L.rick_grid_sparse_batch(arr(*plans), arr(*ws), arr(*planes), n, stream or None))
 
 
 def rick_fft_wcorrect_bytes(plan) -> int | None:

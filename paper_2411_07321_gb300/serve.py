@@ -11,7 +11,12 @@ A scheduler thread admits queued requests as soon as a compatible slot is idle,
 or HBM budget can be freed for a new one.  It enqueues each request's whole
 path (host->device copy, bin, grid, FFT, w-correct, device->host copy) on the
 slot's stream, and completes the request when the stream's event fires.  Work of
-requests admitted while others run overlaps on the device.
+requests admitted while others run overlaps on the device.  Small requests
+admitted together (at most BATCH_MAX_VIS visibilities each, same support and
+tile, FP32, fused transform) are gridded by one launch over all their
+(request, plane, tile) work items (rick_grid_sparse_batch) on the server's
+batch stream, between their binnings and their transforms on their slots'
+streams.
 
 Admission is by HBM footprint: a request needs a slot with the same grid size,
 tile and precision, and visibility and plane capacities at least its own; the
@@ -38,10 +43,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .imager import IMAGE_FLAGS, Imager
+from . import rick as R
+from .imager import IMAGE_FLAGS, Imager, grid_sparse_batch
 
 MIN_CAPACITY = 1 << 20  # smaller requests share slots of this capacity
 MIN_PLANES = 16         # plane capacity of a slot (more if a request needs more)
+BATCH_MAX_VIS = 1 << 21  # requests up to this size are gridded in merged launches
 
 
 def capacity_class(n_vis: int) -> int:
@@ -227,7 +234,9 @@ class Server:
     """Continuous-batching server on one device (see the module docstring)."""
 
     def __init__(self, device="cuda:0", budget_bytes: int | None = None, max_running: int = 8,
-                 max_slots: int | None = None):
+                 max_slots: int | None = None, merge_small: bool = True):
+        """merge_small: grid small requests admitted together in one merged
+        launch (else every request runs its own launches)."""
         import torch
         from concurrent.futures import ThreadPoolExecutor
         self.device = torch.device(device)
@@ -238,8 +247,10 @@ class Server:
         # cap the least recently used idle slot gives its memory back first
         self.admission = Admission(budget_bytes, max_slots or 2 * max_running)
         self.max_running = max_running
+        self.merge_small = bool(merge_small)
         self.counters = dict(new_slots=0, reused=0, evicted=0, host_create_s=0.0,
-                             host_launch_s=0.0)
+                             host_launch_s=0.0, batches=0, batched=0)
+        self._batch_stream = torch.cuda.Stream(device=self.device)
         # finished images leave the pinned buffers on worker threads, so the
         # scheduler never waits on a host copy
         self._copier = ThreadPoolExecutor(max_workers=4, thread_name_prefix="rick-copy")
@@ -286,6 +297,7 @@ class Server:
         does not hold back later jobs that fit now."""
         progressed = False
         waiting = collections.deque()
+        started = []  # (sid, slot, job, future) admitted in this pass, not yet enqueued
         while self._pending and len(self._running()) < self.max_running:
             job, fut = self._pending.popleft()
             try:
@@ -314,15 +326,18 @@ class Server:
                     self.peak_used = max(self.peak_used, self.admission.used())
                     self.counters["new_slots"] += 1
                     self.counters["host_create_s"] += time.perf_counter() - now
-                t0 = time.perf_counter()
-                self._launch(sid, slot, job, fut)
-                self.counters["host_launch_s"] += time.perf_counter() - t0
+                self._prepare(slot, job, fut)
+                started.append((sid, slot, job, fut))
             except Exception as e:
                 fut.set_exception(e)
                 if decision[0] == "reuse":
                     self.admission.release(decision[1], time.perf_counter())
             progressed = True
         self._pending.extendleft(reversed(waiting))
+        if started:
+            t0 = time.perf_counter()
+            self._launch_group(started)
+            self.counters["host_launch_s"] += time.perf_counter() - t0
         return progressed
 
     def _evict(self, sid):
@@ -334,8 +349,9 @@ class Server:
         self.admission.remove(sid)
         self.counters["evicted"] += 1
 
-    def _launch(self, sid, slot, job, fut):
-        import torch
+    def _prepare(self, slot, job, fut):
+        """Claim the slot for the job and re-target its plan (host side; the slot
+        is idle, so none of its work is in flight)."""
         slot.job, slot.future, slot.t_start = job, fut, time.perf_counter()
         if slot.out is None or slot.out.shape[0] != job.side:
             if slot.out is not None:
@@ -348,11 +364,65 @@ class Server:
             slot.imager.set_image_n(job.image_n)
         if slot.imager.n_w != job.n_w:
             slot.imager.set_planes(job.n_w)
+
+    def _launch(self, slot, job):
+        import torch
         with torch.cuda.stream(slot.stream):
             slot.imager.set_geometry(job.fov, job.w_range)
             slot.imager.image_from_host(job.uvw, job.vis, job.weight, slot.out, job.flags)
             slot.event = torch.cuda.Event()
             slot.event.record(slot.stream)
+
+    def _batchable(self, slot, job) -> bool:
+        return (self.merge_small and job.n_vis <= BATCH_MAX_VIS and job.precision == "fp32"
+                and slot.imager.fused
+                and not slot.imager.params.options & R.RICK_OPT_DETERMINISTIC)
+
+    def _launch_group(self, started):
+        """Enqueue the jobs admitted in one pass: small compatible ones with one
+        merged gridding launch per group, the others each on its own."""
+        groups = collections.defaultdict(list)
+        for sid, slot, job, fut in started:
+            key = (job.support, job.tile) if self._batchable(slot, job) else None
+            groups[key].append(slot)
+        for key, slots in groups.items():
+            if key is None or len(slots) == 1:
+                for slot in slots:
+                    self._launch(slot, slot.job)
+                continue
+            for i in range(0, len(slots), R.RICK_GRID_BATCH_MAX):
+                part = slots[i:i + R.RICK_GRID_BATCH_MAX]
+                if len(part) == 1:
+                    self._launch(part[0], part[0].job)
+                else:
+                    self._launch_batch(part)
+
+    def _launch_batch(self, slots):
+        import torch
+        binned = []
+        for slot in slots:
+            job = slot.job
+            with torch.cuda.stream(slot.stream):
+                slot.imager.set_geometry(job.fov, job.w_range)
+                slot.imager.bin_from_host(job.uvw, job.vis, job.weight)
+                ev = torch.cuda.Event()
+                ev.record(slot.stream)
+                binned.append(ev)
+        bs = self._batch_stream
+        with torch.cuda.stream(bs):
+            for ev in binned:
+                bs.wait_event(ev)
+            grid_sparse_batch([slot.imager for slot in slots])
+            gridded = torch.cuda.Event()
+            gridded.record(bs)
+        for slot in slots:
+            with torch.cuda.stream(slot.stream):
+                slot.stream.wait_event(gridded)
+                slot.imager.transform_to_host(slot.out, slot.job.flags)
+                slot.event = torch.cuda.Event()
+                slot.event.record(slot.stream)
+        self.counters["batches"] += 1
+        self.counters["batched"] += len(slots)
 
     def _complete(self) -> bool:
         progressed = False

@@ -126,6 +126,23 @@ def test_null_plan_rejected(R):
     assert R._L.rick_bin_layout(None, ctypes.byref(v)) == R.RICK_EINVAL
 
 
+def test_grid_batch_rejected_on_host(R):
+    """rick_grid_sparse_batch validates its job list before any launch."""
+    import ctypes
+    arr = ctypes.c_void_p * 2
+    none = arr(None, None)
+    assert R._L.rick_grid_sparse_batch(None, None, None, 1, None) == R.RICK_EINVAL
+    assert R._L.rick_grid_sparse_batch(none, none, none, 0, None) == R.RICK_ERANGE
+    assert R._L.rick_grid_sparse_batch(none, none, none, R.RICK_GRID_BATCH_MAX + 1,
+                                       None) == R.RICK_ERANGE
+    assert R._L.rick_grid_sparse_batch(none, none, none, 2, None) == R.RICK_EINVAL
+    with pytest.raises(ValueError):
+        R.rick_grid_sparse_batch([None], [None, None], [None], None)
+    src = open(os.path.join(ROOT, "include", "rick.h")).read()
+    assert re.search(r"#define RICK_GRID_BATCH_MAX (\d+)", src).group(1) == str(
+        R.RICK_GRID_BATCH_MAX)
+
+
 def test_stream_bytes(R):
     """Staging area of the streamed path: two chunk buffers of vis and weight,
     the fused transform's work buffer (tile, tile-row and plane flags, 128-bit tile-row and tile masks, and the

@@ -118,3 +118,21 @@ def test_crops_share_a_slot(S, data):
         o = (n - j.side) // 2
         cc = np.outer(c[o:o + j.side], c[o:o + j.side])
         assert np.abs((r.image - ref) * cc).max() <= 1e-5 * np.abs(ref * cc).max()
+
+
+def test_small_requests_share_a_gridding_launch(S, data):
+    """Small requests admitted together are gridded by one merged launch
+    (rick_grid_sparse_batch on the server's batch stream) and still give their
+    plain per-request images."""
+    specs = [(20_000, 256, 4, "kb"), (150_000, 512, 16, "gauss"), (50_000, 512, 6, "kb"),
+             (333_333, 1024, 8, "kb"), (600_000, 1024, 5, "gauss"), (80_000, 256, 9, "gauss")]
+    jobs = make_jobs(S, data, specs)
+    for j in jobs:
+        j.tile = 32  # one group: same support and tile
+    with S.Server("cuda:0", max_running=8) as srv:
+        futs = [srv.submit(j) for j in jobs]
+        res = [f.result(timeout=120) for f in futs]
+        assert srv.counters["batches"] >= 1 and srv.counters["batched"] >= 2
+    for j, r in zip(jobs, res):
+        assert r.job_id == j.job_id
+        assert tapered_error(r.image, S.run_plain(j), j.n, j.kernel) <= 1e-5, j.job_id
