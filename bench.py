@@ -865,7 +865,7 @@ def main():
                     help="skip the extra keys (LOFAR-like step, serving trace, gradient)")
     ap.add_argument("--extra-serve-jobs", type=int, default=64,
                     help="requests of the serving trace in the default line")
-    ap.add_argument("--chunk", type=int, default=1 << 24,
+    ap.add_argument("--chunk", type=int, default=1 << 25,
                     help="visibilities per chunk of the streamed end-to-end call")
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload instead (its own JSON line)")

@@ -455,12 +455,16 @@ rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
  * chunks (§4: visibilities are read in sequential chunks; §3.2 counts the
  * offload to the GPU in the gridding time).  The set is cut into chunks of at
  * most the plan's max_vis visibilities.  A copy stream owned by the plan
- * moves chunk c + 1 into one of two staging buffers while `stream` bins chunk
- * c and grids it into planes_dev (rick_grid for the first chunk,
- * rick_grid_accumulate after); rick_fft_wplanes and rick_wcorrect_stack then
- * run once.  The image is that of rick_bin + rick_grid + rick_fft_wplanes +
- * rick_wcorrect_stack over the whole set, up to FP32 summation order; the weight
- * sum and drop counts are totals over the chunks, added in chunk order.
+ * moves the next chunks into a ring of RICK_STREAM_BUFS staging buffers while
+ * `stream` bins chunk c and grids it into planes_dev.  Where the fused
+ * transform covers n (256 ... 8192), each chunk writes only the uv-tiles its
+ * records reach (overwriting those no earlier chunk reached, adding into the
+ * others) and rick_fft_wcorrect then reads the tiles any chunk reached; else
+ * rick_grid grids the first chunk, rick_grid_accumulate the later ones, and
+ * rick_fft_wplanes and rick_wcorrect_stack run once.  The image is that of
+ * rick_bin + rick_grid + rick_fft_wplanes + rick_wcorrect_stack over the whole
+ * set, up to FP32 summation order; the weight sum and drop counts are totals
+ * over the chunks, added in chunk order.
  * The w range is the plan's; if it is (NaN, NaN), the exact range of the
  * whole set: uvw is then first copied, in chunks, into a device-resident
  * array in the staging buffer, each chunk's range folded in as it lands, and
@@ -475,7 +479,8 @@ rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
  *   ws_dev, ws_bytes:       workspace of rick_workspace_bytes(params, max_vis)
  *   stage_dev, stage_bytes: staging area of rick_stream_bytes(params, max_vis,
  *               n_vis) bytes, 256-byte aligned
- *   planes_dev: complex64 [n_w][n][n], overwritten
+ *   planes_dev: complex64 [n_w][n][n], scratch (with the fused transform, the
+ *               tiles no record reaches keep what they held)
  *   image_dev:  float32 [m][m]; flags as for rick_wcorrect_stack
  *   stats_dev:  device rick_bin_stats of the whole set, or NULL
  * Work is enqueued on `stream` and on the plan's copy stream, which waits for
@@ -484,6 +489,7 @@ rick_status rick_degrid(rick_plan *plan, void *ws_dev, const void *planes_dev,
  * with the whole set's stats.  Errors: RICK_EINVAL (NULL pointer,
  * misalignment), RICK_ERANGE (stage_bytes or ws_bytes too small, max_vis ==
  * 0 with n_vis > 0), RICK_ECUDA, RICK_ECUFFT. */
+#define RICK_STREAM_BUFS 6
 rick_status rick_stream_bytes(const rick_params *params, int64_t max_vis, int64_t n_vis,
                               size_t *bytes);
 rick_status rick_image_host(rick_plan *plan, int64_t n_vis, const double *uvw_host,

@@ -90,12 +90,15 @@ struct rick_plan {
     // streaming from host memory (created on first use): the copy stream and
     // its events -- start of a call, chunk copied into staging buffer b,
     // staging buffer b free again, uvw chunk resident, resident uvw area a
-    // free again -- and the staging area of the last call with its parity
+    // free again -- and the staging area of the last call with its parity and
+    // the staging buffer its next chunk takes
     cudaStream_t copy;
-    cudaEvent_t ev_start, ev_ready[2], ev_free[2], ev_uvw, ev_area_free[2];
+    cudaEvent_t ev_start, ev_ready[RICK_STREAM_BUFS], ev_free[RICK_STREAM_BUFS], ev_uvw,
+        ev_area_free[2];
     void *stage_prev;
     size_t stage_prev_bytes;
     int parity;
+    int next_buf;
 };
 
 // ------------------------------------------------------------------------
@@ -668,12 +671,16 @@ void rick_launch_wrange(const rick_plan *plan, const double *uvw, int64_t n, WsH
                         cudaStream_t st, int n_chan, const double *scale);
 // rick_grid (RICK_GRID_OVERWRITE), rick_grid_accumulate (RICK_GRID_ACCUMULATE)
 // or rick_grid_sparse (RICK_GRID_RECORD_TILES: only the tiles that records
-// reach are written, the others keep whatever they held).
+// reach are written, the others keep whatever they held).  RICK_GRID_CHUNK_TILES
+// (a chunk of a streamed set): as RICK_GRID_RECORD_TILES, except that a tile
+// flagged in touched (byte per tile, set where an earlier chunk's records
+// reached; NULL: none) is added to instead of overwritten.
 #define RICK_GRID_OVERWRITE 0
 #define RICK_GRID_ACCUMULATE 1
 #define RICK_GRID_RECORD_TILES 2
+#define RICK_GRID_CHUNK_TILES 3
 rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int mode,
-                           void *stream);
+                           void *stream, const uint8_t *touched = NULL);
 // The twiddle tables of the fused transform (rick_fft.cu), on the plan's own
 // stream; nothing for sizes the fused transform does not cover.
 bool rick_fft_tables(rick_plan *pl);

@@ -23,6 +23,7 @@ struct GridArgs {
     float2 *planes;
     int log2T;
     int accumulate;  // add into the planes instead of overwriting them
+    const uint8_t *touched;  // per tile: add into it (tiles an earlier chunk gridded), or NULL
     uint32_t nzero;  // tile-clearing items (RICK_ZERO_GROUP tiles each); 0 when accumulating
     const uint32_t *mcslot;     // deterministic mode: slot of each multi-item tile
     unsigned long long *mcacc;  // deterministic mode: the slots' int64 (re, im) sums
@@ -460,6 +461,7 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
         return;
     }
     const float fxi = DET ? ta.hdr->fx_inv : 0.0f;
+    const bool acc = a.accumulate || (a.touched && a.touched[t]);
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         int row = i >> a.log2T, col = i & (T - 1), ip = row * TP + col;
         int gi = x0 + col, gj = y0 + row;
@@ -472,7 +474,7 @@ __device__ __forceinline__ void grid_item(const GridArgs &a, uint32_t b, uint32_
             im = -im;
         }
         float2 *dst = plane + (size_t)gj * n + gi;
-        if (nch == 1 && !a.accumulate) {
+        if (nch == 1 && !acc) {
             *dst = make_float2(re, im);
         } else if (nch == 1) {  // the only writer of this tile in this launch
             float2 o = *dst;
@@ -555,7 +557,8 @@ struct GridBatchArgs {
 // item) before the grid kernel runs, and reset the grid kernel's counters.
 // Grid-stride, one warp per tile, 16-byte stores.  Tiles without records are
 // cleared by the grid kernel itself; when gridding adds into existing planes
-// nothing is cleared.
+// nothing is cleared, and neither are the tiles flagged in touched (a chunk of a
+// streamed set adds into the tiles earlier chunks gridded).
 // Deterministic mode (mcacc != NULL): the int64 slots of those tiles are
 // zeroed instead, accumulating or not (the slots are added into the planes
 // after gridding).
@@ -563,7 +566,8 @@ __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, u
                                                          int nt, int log2T, int n, float2 *planes,
                                                          WsHeader *hdr, int accumulate,
                                                          const uint32_t *mcslot,
-                                                         unsigned long long *mcacc)
+                                                         unsigned long long *mcacc,
+                                                         const uint8_t *touched)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr->grid_next = 0;
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, u
     }
     if (accumulate) return;
     for (uint32_t t = warp; t < ntiles; t += nwarps) {
-        if (base[t + 1] - base[t] <= 1) continue;
+        if (base[t + 1] - base[t] <= 1 || (touched && touched[t])) continue;
         uint32_t tx = t % nt, ty = (t / nt) % nt, k = t / (nt * nt);
         float4 *plane = (float4 *)(planes + (size_t)k * n * n);
         for (int i = lane; i < T * half; i += 32) {
@@ -900,7 +904,7 @@ static cudaError_t launch_degrid(const DegridArgs &a, int num_sms, cudaStream_t 
     }
 
 rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int mode,
-                           void *stream)
+                           void *stream, const uint8_t *touched)
 {
     const int accumulate = mode == RICK_GRID_ACCUMULATE;
     if (!plan || !ws_dev || !planes_dev) return RICK_EINVAL;
@@ -914,15 +918,17 @@ rick_status rick_grid_impl(rick_plan *plan, void *ws_dev, void *planes_dev, int 
     a.planes = (float2 *)planes_dev;
     a.log2T = ilog2(p.tile);
     a.accumulate = accumulate;
+    a.touched = mode == RICK_GRID_CHUNK_TILES ? touched : NULL;
     a.nzero = mode != RICK_GRID_OVERWRITE ? 0u
                                           : (a.t.ntiles + RICK_ZERO_GROUP - 1) / RICK_ZERO_GROUP;
     cudaError_t err = cudaSuccess;
     const bool det = (p.options & RICK_OPT_DETERMINISTIC) != 0;
+    if (det && mode == RICK_GRID_CHUNK_TILES) return RICK_EINVAL;  // its slots add per tile
     a.mcslot = det ? w.mcslot : NULL;
     a.mcacc = det ? w.mcacc : NULL;
     zero_tiles_kernel<<<(accumulate && !det) ? 1 : plan->num_sms * 8, 256, 0, st>>>(
         w.gbase, a.t.ntiles, a.t.nt, a.log2T, p.n, a.planes, w.hdr, accumulate, a.mcslot,
-        a.mcacc);
+        a.mcacc, a.touched);
     RICK_LAUNCH_CHECK(plan);
     const int gmode = det ? GM_DET : p.precision == RICK_PREC_FP32_COMPENSATED ? GM_COMP : GM_PLAIN;
 #define CALL_GRID(WW) err = launch_grid<WW>(a, gmode, plan->num_sms, st)
@@ -998,6 +1004,7 @@ extern "C" rick_status rick_grid_sparse_batch(rick_plan *const *plans, void *con
         a.planes = (float2 *)planes_dev[j];
         a.log2T = ilog2(p.tile);
         a.accumulate = 0;
+        a.touched = NULL;
         a.nzero = 0;
         a.mcslot = NULL;
         a.mcacc = NULL;

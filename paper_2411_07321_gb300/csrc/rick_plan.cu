@@ -222,11 +222,13 @@ static double bessel_i0_host(double x)
 static void plan_release(rick_plan *pl)
 {
     if (pl->fft) cufftDestroy(pl->fft);
-    cudaEvent_t evs[8] = {pl->ev_start,   pl->ev_ready[0],     pl->ev_ready[1],
-                          pl->ev_free[0],  pl->ev_free[1],      pl->ev_uvw,
-                          pl->ev_area_free[0], pl->ev_area_free[1]};
+    cudaEvent_t evs[4] = {pl->ev_start, pl->ev_uvw, pl->ev_area_free[0], pl->ev_area_free[1]};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
+    for (int b = 0; b < RICK_STREAM_BUFS; ++b) {
+        if (pl->ev_ready[b]) cudaEventDestroy(pl->ev_ready[b]);
+        if (pl->ev_free[b]) cudaEventDestroy(pl->ev_free[b]);
+    }
     if (pl->copy) cudaStreamDestroy(pl->copy);
     if (pl->own) {
         if (pl->taper_inv) cudaFreeAsync(pl->taper_inv, pl->own);

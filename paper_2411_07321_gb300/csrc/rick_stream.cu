@@ -3,16 +3,18 @@
 // sequential chunks; §3.2 counts the offload to the GPU as part of gridding).
 //
 // The set is cut into chunks of at most the plan's max_vis visibilities.  A
-// copy stream of the plan moves chunk c + 1 into one of two staging buffers
-// while the caller's stream bins chunk c and grids it into the planes: the
-// first chunk with rick_grid (every plane cell written), the later ones with
-// rick_grid_accumulate (gridding is linear in the records, so the sum over
-// chunks is the gridding of the whole set).  The plane FFT and the
-// w-correction then run once: fused (rick_fft.cu), reading the tiles that
-// the records of any chunk reach, where the fused transform covers n; else
-// cuFFT in place and the plane-sum kernel.  Gridded weight sums and drop counts are added
-// up over the chunks in chunk order, so the normalisation is that of the
-// whole set.
+// copy stream of the plan moves the next chunks into a ring of
+// RICK_STREAM_BUFS staging buffers while the caller's stream bins chunk c and
+// grids it into the planes (gridding is linear in the records, so the sum over
+// chunks is the gridding of the whole set).  Where the fused transform
+// (rick_fft.cu) covers n, a chunk writes only the tiles its records reach,
+// overwriting those no earlier chunk reached and adding into the others (the
+// tile flags the fused transform keeps say which), and the fused transform then
+// reads the tiles the records of any chunk reach: no plane cell is cleared.
+// Otherwise the first chunk uses rick_grid (every plane cell written) and the
+// later ones rick_grid_accumulate, then cuFFT in place and the plane-sum
+// kernel.  Gridded weight sums and drop counts are added up over the chunks in
+// chunk order, so the normalisation is that of the whole set.
 //
 // The w-planes must be the same for every chunk.  With a given w range (the
 // plan's) every chunk uses it.  Without one, the range of the whole set is
@@ -27,6 +29,9 @@
 // Calls of one plan that pass the same staging area overlap: the copy stream
 // waits only for the binnings that read a buffer before refilling it, so a
 // call's copies run under the previous call's gridding, FFT and w-correction.
+// The ring continues across calls (a call's first chunk takes the buffer after
+// the previous call's last), so every buffer is refilled only after the
+// binning RICK_STREAM_BUFS chunks earlier.
 #include <math.h>
 
 #include "rick_common.cuh"
@@ -42,10 +47,10 @@ struct StageLayout {
     int resident_uvw;
 };
 
-// The staging area: the range header and stats totals, two chunk buffers of
-// vis and of weight, the fused transform's work buffer (for the n it covers),
-// then either two chunk buffers of uvw (given w range) or two resident uvw
-// areas (range from the data), used by alternate calls.
+// The staging area: the range header and stats totals, RICK_STREAM_BUFS chunk
+// buffers of vis and of weight, the fused transform's work buffer (for the n
+// it covers), then either RICK_STREAM_BUFS chunk buffers of uvw (given w range)
+// or two resident uvw areas (range from the data), used by alternate calls.
 // The resident area size is fixed by stage_bytes (0: the size that holds
 // n_vis), so that calls with the same staging area agree on its layout.
 static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n_vis,
@@ -60,8 +65,8 @@ static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n
     S.range = o;  o += rick_align256(sizeof(WsHeader));
     S.total = o;  o += rick_align256(sizeof(rick_bin_stats));
     S.scale = o;  o += 2 * 8 * (size_t)RICK_STREAM_MAX_CHAN;  // channel factors, per area
-    S.vis = o;    o += 2 * S.vis_buf;
-    S.weight = o; o += 2 * S.weight_buf;
+    S.vis = o;    o += RICK_STREAM_BUFS * S.vis_buf;
+    S.weight = o; o += RICK_STREAM_BUFS * S.weight_buf;
     S.fwork_bytes = rick_fft_work_bytes(p);
     S.fwork = o;  o += rick_align256(S.fwork_bytes);
     S.uvw = o;
@@ -72,7 +77,7 @@ static StageLayout stage_layout(const rick_params *p, int64_t max_vis, int64_t n
     } else {
         S.uvw_buf = stage_bytes > o ? (stage_bytes - o) / 2 / 256 * 256 : 0;
     }
-    S.bytes = o + 2 * S.uvw_buf;
+    S.bytes = o + (S.resident_uvw ? 2 : RICK_STREAM_BUFS) * S.uvw_buf;
     return S;
 }
 
@@ -117,11 +122,14 @@ extern "C" rick_status rick_stream_bytes(const rick_params *params, int64_t max_
 static rick_status stream_resources(rick_plan *plan)
 {
     if (plan->copy) return RICK_OK;
-    cudaEvent_t *evs[8] = {&plan->ev_start,  &plan->ev_ready[0], &plan->ev_ready[1],
-                           &plan->ev_free[0], &plan->ev_free[1],  &plan->ev_uvw,
-                           &plan->ev_area_free[0], &plan->ev_area_free[1]};
+    cudaEvent_t *evs[4] = {&plan->ev_start, &plan->ev_uvw, &plan->ev_area_free[0],
+                           &plan->ev_area_free[1]};
     for (cudaEvent_t *e : evs)
         RICK_CUDA_TRY(plan, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (int b = 0; b < RICK_STREAM_BUFS; ++b) {
+        RICK_CUDA_TRY(plan, cudaEventCreateWithFlags(&plan->ev_ready[b], cudaEventDisableTiming));
+        RICK_CUDA_TRY(plan, cudaEventCreateWithFlags(&plan->ev_free[b], cudaEventDisableTiming));
+    }
     RICK_CUDA_TRY(plan, cudaStreamCreateWithFlags(&plan->copy, cudaStreamNonBlocking));
     return RICK_OK;
 }
@@ -187,6 +195,7 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         plan->stage_prev = stage_dev;
         plan->stage_prev_bytes = stage_bytes;
         plan->parity = 0;
+        plan->next_buf = 0;
     }
     const int area = plan->parity;
     plan->parity ^= 1;
@@ -214,16 +223,20 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         }
     }
 
+    // the fused transform's tile flags: the tiles earlier chunks of this call reached
+    const uint8_t *touched = (const uint8_t *)(sb + S.fwork);  // its first field
+    const bool chunk_tiles = S.fwork_bytes && !(plan->p.options & RICK_OPT_DETERMINISTIC);
     for (int64_t c = 0; c < nchunks; ++c) {
-        const int b = (int)(c & 1);
+        const int b = plan->next_buf;
+        plan->next_buf = (b + 1) % RICK_STREAM_BUFS;
         const int64_t off = c * chunk;
         const int64_t nc = n_units - off < chunk ? n_units - off : chunk;
         const double *uvw_c = NULL;
         const void *vis_c = NULL;
         const float *wt_c = NULL;
         if (nc > 0) {
-            // staging buffer b was last read by the binning of chunk c - 2, or
-            // of one of the last two chunks of the previous call
+            // staging buffer b was last read by the binning RICK_STREAM_BUFS
+            // chunks earlier (of this call or the previous ones)
             RICK_CUDA_TRY(plan, cudaStreamWaitEvent(cp, plan->ev_free[b], 0));
             if (S.resident_uvw) {
                 uvw_c = uvw_res + 3 * off;
@@ -252,8 +265,12 @@ static rick_status stream_impl(rick_plan *plan, int64_t n_units, int32_t n_chan,
         RICK_CUDA_TRY(plan, cudaEventRecord(plan->ev_free[b], st));
         stats_add_kernel<<<1, 1, 0, st>>>(hdr, tot, c == 0);
         RICK_LAUNCH_CHECK(plan);
-        RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev,
-                                c > 0 ? RICK_GRID_ACCUMULATE : RICK_GRID_OVERWRITE, st));
+        if (chunk_tiles)
+            RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev, RICK_GRID_CHUNK_TILES, st,
+                                    c > 0 ? touched : NULL));
+        else
+            RICK_TRY(rick_grid_impl(plan, ws_dev, planes_dev,
+                                    c > 0 ? RICK_GRID_ACCUMULATE : RICK_GRID_OVERWRITE, st));
         // the tiles this chunk's records reach, for the fused transform
         if (S.fwork_bytes)
             RICK_TRY(rick_fft_tiles_impl(plan, ws_dev, sb + S.fwork, S.fwork_bytes, c > 0 ? 2 : 1,

@@ -26,6 +26,7 @@ RICK_WAIT_POLLS_DEFAULT = 1 << 24
 RICK_WEIGHT_UNIFORM, RICK_WEIGHT_BRIGGS = 1, 2
 RICK_MAX_CORR = 4
 RICK_GRID_BATCH_MAX = 16
+RICK_STREAM_BUFS = 6
 (RICK_PROBE_SMEM_RMW, RICK_PROBE_SMEM_ATOMIC_F32, RICK_PROBE_SMEM_ATOMIC_U32,
  RICK_PROBE_SMEM_ATOMIC_U64, RICK_PROBE_FFMA, RICK_PROBE_FFMA2, RICK_PROBE_SHFL,
  RICK_PROBE_F2I) = range(8)

@@ -144,25 +144,29 @@ def test_grid_batch_rejected_on_host(R):
 
 
 def test_stream_bytes(R):
-    """Staging area of the streamed path: two chunk buffers of vis and weight,
-    the fused transform's work buffer (tile, tile-row and plane flags, 128-bit tile-row and tile masks, and the
-    transposed row transforms, 8 n_w n^2 bytes), plus two chunk buffers of uvw
-    (given w range) or two areas holding the whole set's uvw, resident while
-    its w range is found and used by alternate calls (range from the data)."""
+    """Staging area of the streamed path: a ring of RICK_STREAM_BUFS chunk
+    buffers of vis and weight, the fused transform's work buffer (tile, tile-row
+    and plane flags, 128-bit tile-row and tile masks, and the transposed row
+    transforms, 8 n_w n^2 bytes), plus a ring of chunk buffers of uvw (given w
+    range) or two areas holding the whole set's uvw, resident while its w range
+    is found and used by alternate calls (range from the data)."""
     al = lambda x: (x + 255) // 256 * 256
+    B = R.RICK_STREAM_BUFS
+    src = open(os.path.join(ROOT, "include", "rick.h")).read()
+    assert re.search(r"#define RICK_STREAM_BUFS (\d+)", src).group(1) == str(B)
     chunk, n = 100_000, 1_234_567
     given = R.make_params(256, 8, 0.035, 1, 7, w_min=-10.0, w_max=10.0, tile=32)
     data = R.make_params(256, 8, 0.035, 1, 7, tile=32)
     nt = 256 // 32
     fwork = al(8 * nt * nt) + al(8 * nt) + al(8) + al(16 * 8) + al(16 * 8 * nt) + 8 * 8 * 256 * 256
-    head = R.rick_stream_bytes(given, chunk, n) - 2 * (al(24 * chunk) + al(8 * chunk) +
+    head = R.rick_stream_bytes(given, chunk, n) - B * (al(24 * chunk) + al(8 * chunk) +
                                                        al(4 * chunk)) - fwork
     assert 0 < head <= 4096 + 2 * 8 * 4096  # headers and two areas of channel factors
-    assert R.rick_stream_bytes(data, chunk, n) == head + fwork + 2 * (al(24 * n) + al(8 * chunk) +
-                                                                      al(4 * chunk))
+    assert R.rick_stream_bytes(data, chunk, n) == head + fwork + 2 * al(24 * n) + B * (
+        al(8 * chunk) + al(4 * chunk))
     # grids the fused transform does not cover (n > 8192) stage no work buffer
     big = R.make_params(16384, 8, 0.035, 1, 7, w_min=-10.0, w_max=10.0, tile=64)
-    assert R.rick_stream_bytes(big, chunk, n) - 2 * (al(24 * chunk) + al(8 * chunk) +
+    assert R.rick_stream_bytes(big, chunk, n) - B * (al(24 * chunk) + al(8 * chunk) +
                                                      al(4 * chunk)) == head
     # a given range keeps nothing of the set resident: independent of n
     assert R.rick_stream_bytes(given, chunk, 10 * n) == R.rick_stream_bytes(given, chunk, n)

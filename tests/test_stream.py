@@ -1,8 +1,10 @@
 """Streamed imaging from host memory (rick_image_host) on the GPU.
 
 A visibility set in host memory is imaged in chunks of the plan's max_vis:
-each chunk is binned and gridded into the same planes (rick_grid, then
-rick_grid_accumulate), then one FFT and w-correction.  The image must be the
+each chunk is binned and gridded into the same planes (the tiles its records
+reach, added into those an earlier chunk reached), then one fused FFT and
+w-correction (rick_grid, rick_grid_accumulate and cuFFT for grids outside the
+fused transform's sizes).  The image must be the
 FP64 oracle's image of the WHOLE set (1e-5 of peak on the tapered image and
 the inner region, as in test_gpu_parity), the stats must be the whole set's
 (counts exact, weight sum to 1e-12), for a w range from the data and a given
