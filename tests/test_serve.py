@@ -121,15 +121,15 @@ def test_crops_share_a_slot(S, data):
 
 
 def test_small_requests_share_a_gridding_launch(S, data):
-    """Small requests admitted together are gridded by one merged launch
-    (rick_grid_sparse_batch on the server's batch stream) and still give their
-    plain per-request images."""
+    """With merge_small, small requests admitted together are gridded by one
+    merged launch (rick_grid_sparse_batch on the server's batch stream) and
+    still give their plain per-request images."""
     specs = [(20_000, 256, 4, "kb"), (150_000, 512, 16, "gauss"), (50_000, 512, 6, "kb"),
              (333_333, 1024, 8, "kb"), (600_000, 1024, 5, "gauss"), (80_000, 256, 9, "gauss")]
     jobs = make_jobs(S, data, specs)
     for j in jobs:
         j.tile = 32  # one group: same support and tile
-    with S.Server("cuda:0", max_running=8) as srv:
+    with S.Server("cuda:0", max_running=8, merge_small=True) as srv:
         futs = [srv.submit(j) for j in jobs]
         res = [f.result(timeout=120) for f in futs]
         assert srv.counters["batches"] >= 1 and srv.counters["batched"] >= 2
