@@ -384,22 +384,38 @@ class Server:
 
     def _launch_group(self, started):
         """Enqueue the jobs admitted in one pass: small compatible ones with one
-        merged gridding launch per group, the others each on its own."""
+        merged gridding launch per group, the others each on its own.  A launch
+        that fails fails only its own request (or its merged group)."""
         groups = collections.defaultdict(list)
         for sid, slot, job, fut in started:
             key = (job.support, job.tile) if self._batchable(slot, job) else None
-            groups[key].append(slot)
-        for key, slots in groups.items():
-            if key is None or len(slots) == 1:
-                for slot in slots:
-                    self._launch(slot, slot.job)
-                continue
-            for i in range(0, len(slots), R.RICK_GRID_BATCH_MAX):
-                part = slots[i:i + R.RICK_GRID_BATCH_MAX]
+            groups[key].append((sid, slot))
+        parts = []
+        for key, members in groups.items():
+            if key is None:
+                parts += [[m] for m in members]
+            else:
+                parts += [members[i:i + R.RICK_GRID_BATCH_MAX]
+                          for i in range(0, len(members), R.RICK_GRID_BATCH_MAX)]
+        for part in parts:
+            try:
                 if len(part) == 1:
-                    self._launch(part[0], part[0].job)
+                    self._launch(part[0][1], part[0][1].job)
                 else:
-                    self._launch_batch(part)
+                    self._launch_batch([slot for _, slot in part])
+            except Exception as e:
+                for sid, slot in part:
+                    self._fail(sid, slot, e)
+
+    def _fail(self, sid, slot, err):
+        """The request on this slot failed at launch: its future gets the error
+        and the slot is idle again once the work enqueued on its stream is done."""
+        fut = slot.future
+        slot.stream.synchronize()
+        slot.job = slot.future = slot.event = None
+        self.admission.release(sid, time.perf_counter())
+        if fut is not None and not fut.done():
+            fut.set_exception(err)
 
     def _launch_batch(self, slots):
         import torch

@@ -97,6 +97,14 @@ def test_failures_stay_with_their_request(S, data):
             futs[2].result(timeout=60)
         for f in (futs[0], futs[3], futs[4]):
             assert f.result(timeout=120).image.shape[0] in (256, 512, 1024)
+        # a request that fails at launch (fewer visibilities than uvw rows): it
+        # fails alone, and its slot serves the next request
+        short = S.ImagingJob(data["uvw"][:1000], data["vis"][:999], data["weight"][:1000],
+                             n=256, n_w=4, fov=good[0].fov, job_id=98, tile=32)
+        f_short = srv.submit(short)
+        with pytest.raises(RuntimeError):
+            f_short.result(timeout=60)
+        assert srv.submit(good[0]).result(timeout=120).image.shape[0] == 256
 
 
 def test_crops_share_a_slot(S, data):
