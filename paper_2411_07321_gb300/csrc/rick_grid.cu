@@ -552,6 +552,7 @@ struct GridBatchArgs {
     int n_jobs;
     GridArgs job[RICK_GRID_BATCH_MAX];
 };
+static_assert(sizeof(GridBatchArgs) <= 32764, "kernel parameters are limited to 32764 bytes");
 
 // Zero the tiles whose chunks add into them with atomics (more than one work
 // item) before the grid kernel runs, and reset the grid kernel's counters.
@@ -600,7 +601,8 @@ __global__ void __launch_bounds__(256) zero_tiles_kernel(const uint32_t *base, u
 
 // The batch's multi-item tiles zeroed (one row of CTAs per job, blockIdx.y) and
 // its item counter reset.
-__global__ void __launch_bounds__(256) zero_tiles_batch_kernel(const __grid_constant__ GridBatchArgs ba)
+__global__ void __launch_bounds__(256)
+    zero_tiles_batch_kernel(const __grid_constant__ GridBatchArgs ba)
 {
     const GridArgs &a = ba.job[blockIdx.y];
     const TileArgs &ta = a.t;
