@@ -99,6 +99,26 @@ def test_streamed_image_matches_oracle(P, n_keep, chunk, w_range, weighted):
     im.close()
 
 
+def test_streamed_deterministic(P):
+    """Deterministic mode through the streamed call (each chunk's tile sums in
+    fixed point, the chunks added into the planes in chunk order): two calls
+    give bitwise equal images, and they match the oracle's image."""
+    wl = synth.WORKLOADS["small"]
+    d = synth.generate(synth.scaled("small", n_keep=40000).obs)
+    im = P.Imager(wl.n, wl.n_w, wl.fov, kernel="kb", support=7, tile=32, max_vis=9000,
+                  device=torch.device("cuda:0"), deterministic=True)
+    h = host(d)
+    a = im.image_streamed(h["uvw"], h["vis"], h["weight"]).clone()
+    b = im.image_streamed(h["uvw"], h["vis"], h["weight"]).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    op = oracle.Params(n=wl.n, n_w=wl.n_w, fov=wl.fov, kernel=oracle.KB, support=7, tile=32)
+    ref, _ = oracle.image(op, d["uvw"], d["vis"], d["weight"])
+    e = errors(a.cpu().numpy(), ref, op)
+    assert e["tapered"] <= TOL and e["inner"] <= TOL
+    im.close()
+
+
 def test_streamed_equals_single_pass_and_reuses_staging(P):
     """Two calls in a row with different data (the second reuses the staging
     buffers while nothing waits in between): each equals the single-pass
