@@ -181,29 +181,17 @@ static __device__ __forceinline__ void fft_stage(float2 (&x)[16], int t, int cb,
 {
     constexpr int P = N / 16, B = 16 / R;
     static_assert(P % 16 == 0 && (NS > 1 || R == 16), "exchange addressing assumes these");
-    // a last radix-2 stage (NS = N / 2): butterfly j = t + P b has the twiddle
-    // e^{2 pi i j / N} = e^{2 pi i t / N} e^{2 pi i b / 16} (P = N / 16), one tabled
-    // factor per thread times a sixteenth root that bfly16 applies
-    constexpr bool ROOT16 = R == 2 && 2 * NS == N;
-    float2 base = make_float2(1.0f, 0.0f);
-    if constexpr (ROOT16) base = __ldg(tw + OFF + t);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = t + P * b, k = j & (NS - 1);
         float2 y[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) y[r] = x[b + B * r];
-        if constexpr (ROOT16) {
-            y[1] = cmul(y[1], base);
-            bfly16(y[0], y[1], b);
-        } else {
-            if constexpr (NS > 1) {
+        if constexpr (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r)
-                    y[r] = cmul(y[r], __ldg(tw + OFF + (r - 1) * NS + k));
-            }
-            dft_inv<R>(y);
+            for (int r = 1; r < R; ++r) y[r] = cmul(y[r], __ldg(tw + OFF + (r - 1) * NS + k));
         }
+        dft_inv<R>(y);
         if constexpr (LAST) {
 #pragma unroll
             for (int m = 0; m < R; ++m) x[b + B * m] = y[m];
