@@ -71,17 +71,19 @@ def build_case(P, name, dev):
 # corners by up to max 1/(C C) (about 3e3 for KB W=7 at these sizes, 3e4 for
 # W=9, unbounded for a truncated Gaussian whose C crosses zero), so the raw
 # error meets the 1e-5 bar only where that amplification is small (W=1, even
-# W=4); elsewhere the bound is twice the measured value, to catch a
-# regression.  Padding the grid (test_padding) brings the raw error of the kept
-# field under 1e-5 for every kernel.
+# W=4); elsewhere the bound catches a regression.  Padding the grid
+# (test_padding) brings the raw error of the kept field under 1e-5 for every
+# kernel.
 # The whole (raw) image divides by C(l)C(m), which near the corners amplifies
 # the FP32 rounding of the planes; that rounding depends on the summation order
 # of the records inside a bin, which is free outside the deterministic mode, so
 # the raw error varies from run to run (kb9_t32_ragged: 1.9e-4 .. 5.2e-4 over
-# five runs, tapered 2.9e-7 .. 3.6e-7).  Each bound is about three times the
-# largest value seen.
-RAW_BOUND = {"gauss7_t32": 1e-1, "kb7_t16": 5e-5, "kb9_t32_ragged": 1.5e-3, "w1_t8": 1e-5,
-             "even_w4_t16": 1e-5, "nw1": 2e-5, "given_range": 5e-5, "compensated": 7e-5,
+# five runs, tapered 2.9e-7 .. 3.6e-7; the KB W=7 cases kb7_t16, given_range
+# and compensated: 1.4e-5 .. 3.8e-5 over three runs, 5.2e-5 once, tapered
+# 3.6e-7 .. 5.0e-7).  Each bound is about two to three times the largest
+# value seen.
+RAW_BOUND = {"gauss7_t32": 1e-1, "kb7_t16": 1e-4, "kb9_t32_ragged": 1.5e-3, "w1_t8": 1e-5,
+             "even_w4_t16": 1e-5, "nw1": 2e-5, "given_range": 1e-4, "compensated": 1e-4,
              "gauss_small_fov_drops": 1.2e-1}
 
 
