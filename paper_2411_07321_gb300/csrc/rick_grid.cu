@@ -239,13 +239,15 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
     auto ring_at = [&](uint32_t i) { return (int)((i / RB) & 1u) * Ring::SLOTS + rg * RB + (int)(i % RB); };
     uint32_t cur;
     float4 q;
+    int ri = 0;  // ring slot of the record being read (running: reset at chunk starts)
     if constexpr (Ring::ON) {
         ring_issue<W>(ta, wrec, wcel, 0, cr0, clast);
         ring_issue<W>(ta, wrec, wcel, 1, cr0, clast);
         cp_async_wait1();
         __syncwarp();
-        q = wrec[ring_at(0)];
-        cur = wcel[ring_at(0)];
+        ri = ring_at(0);
+        q = wrec[ri];
+        cur = wcel[ri];
     } else {
         cur = rcell[0];
         q = rec[0];
@@ -269,17 +271,22 @@ __device__ __forceinline__ void grid_stream(const TileArgs &ta, uint32_t r0, uin
         uint32_t ncell;
         if constexpr (Ring::ON) {
             const uint32_t i1 = i + 1;
-            if (i1 % RB == 0 && i1 < ntrip) {
-                // entering chunk c = i1 / RB: the warp is done with chunk c - 1
-                // (record i was read last iteration), so its buffer takes chunk
-                // c + 1; chunk c has landed once only that copy is pending
-                __syncwarp();
-                ring_issue<W>(ta, wrec, wcel, i1 / RB + 1, cr0, clast);
-                cp_async_wait1();
-                __syncwarp();
+            if (i1 % RB == 0) {
+                if (i1 < ntrip) {
+                    // entering chunk c = i1 / RB: the warp is done with chunk c - 1
+                    // (record i was read last iteration), so its buffer takes chunk
+                    // c + 1; chunk c has landed once only that copy is pending
+                    __syncwarp();
+                    ring_issue<W>(ta, wrec, wcel, i1 / RB + 1, cr0, clast);
+                    cp_async_wait1();
+                    __syncwarp();
+                }
+                ri = ring_at(i1);
+            } else {
+                ++ri;
             }
-            nq = wrec[ring_at(i1)];
-            ncell = wcel[ring_at(i1)];
+            nq = wrec[ri];
+            ncell = wcel[ri];
         } else {
             const uint32_t ln = min(i + 1, last);
             nq = rec[ln];
