@@ -152,3 +152,81 @@ def test_job_key_leaves_out_kernel_planes_and_capacity(S):
     assert a.key() != c.key()
     d = S.ImagingJob(uvw, None, None, n=512, n_w=8, fov=0.01, image_n=300)
     assert d.key() == a.key() and (d.side, a.side) == (300, 512)
+
+
+class _FakeImager:
+    def __init__(self, fused=True, options=0):
+        self.fused = fused
+        self.params = type("P", (), {"options": options})()
+
+
+class _FakeSlot:
+    def __init__(self, job, fused=True, options=0):
+        self.job = job
+        self.imager = _FakeImager(fused, options)
+        self.future = None
+        self.event = None
+
+
+def _job(S, n_vis, support=7, tile=64, precision="fp32", job_id=0):
+    import numpy as np
+    uvw = np.zeros((n_vis, 3))
+    return S.ImagingJob(uvw, None, None, n=512, n_w=4, fov=0.01, support=support, tile=tile,
+                        precision=precision, job_id=job_id)
+
+
+def _server(S, merge_small):
+    """A Server whose launch steps are recorded instead of run (no device)."""
+    srv = S.Server.__new__(S.Server)
+    srv.merge_small = merge_small
+    srv.launched = []
+    srv.failed = []
+    srv._launch = lambda slot, job: srv.launched.append(("alone", job.job_id))
+    srv._launch_batch = lambda slots: srv.launched.append(
+        ("merged", tuple(sl.job.job_id for sl in slots)))
+    srv._fail = lambda sid, slot, err: srv.failed.append(slot.job.job_id)
+    return srv
+
+
+def test_merged_groups_by_support_and_tile(S):
+    """Small FP32 requests on fused grids are grouped by (support, tile) and
+    split at RICK_GRID_BATCH_MAX; a group of one, a large request, a
+    compensated one, one on a grid outside the fused sizes and a
+    deterministic plan are launched alone."""
+    B = S.R.RICK_GRID_BATCH_MAX
+    jobs = [_job(S, 1000, job_id=i) for i in range(B + 2)]           # one group, split
+    jobs += [_job(S, 1000, support=9, job_id=100),                     # a group of one
+             _job(S, 1000, tile=32, job_id=101), _job(S, 2000, tile=32, job_id=102),
+             _job(S, S.BATCH_MAX_VIS + 1, job_id=103),                 # too large
+             _job(S, 1000, precision="compensated", job_id=104)]
+    slots = [_FakeSlot(j) for j in jobs]
+    slots.append(_FakeSlot(_job(S, 1000, job_id=105), fused=False))   # no fused transform
+    slots.append(_FakeSlot(_job(S, 1000, job_id=106), options=S.R.RICK_OPT_DETERMINISTIC))
+    started = [(i, sl, sl.job, None) for i, sl in enumerate(slots)]
+    srv = _server(S, merge_small=True)
+    srv._launch_group(started)
+    merged = [ids for kind, ids in srv.launched if kind == "merged"]
+    alone = sorted(ids for kind, ids in srv.launched if kind == "alone")
+    assert merged == [tuple(range(B)), (B, B + 1), (101, 102)]
+    assert alone == [100, 103, 104, 105, 106]
+    # off: every request on its own launches
+    srv = _server(S, merge_small=False)
+    srv._launch_group(started)
+    assert sorted(ids for _, ids in srv.launched) == sorted(sl.job.job_id for sl in slots)
+    assert all(kind == "alone" for kind, _ in srv.launched)
+
+
+def test_a_failed_launch_fails_only_its_part(S):
+    """An exception from one launch (or one merged group) fails exactly the
+    requests of that launch; the others are still launched."""
+    jobs = [_job(S, 1000, job_id=i) for i in range(3)] + [_job(S, 1000, tile=32, job_id=10),
+                                                          _job(S, 1000, support=9, job_id=20)]
+    started = [(i, _FakeSlot(j), j, None) for i, j in enumerate(jobs)]
+    srv = _server(S, merge_small=True)
+
+    def bad_batch(slots):
+        raise RuntimeError("merged launch failed")
+    srv._launch_batch = bad_batch
+    srv._launch_group(started)
+    assert sorted(srv.failed) == [0, 1, 2]          # the merged group of tile 64
+    assert sorted(ids for _, ids in srv.launched) == [10, 20]
